@@ -1,0 +1,383 @@
+"""Pins of the FP64 oracle against facts the paper and the mathematics fix.
+
+None of these compares the oracle with itself: each checks a closed form, an invariant,
+a textbook special case, a finite difference of a separately computed energy, or a
+brute-force property.  Rotations used to *build* test frames come from scipy.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy.spatial.transform import Rotation as R
+
+import oracle
+from paper_2509_04277_gb300 import workloads as W
+
+
+def _rod(n=12, length=0.3, **kw):
+    base = dict(radius=1e-3, E_bend=100e9, E_stretch=100e9, G=40e9, density=6500.0, dt=1e-5,
+                n_iters=10, inextensible=True, clamp=1, damping_alpha=0.0)
+    base.update(kw)
+    orientation = base.pop("orientation", None)
+    return W.straight_rod(n, length, orientation=orientation, **base)
+
+
+def _continuous(q):
+    q = np.array(q, dtype=np.float64)
+    for j in range(1, len(q)):
+        if np.dot(q[j - 1], q[j]) < 0:
+            q[j] = -q[j]
+    return q
+
+
+def _frames_constant_increment(m, theta, axis, q0=None):
+    """Frames q_j = q0 * Rot(j theta axis) (body-frame increments), via scipy."""
+    q0 = R.identity() if q0 is None else q0
+    axis = np.asarray(axis, float) / np.linalg.norm(axis)
+    return _continuous([(q0 * R.from_rotvec(j * theta * axis)).as_quat() for j in range(m)])
+
+
+def _centreline_from_frames(quat, l0, start=(0.0, 0.0, 0.0)):
+    """Positions with every segment along its frame's third director (penalty-free)."""
+    d3 = R.from_quat(quat).apply([0.0, 0.0, 1.0])
+    pos = np.zeros((len(quat) + 1, 3))
+    pos[0] = start
+    pos[1:] = np.asarray(start)[None, :] + np.cumsum(l0 * d3, axis=0)
+    return pos
+
+
+def _elastic(rod, pos, quat):
+    e = oracle.energy(rod, {"pos": pos, "quat": quat})
+    return e["bend"] + e["penalty"] + e["stretch"]
+
+
+# ------------------------------------------------------------------ Darboux vector (Eq. 5-6)
+
+
+@pytest.mark.parametrize("theta", [1e-3, 0.05, 0.7])
+def test_darboux_constant_increment_closed_form(theta):
+    """Frames related by a constant body-frame rotation theta about a: the discrete
+    Darboux vector is exactly (2/l) sin(theta/2) a, for any axis and base frame."""
+    rod = _rod(10)
+    l0 = rod.length / (rod.n_nodes - 1)
+    g = np.random.default_rng(3)
+    for _ in range(3):
+        axis = g.standard_normal(3)
+        axis /= np.linalg.norm(axis)
+        q = _frames_constant_increment(rod.n_nodes - 1, theta, axis, R.random(random_state=g))
+        u = oracle.darboux(rod, q)
+        expect = (2.0 / l0) * math.sin(theta / 2) * axis
+        np.testing.assert_allclose(u, np.tile(expect, (len(u), 1)), rtol=1e-12, atol=1e-12)
+
+
+def test_darboux_circular_arc_curvature():
+    """A circular arc of radius rho: the bending component tends to 1/rho with O(theta^2)
+    relative error, theta = l/rho (Eq. 1 in the continuum limit)."""
+    rho = 0.25
+    for n in (33, 129):
+        rod = _rod(n, length=0.5)
+        l0 = rod.length / (n - 1)
+        th = l0 / rho
+        q = _frames_constant_increment(n - 1, th, [1.0, 0.0, 0.0])
+        u = oracle.darboux(rod, q)
+        rel = abs(u[:, 0].mean() * rho - 1.0)
+        assert rel < th * th / 20, (n, rel)
+        assert np.abs(u[:, 1:]).max() < 1e-12
+
+
+# ------------------------------------------------------------------ energies and forces
+
+
+def test_bending_and_twist_energy_textbook():
+    """Uniform curvature kappa and twist tau: V_b -> 1/2 (E I kappa^2 + G J tau^2) L_joint,
+    with I = pi r^4 / 4 and J = pi r^4 / 2 (the second-moment reading of Eq. 3)."""
+    n = 257
+    rod = _rod(n, length=1.0, radius=2e-3, E_bend=70e9, G=26e9)
+    l0 = rod.length / (n - 1)
+    kappa, tw = 0.5, 0.8
+    w = np.array([kappa, 0.0, tw])
+    theta = np.linalg.norm(w) * l0
+    q = _frames_constant_increment(n - 1, theta, w)
+    pos = _centreline_from_frames(q, l0)
+    e = oracle.energy(rod, {"pos": pos, "quat": q})
+    r = rod.radius
+    I = math.pi * r**4 / 4
+    Jp = math.pi * r**4 / 2
+    expect = 0.5 * (rod.E_bend * I * kappa**2 + rod.G * Jp * tw**2) * (n - 2) * l0
+    assert abs(e["bend"] / expect - 1) < 1e-4
+    assert e["penalty"] < 1e-20
+
+
+def test_rest_state_has_zero_force_and_torque():
+    """The rest shape carries no force or torque, straight or curved (helical) rest."""
+    n = 24
+    for curved in (False, True):
+        rod = _rod(n, length=0.4, orientation=R.random(random_state=np.random.default_rng(5)))
+        l0 = rod.length / (n - 1)
+        if curved:
+            q0 = R.random(random_state=np.random.default_rng(6))
+            rod.rest_quat = _frames_constant_increment(n - 1, 0.2, [0.3, -0.4, 0.8], q0)
+        q = rod.rest_quat
+        pos = _centreline_from_frames(q, l0, start=(0.1, -0.2, 0.3))
+        F, tau, _ = oracle.forces(rod, pos, q)
+        scaleF = rod.E_bend * math.pi * rod.radius**4 / 4 / l0**2
+        assert np.abs(F).max() < 1e-9 * scaleF
+        assert np.abs(tau).max() < 1e-9 * scaleF * l0
+
+
+@pytest.mark.parametrize("extensible", [False, True])
+def test_forces_are_minus_energy_gradient(extensible):
+    """F_i = -dV/dr_i, checked against central differences of the energy."""
+    rod = _rod(9, length=0.2, inextensible=not extensible, pos_sigma=2e-3, ang_sigma=0.1, seed=11)
+    rod.rest_quat = _frames_constant_increment(8, 0.1, [1.0, 0.5, 0.2], R.from_rotvec([0, math.pi / 2, 0]))
+    pos, quat = rod.pos.copy(), rod.quat.copy()
+    F, _, g = oracle.forces(rod, pos, quat)
+    h = 1e-7
+    Ffd = np.zeros_like(F)
+    for i in range(pos.shape[0]):
+        for k in range(3):
+            p1, p2 = pos.copy(), pos.copy()
+            p1[i, k] += h
+            p2[i, k] -= h
+            Ffd[i, k] = -(_elastic(rod, p1, quat) - _elastic(rod, p2, quat)) / (2 * h)
+    np.testing.assert_allclose(F, Ffd, rtol=1e-6, atol=1e-6 * np.abs(F).max())
+    # quaternion 4-gradient (components treated as independent coordinates)
+    gfd = np.zeros_like(g)
+    for j in range(quat.shape[0]):
+        for k in range(4):
+            q1, q2 = quat.copy(), quat.copy()
+            q1[j, k] += h
+            q2[j, k] -= h
+            gfd[j, k] = (_elastic(rod, pos, q1) - _elastic(rod, pos, q2)) / (2 * h)
+    np.testing.assert_allclose(g, gfd, rtol=1e-6, atol=1e-6 * np.abs(g).max())
+
+
+def test_torque_is_minus_energy_derivative_under_body_rotation():
+    """tau_k = -d/d eps V(q_j * Rot(eps e_k)) (body-frame rotation of one frame)."""
+    rod = _rod(9, length=0.2, pos_sigma=2e-3, ang_sigma=0.1, seed=12)
+    pos, quat = rod.pos.copy(), rod.quat.copy()
+    _, tau, _ = oracle.forces(rod, pos, quat)
+    h = 1e-6
+    tfd = np.zeros_like(tau)
+    for j in range(quat.shape[0]):
+        for k in range(3):
+            e = np.zeros(3)
+            e[k] = h
+            q1, q2 = quat.copy(), quat.copy()
+            a = (R.from_quat(quat[j]) * R.from_rotvec(e)).as_quat()
+            b = (R.from_quat(quat[j]) * R.from_rotvec(-e)).as_quat()
+            q1[j] = a if np.dot(a, quat[j]) > 0 else -a
+            q2[j] = b if np.dot(b, quat[j]) > 0 else -b
+            tfd[j, k] = -(_elastic(rod, pos, q1) - _elastic(rod, pos, q2)) / (2 * h)
+    np.testing.assert_allclose(tau, tfd, rtol=1e-5, atol=1e-6 * np.abs(tau).max())
+
+
+def test_translation_and_rotation_invariance():
+    """Internal forces: sum F = 0 and total world torque sum r x F + sum R tau = 0."""
+    rod = _rod(15, length=0.3, pos_sigma=3e-3, ang_sigma=0.2, seed=13, inextensible=False)
+    rod.rest_quat = _frames_constant_increment(14, 0.15, [0.2, 1.0, -0.3], R.from_rotvec([0.1, 0.2, 0.3]))
+    F, tau, _ = oracle.forces(rod, rod.pos, rod.quat)
+    scale = np.abs(F).max()
+    assert np.abs(F.sum(axis=0)).max() < 1e-10 * scale
+    world_tau = R.from_quat(rod.quat).apply(tau)
+    total = np.cross(rod.pos, F).sum(axis=0) + world_tau.sum(axis=0)
+    assert np.abs(total).max() < 1e-10 * scale * rod.length
+
+
+# ------------------------------------------------------------------ dynamics
+
+
+def test_quaternions_stay_unit():
+    rod = W.guidewire(64, seed=21)
+    s = oracle.step(rod, oracle.state_of(rod), 200, drive=np.array([0.01, 0, 0, 0, 0, 0, 2.0, 0]))
+    assert np.abs(np.linalg.norm(s["quat"], axis=1) - 1).max() < 1e-12
+
+
+def test_driven_base_follows_input_exactly():
+    """Node 0 and frame 0 are kinematic: r_0(t) = r_0 + t dt v, q_0 follows omega."""
+    rod = W.guidewire(32, seed=22)
+    v = np.array([0.02, -0.01, 0.005])
+    w = np.array([0.0, 0.0, 3.0])
+    drive = np.concatenate([v, [0], w, [0]])
+    n = 50
+    s = oracle.step(rod, oracle.state_of(rod), n, drive=drive)
+    np.testing.assert_allclose(s["pos"][0], rod.pos[0] + n * rod.dt * v, rtol=0, atol=1e-14)
+    # rotation about the body z axis by n * dt * |w| (to first order in dt per step)
+    ang = 2 * math.atan2(*(R.from_quat(rod.quat[0]).inv() * R.from_quat(s["quat"][0])).as_quat()[[2, 3]])
+    assert abs(ang - n * rod.dt * w[2]) < 1e-6
+
+
+def test_gravity_accelerates_free_rod_at_g_over_mass_scale():
+    """A free rod in its rest shape under gravity: every node accelerates at g / mass_scale
+    (gravity uses the physical mass, the dynamics the scaled inertial mass)."""
+    rod = _rod(10, length=0.2, clamp=0, gravity=(0.0, 0.0, -9.81), mass_scale=7.0, inertia_scale=3.0)
+    n = 20
+    s = oracle.step(rod, oracle.state_of(rod), n)
+    a = -9.81 / 7.0
+    np.testing.assert_allclose(s["vel"][:, 2], n * rod.dt * a, rtol=1e-9)
+    np.testing.assert_allclose(s["pos"][:, 2] - rod.pos[:, 2], a * rod.dt**2 * n * (n + 1) / 2, rtol=1e-9)
+
+
+def test_rayleigh_damping_decay():
+    """Rigid translation of a free rod decays as (1 + alpha dt)^-n (implicit damping)."""
+    rod = _rod(8, length=0.1, clamp=0, damping_alpha=50.0)
+    st = oracle.state_of(rod)
+    st["vel"][:] = [0.1, 0.2, -0.3]
+    n = 40
+    s = oracle.step(rod, st, n)
+    expect = np.array([[0.1, 0.2, -0.3]]) * (1 + 50.0 * rod.dt) ** -n
+    np.testing.assert_allclose(s["vel"], np.broadcast_to(expect, s["vel"].shape), rtol=1e-9)
+
+
+def test_two_node_constraint_projection_exact():
+    """One distance constraint (N = 2): after the step |r_1 - r_0| = l0 exactly, the
+    impulse is along the constraint direction and momentum is conserved."""
+    rod = _rod(2, length=0.01, clamp=0, n_iters=1, mass_scale=2.0, inertia_scale=1.0)
+    st = oracle.state_of(rod)
+    st["vel"] = np.array([[0.3, -0.2, 0.1], [-0.5, 0.4, 0.2]])
+    s = oracle.step(rod, st, 1)
+    d = oracle.derive(rod)
+    assert abs(np.linalg.norm(s["pos"][1] - s["pos"][0]) - d["l0"]) < 1e-16
+    m = 1.0 / d["w_interior"] / 2  # end nodes carry half mass
+    # momentum: elastic forces are internal (sum zero) and impulses are equal and opposite
+    np.testing.assert_allclose((s["vel"] * m).sum(axis=0), (st["vel"] * m).sum(axis=0), atol=1e-14)
+
+
+def test_constraint_error_decreases_with_iterations():
+    """Gauss-Seidel sweeps on a state that violates the constraints by ~1 % (node
+    jitter): the max relative length error after a step does not grow with the
+    iteration count and falls by an order of magnitude."""
+    rod = W.guidewire(128, seed=23)
+    st = oracle.state_of(rod)
+    st["vel"] = np.random.default_rng(1).standard_normal(st["vel"].shape) * 0.05
+    st["vel"][0] = 0
+    errs = []
+    for it in (1, 2, 4, 10, 40):
+        rod.n_iters = it
+        s = oracle.step(rod, st, 1)
+        seg = np.linalg.norm(np.diff(s["pos"], axis=0), axis=1)
+        errs.append(np.abs(seg / (rod.length / 127) - 1).max())
+    assert all(b <= a * 1.0000001 for a, b in zip(errs, errs[1:])), errs
+    assert errs[-1] < errs[0] / 10
+
+
+def test_guidewire_inextensibility_over_rollout():
+    rod = W.guidewire(512, seed=2)
+    drive = W.sinusoid_drive(2, 30, 10 * rod.dt)
+    s = oracle.state_of(rod)
+    worst = 0.0
+    for k in range(30):
+        s = oracle.step(rod, s, 10, drive=drive[k])
+        seg = np.linalg.norm(np.diff(s["pos"], axis=0), axis=1)
+        worst = max(worst, np.abs(seg / (rod.length / 511) - 1).max())
+    assert worst < 1e-3
+
+
+def test_literal_masses_blow_up_and_default_scaling_is_stable():
+    """The extensible 64-element rod with physical masses is beyond explicit stability
+    at dt = 1e-5 s (the default inertial scaling exists for this reason)."""
+    lit = W.extensible_pendulum(literal_masses=True)
+    with np.errstate(all="ignore"):
+        s = oracle.step(lit, oracle.state_of(lit), 1000)
+    assert not np.isfinite(s["pos"]).all() or np.abs(s["pos"]).max() > 10.0
+    rod = W.extensible_pendulum()
+    s = oracle.step(rod, oracle.state_of(rod), 1000)
+    assert np.isfinite(s["pos"]).all()
+    seg = np.linalg.norm(np.diff(s["pos"], axis=0), axis=1)
+    assert np.abs(seg / (1.0 / 63) - 1).max() < 0.05
+
+
+def test_energy_bounded_without_damping():
+    """alpha = 0, extensible rod, omega dt ~ 0.01: the total energy oscillates by
+    less than 1 % over 10^4 steps with no secular trend (symplectic Euler)."""
+    rod = W.straight_rod(16, 0.5, pos_sigma=2e-4, ang_sigma=2e-3, seed=7, radius=1e-3, E_bend=50e9,
+                         E_stretch=50e9, G=20e9, density=6500.0, dt=1e-5, n_iters=0, inextensible=False,
+                         clamp=1, damping_alpha=0.0)
+    d = oracle.derive(rod)
+    rod.mass_scale, rod.inertia_scale, rod.dt = d["mass_scale"], d["inertia_scale"], 1e-5 / 50
+    s = oracle.state_of(rod)
+    E0 = oracle.energy(rod, s)["total"]
+    Es = []
+    for _ in range(100):
+        s = oracle.step(rod, s, 100)
+        Es.append(oracle.energy(rod, s)["total"])
+    Es = np.array(Es) / E0
+    assert Es.max() - Es.min() < 0.01
+    slope = np.polyfit(np.arange(len(Es)), Es, 1)[0] * len(Es)
+    assert abs(slope) < 2e-3
+
+
+def _cantilever(n, steps=40000):
+    rod = W.straight_rod(n, 0.2, radius=1e-3, E_bend=250e9, E_stretch=250e9, G=250e9 / 2.6, density=6500.0,
+                         dt=1e-5, n_iters=10, inextensible=True, clamp=1, damping_alpha=150.0,
+                         gravity=(0.0, 0.0, -9.81))
+    s = oracle.step(rod, oracle.state_of(rod), steps)
+    d = oracle.derive(rod)
+    w = rod.density * d["A"] * 9.81
+    theory = w * rod.length**4 / (8 * d["K1"]) + w * rod.length**2 / (2 * d["Kp"])
+    return -s["pos"][-1, 2], theory, np.abs(s["vel"]).max()
+
+
+def test_cantilever_tip_deflection_timoshenko():
+    """Clamped rod under its own weight at damped equilibrium: tip deflection
+    w L^4 / (8 E I) + w L^2 / (2 Kp) (Euler-Bernoulli plus the penalty as shear
+    stiffness).  The discrete clamp (frame 0 fixed over the first segment) gives a
+    first-order offset -2/(N-1); Richardson extrapolation over N = 33, 65 removes it."""
+    d33, theory, v33 = _cantilever(33)
+    d65, _, v65 = _cantilever(65)
+    assert max(v33, v65) < 1e-8
+    for n, dn in ((33, d33), (65, d65)):
+        rel = dn / theory - 1
+        assert abs(rel + 2.0 / (n - 1)) < 0.25 * 2.0 / (n - 1), (n, rel)
+    extrap = 2 * d65 - d33
+    assert abs(extrap / theory - 1) < 5e-3
+
+
+def test_static_twist_profile_linear():
+    """Frame 0 clamped, end torque T about the axis: every joint carries T, so
+    (K3 / l) sin(dtheta) = T and the twist angle is linear, theta_j = j asin(T l / K3)."""
+    n = 17
+    rod = _rod(n, length=0.2, orientation=R.identity(), E_bend=200e9, G=80e9, damping_alpha=300.0)
+    d = oracle.derive(rod)
+    T = 0.3 * d["K3"] / d["l0"]
+    tau = np.zeros((n - 1, 3))
+    tau[-1, 2] = T
+    s = oracle.step(rod, oracle.state_of(rod), 60000, tau_ext=tau)
+    q = s["quat"]
+    theta = 2 * np.arctan2(q[:, 2], q[:, 3])
+    np.testing.assert_allclose(theta, np.arange(n - 1) * math.asin(0.3), atol=1e-9)
+    assert abs(math.asin(0.3) - 0.3) > 1e-3  # the check separates asin from the linear law
+
+
+# ------------------------------------------------------------------ forward-mode derivative
+
+
+def test_jvp_matches_central_differences():
+    rod = W.adjoint_rod(12, seed=31)
+    st = oracle.state_of(rod)
+    K, uhat = oracle.material(rod)
+    steps = 30
+    g = np.random.default_rng(2)
+    d_pos = g.standard_normal(st["pos"].shape) * 1e-3
+    d_pos[0] = 0
+    d_vel = g.standard_normal(st["vel"].shape) * 1e-2
+    d_K = g.standard_normal(K.shape) * K * 0.1
+    d_uhat = g.standard_normal(uhat.shape) * 0.5
+    _, dtraj = oracle.rollout_jvp(rod, st, steps, K=K, uhat=uhat, d_pos=d_pos, d_vel=d_vel, d_K=d_K, d_uhat=d_uhat)
+    h = 1e-6
+
+    def run(sg):
+        s2 = {k: v.copy() for k, v in st.items()}
+        s2["pos"] = st["pos"] + sg * h * d_pos
+        s2["vel"] = st["vel"] + sg * h * d_vel
+        traj, _ = oracle.rollout(rod, s2, steps, K=K + sg * h * d_K, uhat=uhat + sg * h * d_uhat)
+        return traj
+
+    fd = (run(1) - run(-1)) / (2 * h)
+    np.testing.assert_allclose(dtraj, fd, rtol=1e-4, atol=1e-6 * np.abs(fd).max())
+
+
+def test_flop_count_linear_in_elements():
+    a = oracle.count_flops(W.guidewire(64), 2)
+    b = oracle.count_flops(W.guidewire(128), 2)
+    assert 1.9 < b / a < 2.05
