@@ -1,0 +1,508 @@
+"""Benchmark of the GB300 CoRdE stepper; prints ONE JSON line on rank 0.
+
+Headline (``value``): device time per simulated time step of one 512-element
+inextensible guidewire rod (10 constraint iterations, dt = 1e-4 s) stepped 10 time steps
+per persistent launch with a seeded 1 kHz insertion/twist drive (the paper's Section 3.3
+instrument; metric "us/step 512-elem rod (10 steps/launch)").  One bench step is 100
+launches = 1000 time steps = 0.1 s of simulated time.  L2 is flushed (a 256 MiB write)
+between bench steps, outside the timed intervals.
+
+Also reported: ``e2e`` (the haptic loop through the C ABI with host buffers: per launch
+the drive goes host->device, 10 steps run, the node positions come back and the stream
+is synchronised), ``roofline`` of the step kernel, ``cpu_baseline`` (the FP64 oracle on
+the host cores, one core, as the paper's serial CPU version), and ``batched`` (4096
+rods of log-uniform length in [16, 2048], element-steps/s and its rooflines).
+
+``--impl reference`` times the FP64 CPU oracle on the same workload and metric.
+For N > 1 (torchrun) every rank runs its own replica of the single-rod workload and the
+batched workload sharded by rods (weak scaling, no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "µs/step 512-elem rod (10 steps/launch); batched element-steps/s; adjoint/fwd"
+UNIT = "us/step"
+STEPS_PER_LAUNCH = 10
+LAUNCHES_PER_BENCH_STEP = 100
+
+# Algorithmic FP32 operations per element per time step (adds, multiplies, divides,
+# square roots of the method as stated, counted by the oracle's op-counting scalar):
+# inextensible rod 293 + 41 per constraint iteration; extensible rod 306.
+FLOPS_PER_EL_STEP_BASE = 293.0
+FLOPS_PER_EL_ITER = 41.0
+# Algorithmic HBM bytes per element per launch: state read + written (r, w, v, q, omega:
+# 4 float4 = 64 B each way) plus the per-joint parameters read (u-hat, K: 32 B).
+BYTES_PER_EL_LAUNCH = 64 + 64 + 32
+FP32_LANES_PER_SM = 128
+NUM_SMS = 152
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        cmd = ["nvidia-smi", "-i", str(self.gpu),
+               "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+               "clocks_event_reasons.sw_power_cap",
+               "--format=csv,noheader,nounits", "-lms", "100"]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.reader = threading.Thread(target=self._read, daemon=True)
+            self.reader.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if parts[3 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("corde_step.cuh", "corde_common.cuh"):
+        with open(os.path.join(ROOT, "paper_2509_04277_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(kernel_key):
+    """DRAM bytes per launch from the committed ncu summary, if taken on this kernel source."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None, None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(kernel_key)
+    if not e or e.get("source_hash") != _kernel_source_hash():
+        return None, None
+    return e.get("dram_bytes_per_launch"), e.get("units_per_launch")
+
+
+def flops_per_el_step(n_iters: int, inextensible: bool = True) -> float:
+    if not inextensible:
+        return 306.0
+    return FLOPS_PER_EL_STEP_BASE + FLOPS_PER_EL_ITER * n_iters
+
+
+# --------------------------------------------------------------------------- our arm
+
+
+def run_single_rod(args, torch, corde, W, rank):
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    rod = W.guidewire(512, seed=2 + rank)
+    n_launch_total = LAUNCHES_PER_BENCH_STEP * (args.warmup + args.steps)
+    drive_np = W.sinusoid_drive(2 + rank, n_launch_total, STEPS_PER_LAUNCH * rod.dt).astype(np.float32)
+    drive = torch.as_tensor(drive_np, device=dev).contiguous()
+    b = corde.RodBatch([rod])
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def bench_step(k, events=None):
+        for j in range(LAUNCHES_PER_BENCH_STEP):
+            row = drive[k * LAUNCHES_PER_BENCH_STEP + j]
+            if events is not None:
+                events[j][0].record(stream)
+            b.step(STEPS_PER_LAUNCH, drive=row)
+            if events is not None:
+                events[j][1].record(stream)
+
+    for k in range(args.warmup):
+        bench_step(k)
+    torch.cuda.synchronize()
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(LAUNCHES_PER_BENCH_STEP)] for _ in range(args.steps)]
+    brackets = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                for _ in range(args.steps)]
+    clocks = ClockSampler(torch.cuda.current_device())
+    if rank == 0:
+        clocks.start()
+    _barrier(torch)
+    torch.cuda.synchronize()
+    launches = 0
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        brackets[k][0].record(stream)
+        bench_step(args.warmup + k, ev[k])
+        brackets[k][1].record(stream)
+        launches += LAUNCHES_PER_BENCH_STEP * b.last_launch_count()
+    torch.cuda.synchronize()
+    _barrier(torch)
+    clk = clocks.stop() if rank == 0 else None
+    total_ms = sum(s.elapsed_time(e) for s, e in brackets)
+    kern_ms = [s.elapsed_time(e) for row in ev for s, e in row]
+    us_per_step = total_ms * 1e3 / (args.steps * LAUNCHES_PER_BENCH_STEP * STEPS_PER_LAUNCH)
+    rc, diag = b.diagnostics()
+
+    # e2e: the haptic loop through the C ABI with host buffers
+    pin_drive = torch.empty((1, 8), dtype=torch.float32, pin_memory=True)
+    pin_pos = torch.empty((512, 4), dtype=torch.float32, pin_memory=True)
+    n_e2e = LAUNCHES_PER_BENCH_STEP * max(1, args.steps)
+    for j in range(20):
+        pin_drive.copy_(drive[j % drive.shape[0]].view(1, 8).cpu())
+        corde.rod_set_input(b.handle, pin_drive, stream)
+        b.step(STEPS_PER_LAUNCH)
+        corde.rod_get_state(b.handle, pin_pos, None, None, None, stream)
+        stream.synchronize()
+    host_drive = drive_np
+    t0 = time.perf_counter()
+    for j in range(n_e2e):
+        pin_drive.numpy()[0] = host_drive[j % host_drive.shape[0]]
+        corde.rod_set_input(b.handle, pin_drive, stream)
+        b.step(STEPS_PER_LAUNCH)
+        corde.rod_get_state(b.handle, pin_pos, None, None, None, stream)
+        stream.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_us = e2e_s * 1e6 / (n_e2e * STEPS_PER_LAUNCH)
+    b.close()
+    return {
+        "us_per_step": us_per_step,
+        "total_ms": total_ms,
+        "kernel_ms_avg": float(np.mean(kern_ms)),
+        "kernel_ms_median": float(np.median(kern_ms)),
+        "launches": launches,
+        "clocks": clk,
+        "diag": diag[0].tolist(),
+        "diag_rc": rc,
+        "e2e_us": e2e_us,
+        "e2e_launch_us": e2e_s * 1e6 / n_e2e,
+        "n_nodes": 512,
+        "n_iters": rod.n_iters,
+    }
+
+
+def run_batched(args, torch, corde, W, rank, world):
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    rods = W.batched_rods(4096, seed=4)
+    mine = rods[rank::world] if world > 1 else rods
+    b = corde.RodBatch(mine)
+    n_elem = b.n_elem
+    S = args.batched_steps_per_launch
+    n_launch = max(1, args.batched_steps // S)
+    b.autotune(S)
+    plan = b.plan()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    b.step(S)
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(n_launch)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(n_launch)]
+    _barrier(torch)
+    torch.cuda.synchronize()
+    launches = 0
+    for k in range(n_launch):
+        flush.fill_(float(k))
+        starts[k].record(stream)
+        b.step(S)
+        ends[k].record(stream)
+        launches += b.last_launch_count()
+    torch.cuda.synchronize()
+    _barrier(torch)
+    ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    rc, diag = b.diagnostics()
+    b.close()
+    total_s = sum(ms) / 1e3
+    el_steps = n_elem * S * n_launch
+    return {
+        "n_rods": len(mine),
+        "n_elements": n_elem,
+        "steps_per_launch": S,
+        "launches": n_launch,
+        "gpu_launches": launches,
+        "seconds": total_s,
+        "element_steps_per_s": el_steps / total_s,
+        "ms_per_launch": float(np.mean(ms)),
+        "plan": sorted({(int(a), int(c)) for a, c in plan}),
+        "max_len_err": float(diag[:, 0].max()),
+        "diag_rc": rc,
+        "flops_per_launch": flops_per_el_step(10) * n_elem * S,
+        "bytes_per_launch": BYTES_PER_EL_LAUNCH * n_elem,
+    }
+
+
+def cpu_baseline_single(seconds=10.0):
+    """The FP64 oracle as it stands, one host core, on the 512-element guidewire."""
+    import oracle
+    from paper_2509_04277_gb300 import workloads as W
+
+    rod = W.guidewire(512, seed=2)
+    drive = W.sinusoid_drive(2, 100000, STEPS_PER_LAUNCH * rod.dt)
+    s = oracle.state_of(rod)
+    oracle.step(rod, s, 10)
+    steps = 0
+    t0 = time.perf_counter()
+    k = 0
+    while steps == 0 or time.perf_counter() - t0 < seconds:
+        s = oracle.step(rod, s, STEPS_PER_LAUNCH, drive=drive[k % len(drive)])
+        steps += STEPS_PER_LAUNCH
+        k += 1
+    el = time.perf_counter() - t0
+    return {"value": el * 1e6 / steps, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"512-element guidewire, {steps} time steps (10 per call, 1 kHz drive), FP64, serial"}
+
+
+def cpu_baseline_batched(seconds=10.0):
+    """The FP64 oracle over a sample of the 4096-rod batch, OpenMP over rods on all cores."""
+    import oracle
+    from paper_2509_04277_gb300 import workloads as W
+
+    rods = W.batched_rods(4096, seed=4)[:256]
+    states = [oracle.state_of(r) for r in rods]
+    n_el = sum(r.n_nodes for r in rods)
+    threads = oracle.step_batch(rods, states, 1)
+    steps = 0
+    t0 = time.perf_counter()
+    while steps == 0 or time.perf_counter() - t0 < seconds:
+        oracle.step_batch(rods, states, 10)
+        steps += 10
+    el = time.perf_counter() - t0
+    return {"value": n_el * steps / el, "unit": "element-steps/s", "cores": threads, "kind": "oracle",
+            "sample": f"first 256 of the 4096 rods ({n_el} elements), {steps} steps, FP64, OpenMP over rods"}
+
+
+def _barrier(torch):
+    import torch.distributed as dist
+
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+def _max_over_ranks(torch, x: float) -> float:
+    import torch.distributed as dist
+
+    if dist.is_available() and dist.is_initialized():
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+    return x
+
+
+def _sum_over_ranks(torch, x: float) -> float:
+    import torch.distributed as dist
+
+    if dist.is_available() and dist.is_initialized():
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+    return x
+
+
+def main_ours(args):
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    import __graft_entry__
+
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    _barrier(torch)
+    from paper_2509_04277_gb300 import corde
+    from paper_2509_04277_gb300 import workloads as W
+
+    corde.load()
+    single = run_single_rod(args, torch, corde, W, rank)
+    batched = run_batched(args, torch, corde, W, rank, world) if not args.skip_batched else None
+    value = _max_over_ranks(torch, single["us_per_step"])
+    e2e = _max_over_ranks(torch, single["e2e_us"])
+    out = None
+    if rank == 0:
+        peaks, which = _peaks()
+        sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+        fp32_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s
+        flops_launch = flops_per_el_step(single["n_iters"]) * single["n_nodes"] * STEPS_PER_LAUNCH
+        achieved = flops_launch / (single["kernel_ms_avg"] * 1e-3) / 1e12
+        traffic, _ = _traffic("step_kernel_guidewire512")
+        cpu = cpu_baseline_single(args.cpu_seconds)
+        out = {
+            "metric": METRIC,
+            "value": round(value, 4),
+            "unit": UNIT,
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": round(single["total_ms"] / args.steps, 4),
+            "higher_is_better": False,
+            "scaling": "weak",
+            "vs_baseline": round(value / 32.0, 5),
+            "dtype": "f32",
+            "data": "synthetic (seeded guidewire, 1 kHz sinusoidal insertion/twist drive)",
+            "config": {
+                "workload": "guidewire: 1 inextensible rod, 512 elements, L=1.5 m, r=0.45 mm, E=60 GPa, "
+                            "10 constraint iterations, dt=1e-4 s, 10 time steps per persistent launch",
+                "n_rods": 1, "n_elements": 512, "steps_per_launch": STEPS_PER_LAUNCH,
+                "time_steps_per_bench_step": STEPS_PER_LAUNCH * LAUNCHES_PER_BENCH_STEP,
+                "l2": "flushed (256 MiB write) between bench steps, outside the timed intervals",
+                "parallelism": f"replicas x{world}" if world > 1 else "single GPU, one thread block per rod",
+            },
+            "gpu_launches": single["launches"],
+            "e2e": {"value": round(e2e, 4), "unit": UNIT,
+                    "h2d_bytes_per_step": 32 * LAUNCHES_PER_BENCH_STEP,
+                    "d2h_bytes_per_step": 512 * 16 * LAUNCHES_PER_BENCH_STEP,
+                    "per_launch_us": round(single["e2e_launch_us"], 3),
+                    "what": "per launch: drive H2D (pinned) + 10 steps + positions D2H (pinned) + stream sync, "
+                            "host wall clock"},
+            "roofline": {"bound": "alu", "achieved": round(achieved, 6), "peak": round(fp32_peak, 2),
+                         "unit": "TFLOP/s", "frac": round(achieved / fp32_peak, 8), "traffic": traffic,
+                         "peak_source": f"derived: {NUM_SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
+                                        f"{sm_mhz:.0f} MHz ({which} sm_max_mhz)",
+                         "note": "one rod = one thread block on one of 152 SMs; latency-bound by design",
+                         "kernel_us_per_launch": round(single["kernel_ms_avg"] * 1e3, 3)},
+            "latency": {"us_per_step": round(value, 4), "barriers_per_step": 2 + single["n_iters"],
+                        "launch_rate_khz": round(1e3 / (value * STEPS_PER_LAUNCH), 2),
+                        "haptic_1khz_realtime": bool(value * STEPS_PER_LAUNCH < 1000.0)},
+            "cpu_baseline": cpu,
+            "clocks": single["clocks"],
+            "checks": {"max_len_err": single["diag"][0], "max_qnorm_err": single["diag"][1],
+                       "nonfinite": single["diag"][2]},
+            "paper_context": {"us_per_step_512_single_block_10tskl": 32.0, "hardware": "GeForce GTX 560 (Fermi)",
+                              "note": "host-visible time incl. launch and D2H; compare with e2e"},
+        }
+        if batched is not None:
+            bw = peaks.get("hbm_gbs", 6800.0)
+            sec = batched["seconds"] / batched["launches"]
+            out["batched"] = {
+                "element_steps_per_s": batched["element_steps_per_s"],
+                "n_rods": batched["n_rods"], "n_elements": batched["n_elements"],
+                "steps_per_launch": batched["steps_per_launch"], "launches": batched["launches"],
+                "gpu_launches": batched["gpu_launches"], "ms_per_launch": round(batched["ms_per_launch"], 4),
+                "plan": batched["plan"], "max_len_err": batched["max_len_err"],
+                "roofline_alu": {"achieved": batched["flops_per_launch"] / sec / 1e12, "peak": round(fp32_peak, 2),
+                                 "unit": "TFLOP/s",
+                                 "frac": batched["flops_per_launch"] / sec / 1e12 / fp32_peak},
+                "roofline_hbm": {"achieved": batched["bytes_per_launch"] / sec / 1e9, "peak": bw, "unit": "GB/s",
+                                 "frac": batched["bytes_per_launch"] / sec / 1e9 / bw},
+                "cpu_baseline": cpu_baseline_batched(args.cpu_seconds) if not args.skip_cpu_batched else None,
+            }
+        print(json.dumps(out), flush=True)
+    _barrier(torch)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+# --------------------------------------------------------------------------- reference arm
+
+
+def main_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    from paper_2509_04277_gb300 import workloads as W
+
+    oracle.build()
+    rod = W.guidewire(512, seed=2)
+    steps_per_bench = 1000
+    drive = W.sinusoid_drive(2, (args.warmup + args.steps) * steps_per_bench // STEPS_PER_LAUNCH,
+                             STEPS_PER_LAUNCH * rod.dt)
+    s = oracle.state_of(rod)
+    k = 0
+    for _ in range(args.warmup):
+        for _ in range(steps_per_bench // STEPS_PER_LAUNCH):
+            s = oracle.step(rod, s, STEPS_PER_LAUNCH, drive=drive[k])
+            k += 1
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for _ in range(steps_per_bench // STEPS_PER_LAUNCH):
+            s = oracle.step(rod, s, STEPS_PER_LAUNCH, drive=drive[k])
+            k += 1
+    el = time.perf_counter() - t0
+    value = el * 1e6 / (args.steps * steps_per_bench)
+    out = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(el * 1e3 / args.steps, 4),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "guidewire: 1 inextensible rod, 512 elements, 10 constraint iterations, dt=1e-4 s, "
+                               "10 time steps per call", "time_steps_per_bench_step": steps_per_bench},
+        "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} x {steps_per_bench} time steps of the 512-element guidewire"},
+        "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batched-steps", type=int, default=1000)
+    ap.add_argument("--batched-steps-per-launch", type=int, default=100)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--skip-batched", action="store_true")
+    ap.add_argument("--skip-cpu-batched", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        main_reference(args)
+    else:
+        main_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,159 @@
+/*
+ * corde.h - C ABI of the GB300 (sm_103a) CoRdE Cosserat-rod time stepper.
+ *
+ * The method is the CoRdE rod of Korzeniowski, Hald and Bello, "Massively-Parallel
+ * Implementation of Inextensible Elastic Rods Using Inter-block GPU Synchronization":
+ * N centreline points r_i and N-1 material frames stored as unit quaternions q_j
+ * (Section 2.1, "Discretization"); stretch energy (Eq. 2), bend/twist energy with the
+ * Darboux vector from adjacent quaternions (Eq. 3, 5, 6), the parallel-constraint
+ * penalty (Eq. 7-8); per time step the order of Fig. 5: external forces, elastic forces
+ * and torques, force integration, j iterations of distance-constraint impulses
+ * (inextensible variant, Section 2.1 "Constraints"), then semi-implicit Euler
+ * integration of the velocities.  Many time steps run inside one kernel launch
+ * (Section 2.2): the paper's launch takes the number of steps, the number of
+ * constraint iterations, the material and the haptic input, which map to rod_step,
+ * RodParams and rod_set_input.
+ *
+ * Conventions
+ *  - A handle holds a batch of independent rods (a single rod is a batch of one).
+ *    Rod r has n_nodes[r] = N_r nodes and N_r - 1 frames.  Elements are numbered
+ *    globally: rod r owns elements [off_r, off_r + N_r), off_r = sum of earlier N.
+ *    Element i carries node i and, except for a rod's last element, frame i.
+ *  - Quaternions are (x, y, z, w) with w the real part; they map body to world, the
+ *    frame's third director d3 = R(q) e_z is the tangent direction.
+ *  - Angular velocities are in the body frame.
+ *  - Node 0 and frame 0 of a rod with clamp != 0 are kinematic (the clamped or
+ *    driven base): their velocities come from the drive input, forces do not move them.
+ *  - Pointer arguments may point to host memory (pageable or pinned) or device memory
+ *    unless stated otherwise; the library copies with cudaMemcpyAsync (default kind).
+ *    Caller buffers are borrowed for the duration of the call on the given stream and
+ *    are never freed by the library.  `stream` is a cudaStream_t (NULL = legacy default).
+ *  - All calls are asynchronous on `stream` unless stated otherwise.  Return value:
+ *    CORDE_OK (0) or a negative CORDE_ERR_* code; rod_last_error() gives a message.
+ *    Argument errors are detected on the host before anything is enqueued.
+ *  - Device state is owned by the handle and freed by rod_destroy.
+ */
+#ifndef CORDE_H_
+#define CORDE_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CORDE_OK 0
+#define CORDE_ERR_ARG (-1)         /* invalid argument (sizes, NULL, parameter range)  */
+#define CORDE_ERR_CUDA (-2)        /* a CUDA runtime call failed                       */
+#define CORDE_ERR_OOM (-3)         /* device allocation failed                         */
+#define CORDE_ERR_UNSUPPORTED (-4) /* rod longer than any kernel variant, or no GPU    */
+#define CORDE_ERR_NONFINITE (-5)   /* diagnostics found a non-finite state             */
+
+typedef struct corde_rods* rod_handle;
+
+/* Material, geometry and stepping parameters of one rod (SI units).
+ *  length, radius          rod length L and cross-section radius r
+ *  E_bend, E_stretch, G    Young's moduli for bending and stretching, shear modulus;
+ *                          K1 = K2 = E_bend pi r^4/4, K3 = G pi r^4/2 (Eq. 3, read with
+ *                          the second moments), Ks = E_stretch pi r^2 (Eq. 2)
+ *  density                 mass density rho; node masses rho pi r^2 l0 (half at ends)
+ *  Kp                      penalty constant of Eq. 8 (N); <= 0 selects 100 * 4 K1 / L^2
+ *  damping_alpha           mass-proportional internal friction alpha (1/s), implicit
+ *  mass_scale, inertia_scale  factors on the inertial node masses and frame inertias
+ *                          (gravity keeps the physical mass); <= 0 selects the smallest
+ *                          factor that keeps the estimated highest mode at omega dt <= 0.5
+ *  dt                      time step (s)
+ *  gravity                 acceleration vector (m/s^2)
+ *  n_nodes                 N >= 2
+ *  n_iters                 constraint iterations per step (Fig. 5 "j"), >= 0
+ *  inextensible            1: distance constraints replace Eq. 2; 0: extensible rod
+ *  clamp                   1: node 0 and frame 0 are kinematic (driven base); 0: free
+ */
+typedef struct {
+  double length, radius, E_bend, E_stretch, G, density, Kp, damping_alpha;
+  double mass_scale, inertia_scale, dt;
+  double gravity[3];
+  int n_nodes, n_iters, inextensible, clamp;
+} RodParams;
+
+/* Create a batch of n_rods rods.
+ *  params     [n_rods] host array.
+ *  pos        [sum N][3]  initial node positions.
+ *  quat       [sum (N-1)][4] initial frames (x, y, z, w), unit norm.
+ *  rest_quat  [sum (N-1)][4] rest frames defining the intrinsic Darboux vectors u-hat
+ *             of Eq. 3 (computed from them with the same formula as u), or NULL for a
+ *             straight, untwisted rest shape (u-hat = 0).
+ *  vel        [sum N][3] initial velocities or NULL (zero).
+ *  omega      [sum (N-1)][3] initial body angular velocities or NULL (zero).
+ *  stiff_mul  [sum (N-2)][3] per-joint multipliers of (K1, K2, K3) or NULL (ones).
+ * Frames of one rod must be on one hemisphere (q_j . q_{j+1} > 0).
+ * Blocks until the device state is initialised.  On success *out receives the handle. */
+int rod_create(int n_rods, const RodParams* params, const float* pos, const float* quat,
+               const float* rest_quat, const float* vel, const float* omega,
+               const float* stiff_mul, void* stream, rod_handle* out);
+
+/* Advance every rod by n_steps time steps in one persistent launch per kernel variant
+ * of the handle's plan (one launch for a single rod).  drive: [n_rods][8] device
+ * pointer (v_x v_y v_z _ w_x w_y w_z _), the base velocity and body angular velocity
+ * held for the whole call, or NULL to use the values last given to rod_set_input
+ * (initially zero).  n_steps >= 0. */
+int rod_step(rod_handle h, int n_steps, const float* drive, void* stream);
+
+/* Copy the drive input [n_rods][8] (host or device) into the handle. */
+int rod_set_input(rod_handle h, const float* drive, void* stream);
+
+/* Copy the state out.  Each destination is [n_elements][4] float, element-indexed,
+ * host or device, or NULL to skip:
+ *  pos4   (x, y, z, inverse inertial node mass; 0 for a kinematic node)
+ *  quat4  (x, y, z, w); the frame slot of each rod's last element is unused
+ *  vel4   (vx, vy, vz, 0)
+ *  omega4 (wx, wy, wz, 0), body frame; last element of each rod unused */
+int rod_get_state(rod_handle h, float* pos4, float* quat4, float* vel4, float* omega4, void* stream);
+
+/* Overwrite the state (same layouts; pos4.w is ignored, masses stay).  NULL skips. */
+int rod_set_state(rod_handle h, const float* pos4, const float* quat4, const float* vel4,
+                  const float* omega4, void* stream);
+
+/* Sizes of the batch. */
+int rod_info(rod_handle h, int* n_rods, int64_t* n_elements);
+
+/* Derived constants (synchronous).  per_rod: [n_rods][16] host doubles
+ *  l0, A, I, K1, K2, K3, Ks, Kp, mass_scale, inertia_scale, m_interior, J1, J2, J3,
+ *  w_interior, 0.   per_joint: [n_elements][8] host floats (K1, K2, K3, 0, u-hat x, y,
+ *  z, 0) for joint i between frames i and i+1; NULL skips either. */
+int rod_get_derived(rod_handle h, double* per_rod, float* per_joint);
+
+/* Override the per-joint stiffness and intrinsic Darboux vectors: [n_elements][8]
+ * floats in the per_joint layout of rod_get_derived (host or device). */
+int rod_set_material(rod_handle h, const float* per_joint, void* stream);
+
+/* Per-rod diagnostics (synchronous): out [n_rods][4] host doubles =
+ *  max |l_j / l0 - 1| over segments, max ||q_j| - 1|, number of non-finite state
+ *  values, elastic energy (bend + penalty + stretch, FP64 accumulation).
+ * Returns CORDE_ERR_NONFINITE if any rod holds a non-finite value. */
+int rod_diagnostics(rod_handle h, double* out);
+
+/* Kernel variants: elements per thread (ept) and threads per block (nt).  rod_set_plan
+ * forces one variant for every rod whose length it can hold (ept = 0 restores the
+ * default plan); rod_autotune times the variants that hold each length bin on the
+ * current state (state is saved and restored) and keeps the fastest per bin.
+ * rod_get_plan writes [n_rods][2] ints (ept, nt).  Autotune is synchronous. */
+int rod_set_plan(rod_handle h, int ept, int nt);
+int rod_autotune(rod_handle h, int n_steps, void* stream);
+int rod_get_plan(rod_handle h, int* plan);
+
+/* Number of kernel launches the last rod_step enqueued. */
+int rod_last_launch_count(rod_handle h);
+
+/* Free the device state (synchronises the device first).  NULL is ignored. */
+void rod_destroy(rod_handle h);
+
+/* Static description of an error code; message of the last failing call (thread-local). */
+const char* rod_strerror(int code);
+const char* rod_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CORDE_H_ */

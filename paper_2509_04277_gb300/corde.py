@@ -1,0 +1,308 @@
+"""Thin ctypes binding of ``libcorde.so`` (declared in ``include/corde.h``).
+
+The module-level functions carry the C names and only marshal arguments; every step of
+the rod computation runs in the library's CUDA kernels.  ``RodBatch`` bundles a handle
+with numpy/torch conveniences for tests and the benchmark.  There is no CPU fallback:
+if the library is missing or fails to load, every entry point raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libcorde.so")
+
+CORDE_OK = 0
+CORDE_ERR_ARG = -1
+CORDE_ERR_CUDA = -2
+CORDE_ERR_OOM = -3
+CORDE_ERR_UNSUPPORTED = -4
+CORDE_ERR_NONFINITE = -5
+
+
+class CordeError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{msg} (code {code})")
+        self.code = code
+
+
+class RodParams(ctypes.Structure):
+    _fields_ = [
+        ("length", ctypes.c_double), ("radius", ctypes.c_double), ("E_bend", ctypes.c_double),
+        ("E_stretch", ctypes.c_double), ("G", ctypes.c_double), ("density", ctypes.c_double),
+        ("Kp", ctypes.c_double), ("damping_alpha", ctypes.c_double), ("mass_scale", ctypes.c_double),
+        ("inertia_scale", ctypes.c_double), ("dt", ctypes.c_double), ("gravity", ctypes.c_double * 3),
+        ("n_nodes", ctypes.c_int), ("n_iters", ctypes.c_int), ("inextensible", ctypes.c_int),
+        ("clamp", ctypes.c_int),
+    ]
+
+
+_VP = ctypes.c_void_p
+_lib = None
+
+# name -> (restype, argtypes); the exported C ABI
+SIGNATURES = {
+    "rod_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(RodParams), _VP, _VP, _VP, _VP, _VP, _VP, _VP,
+                                  ctypes.POINTER(_VP)]),
+    "rod_step": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP]),
+    "rod_set_input": (ctypes.c_int, [_VP, _VP, _VP]),
+    "rod_get_state": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    "rod_set_state": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    "rod_info": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64)]),
+    "rod_get_derived": (ctypes.c_int, [_VP, _VP, _VP]),
+    "rod_set_material": (ctypes.c_int, [_VP, _VP, _VP]),
+    "rod_diagnostics": (ctypes.c_int, [_VP, _VP]),
+    "rod_set_plan": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
+    "rod_autotune": (ctypes.c_int, [_VP, ctypes.c_int, _VP]),
+    "rod_get_plan": (ctypes.c_int, [_VP, _VP]),
+    "rod_last_launch_count": (ctypes.c_int, [_VP]),
+    "rod_destroy": (None, [_VP]),
+    "rod_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "rod_last_error": (ctypes.c_char_p, []),
+}
+
+
+def load(path: str = LIB_PATH):
+    """Load the library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise CordeError(CORDE_ERR_UNSUPPORTED,
+                             f"libcorde.so not found at {path}; build it with __graft_entry__.build()")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, what: str):
+    if rc != CORDE_OK:
+        msg = load().rod_last_error()
+        raise CordeError(rc, f"{what}: {msg.decode() if msg else load().rod_strerror(rc).decode()}")
+
+
+def _ptr(x):
+    """Pointer of a numpy array / torch tensor / int / None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()  # torch tensor
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            pass
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ------------------------------------------------------------------ C names
+
+
+def rod_create(params, pos, quat, rest_quat=None, vel=None, omega=None, stiff_mul=None, stream=None):
+    P = (RodParams * len(params))(*params)
+    h = _VP()
+    _check(load().rod_create(len(params), P, _ptr(pos), _ptr(quat), _ptr(rest_quat), _ptr(vel), _ptr(omega),
+                             _ptr(stiff_mul), _stream(stream), ctypes.byref(h)), "rod_create")
+    return h
+
+
+def rod_step(h, n_steps, drive=None, stream=None):
+    _check(load().rod_step(h, int(n_steps), _ptr(drive), _stream(stream)), "rod_step")
+
+
+def rod_set_input(h, drive, stream=None):
+    _check(load().rod_set_input(h, _ptr(drive), _stream(stream)), "rod_set_input")
+
+
+def rod_get_state(h, pos4=None, quat4=None, vel4=None, omega4=None, stream=None):
+    _check(load().rod_get_state(h, _ptr(pos4), _ptr(quat4), _ptr(vel4), _ptr(omega4), _stream(stream)),
+           "rod_get_state")
+
+
+def rod_set_state(h, pos4=None, quat4=None, vel4=None, omega4=None, stream=None):
+    _check(load().rod_set_state(h, _ptr(pos4), _ptr(quat4), _ptr(vel4), _ptr(omega4), _stream(stream)),
+           "rod_set_state")
+
+
+def rod_info(h):
+    n = ctypes.c_int()
+    e = ctypes.c_int64()
+    _check(load().rod_info(h, ctypes.byref(n), ctypes.byref(e)), "rod_info")
+    return n.value, e.value
+
+
+def rod_get_derived(h, per_rod=None, per_joint=None):
+    _check(load().rod_get_derived(h, _ptr(per_rod), _ptr(per_joint)), "rod_get_derived")
+
+
+def rod_set_material(h, per_joint, stream=None):
+    _check(load().rod_set_material(h, _ptr(per_joint), _stream(stream)), "rod_set_material")
+
+
+def rod_diagnostics(h, out):
+    return load().rod_diagnostics(h, _ptr(out))
+
+
+def rod_set_plan(h, ept, nt):
+    _check(load().rod_set_plan(h, int(ept), int(nt)), "rod_set_plan")
+
+
+def rod_autotune(h, n_steps, stream=None):
+    _check(load().rod_autotune(h, int(n_steps), _stream(stream)), "rod_autotune")
+
+
+def rod_get_plan(h, out):
+    _check(load().rod_get_plan(h, _ptr(out)), "rod_get_plan")
+
+
+def rod_last_launch_count(h) -> int:
+    return int(load().rod_last_launch_count(h))
+
+
+def rod_destroy(h):
+    load().rod_destroy(h)
+
+
+# ------------------------------------------------------------------ convenience
+
+
+def params_of(rod) -> RodParams:
+    p = RodParams()
+    for k in ("length", "radius", "E_bend", "E_stretch", "G", "density", "Kp", "damping_alpha",
+              "mass_scale", "inertia_scale", "dt"):
+        setattr(p, k, float(getattr(rod, k)))
+    for i in range(3):
+        p.gravity[i] = float(rod.gravity[i])
+    p.n_nodes = int(rod.n_nodes)
+    p.n_iters = int(rod.n_iters)
+    p.inextensible = int(bool(rod.inextensible))
+    p.clamp = int(rod.clamp)
+    return p
+
+
+def _cat(arrs, cols):
+    return np.ascontiguousarray(np.concatenate([np.asarray(a, dtype=np.float32).reshape(-1, cols) for a in arrs]))
+
+
+class RodBatch:
+    """A handle over a list of rod descriptions (objects with the RodSpec attributes)."""
+
+    def __init__(self, rods, stream=None):
+        self.rods = list(rods)
+        self.n_nodes = np.array([r.n_nodes for r in self.rods], dtype=np.int64)
+        self.offsets = np.concatenate([[0], np.cumsum(self.n_nodes)])
+        self.n_rods = len(self.rods)
+        self.n_elem = int(self.offsets[-1])
+        pos = _cat([r.pos for r in self.rods], 3)
+        quat = _cat([r.quat for r in self.rods], 4)
+        rest = _cat([r.rest_quat for r in self.rods], 4) if all(r.rest_quat is not None for r in self.rods) else None
+        vel = _cat([r.vel for r in self.rods], 3) if all(r.vel is not None for r in self.rods) else None
+        om = _cat([r.omega for r in self.rods], 3) if all(r.omega is not None for r in self.rods) else None
+        mul = None
+        if any(r.stiff_mul is not None for r in self.rods):
+            mul = _cat([r.stiff_mul if r.stiff_mul is not None else np.ones((r.n_nodes - 2, 3)) for r in self.rods],
+                       3)
+        self.handle = rod_create([params_of(r) for r in self.rods], pos, quat, rest, vel, om, mul, stream)
+
+    def close(self):
+        if self.handle is not None:
+            rod_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n_steps, drive=None, stream=None):
+        rod_step(self.handle, n_steps, drive, stream)
+
+    def set_input(self, drive, stream=None):
+        d = drive
+        if isinstance(drive, np.ndarray):
+            d = np.ascontiguousarray(drive, dtype=np.float32).reshape(self.n_rods, 8)
+        rod_set_input(self.handle, d, stream)
+
+    def state_numpy(self) -> dict:
+        """Synchronous copy of the whole state into host float32 arrays [E, 4]."""
+        import torch
+
+        out = {k: np.zeros((self.n_elem, 4), dtype=np.float32) for k in ("pos4", "quat4", "vel4", "omega4")}
+        rod_get_state(self.handle, out["pos4"], out["quat4"], out["vel4"], out["omega4"])
+        if torch.cuda.is_available():
+            torch.cuda.current_stream().synchronize()
+        return out
+
+    def rod_state(self, st: dict, r: int) -> dict:
+        """Per-rod views (pos N x 3, quat (N-1) x 4, vel N x 3, omega (N-1) x 3), float64 copies."""
+        a, b = int(self.offsets[r]), int(self.offsets[r + 1])
+        return {
+            "pos": st["pos4"][a:b, :3].astype(np.float64),
+            "quat": st["quat4"][a:b - 1].astype(np.float64),
+            "vel": st["vel4"][a:b, :3].astype(np.float64),
+            "omega": st["omega4"][a:b - 1, :3].astype(np.float64),
+        }
+
+    def set_rod_states(self, states: list):
+        """Overwrite every rod's state from per-rod dicts in the rod_state layout (host, synchronous)."""
+        import torch
+
+        buf = {k: np.zeros((self.n_elem, 4), dtype=np.float32) for k in ("pos4", "quat4", "vel4", "omega4")}
+        buf["quat4"][:, 3] = 1.0
+        for r, s in enumerate(states):
+            a, b = int(self.offsets[r]), int(self.offsets[r + 1])
+            buf["pos4"][a:b, :3] = s["pos"]
+            buf["vel4"][a:b, :3] = s["vel"]
+            buf["quat4"][a:b - 1] = s["quat"]
+            buf["omega4"][a:b - 1, :3] = s["omega"]
+        rod_set_state(self.handle, buf["pos4"], buf["quat4"], buf["vel4"], buf["omega4"])
+        if torch.cuda.is_available():
+            torch.cuda.current_stream().synchronize()
+
+    def derived(self) -> np.ndarray:
+        out = np.zeros((self.n_rods, 16), dtype=np.float64)
+        rod_get_derived(self.handle, out, None)
+        return out
+
+    def per_joint(self) -> np.ndarray:
+        out = np.zeros((self.n_elem, 8), dtype=np.float32)
+        rod_get_derived(self.handle, None, out)
+        return out
+
+    def diagnostics(self):
+        out = np.zeros((self.n_rods, 4), dtype=np.float64)
+        rc = rod_diagnostics(self.handle, out)
+        return rc, out
+
+    def plan(self) -> np.ndarray:
+        out = np.zeros((self.n_rods, 2), dtype=np.int32)
+        rod_get_plan(self.handle, out)
+        return out
+
+    def set_plan(self, ept, nt):
+        rod_set_plan(self.handle, ept, nt)
+
+    def autotune(self, n_steps, stream=None):
+        rod_autotune(self.handle, n_steps, stream)
+
+    def last_launch_count(self) -> int:
+        return rod_last_launch_count(self.handle)

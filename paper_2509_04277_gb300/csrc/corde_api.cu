@@ -1,0 +1,686 @@
+// C ABI of the CoRdE stepper: creation (derived constants and packing on the device),
+// kernel-variant plans, the persistent step launches, state I/O and diagnostics.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/corde.h"
+#include "corde_common.cuh"
+#include "corde_variants.cuh"
+
+using namespace corde;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess) {                                                              \
+      return fail(e_ == cudaErrorMemoryAllocation ? CORDE_ERR_OOM : CORDE_ERR_CUDA,       \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                    \
+    }                                                                                     \
+  } while (0)
+
+// All compiled variants, in preference order of the default plan.
+std::vector<StepVariant> all_variants() {
+  std::vector<StepVariant> v;
+  for (int i = 0; i < kNumStepVariantsE2; ++i) v.push_back(kStepVariantsE2[i]);
+  for (int i = 0; i < kNumStepVariantsE4; ++i) v.push_back(kStepVariantsE4[i]);
+  return v;
+}
+
+const std::vector<StepVariant>& variants() {
+  static const std::vector<StepVariant> v = all_variants();
+  return v;
+}
+
+int max_capacity() {
+  int c = 0;
+  for (const auto& v : variants()) c = std::max(c, v.capacity());
+  return c;
+}
+
+int find_variant(int ept, int nt) {
+  const auto& vs = variants();
+  for (size_t i = 0; i < vs.size(); ++i)
+    if (vs[i].ept == ept && vs[i].nt == nt) return (int)i;
+  return -1;
+}
+
+// Default plan: two elements per thread up to one warp, four elements per thread above,
+// with the smallest power-of-two block that holds the rod.
+int default_variant(int n) {
+  const int ept = n <= 64 ? 2 : 4;
+  int nt = 32;
+  while (nt * ept < n && nt < 512) nt *= 2;
+  int v = find_variant(ept, nt);
+  if (v >= 0 && variants()[v].capacity() >= n) return v;
+  int best = -1;
+  for (size_t i = 0; i < variants().size(); ++i)
+    if (variants()[i].capacity() >= n && (best < 0 || variants()[i].capacity() < variants()[best].capacity()))
+      best = (int)i;
+  return best;
+}
+
+struct Bin {
+  int variant;
+  int count;
+  int* d_work;
+};
+
+}  // namespace
+
+struct corde_rods {
+  int device = 0;
+  int n_rods = 0;
+  int64_t n_elem = 0;
+  std::vector<int> n_nodes, off;
+  std::vector<int> flags;
+  std::vector<double> derived;  // [n_rods][16]
+  RodDev* d_rods = nullptr;
+  double* d_derived = nullptr;
+  float4 *d_x = nullptr, *d_v = nullptr, *d_q = nullptr, *d_o = nullptr, *d_u = nullptr, *d_k = nullptr;
+  float4* d_drive = nullptr;
+  int* d_elem_rod = nullptr;
+  std::vector<int> plan;  // variant index per rod
+  std::vector<Bin> bins;
+  int last_launches = 0;
+};
+
+namespace {
+
+const double kPi = 3.14159265358979323846;
+
+// Section 2.1 constants (Eq. 2-3 with the second-moment reading), lumped masses, frame
+// inertias and the default rules for Kp and the inertial scaling; FP64, one thread per rod.
+__global__ void derive_kernel(int n_rods, const RodParams* __restrict__ P, const int* __restrict__ off,
+                              RodDev* __restrict__ rods, double* __restrict__ derived) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n_rods) return;
+  const RodParams p = P[r];
+  const int N = p.n_nodes;
+  const double l0 = p.length / (N - 1);
+  const double r2 = p.radius * p.radius;
+  const double A = kPi * r2;
+  const double I = kPi * r2 * r2 / 4.0;
+  const double K1 = p.E_bend * I, K3 = p.G * 2.0 * I, Ks = p.E_stretch * A;
+  const double Kp = p.Kp > 0 ? p.Kp : 100.0 * 4.0 * K1 / (p.length * p.length);
+  const double m_el = p.density * A * l0;
+  const double J_el = p.density * l0 * I;
+  double ms = p.mass_scale;
+  if (!(ms > 0)) {
+    double k_node = Kp / l0;
+    if (!p.inextensible && Ks / l0 > k_node) k_node = Ks / l0;
+    const double w2 = p.dt * p.dt * 4.0 * k_node / m_el;
+    ms = w2 / 0.25 > 1.0 ? w2 / 0.25 : 1.0;
+  }
+  double is = p.inertia_scale;
+  if (!(is > 0)) {
+    const double kb = K1 > K3 ? K1 : K3;
+    const double w2 = p.dt * p.dt * (4.0 * kb / l0 + Kp * l0) / J_el;
+    is = w2 / 0.25 > 1.0 ? w2 / 0.25 : 1.0;
+  }
+  const double J1 = is * J_el, J3 = is * 2.0 * J_el;
+  RodDev R;
+  R.off = off[r];
+  R.n = N;
+  R.flags = (p.inextensible ? F_INEXT : 0) | (p.clamp ? F_CLAMP : 0);
+  R.n_iters = p.n_iters;
+  R.dt = (float)p.dt;
+  R.l0 = (float)l0;
+  R.two_over_l = (float)(2.0 / l0);
+  R.lKp = (float)(l0 * Kp);
+  R.Ks = (float)Ks;
+  R.inv_l0 = (float)(1.0 / l0);
+  R.damp = (float)(1.0 / (1.0 + p.damping_alpha * p.dt));
+  R.pad0 = 0.f;
+  R.gx = (float)(p.gravity[0] / ms);
+  R.gy = (float)(p.gravity[1] / ms);
+  R.gz = (float)(p.gravity[2] / ms);
+  R.pad1 = 0.f;
+  R.J1 = (float)J1;
+  R.J3 = (float)J3;
+  R.Jinv1 = (float)(1.0 / J1);
+  R.Jinv3 = (float)(1.0 / J3);
+  rods[r] = R;
+  double* d = derived + 16 * (size_t)r;
+  d[0] = l0; d[1] = A; d[2] = I; d[3] = K1; d[4] = K1; d[5] = K3; d[6] = Ks; d[7] = Kp;
+  d[8] = ms; d[9] = is; d[10] = m_el; d[11] = J1; d[12] = J1; d[13] = J3; d[14] = 1.0 / (ms * m_el); d[15] = 0.0;
+}
+
+// Packs caller arrays into the element-indexed float4 layout; per-joint stiffness and
+// intrinsic Darboux vectors (computed from the rest frames with the step's formula, so
+// that the rest state carries no bending torque).
+__global__ void pack_kernel(int64_t E, const int* __restrict__ elem_rod, const RodDev* __restrict__ rods,
+                            const RodParams* __restrict__ P, const double* __restrict__ derived,
+                            const float* __restrict__ pos, const float* __restrict__ quat,
+                            const float* __restrict__ rest, const float* __restrict__ vel,
+                            const float* __restrict__ omega, const float* __restrict__ mul, float4* x4, float4* v4,
+                            float4* q4, float4* o4, float4* u4, float4* k4) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= E) return;
+  const int r = elem_rod[i];
+  const RodDev R = rods[r];
+  const RodParams p = P[r];
+  const double* d = derived + 16 * (size_t)r;
+  const int li = (int)(i - R.off);
+  const int n = R.n;
+  const int64_t fi = i - r;      // global frame index
+  const int64_t ji = i - 2 * r;  // global joint index
+  const double l0 = d[0];
+  const double left = li > 0 ? l0 : 0.0, right = li < n - 1 ? l0 : 0.0;
+  const double m = p.density * d[1] * (left + right) / 2.0;
+  float w = (float)(1.0 / (d[8] * m));
+  if ((R.flags & F_CLAMP) && li == 0) w = 0.f;
+  x4[i] = make_float4(pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], w);
+  v4[i] = vel ? make_float4(vel[3 * i], vel[3 * i + 1], vel[3 * i + 2], 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
+  if (li <= n - 2) {
+    q4[i] = make_float4(quat[4 * fi], quat[4 * fi + 1], quat[4 * fi + 2], quat[4 * fi + 3]);
+    o4[i] = omega ? make_float4(omega[3 * fi], omega[3 * fi + 1], omega[3 * fi + 2], 0.f)
+                  : make_float4(0.f, 0.f, 0.f, 0.f);
+  } else {
+    q4[i] = make_float4(0.f, 0.f, 0.f, 1.f);
+    o4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  if (li <= n - 3) {
+    const double m1 = mul ? mul[3 * ji] : 1.0, m2 = mul ? mul[3 * ji + 1] : 1.0, m3 = mul ? mul[3 * ji + 2] : 1.0;
+    k4[i] = make_float4((float)(d[3] * m1), (float)(d[4] * m2), (float)(d[5] * m3), 0.f);
+    float3 uh = zero3();
+    if (rest) {
+      const float4 a = make_float4(rest[4 * fi], rest[4 * fi + 1], rest[4 * fi + 2], rest[4 * fi + 3]);
+      const float4 b = make_float4(rest[4 * fi + 4], rest[4 * fi + 5], rest[4 * fi + 6], rest[4 * fi + 7]);
+      uh = darboux(a, b, R.two_over_l);
+    }
+    u4[i] = make_float4(uh.x, uh.y, uh.z, 0.f);
+  } else {
+    k4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    u4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+// Per-rod diagnostics: max segment-length error, max quaternion-norm error, count of
+// non-finite values, elastic energy (FP64 accumulation).
+__global__ void diag_kernel(const RodDev* __restrict__ rods, const double* __restrict__ derived,
+                            const float4* __restrict__ x4, const float4* __restrict__ q4,
+                            const float4* __restrict__ v4, const float4* __restrict__ o4,
+                            const float4* __restrict__ u4, const float4* __restrict__ k4, double* out) {
+  const int r = blockIdx.x;
+  const RodDev R = rods[r];
+  const double* d = derived + 16 * (size_t)r;
+  const double l0 = d[0], Kp = d[7], Ks = d[6];
+  double len_err = 0, qn_err = 0, nonfin = 0, energy = 0;
+  for (int li = threadIdx.x; li < R.n; li += blockDim.x) {
+    const int64_t i = R.off + li;
+    const float4 a = x4[i], q = q4[i], v = v4[i], o = o4[i];
+    const float vals[12] = {a.x, a.y, a.z, v.x, v.y, v.z, q.x, q.y, q.z, q.w, o.x, o.y};
+    for (int k = 0; k < 12; ++k)
+      if (!isfinite(vals[k])) nonfin += 1;
+    if (li <= R.n - 2) {
+      const float4 b = x4[i + 1];
+      const double ex = (double)b.x - a.x, ey = (double)b.y - a.y, ez = (double)b.z - a.z;
+      const double len = sqrt(ex * ex + ey * ey + ez * ez);
+      len_err = fmax(len_err, fabs(len / l0 - 1.0));
+      const double qn = sqrt((double)q.x * q.x + (double)q.y * q.y + (double)q.z * q.z + (double)q.w * q.w);
+      qn_err = fmax(qn_err, fabs(qn - 1.0));
+      const double tx = ex / len, ty = ey / len, tz = ez / len;
+      const double dx = 2.0 * ((double)q.x * q.z + (double)q.w * q.y);
+      const double dy = 2.0 * ((double)q.y * q.z - (double)q.w * q.x);
+      const double dz = 1.0 - 2.0 * ((double)q.x * q.x + (double)q.y * q.y);
+      energy += 0.5 * l0 * Kp * ((tx - dx) * (tx - dx) + (ty - dy) * (ty - dy) + (tz - dz) * (tz - dz));
+      if (!(R.flags & F_INEXT)) energy += 0.5 * l0 * Ks * (len / l0 - 1.0) * (len / l0 - 1.0);
+    }
+    if (li <= R.n - 3) {
+      const float4 b = q4[i + 1];
+      const double ux = (2.0 / l0) * ((double)q.w * b.x - (double)q.x * b.w - (double)q.y * b.z + (double)q.z * b.y);
+      const double uy = (2.0 / l0) * ((double)q.w * b.y - (double)q.y * b.w - (double)q.z * b.x + (double)q.x * b.z);
+      const double uz = (2.0 / l0) * ((double)q.w * b.z - (double)q.z * b.w - (double)q.x * b.y + (double)q.y * b.x);
+      const float4 uh = u4[i], K = k4[i];
+      energy += 0.5 * l0 *
+                (K.x * (ux - uh.x) * (ux - uh.x) + K.y * (uy - uh.y) * (uy - uh.y) + K.z * (uz - uh.z) * (uz - uh.z));
+    }
+  }
+  __shared__ double red[4][256];
+  red[0][threadIdx.x] = len_err;
+  red[1][threadIdx.x] = qn_err;
+  red[2][threadIdx.x] = nonfin;
+  red[3][threadIdx.x] = energy;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) {
+      red[0][threadIdx.x] = fmax(red[0][threadIdx.x], red[0][threadIdx.x + s]);
+      red[1][threadIdx.x] = fmax(red[1][threadIdx.x], red[1][threadIdx.x + s]);
+      red[2][threadIdx.x] += red[2][threadIdx.x + s];
+      red[3][threadIdx.x] += red[3][threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 4; ++k) out[4 * r + k] = red[k][0];
+}
+
+int check_handle(rod_handle h) {
+  if (!h) return fail(CORDE_ERR_ARG, "NULL rod handle");
+  cudaError_t e = cudaSetDevice(h->device);
+  if (e != cudaSuccess) return fail(CORDE_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+  return CORDE_OK;
+}
+
+void free_bins(rod_handle h) {
+  for (auto& b : h->bins) cudaFree(b.d_work);
+  h->bins.clear();
+}
+
+// Group rods by variant; each group's work list is sorted by decreasing length so that
+// the longest rods start first.
+int build_bins(rod_handle h) {
+  free_bins(h);
+  const auto& vs = variants();
+  for (size_t vi = 0; vi < vs.size(); ++vi) {
+    std::vector<int> rods;
+    for (int r = 0; r < h->n_rods; ++r)
+      if (h->plan[r] == (int)vi) rods.push_back(r);
+    if (rods.empty()) continue;
+    std::stable_sort(rods.begin(), rods.end(), [&](int a, int b) { return h->n_nodes[a] > h->n_nodes[b]; });
+    Bin b{(int)vi, (int)rods.size(), nullptr};
+    CK(cudaMalloc(&b.d_work, rods.size() * sizeof(int)));
+    CK(cudaMemcpy(b.d_work, rods.data(), rods.size() * sizeof(int), cudaMemcpyHostToDevice));
+    h->bins.push_back(b);
+  }
+  return CORDE_OK;
+}
+
+int launch_bins(rod_handle h, const std::vector<Bin>& bins, int n_steps, const float4* drive, cudaStream_t s) {
+  StepArgs a;
+  a.rods = h->d_rods;
+  a.x4 = h->d_x;
+  a.v4 = h->d_v;
+  a.q4 = h->d_q;
+  a.o4 = h->d_o;
+  a.u4 = h->d_u;
+  a.k4 = h->d_k;
+  a.drive = drive;
+  a.n_steps = n_steps;
+  int launches = 0;
+  for (const auto& b : bins) {
+    a.work = b.d_work;
+    const StepVariant& v = variants()[b.variant];
+    cudaError_t e = v.launch(a, b.count, s);
+    if (e != cudaSuccess)
+      return fail(CORDE_ERR_CUDA, std::string("step launch (ept=") + std::to_string(v.ept) +
+                                      ", nt=" + std::to_string(v.nt) + "): " + cudaGetErrorString(e));
+    ++launches;
+  }
+  h->last_launches = launches;
+  return CORDE_OK;
+}
+
+template <class T>
+int upload(const T* src, size_t count, T** dst, cudaStream_t s) {
+  *dst = nullptr;
+  if (!src) return CORDE_OK;
+  CK(cudaMalloc(dst, count * sizeof(T) + 16));
+  CK(cudaMemcpyAsync(*dst, src, count * sizeof(T), cudaMemcpyDefault, s));
+  return CORDE_OK;
+}
+
+bool params_valid(const RodParams& p, std::string& why) {
+  if (p.n_nodes < 2) { why = "n_nodes must be >= 2"; return false; }
+  if (!(p.length > 0) || !(p.radius > 0) || !(p.density > 0) || !(p.dt > 0)) {
+    why = "length, radius, density and dt must be positive";
+    return false;
+  }
+  if (!(p.E_bend >= 0) || !(p.E_stretch >= 0) || !(p.G >= 0) || !(p.damping_alpha >= 0)) {
+    why = "moduli and damping must be non-negative";
+    return false;
+  }
+  if (p.n_iters < 0) { why = "n_iters must be >= 0"; return false; }
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* rod_strerror(int code) {
+  switch (code) {
+    case CORDE_OK: return "ok";
+    case CORDE_ERR_ARG: return "invalid argument";
+    case CORDE_ERR_CUDA: return "CUDA runtime error";
+    case CORDE_ERR_OOM: return "device out of memory";
+    case CORDE_ERR_UNSUPPORTED: return "unsupported (rod too long for the compiled kernels, or no device)";
+    case CORDE_ERR_NONFINITE: return "non-finite state";
+    default: return "unknown error";
+  }
+}
+
+const char* rod_last_error(void) { return g_last_error.c_str(); }
+
+int rod_create(int n_rods, const RodParams* params, const float* pos, const float* quat, const float* rest_quat,
+               const float* vel, const float* omega, const float* stiff_mul, void* stream, rod_handle* out) {
+  if (!out) return fail(CORDE_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (n_rods < 1 || !params || !pos || !quat) return fail(CORDE_ERR_ARG, "need n_rods >= 1, params, pos and quat");
+  const int cap = max_capacity();
+  std::vector<int> nn(n_rods), off(n_rods);
+  int64_t E = 0;
+  for (int r = 0; r < n_rods; ++r) {
+    std::string why;
+    if (!params_valid(params[r], why)) return fail(CORDE_ERR_ARG, "rod " + std::to_string(r) + ": " + why);
+    if (params[r].n_nodes > cap)
+      return fail(CORDE_ERR_UNSUPPORTED, "rod " + std::to_string(r) + " has " + std::to_string(params[r].n_nodes) +
+                                             " nodes; the compiled kernels hold at most " + std::to_string(cap));
+    nn[r] = params[r].n_nodes;
+    off[r] = (int)E;
+    E += nn[r];
+  }
+  if (E > (int64_t)0x7fffffff) return fail(CORDE_ERR_ARG, "too many elements");
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  cudaStream_t s = (cudaStream_t)stream;
+
+  rod_handle h = new corde_rods();
+  h->device = dev;
+  h->n_rods = n_rods;
+  h->n_elem = E;
+  h->n_nodes = nn;
+  h->off = off;
+  const int64_t F = E - n_rods, J = E - 2 * (int64_t)n_rods;
+  std::vector<int> elem_rod(E);
+  for (int r = 0; r < n_rods; ++r)
+    for (int k = 0; k < nn[r]; ++k) elem_rod[off[r] + k] = r;
+
+  RodParams* d_params = nullptr;
+  int *d_off = nullptr;
+  float *d_pos = nullptr, *d_quat = nullptr, *d_rest = nullptr, *d_vel = nullptr, *d_om = nullptr, *d_mul = nullptr;
+  auto cleanup_staging = [&]() {
+    cudaFree(d_params); cudaFree(d_off); cudaFree(d_pos); cudaFree(d_quat); cudaFree(d_rest);
+    cudaFree(d_vel); cudaFree(d_om); cudaFree(d_mul);
+  };
+  int rc = CORDE_OK;
+  auto step_rc = [&](int c) { if (rc == CORDE_OK) rc = c; };
+  do {
+    const size_t b4 = (size_t)E * sizeof(float4);
+    cudaError_t e = cudaSuccess;
+    if ((e = cudaMalloc(&h->d_rods, n_rods * sizeof(RodDev))) != cudaSuccess ||
+        (e = cudaMalloc(&h->d_derived, n_rods * 16 * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&h->d_x, b4)) != cudaSuccess || (e = cudaMalloc(&h->d_v, b4)) != cudaSuccess ||
+        (e = cudaMalloc(&h->d_q, b4)) != cudaSuccess || (e = cudaMalloc(&h->d_o, b4)) != cudaSuccess ||
+        (e = cudaMalloc(&h->d_u, b4)) != cudaSuccess || (e = cudaMalloc(&h->d_k, b4)) != cudaSuccess ||
+        (e = cudaMalloc(&h->d_drive, n_rods * 2 * sizeof(float4))) != cudaSuccess ||
+        (e = cudaMalloc(&h->d_elem_rod, E * sizeof(int))) != cudaSuccess) {
+      rc = fail(CORDE_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+      break;
+    }
+    step_rc(upload(params, n_rods, &d_params, s));
+    step_rc(upload(off.data(), n_rods, &d_off, s));
+    step_rc(upload(pos, 3 * E, &d_pos, s));
+    step_rc(upload(quat, 4 * F, &d_quat, s));
+    step_rc(upload(rest_quat, 4 * F, &d_rest, s));
+    step_rc(upload(vel, 3 * E, &d_vel, s));
+    step_rc(upload(omega, 3 * F, &d_om, s));
+    step_rc(upload(stiff_mul, 3 * J, &d_mul, s));
+    if (rc != CORDE_OK) break;
+    if ((e = cudaMemcpyAsync(h->d_elem_rod, elem_rod.data(), E * sizeof(int), cudaMemcpyHostToDevice, s)) !=
+            cudaSuccess ||
+        (e = cudaMemsetAsync(h->d_drive, 0, n_rods * 2 * sizeof(float4), s)) != cudaSuccess) {
+      rc = fail(CORDE_ERR_CUDA, std::string("copy: ") + cudaGetErrorString(e));
+      break;
+    }
+    derive_kernel<<<(n_rods + 127) / 128, 128, 0, s>>>(n_rods, d_params, d_off, h->d_rods, h->d_derived);
+    pack_kernel<<<(unsigned)((E + 255) / 256), 256, 0, s>>>(E, h->d_elem_rod, h->d_rods, d_params, h->d_derived,
+                                                           d_pos, d_quat, d_rest, d_vel, d_om, d_mul, h->d_x,
+                                                           h->d_v, h->d_q, h->d_o, h->d_u, h->d_k);
+    if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaStreamSynchronize(s)) != cudaSuccess) {
+      rc = fail(CORDE_ERR_CUDA, std::string("init kernels: ") + cudaGetErrorString(e));
+      break;
+    }
+    h->derived.resize(16 * (size_t)n_rods);
+    if ((e = cudaMemcpy(h->derived.data(), h->d_derived, 16 * n_rods * sizeof(double), cudaMemcpyDeviceToHost)) !=
+        cudaSuccess) {
+      rc = fail(CORDE_ERR_CUDA, std::string("copy derived: ") + cudaGetErrorString(e));
+      break;
+    }
+    h->plan.resize(n_rods);
+    for (int r = 0; r < n_rods; ++r) h->plan[r] = default_variant(nn[r]);
+    rc = build_bins(h);
+  } while (0);
+  cleanup_staging();
+  if (rc != CORDE_OK) {
+    std::string msg = g_last_error;
+    rod_destroy(h);
+    g_last_error = msg;
+    return rc;
+  }
+  *out = h;
+  return CORDE_OK;
+}
+
+int rod_step(rod_handle h, int n_steps, const float* drive, void* stream) {
+  if (int rc = check_handle(h)) return rc;
+  if (n_steps < 0) return fail(CORDE_ERR_ARG, "n_steps must be >= 0");
+  if (n_steps == 0) {
+    h->last_launches = 0;
+    return CORDE_OK;
+  }
+  const float4* d = h->d_drive;
+  if (drive) {
+    // The kernel dereferences `drive`: accept device, managed or mapped pinned host memory.
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, drive) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(CORDE_ERR_ARG, "drive is not a device-accessible pointer");
+    }
+    if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) {
+      d = reinterpret_cast<const float4*>(drive);
+    } else if (at.type == cudaMemoryTypeHost && at.devicePointer != nullptr) {
+      d = reinterpret_cast<const float4*>(at.devicePointer);
+    } else {
+      return fail(CORDE_ERR_ARG, "drive must be device, managed or mapped pinned host memory");
+    }
+    if (reinterpret_cast<uintptr_t>(d) % 16 != 0) return fail(CORDE_ERR_ARG, "drive must be 16-byte aligned");
+  }
+  return launch_bins(h, h->bins, n_steps, d, (cudaStream_t)stream);
+}
+
+int rod_set_input(rod_handle h, const float* drive, void* stream) {
+  if (int rc = check_handle(h)) return rc;
+  if (!drive) return fail(CORDE_ERR_ARG, "drive is NULL");
+  CK(cudaMemcpyAsync(h->d_drive, drive, h->n_rods * 2 * sizeof(float4), cudaMemcpyDefault, (cudaStream_t)stream));
+  return CORDE_OK;
+}
+
+int rod_get_state(rod_handle h, float* pos4, float* quat4, float* vel4, float* omega4, void* stream) {
+  if (int rc = check_handle(h)) return rc;
+  const size_t b = (size_t)h->n_elem * sizeof(float4);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (pos4) CK(cudaMemcpyAsync(pos4, h->d_x, b, cudaMemcpyDefault, s));
+  if (quat4) CK(cudaMemcpyAsync(quat4, h->d_q, b, cudaMemcpyDefault, s));
+  if (vel4) CK(cudaMemcpyAsync(vel4, h->d_v, b, cudaMemcpyDefault, s));
+  if (omega4) CK(cudaMemcpyAsync(omega4, h->d_o, b, cudaMemcpyDefault, s));
+  return CORDE_OK;
+}
+
+int rod_set_state(rod_handle h, const float* pos4, const float* quat4, const float* vel4, const float* omega4,
+                  void* stream) {
+  if (int rc = check_handle(h)) return rc;
+  const size_t b = (size_t)h->n_elem * sizeof(float4);
+  cudaStream_t s = (cudaStream_t)stream;
+  // positions: copy x, y, z only (12 of every 16 bytes) so that the masses in .w stay
+  if (pos4)
+    CK(cudaMemcpy2DAsync(h->d_x, sizeof(float4), pos4, sizeof(float4), 3 * sizeof(float), h->n_elem,
+                         cudaMemcpyDefault, s));
+  if (quat4) CK(cudaMemcpyAsync(h->d_q, quat4, b, cudaMemcpyDefault, s));
+  if (vel4) CK(cudaMemcpyAsync(h->d_v, vel4, b, cudaMemcpyDefault, s));
+  if (omega4) CK(cudaMemcpyAsync(h->d_o, omega4, b, cudaMemcpyDefault, s));
+  return CORDE_OK;
+}
+
+int rod_info(rod_handle h, int* n_rods, int64_t* n_elements) {
+  if (!h) return fail(CORDE_ERR_ARG, "NULL rod handle");
+  if (n_rods) *n_rods = h->n_rods;
+  if (n_elements) *n_elements = h->n_elem;
+  return CORDE_OK;
+}
+
+int rod_get_derived(rod_handle h, double* per_rod, float* per_joint) {
+  if (int rc = check_handle(h)) return rc;
+  if (per_rod) std::memcpy(per_rod, h->derived.data(), h->derived.size() * sizeof(double));
+  if (per_joint) {
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy2D(per_joint, 2 * sizeof(float4), h->d_k, sizeof(float4), sizeof(float4), h->n_elem,
+                    cudaMemcpyDefault));
+    CK(cudaMemcpy2D(per_joint + 4, 2 * sizeof(float4), h->d_u, sizeof(float4), sizeof(float4), h->n_elem,
+                    cudaMemcpyDefault));
+  }
+  return CORDE_OK;
+}
+
+int rod_set_material(rod_handle h, const float* per_joint, void* stream) {
+  if (int rc = check_handle(h)) return rc;
+  if (!per_joint) return fail(CORDE_ERR_ARG, "per_joint is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaMemcpy2DAsync(h->d_k, sizeof(float4), per_joint, 2 * sizeof(float4), sizeof(float4), h->n_elem,
+                       cudaMemcpyDefault, s));
+  CK(cudaMemcpy2DAsync(h->d_u, sizeof(float4), per_joint + 4, 2 * sizeof(float4), sizeof(float4), h->n_elem,
+                       cudaMemcpyDefault, s));
+  return CORDE_OK;
+}
+
+int rod_diagnostics(rod_handle h, double* out) {
+  if (int rc = check_handle(h)) return rc;
+  if (!out) return fail(CORDE_ERR_ARG, "out is NULL");
+  double* d_out = nullptr;
+  CK(cudaMalloc(&d_out, 4 * h->n_rods * sizeof(double)));
+  diag_kernel<<<h->n_rods, 256>>>(h->d_rods, h->d_derived, h->d_x, h->d_q, h->d_v, h->d_o, h->d_u, h->d_k, d_out);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(out, d_out, 4 * h->n_rods * sizeof(double), cudaMemcpyDeviceToHost);
+  cudaFree(d_out);
+  if (e != cudaSuccess) return fail(CORDE_ERR_CUDA, std::string("diagnostics: ") + cudaGetErrorString(e));
+  for (int r = 0; r < h->n_rods; ++r)
+    if (out[4 * r + 2] > 0) return fail(CORDE_ERR_NONFINITE, "rod " + std::to_string(r) + " has non-finite state");
+  return CORDE_OK;
+}
+
+int rod_set_plan(rod_handle h, int ept, int nt) {
+  if (int rc = check_handle(h)) return rc;
+  if (ept == 0) {
+    for (int r = 0; r < h->n_rods; ++r) h->plan[r] = default_variant(h->n_nodes[r]);
+    return build_bins(h);
+  }
+  const int v = find_variant(ept, nt);
+  if (v < 0) return fail(CORDE_ERR_ARG, "no compiled variant with ept=" + std::to_string(ept) + ", nt=" + std::to_string(nt));
+  for (int r = 0; r < h->n_rods; ++r)
+    if (variants()[v].capacity() >= h->n_nodes[r]) h->plan[r] = v;
+  return build_bins(h);
+}
+
+int rod_get_plan(rod_handle h, int* plan) {
+  if (!h || !plan) return fail(CORDE_ERR_ARG, "NULL argument");
+  for (int r = 0; r < h->n_rods; ++r) {
+    plan[2 * r] = variants()[h->plan[r]].ept;
+    plan[2 * r + 1] = variants()[h->plan[r]].nt;
+  }
+  return CORDE_OK;
+}
+
+int rod_last_launch_count(rod_handle h) { return h ? h->last_launches : 0; }
+
+int rod_autotune(rod_handle h, int n_steps, void* stream) {
+  if (int rc = check_handle(h)) return rc;
+  if (n_steps < 1) return fail(CORDE_ERR_ARG, "n_steps must be >= 1");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t b = (size_t)h->n_elem * sizeof(float4);
+  float4 *sx = nullptr, *sv = nullptr, *sq = nullptr, *so = nullptr;
+  CK(cudaMalloc(&sx, b));
+  CK(cudaMalloc(&sv, b));
+  CK(cudaMalloc(&sq, b));
+  CK(cudaMalloc(&so, b));
+  CK(cudaMemcpyAsync(sx, h->d_x, b, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(sv, h->d_v, b, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(sq, h->d_q, b, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(so, h->d_o, b, cudaMemcpyDeviceToDevice, s));
+  auto restore = [&]() {
+    cudaMemcpyAsync(h->d_x, sx, b, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(h->d_v, sv, b, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(h->d_q, sq, b, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(h->d_o, so, b, cudaMemcpyDeviceToDevice, s);
+  };
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  // Length classes: powers of two (rods in (2^(k-1), 2^k]).
+  std::vector<int> cls(h->n_rods);
+  int max_cls = 0;
+  for (int r = 0; r < h->n_rods; ++r) {
+    int c = 5;
+    while ((1 << c) < h->n_nodes[r]) ++c;
+    cls[r] = c;
+    max_cls = std::max(max_cls, c);
+  }
+  int rc = CORDE_OK;
+  for (int c = 5; c <= max_cls && rc == CORDE_OK; ++c) {
+    std::vector<int> rods;
+    int nmax = 0;
+    for (int r = 0; r < h->n_rods; ++r)
+      if (cls[r] == c) {
+        rods.push_back(r);
+        nmax = std::max(nmax, h->n_nodes[r]);
+      }
+    if (rods.empty()) continue;
+    std::stable_sort(rods.begin(), rods.end(), [&](int a, int bb) { return h->n_nodes[a] > h->n_nodes[bb]; });
+    int* d_work = nullptr;
+    if (cudaMalloc(&d_work, rods.size() * sizeof(int)) != cudaSuccess) { rc = fail(CORDE_ERR_OOM, "autotune work list"); break; }
+    cudaMemcpy(d_work, rods.data(), rods.size() * sizeof(int), cudaMemcpyHostToDevice);
+    float best_ms = 1e30f;
+    int best_v = -1;
+    for (size_t vi = 0; vi < variants().size(); ++vi) {
+      const StepVariant& v = variants()[vi];
+      if (v.capacity() < nmax) continue;
+      if (v.capacity() >= 8 * nmax && v.nt > 32) continue;  // mostly idle threads
+      std::vector<Bin> one{Bin{(int)vi, (int)rods.size(), d_work}};
+      float ms = 0.f;
+      restore();
+      if ((rc = launch_bins(h, one, n_steps, h->d_drive, s)) != CORDE_OK) break;  // warm-up
+      restore();
+      cudaEventRecord(e0, s);
+      if ((rc = launch_bins(h, one, n_steps, h->d_drive, s)) != CORDE_OK) break;
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess) { rc = fail(CORDE_ERR_CUDA, "autotune timing"); break; }
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best_ms) { best_ms = ms; best_v = (int)vi; }
+    }
+    cudaFree(d_work);
+    if (best_v >= 0)
+      for (int r : rods) h->plan[r] = best_v;
+  }
+  restore();
+  cudaStreamSynchronize(s);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(sx); cudaFree(sv); cudaFree(sq); cudaFree(so);
+  if (rc != CORDE_OK) return rc;
+  return build_bins(h);
+}
+
+void rod_destroy(rod_handle h) {
+  if (!h) return;
+  cudaSetDevice(h->device);
+  cudaDeviceSynchronize();
+  free_bins(h);
+  cudaFree(h->d_rods); cudaFree(h->d_derived);
+  cudaFree(h->d_x); cudaFree(h->d_v); cudaFree(h->d_q); cudaFree(h->d_o); cudaFree(h->d_u); cudaFree(h->d_k);
+  cudaFree(h->d_drive); cudaFree(h->d_elem_rod);
+  delete h;
+}
+
+}  // extern "C"

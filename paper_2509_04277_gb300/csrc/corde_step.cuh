@@ -1,0 +1,320 @@
+// Persistent multi-step CoRdE kernel: one thread block per rod, EPT consecutive
+// elements per thread kept in registers for the whole launch (Section 2.2: the state is
+// loaded once per launch and many time steps run before it is written back).
+//
+// Per time step, in the order of Fig. 5:
+//   1. exchange: each thread publishes its first element's (r, q) to its left neighbour;
+//   2. elastic forces and torques of the joints and segments the thread owns (bend and
+//      twist, Eq. 3 with Eq. 5-6; penalty, Eq. 8; stretch, Eq. 2 for extensible rods);
+//      the contribution of a thread's last joint / segment to the right neighbour's
+//      first element is carried over in a second exchange;
+//   3. force integration: v += dt (F / m~ + g / mass_scale), omega += dt J~^-1 (tau -
+//      omega x J~ omega), implicit Rayleigh damping; the kinematic base takes the drive;
+//   4. n_iters iterations of red-black distance-constraint impulses (inextensible
+//      variant, Section 2.1 "Constraints"): the even segments of a thread are local
+//      (EPT is even and every thread starts on an even element); the odd sweep needs one
+//      exchange for the segment crossing each thread boundary;
+//   5. integration of the velocities: r += dt v, q <- normalize(q + dt/2 q (x) (0, omega)).
+// A step costs 2 + n_iters block barriers (the paper's single-block kernel uses two
+// __syncthreads per constraint iteration, one thread per element).  Neighbour data moves
+// through a ping-pong pair of shared-memory buffers, so one barrier per exchange suffices.
+#pragma once
+
+#include "corde_common.cuh"
+
+namespace corde {
+
+template <int NT>
+__device__ __forceinline__ void block_sync() {
+  if constexpr (NT == 32) {
+    __syncwarp();
+  } else {
+    __syncthreads();
+  }
+}
+
+// Bend/twist torques of the joint between frames a and b (Eq. 3): with
+// D = conj(qa) (x) qb, u = (2/l) Im(D) and m = 2 K (u - u-hat), the body torques are
+// tau_a = 1/2 Im(D (x) (0, m)) and tau_b = -1/2 Im(conj(D) (x) (0, m)).
+__device__ __forceinline__ void joint_torques(float4 qa, float4 qb, float4 uh, float4 K, float two_over_l,
+                                              float3& ta, float3& tb) {
+  const float dw = qa.x * qb.x + qa.y * qb.y + qa.z * qb.z + qa.w * qb.w;
+  const float3 dv = im_conj_mul(qa, qb);
+  const float3 u = two_over_l * dv;
+  const float3 m = f3(2.f * K.x * (u.x - uh.x), 2.f * K.y * (u.y - uh.y), 2.f * K.z * (u.z - uh.z));
+  const float3 c = cross3(dv, m);
+  ta = 0.5f * (dw * m + c);
+  tb = 0.5f * (c - dw * m);
+}
+
+// Segment forces between nodes a and b and the penalty torque on frame q (Eq. 8, and
+// Eq. 2 when the rod is extensible).  Penalty: E = 1/2 l0 Kp |t - d3|^2 gives the force
+// l0 Kp (d3 - (t . d3) t) / |e| on node b (opposite on a) and the world torque
+// l0 Kp d3 x t on the frame.
+__device__ __forceinline__ void segment_forces(float3 ra, float3 rb, float4 q, const RodDev& R, bool extensible,
+                                               float3& fa, float3& fb, float3& tq) {
+  const float3 e = rb - ra;
+  const float ee = dot3(e, e);
+  const float il = rsqrtf(ee);
+  const float3 t = il * e;
+  const float3 d3 = director3(q);
+  const float c = dot3(t, d3);
+  const float3 f = (R.lKp * il) * (d3 - c * t);
+  fb = f;
+  fa = -f;
+  if (extensible) {
+    const float len = ee * il;
+    const float3 fs = (R.Ks * (len * R.inv_l0 - 1.f)) * t;
+    fa += fs;
+    fb -= fs;
+  }
+  tq = rotate_inv(q, R.lKp * cross3(d3, t));
+}
+
+// Velocity-impulse factor of one distance constraint (predictive: makes |pb' - pa'| = l0
+// after the update).  Returns s = lambda / |d| with lambda = -(|d| - l0) / (dt (wa + wb)),
+// d = pb - pa; the caller applies va -= wa s d, vb += wb s d.  Written with explicit
+// round-to-nearest intrinsics so that the two threads sharing a boundary constraint
+// compute bit-identical impulses.
+__device__ __forceinline__ float constraint_factor(float3 pa, float3 pb, float wsum, float l0, float dt, float3& d) {
+  d = f3(__fsub_rn(pb.x, pa.x), __fsub_rn(pb.y, pa.y), __fsub_rn(pb.z, pa.z));
+  const float dd = __fmaf_rn(d.x, d.x, __fmaf_rn(d.y, d.y, __fmul_rn(d.z, d.z)));
+  const float il = rsqrtf(dd);
+  const float C = __fsub_rn(__fmul_rn(dd, il), l0);
+  return __fdiv_rn(__fmul_rn(-C, il), __fmul_rn(dt, wsum));
+}
+
+// Dynamic shared memory of a <EPT, NT> block: per-element joint parameters (u-hat and
+// K), element-major so that thread t's accesses are conflict-free, then the two
+// ping-pong exchange buffers of two float4 slots per thread.
+template <int EPT, int NT>
+constexpr int step_smem_bytes() {
+  return (2 * EPT * NT + 2 * 2 * NT) * (int)sizeof(float4);
+}
+
+template <int EPT, int NT>
+__global__ void __launch_bounds__(NT)
+step_kernel(const RodDev* __restrict__ rods, const int* __restrict__ work, float4* __restrict__ x4,
+            float4* __restrict__ v4, float4* __restrict__ q4, float4* __restrict__ o4,
+            const float4* __restrict__ u4, const float4* __restrict__ k4, const float4* __restrict__ drive,
+            int n_steps) {
+  static_assert(EPT % 2 == 0, "elements per thread must be even (red-black sweeps)");
+  extern __shared__ float4 smem[];
+  float4* par_u = smem;
+  float4* par_k = smem + EPT * NT;
+  float4* halo = smem + 2 * EPT * NT;
+
+  const int rid = work[blockIdx.x];
+  const RodDev R = rods[rid];
+  const int t = threadIdx.x;
+  const int e0 = t * EPT;
+  const int n = R.n;
+  const bool inext = (R.flags & F_INEXT) != 0;
+  const bool clamp = (R.flags & F_CLAMP) != 0;
+  const float dt = R.dt;
+  const float half_dt = 0.5f * dt;
+
+  float3 r[EPT], v[EPT], om[EPT];
+  float4 q[EPT];
+  float w[EPT];
+#pragma unroll
+  for (int e = 0; e < EPT; ++e) {
+    const int i = e0 + e;
+    if (i < n) {
+      const float4 a = x4[R.off + i];
+      r[e] = f3(a);
+      w[e] = a.w;
+      v[e] = f3(v4[R.off + i]);
+      q[e] = q4[R.off + i];
+      om[e] = f3(o4[R.off + i]);
+      par_u[e * NT + t] = u4[R.off + i];
+      par_k[e * NT + t] = k4[R.off + i];
+    } else {
+      r[e] = zero3();
+      v[e] = zero3();
+      om[e] = zero3();
+      q[e] = make_float4(0.f, 0.f, 0.f, 1.f);
+      w[e] = 0.f;
+    }
+  }
+  float3 v_drive = zero3(), w_drive = zero3();
+  if (drive != nullptr) {
+    v_drive = f3(drive[2 * rid]);
+    w_drive = f3(drive[2 * rid + 1]);
+  }
+  // Parameters are read back only by the thread that wrote them: no barrier needed.
+
+  int xc = 0;  // exchange counter selects the ping-pong buffer
+  for (int step = 0; step < n_steps; ++step) {
+    // ---- exchange 1: first element's position and frame to the left neighbour
+    float4* hb = halo + (xc & 1) * 2 * NT;
+    ++xc;
+    hb[t] = make_float4(r[0].x, r[0].y, r[0].z, 0.f);
+    hb[NT + t] = q[0];
+    block_sync<NT>();
+    float3 r_next = zero3();
+    float4 q_next = make_float4(0.f, 0.f, 0.f, 1.f);
+    if (t + 1 < NT) {
+      r_next = f3(hb[t + 1]);
+      q_next = hb[NT + t + 1];
+    }
+
+    // ---- elastic forces and torques
+    float3 F[EPT], tau[EPT];
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) {
+      F[e] = zero3();
+      tau[e] = zero3();
+    }
+    float3 F_carry = zero3(), tau_carry = zero3();
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) {
+      const int j = e0 + e;
+      const float4 qb = (e + 1 < EPT) ? q[(e + 1) % EPT] : q_next;
+      const float3 rb = (e + 1 < EPT) ? r[(e + 1) % EPT] : r_next;
+      if (j <= n - 3) {  // joint between frames j and j+1
+        float3 ta, tb;
+        joint_torques(q[e], qb, par_u[e * NT + t], par_k[e * NT + t], R.two_over_l, ta, tb);
+        tau[e] += ta;
+        if (e + 1 < EPT) {
+          tau[(e + 1) % EPT] += tb;
+        } else {
+          tau_carry = tb;
+        }
+      }
+      if (j <= n - 2) {  // segment between nodes j and j+1, frame j
+        float3 fa, fb, tq;
+        segment_forces(r[e], rb, q[e], R, !inext, fa, fb, tq);
+        F[e] += fa;
+        tau[e] += tq;
+        if (e + 1 < EPT) {
+          F[(e + 1) % EPT] += fb;
+        } else {
+          F_carry = fb;
+        }
+      }
+    }
+    // ---- exchange 2: carries to the right neighbour's first element
+    hb = halo + (xc & 1) * 2 * NT;
+    ++xc;
+    hb[t] = make_float4(F_carry.x, F_carry.y, F_carry.z, 0.f);
+    hb[NT + t] = make_float4(tau_carry.x, tau_carry.y, tau_carry.z, 0.f);
+    block_sync<NT>();
+    if (t > 0) {
+      F[0] += f3(hb[t - 1]);
+      tau[0] += f3(hb[NT + t - 1]);
+    }
+
+    // ---- integrate forces and torques into velocities
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) {
+      const int i = e0 + e;
+      if (w[e] > 0.f) {
+        const float3 a = f3(w[e] * F[e].x + R.gx, w[e] * F[e].y + R.gy, w[e] * F[e].z + R.gz);
+        v[e] = R.damp * (v[e] + dt * a);
+      }
+      const bool frame_dynamic = (i <= n - 2) && !(clamp && i == 0);
+      if (frame_dynamic) {
+        const float3 o = om[e];
+        const float3 Jw = f3(R.J1 * o.x, R.J1 * o.y, R.J3 * o.z);
+        const float3 rhs = tau[e] - cross3(o, Jw);
+        const float3 on = f3(o.x + dt * R.Jinv1 * rhs.x, o.y + dt * R.Jinv1 * rhs.y, o.z + dt * R.Jinv3 * rhs.z);
+        om[e] = R.damp * on;
+      }
+    }
+    if (clamp && t == 0) {
+      v[0] = v_drive;
+      om[0] = w_drive;
+    }
+
+    // ---- distance-constraint iterations (inextensible rod), red-black
+    if (inext) {
+      for (int it = 0; it < R.n_iters; ++it) {
+        // even segments (e0 + 2k, e0 + 2k + 1): local to the thread
+#pragma unroll
+        for (int k = 0; k < EPT / 2; ++k) {
+          const int a = 2 * k, b = 2 * k + 1;
+          const float ws = w[a] + w[b];
+          if (e0 + b <= n - 1 && ws > 0.f) {
+            float3 d;
+            const float s = constraint_factor(r[a] + dt * v[a], r[b] + dt * v[b], ws, R.l0, dt, d);
+            v[a] -= (w[a] * s) * d;
+            v[b] += (w[b] * s) * d;
+          }
+        }
+        // exchange 3: predicted positions and inverse masses of the first and last element
+        const float3 p_first = r[0] + dt * v[0];
+        const float3 p_last = r[EPT - 1] + dt * v[EPT - 1];
+        hb = halo + (xc & 1) * 2 * NT;
+        ++xc;
+        hb[t] = make_float4(p_first.x, p_first.y, p_first.z, w[0]);
+        hb[NT + t] = make_float4(p_last.x, p_last.y, p_last.z, w[EPT - 1]);
+        block_sync<NT>();
+        // odd segments inside the thread
+#pragma unroll
+        for (int k = 0; k + 1 < EPT / 2; ++k) {
+          const int a = 2 * k + 1, b = 2 * k + 2;
+          const float ws = w[a] + w[b];
+          if (e0 + b <= n - 1 && ws > 0.f) {
+            float3 d;
+            const float s = constraint_factor(r[a] + dt * v[a], r[b] + dt * v[b], ws, R.l0, dt, d);
+            v[a] -= (w[a] * s) * d;
+            v[b] += (w[b] * s) * d;
+          }
+        }
+        // odd segment across the right boundary: (my last, right neighbour's first)
+        if (t + 1 < NT && e0 + EPT <= n - 1) {
+          const float4 nb = hb[t + 1];
+          const float ws = w[EPT - 1] + nb.w;
+          if (ws > 0.f) {
+            float3 d;
+            const float s = constraint_factor(p_last, f3(nb), ws, R.l0, dt, d);
+            v[EPT - 1] -= (w[EPT - 1] * s) * d;
+          }
+        }
+        // odd segment across the left boundary: (left neighbour's last, my first)
+        if (t > 0 && e0 <= n - 1) {
+          const float4 pa = hb[NT + t - 1];
+          const float ws = pa.w + w[0];
+          if (ws > 0.f) {
+            float3 d;
+            const float s = constraint_factor(f3(pa), p_first, ws, R.l0, dt, d);
+            v[0] += (w[0] * s) * d;
+          }
+        }
+      }
+    }
+
+    // ---- integrate linear and angular velocities (semi-implicit Euler)
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) {
+      const int i = e0 + e;
+      r[e] += dt * v[e];
+      if (i <= n - 2) {
+        const float4 a = q[e];
+        const float3 o = om[e];
+        // q (x) (0, omega)
+        const float dx = a.w * o.x + a.y * o.z - a.z * o.y;
+        const float dy = a.w * o.y + a.z * o.x - a.x * o.z;
+        const float dz = a.w * o.z + a.x * o.y - a.y * o.x;
+        const float dwq = -(a.x * o.x + a.y * o.y + a.z * o.z);
+        float4 b = make_float4(a.x + half_dt * dx, a.y + half_dt * dy, a.z + half_dt * dz, a.w + half_dt * dwq);
+        const float inv = rsqrtf(b.x * b.x + b.y * b.y + b.z * b.z + b.w * b.w);
+        q[e] = make_float4(b.x * inv, b.y * inv, b.z * inv, b.w * inv);
+      }
+    }
+  }
+
+#pragma unroll
+  for (int e = 0; e < EPT; ++e) {
+    const int i = e0 + e;
+    if (i < n) {
+      x4[R.off + i] = make_float4(r[e].x, r[e].y, r[e].z, w[e]);
+      v4[R.off + i] = make_float4(v[e].x, v[e].y, v[e].z, 0.f);
+      q4[R.off + i] = q[e];
+      o4[R.off + i] = make_float4(om[e].x, om[e].y, om[e].z, 0.f);
+    }
+  }
+}
+
+}  // namespace corde

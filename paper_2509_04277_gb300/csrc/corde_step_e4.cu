@@ -1,0 +1,24 @@
+// Step-kernel instantiations with 4 elements per thread.
+#include "corde_step.cuh"
+#include "corde_variants.cuh"
+
+namespace corde {
+
+template <int EPT, int NT>
+static cudaError_t launch_step(const StepArgs& a, int n_blocks, cudaStream_t s) {
+  constexpr int smem = step_smem_bytes<EPT, NT>();
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(step_kernel<EPT, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+  }
+  step_kernel<EPT, NT><<<n_blocks, NT, smem, s>>>(a.rods, a.work, a.x4, a.v4, a.q4, a.o4, a.u4, a.k4, a.drive,
+                                                  a.n_steps);
+  return cudaGetLastError();
+}
+
+#define V(NT) {4, NT, step_smem_bytes<4, NT>(), &launch_step<4, NT>}
+const StepVariant kStepVariantsE4[] = {V(32), V(64), V(128), V(256), V(512)};
+#undef V
+const int kNumStepVariantsE4 = 5;
+
+}  // namespace corde

@@ -1,0 +1,238 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on seeded inputs.
+
+Tolerances (positions relative to the rod length L, quaternion components absolute):
+  * one step from a shared state ........ |dr| <= 1e-5 L, |dq| <= 1e-4
+  * 100 free-running steps ............... |dr| <= 1e-4 L, |dq| <= 1e-4
+The GPU computes in FP32, the oracle in FP64; each one-step comparison restarts the
+oracle from the GPU's own state, so errors do not accumulate across steps there.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2509_04277_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+STEP_TOL = 1e-5
+ROLL_TOL = 1e-4
+QUAT_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def corde(cuda):
+    from paper_2509_04277_gb300 import build, corde as C
+
+    build.build()
+    C.load()
+    return C
+
+
+def _cmp(rod, gpu, ref, tol):
+    L = rod.length
+    dr = np.abs(gpu["pos"] - ref["pos"]).max() / L
+    dq = np.abs(gpu["quat"] - ref["quat"]).max()
+    assert np.isfinite(gpu["pos"]).all() and np.isfinite(gpu["quat"]).all()
+    assert dr <= tol, f"position error {dr:.3e} L > {tol:.1e} L"
+    assert dq <= QUAT_TOL, f"quaternion error {dq:.3e} > {QUAT_TOL:.1e}"
+    return dr, dq
+
+
+def _drive_dev(torch, drive):
+    return torch.as_tensor(np.asarray(drive, np.float32).reshape(-1, 8), device="cuda").contiguous()
+
+
+def test_derived_constants_match_oracle(corde):
+    rods = [W.extensible_pendulum(), W.guidewire(), W.catheter()] + W.batched_rods(8, seed=40)
+    b = corde.RodBatch(rods)
+    got = b.derived()
+    keys = ["l0", "A", "I", "K1", "K2", "K3", "Ks", "Kp", "mass_scale", "inertia_scale", "m_interior", "J1", "J2",
+            "J3", "w_interior"]
+    for r, rod in enumerate(rods):
+        want = oracle.derive(rod)
+        for k, key in enumerate(keys):
+            assert got[r, k] == pytest.approx(want[key], rel=1e-12), (r, key)
+    b.close()
+
+
+def test_rest_darboux_and_stiffness_match_oracle(corde):
+    from scipy.spatial.transform import Rotation as R
+
+    rod = W.guidewire(40, seed=41)
+    # curved rest shape: constant body-frame increment
+    q0 = R.from_rotvec([0, np.pi / 2, 0])
+    rest = np.array([(q0 * R.from_rotvec(j * 0.05 * np.array([0.3, -0.5, 0.8]))).as_quat() for j in range(39)])
+    rod.rest_quat = rest
+    rod.stiff_mul = np.exp(np.random.default_rng(0).standard_normal((38, 3)) * 0.3)
+    b = corde.RodBatch([rod])
+    pj = b.per_joint()
+    K, uhat = oracle.material(rod)
+    np.testing.assert_allclose(pj[:38, 0:3], K, rtol=1e-6)
+    np.testing.assert_allclose(pj[:38, 4:7], uhat, rtol=1e-4, atol=1e-4 * np.abs(uhat).max())
+    b.close()
+
+
+def _one_step_parity(corde, torch, rod, n_checks=5, drive=None, plan=None):
+    b = corde.RodBatch([rod])
+    if plan is not None:
+        b.set_plan(*plan)
+    d = None if drive is None else _drive_dev(torch, drive)
+    worst = (0.0, 0.0)
+    for _ in range(n_checks):
+        st0 = b.rod_state(b.state_numpy(), 0)
+        b.step(1, drive=d)
+        gpu = b.rod_state(b.state_numpy(), 0)
+        ref = oracle.step(rod, st0, 1, drive=None if drive is None else np.asarray(drive, np.float64))
+        dr, dq = _cmp(rod, gpu, ref, STEP_TOL)
+        worst = (max(worst[0], dr), max(worst[1], dq))
+    b.close()
+    return worst
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 5, 16, 17, 33, 63, 64, 65, 100, 129, 255, 256, 257, 511, 512, 1000, 2048])
+def test_one_step_parity_inextensible_sizes(corde, n):
+    import torch
+
+    rod = W.guidewire(n, seed=100 + n)
+    drive = np.array([0.02, -0.01, 0.005, 0, 0.1, -0.2, 3.0, 0])
+    _one_step_parity(corde, torch, rod, n_checks=3, drive=drive)
+
+
+@pytest.mark.parametrize("n", [2, 5, 33, 64, 200])
+def test_one_step_parity_extensible(corde, n):
+    import torch
+
+    rod = W.extensible_pendulum(n, seed=200 + n)
+    _one_step_parity(corde, torch, rod, n_checks=3)
+
+
+@pytest.mark.parametrize("plan", [(2, 32), (2, 64), (2, 128), (2, 256), (2, 512), (4, 32), (4, 64), (4, 128),
+                                  (4, 256), (4, 512)])
+def test_every_variant_matches_oracle(corde, plan):
+    import torch
+
+    n = min(plan[0] * plan[1], 301)
+    rod = W.guidewire(n, seed=300 + plan[0] * 1000 + plan[1])
+    b = corde.RodBatch([rod])
+    b.set_plan(*plan)
+    assert tuple(b.plan()[0]) == plan
+    b.close()
+    _one_step_parity(corde, torch, rod, n_checks=2, drive=np.array([0.01, 0, 0, 0, 0, 0, 1.0, 0]), plan=plan)
+
+
+def test_guidewire_100_steps_free_running(corde):
+    """512-element guidewire, 10 launches of 10 steps with a 1 kHz drive, vs the oracle."""
+    import torch
+
+    rod = W.guidewire()
+    drive = W.sinusoid_drive(2, 10, 10 * rod.dt)
+    b = corde.RodBatch([rod])
+    ref = oracle.state_of(rod)
+    for k in range(10):
+        b.step(10, drive=_drive_dev(torch, drive[k]))
+        ref = oracle.step(rod, ref, 10, drive=drive[k])
+    gpu = b.rod_state(b.state_numpy(), 0)
+    _cmp(rod, gpu, ref, ROLL_TOL)
+    rc, diag = b.diagnostics()
+    assert rc == 0
+    seg = np.linalg.norm(np.diff(ref["pos"], axis=0), axis=1)
+    ora_err = np.abs(seg / (rod.length / 511) - 1).max()
+    assert diag[0, 0] <= 2 * ora_err + 1e-5
+    assert diag[0, 1] < 1e-6
+    b.close()
+
+
+def test_extensible_pendulum_100_steps_free_running(corde):
+    rod = W.extensible_pendulum()
+    b = corde.RodBatch([rod])
+    for _ in range(10):
+        b.step(10)
+    gpu = b.rod_state(b.state_numpy(), 0)
+    ref = oracle.step(rod, oracle.state_of(rod), 100)
+    _cmp(rod, gpu, ref, ROLL_TOL)
+    b.close()
+
+
+def test_set_input_drives_the_base(corde):
+    """rod_set_input (host buffer) then rod_step with no drive pointer: the kinematic base
+    moves exactly with the given velocity."""
+    rod = W.guidewire(64, seed=7)
+    b = corde.RodBatch([rod])
+    drive = np.array([[0.03, 0.01, -0.02, 0, 0, 0, 0.5, 0]], np.float32)
+    b.set_input(drive)
+    b.step(20)
+    gpu = b.rod_state(b.state_numpy(), 0)
+    np.testing.assert_allclose(gpu["pos"][0], rod.pos[0] + 20 * rod.dt * drive[0, :3].astype(np.float64),
+                               rtol=0, atol=2e-7)
+    ref = oracle.step(rod, oracle.state_of(rod), 20, drive=drive[0].astype(np.float64))
+    _cmp(rod, gpu, ref, ROLL_TOL)
+    b.close()
+
+
+def test_batched_small_rods_match_oracle(corde):
+    rods = W.batched_rods(48, seed=44, n_max=600)
+    b = corde.RodBatch(rods)
+    assert b.last_launch_count() == 0
+    b.step(10)
+    assert b.last_launch_count() >= 1
+    st = b.state_numpy()
+    for r, rod in enumerate(rods):
+        ref = oracle.step(rod, oracle.state_of(rod), 10)
+        _cmp(rod, b.rod_state(st, r), ref, ROLL_TOL)
+    b.close()
+
+
+def test_batched_full_size_sampled_rods(corde):
+    """The full 4096-rod batch (element counts log-uniform in [16, 2048]) in the launch
+    configuration the benchmark uses: 16 sampled rods compared with the oracle, and
+    invariants (finite state, unit quaternions) over every rod."""
+    rods = W.batched_rods()
+    b = corde.RodBatch(rods)
+    b.step(10)
+    st = b.state_numpy()
+    rc, diag = b.diagnostics()
+    assert rc == 0
+    assert diag[:, 1].max() < 1e-6
+    order = np.argsort([r.n_nodes for r in rods])
+    sample = order[np.linspace(0, len(rods) - 1, 16).astype(int)]
+    for r in sample:
+        ref = oracle.step(rods[r], oracle.state_of(rods[r]), 10)
+        _cmp(rods[r], b.rod_state(st, r), ref, ROLL_TOL)
+    b.close()
+
+
+def test_zero_steps_and_state_roundtrip(corde):
+    rod = W.guidewire(100, seed=8)
+    b = corde.RodBatch([rod])
+    st = b.state_numpy()
+    b.step(0)
+    assert b.last_launch_count() == 0
+    st2 = b.state_numpy()
+    for k in st:
+        np.testing.assert_array_equal(st[k], st2[k])
+    # set_state keeps the masses in pos4.w
+    s = b.rod_state(st, 0)
+    s["pos"] = s["pos"] + 1e-3
+    b.set_rod_states([s])
+    st3 = b.state_numpy()
+    np.testing.assert_allclose(st3["pos4"][:, :3], st["pos4"][:, :3] + np.float32(1e-3), atol=1e-7)
+    np.testing.assert_array_equal(st3["pos4"][:, 3], st["pos4"][:, 3])
+    b.close()
+
+
+def test_rest_state_stays_at_rest(corde):
+    """A rod created in its rest shape (no drive, no gravity) does not move."""
+    from scipy.spatial.transform import Rotation as R
+
+    rod = W.guidewire(300, seed=9)
+    q = np.tile(R.from_rotvec([0, np.pi / 2, 0]).as_quat(), (299, 1))
+    rod.quat = q
+    rod.rest_quat = q.copy()
+    rod.pos = np.zeros((300, 3))
+    rod.pos[:, 0] = np.arange(300) * rod.length / 299
+    b = corde.RodBatch([rod])
+    b.step(50)
+    gpu = b.rod_state(b.state_numpy(), 0)
+    assert np.abs(gpu["pos"] - rod.pos).max() < 1e-6 * rod.length
+    assert np.abs(gpu["vel"]).max() < 1e-6
+    b.close()
