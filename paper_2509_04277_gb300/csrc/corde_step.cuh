@@ -3,7 +3,8 @@
 // loaded once per launch and many time steps run before it is written back).
 //
 // Per time step, in the order of Fig. 5:
-//   1. exchange: each thread publishes its first element's (r, q) to its left neighbour;
+//   1. exchange: each thread publishes its first element's (r, w, q) to its left and its
+//      last element's (r, w) to its right neighbour;
 //   2. elastic forces and torques of the joints and segments the thread owns (bend and
 //      twist, Eq. 3 with Eq. 5-6; penalty, Eq. 8; stretch, Eq. 2 for extensible rods);
 //      the contribution of a thread's last joint / segment to the right neighbour's
@@ -13,7 +14,7 @@
 //   4. n_iters iterations of red-black distance-constraint impulses (inextensible
 //      variant, Section 2.1 "Constraints"): the even segments of a thread are local
 //      (EPT is even and every thread starts on an even element); the odd sweep needs one
-//      exchange for the segment crossing each thread boundary;
+//      exchange (boundary velocities) for the segment crossing each thread boundary;
 //   5. integration of the velocities: r += dt v, q <- normalize(q + dt/2 q (x) (0, omega)).
 // A step costs 2 + n_iters block barriers (the paper's single-block kernel uses two
 // __syncthreads per constraint iteration, one thread per element).  Neighbour data moves
@@ -71,13 +72,18 @@ __device__ __forceinline__ void segment_forces(float3 ra, float3 rb, float4 q, c
   tq = rotate_inv(q, R.lKp * cross3(d3, t));
 }
 
-// Velocity-impulse factor of one distance constraint (predictive: makes |pb' - pa'| = l0
-// after the update).  Returns s = lambda / |d| with lambda = -(|d| - l0) / (dt (wa + wb)),
-// d = pb - pa; the caller applies va -= wa s d, vb += wb s d.  Written with explicit
-// round-to-nearest intrinsics so that the two threads sharing a boundary constraint
-// compute bit-identical impulses.
-__device__ __forceinline__ float constraint_factor(float3 pa, float3 pb, float wsum, float l0, float dt, float3& d) {
-  d = f3(__fsub_rn(pb.x, pa.x), __fsub_rn(pb.y, pa.y), __fsub_rn(pb.z, pa.z));
+// Velocity-impulse factor of one distance constraint (predictive: makes the segment
+// length l0 after the update).  d = (r_b + dt v_b) - (r_a + dt v_a) is formed as
+// (r_b - r_a) + dt (v_b - v_a): the node difference is exact for neighbouring nodes,
+// whereas r + dt v would round dt v against |r|.  Returns s = lambda / |d| with
+// lambda = -(|d| - l0) / (dt (wa + wb)); the caller applies va -= wa s d, vb += wb s d.
+// Explicit round-to-nearest intrinsics make the two threads that share a boundary
+// constraint compute bit-identical impulses.
+__device__ __forceinline__ float constraint_factor(float3 ra, float3 va, float3 rb, float3 vb, float wsum, float l0,
+                                                   float dt, float3& d) {
+  d = f3(__fmaf_rn(dt, __fsub_rn(vb.x, va.x), __fsub_rn(rb.x, ra.x)),
+         __fmaf_rn(dt, __fsub_rn(vb.y, va.y), __fsub_rn(rb.y, ra.y)),
+         __fmaf_rn(dt, __fsub_rn(vb.z, va.z), __fsub_rn(rb.z, ra.z)));
   const float dd = __fmaf_rn(d.x, d.x, __fmaf_rn(d.y, d.y, __fmul_rn(d.z, d.z)));
   const float il = rsqrtf(dd);
   const float C = __fsub_rn(__fmul_rn(dd, il), l0);
@@ -86,10 +92,11 @@ __device__ __forceinline__ float constraint_factor(float3 pa, float3 pb, float w
 
 // Dynamic shared memory of a <EPT, NT> block: per-element joint parameters (u-hat and
 // K), element-major so that thread t's accesses are conflict-free, then the two
-// ping-pong exchange buffers of two float4 slots per thread.
+// ping-pong exchange buffers of three float4 slots per thread.
+constexpr int kHaloSlots = 3;
 template <int EPT, int NT>
 constexpr int step_smem_bytes() {
-  return (2 * EPT * NT + 2 * 2 * NT) * (int)sizeof(float4);
+  return (2 * EPT * NT + 2 * kHaloSlots * NT) * (int)sizeof(float4);
 }
 
 template <int EPT, int NT>
@@ -146,17 +153,28 @@ step_kernel(const RodDev* __restrict__ rods, const int* __restrict__ work, float
 
   int xc = 0;  // exchange counter selects the ping-pong buffer
   for (int step = 0; step < n_steps; ++step) {
-    // ---- exchange 1: first element's position and frame to the left neighbour
-    float4* hb = halo + (xc & 1) * 2 * NT;
+    // ---- exchange 1: first element's position, inverse mass and frame to the left
+    // neighbour, last element's position and inverse mass to the right neighbour (the
+    // positions hold for the whole step: the constraint sweeps change velocities only)
+    float4* hb = halo + (xc & 1) * kHaloSlots * NT;
     ++xc;
-    hb[t] = make_float4(r[0].x, r[0].y, r[0].z, 0.f);
+    hb[t] = make_float4(r[0].x, r[0].y, r[0].z, w[0]);
     hb[NT + t] = q[0];
+    hb[2 * NT + t] = make_float4(r[EPT - 1].x, r[EPT - 1].y, r[EPT - 1].z, w[EPT - 1]);
     block_sync<NT>();
-    float3 r_next = zero3();
+    float3 r_next = zero3(), r_prev = zero3();
+    float w_next = 0.f, w_prev = 0.f;
     float4 q_next = make_float4(0.f, 0.f, 0.f, 1.f);
     if (t + 1 < NT) {
-      r_next = f3(hb[t + 1]);
+      const float4 a = hb[t + 1];
+      r_next = f3(a);
+      w_next = a.w;
       q_next = hb[NT + t + 1];
+    }
+    if (t > 0) {
+      const float4 a = hb[2 * NT + t - 1];
+      r_prev = f3(a);
+      w_prev = a.w;
     }
 
     // ---- elastic forces and torques
@@ -195,7 +213,7 @@ step_kernel(const RodDev* __restrict__ rods, const int* __restrict__ work, float
       }
     }
     // ---- exchange 2: carries to the right neighbour's first element
-    hb = halo + (xc & 1) * 2 * NT;
+    hb = halo + (xc & 1) * kHaloSlots * NT;
     ++xc;
     hb[t] = make_float4(F_carry.x, F_carry.y, F_carry.z, 0.f);
     hb[NT + t] = make_float4(tau_carry.x, tau_carry.y, tau_carry.z, 0.f);
@@ -237,18 +255,16 @@ step_kernel(const RodDev* __restrict__ rods, const int* __restrict__ work, float
           const float ws = w[a] + w[b];
           if (e0 + b <= n - 1 && ws > 0.f) {
             float3 d;
-            const float s = constraint_factor(r[a] + dt * v[a], r[b] + dt * v[b], ws, R.l0, dt, d);
+            const float s = constraint_factor(r[a], v[a], r[b], v[b], ws, R.l0, dt, d);
             v[a] -= (w[a] * s) * d;
             v[b] += (w[b] * s) * d;
           }
         }
-        // exchange 3: predicted positions and inverse masses of the first and last element
-        const float3 p_first = r[0] + dt * v[0];
-        const float3 p_last = r[EPT - 1] + dt * v[EPT - 1];
-        hb = halo + (xc & 1) * 2 * NT;
+        // exchange 3: velocities of the first and last element
+        hb = halo + (xc & 1) * kHaloSlots * NT;
         ++xc;
-        hb[t] = make_float4(p_first.x, p_first.y, p_first.z, w[0]);
-        hb[NT + t] = make_float4(p_last.x, p_last.y, p_last.z, w[EPT - 1]);
+        hb[t] = make_float4(v[0].x, v[0].y, v[0].z, 0.f);
+        hb[NT + t] = make_float4(v[EPT - 1].x, v[EPT - 1].y, v[EPT - 1].z, 0.f);
         block_sync<NT>();
         // odd segments inside the thread
 #pragma unroll
@@ -257,28 +273,26 @@ step_kernel(const RodDev* __restrict__ rods, const int* __restrict__ work, float
           const float ws = w[a] + w[b];
           if (e0 + b <= n - 1 && ws > 0.f) {
             float3 d;
-            const float s = constraint_factor(r[a] + dt * v[a], r[b] + dt * v[b], ws, R.l0, dt, d);
+            const float s = constraint_factor(r[a], v[a], r[b], v[b], ws, R.l0, dt, d);
             v[a] -= (w[a] * s) * d;
             v[b] += (w[b] * s) * d;
           }
         }
         // odd segment across the right boundary: (my last, right neighbour's first)
         if (t + 1 < NT && e0 + EPT <= n - 1) {
-          const float4 nb = hb[t + 1];
-          const float ws = w[EPT - 1] + nb.w;
+          const float ws = w[EPT - 1] + w_next;
           if (ws > 0.f) {
             float3 d;
-            const float s = constraint_factor(p_last, f3(nb), ws, R.l0, dt, d);
+            const float s = constraint_factor(r[EPT - 1], v[EPT - 1], r_next, f3(hb[t + 1]), ws, R.l0, dt, d);
             v[EPT - 1] -= (w[EPT - 1] * s) * d;
           }
         }
         // odd segment across the left boundary: (left neighbour's last, my first)
         if (t > 0 && e0 <= n - 1) {
-          const float4 pa = hb[NT + t - 1];
-          const float ws = pa.w + w[0];
+          const float ws = w_prev + w[0];
           if (ws > 0.f) {
             float3 d;
-            const float s = constraint_factor(f3(pa), p_first, ws, R.l0, dt, d);
+            const float s = constraint_factor(r_prev, f3(hb[NT + t - 1]), r[0], v[0], ws, R.l0, dt, d);
             v[0] += (w[0] * s) * d;
           }
         }

@@ -188,7 +188,8 @@ def test_batched_full_size_sampled_rods(corde):
     invariants (finite state, unit quaternions) over every rod."""
     rods = W.batched_rods()
     b = corde.RodBatch(rods)
-    b.step(10)
+    b.autotune(100)
+    b.step(100)
     st = b.state_numpy()
     rc, diag = b.diagnostics()
     assert rc == 0
@@ -196,7 +197,7 @@ def test_batched_full_size_sampled_rods(corde):
     order = np.argsort([r.n_nodes for r in rods])
     sample = order[np.linspace(0, len(rods) - 1, 16).astype(int)]
     for r in sample:
-        ref = oracle.step(rods[r], oracle.state_of(rods[r]), 10)
+        ref = oracle.step(rods[r], oracle.state_of(rods[r]), 100)
         _cmp(rods[r], b.rod_state(st, r), ref, ROLL_TOL)
     b.close()
 
@@ -221,7 +222,10 @@ def test_zero_steps_and_state_roundtrip(corde):
 
 
 def test_rest_state_stays_at_rest(corde):
-    """A rod created in its rest shape (no drive, no gravity) does not move."""
+    """A rod created in its rest shape (no drive, no gravity) stays put: the GPU matches
+    the oracle started from the same FP32-rounded state, and the nodes move by less than
+    the one-step tolerance.  (FP32 coordinates of a 1.5 m rod round at ~1e-7 m, so the
+    constraint sweeps see length errors of that size and correct them.)"""
     from scipy.spatial.transform import Rotation as R
 
     rod = W.guidewire(300, seed=9)
@@ -231,8 +235,11 @@ def test_rest_state_stays_at_rest(corde):
     rod.pos = np.zeros((300, 3))
     rod.pos[:, 0] = np.arange(300) * rod.length / 299
     b = corde.RodBatch([rod])
+    st0 = b.rod_state(b.state_numpy(), 0)
     b.step(50)
     gpu = b.rod_state(b.state_numpy(), 0)
-    assert np.abs(gpu["pos"] - rod.pos).max() < 1e-6 * rod.length
-    assert np.abs(gpu["vel"]).max() < 1e-6
+    ref = oracle.step(rod, st0, 50)
+    _cmp(rod, gpu, ref, ROLL_TOL)
+    assert np.abs(gpu["pos"] - rod.pos).max() < STEP_TOL * rod.length
+    assert np.abs(gpu["vel"]).max() < 5e-3
     b.close()
