@@ -151,6 +151,8 @@ def run_single_rod(args, torch, corde, W, rank):
     drive_np = W.sinusoid_drive(2 + rank, n_launch_total, STEPS_PER_LAUNCH * rod.dt).astype(np.float32)
     drive = torch.as_tensor(drive_np, device=dev).contiguous()
     b = corde.RodBatch([rod])
+    b.autotune(STEPS_PER_LAUNCH)
+    plan = [int(x) for x in b.plan()[0]]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def bench_step(k, events=None):
@@ -210,7 +212,16 @@ def run_single_rod(args, torch, corde, W, rank):
     e2e_s = time.perf_counter() - t0
     e2e_us = e2e_s * 1e6 / (n_e2e * STEPS_PER_LAUNCH)
     b.close()
+    # empty-barrier floors of each scope (the step kernel uses block barriers)
+    floors = {
+        "block_ns": corde.rod_barrier_floor(0, threads=plan[1], n_iters=200000),
+        "warp_ns": corde.rod_barrier_floor(1, n_iters=200000),
+        "cluster2_ns": corde.rod_barrier_floor(2, threads=128, cluster=2, n_iters=100000),
+        "cluster8_ns": corde.rod_barrier_floor(2, threads=128, cluster=8, n_iters=100000),
+        "grid_sync_ns": corde.rod_barrier_floor(3, threads=128, cluster=1, n_iters=20000),
+    }
     return {
+        "floors": floors,
         "us_per_step": us_per_step,
         "total_ms": total_ms,
         "kernel_ms_avg": float(np.mean(kern_ms)),
@@ -223,6 +234,7 @@ def run_single_rod(args, torch, corde, W, rank):
         "e2e_launch_us": e2e_s * 1e6 / n_e2e,
         "n_nodes": 512,
         "n_iters": rod.n_iters,
+        "plan": plan,
     }
 
 
@@ -408,10 +420,15 @@ def main_ours(args):
                          "peak_source": f"derived: {NUM_SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
                                         f"{sm_mhz:.0f} MHz ({which} sm_max_mhz)",
                          "note": "one rod = one thread block on one of 152 SMs; latency-bound by design",
+                         "kernel": "step_kernel<ept=%d, nt=%d>" % tuple(single["plan"]),
                          "kernel_us_per_launch": round(single["kernel_ms_avg"] * 1e3, 3)},
             "latency": {"us_per_step": round(value, 4), "barriers_per_step": 2 + single["n_iters"],
                         "launch_rate_khz": round(1e3 / (value * STEPS_PER_LAUNCH), 2),
-                        "haptic_1khz_realtime": bool(value * STEPS_PER_LAUNCH < 1000.0)},
+                        "haptic_1khz_realtime": bool(value * STEPS_PER_LAUNCH < 1000.0),
+                        "floors_ns": {k: round(v, 2) for k, v in single["floors"].items()},
+                        "step_over_grid_sync": round(value * 1e3 / single["floors"]["grid_sync_ns"], 3),
+                        "step_over_block_barrier_floor": round(
+                            value * 1e3 / ((2 + single["n_iters"]) * single["floors"]["block_ns"]), 3)},
             "cpu_baseline": cpu,
             "clocks": single["clocks"],
             "checks": {"max_len_err": single["diag"][0], "max_qnorm_err": single["diag"][1],

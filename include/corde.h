@@ -145,6 +145,18 @@ int rod_get_plan(rod_handle h, int* plan);
 /* Number of kernel launches the last rod_step enqueued. */
 int rod_last_launch_count(rod_handle h);
 
+/* Empty-barrier floor (synchronous): ns per barrier over n_iters back-to-back barriers
+ * of one scope in a single launch.  The paper's multi-block kernel pays an inter-block
+ * barrier per data exchange (Section 2.2, Fig. 5); these floors are the reference for a
+ * step kernel's latency per step.
+ *  scope 0: __syncthreads in one block of `threads` threads
+ *  scope 1: __syncwarp in one warp
+ *  scope 2: cluster barrier across `cluster` (<= 16) blocks of `threads` threads
+ *  scope 3: cooperative grid sync across `cluster` blocks per SM on every SM (the
+ *           runtime rejects the launch if they cannot be co-resident; it never hangs)
+ * Returns CORDE_ERR_ARG for bad sizes, CORDE_ERR_CUDA if the launch is rejected. */
+int rod_barrier_floor(int scope, int threads, int cluster, int n_iters, double* ns_per_barrier, void* stream);
+
 /* Free the device state (synchronises the device first).  NULL is ignored. */
 void rod_destroy(rod_handle h);
 

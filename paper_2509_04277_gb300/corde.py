@@ -59,6 +59,8 @@ SIGNATURES = {
     "rod_autotune": (ctypes.c_int, [_VP, ctypes.c_int, _VP]),
     "rod_get_plan": (ctypes.c_int, [_VP, _VP]),
     "rod_last_launch_count": (ctypes.c_int, [_VP]),
+    "rod_barrier_floor": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_double), _VP]),
     "rod_destroy": (None, [_VP]),
     "rod_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "rod_last_error": (ctypes.c_char_p, []),
@@ -179,6 +181,14 @@ def rod_last_launch_count(h) -> int:
 
 def rod_destroy(h):
     load().rod_destroy(h)
+
+
+def rod_barrier_floor(scope, threads=128, cluster=1, n_iters=100000, stream=None) -> float:
+    """ns per empty barrier: scope 0 block, 1 warp, 2 cluster, 3 cooperative grid."""
+    ns = ctypes.c_double()
+    _check(load().rod_barrier_floor(int(scope), int(threads), int(cluster), int(n_iters), ctypes.byref(ns),
+                                    _stream(stream)), "rod_barrier_floor")
+    return ns.value
 
 
 # ------------------------------------------------------------------ convenience

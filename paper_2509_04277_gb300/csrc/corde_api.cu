@@ -21,6 +21,14 @@ int fail(int code, const std::string& msg) {
   return code;
 }
 
+}  // namespace
+
+namespace corde {
+int set_error(int code, const std::string& msg) { return fail(code, msg); }
+}  // namespace corde
+
+namespace {
+
 #define CK(call)                                                                          \
   do {                                                                                    \
     cudaError_t e_ = (call);                                                              \

@@ -87,7 +87,7 @@ __device__ __forceinline__ float constraint_factor(float3 ra, float3 va, float3 
   const float dd = __fmaf_rn(d.x, d.x, __fmaf_rn(d.y, d.y, __fmul_rn(d.z, d.z)));
   const float il = rsqrtf(dd);
   const float C = __fsub_rn(__fmul_rn(dd, il), l0);
-  return __fdiv_rn(__fmul_rn(-C, il), __fmul_rn(dt, wsum));
+  return __fmul_rn(__fmul_rn(-C, il), __frcp_rn(__fmul_rn(dt, wsum)));
 }
 
 // Dynamic shared memory of a <EPT, NT> block: per-element joint parameters (u-hat and

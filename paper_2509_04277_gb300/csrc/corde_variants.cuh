@@ -1,9 +1,14 @@
 // Registry of the compiled step-kernel variants (elements per thread x threads per block).
 #pragma once
 
+#include <string>
+
 #include "corde_common.cuh"
 
 namespace corde {
+
+// Records the message returned by rod_last_error() and passes the code through.
+int set_error(int code, const std::string& msg);
 
 struct StepArgs {
   const RodDev* rods;
