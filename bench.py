@@ -287,6 +287,49 @@ def run_batched(args, torch, corde, W, rank, world):
     }
 
 
+def run_adjoint(args, torch, corde, W, n_rods=1):
+    """Adjoint workload: 256-element rod(s), 200 steps at dt = 1e-4 s, checkpoints every
+    20 steps.  Times the plain forward (one persistent launch), the recorded rollout and
+    the reverse pass."""
+    stream = torch.cuda.current_stream()
+    rods = [W.adjoint_rod(256, seed=5 + k) for k in range(n_rods)]
+    b = corde.RodBatch(rods)
+    n_steps, ckpt = 200, 20
+    st = b.state_numpy()
+    targets = [W.tip_target(5 + k, n_steps, r.dt, r.pos[-1]) for k, r in enumerate(rods)]
+    g = torch.zeros((n_steps, b.n_elem, 4), dtype=torch.float32, device="cuda")
+
+    def timed(fn, reps=5):
+        ts = []
+        for _ in range(reps):
+            b.set_rod_states([b.rod_state(st, r) for r in range(n_rods)])
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts)), out
+
+    fwd_ms, _ = timed(lambda: b.step(n_steps))
+    fwd_launches = b.last_launch_count()
+    roll_ms, traj = timed(lambda: b.rollout(n_steps, ckpt))
+    for k, rod in enumerate(rods):
+        tip = int(b.offsets[k + 1]) - 1
+        g[:, tip, :3] = 2.0 * (traj[:, tip, :3] - torch.as_tensor(targets[k], dtype=torch.float32, device="cuda"))
+    adj_ms, grads = timed(lambda: b.adjoint(g))
+    finite = bool(all(torch.isfinite(v).all().item() for v in grads.values()))
+    b.close()
+    el_steps = sum(r.n_nodes for r in rods) * n_steps
+    return {"n_rods": n_rods, "n_nodes": 256, "n_steps": n_steps, "ckpt_every": ckpt,
+            "fwd_ms": round(fwd_ms, 4), "fwd_launches": fwd_launches, "rollout_recorded_ms": round(roll_ms, 4),
+            "adjoint_ms": round(adj_ms, 4), "adjoint_over_fwd": round(adj_ms / fwd_ms, 3),
+            "adjoint_over_recorded_rollout": round(adj_ms / roll_ms, 3),
+            "fwd_element_steps_per_s": el_steps / (fwd_ms * 1e-3),
+            "adjoint_element_steps_per_s": el_steps / (adj_ms * 1e-3), "gradients_finite": finite}
+
+
 def cpu_baseline_single(seconds=10.0):
     """The FP64 oracle as it stands, one host core, on the 512-element guidewire."""
     import oracle
@@ -376,6 +419,9 @@ def main_ours(args):
     corde.load()
     single = run_single_rod(args, torch, corde, W, rank)
     batched = run_batched(args, torch, corde, W, rank, world) if not args.skip_batched else None
+    adjoint = None
+    if not args.skip_adjoint:
+        adjoint = {"single": run_adjoint(args, torch, corde, W, 1), "batched": run_adjoint(args, torch, corde, W, 256)}
     value = _max_over_ranks(torch, single["us_per_step"])
     e2e = _max_over_ranks(torch, single["e2e_us"])
     out = None
@@ -452,6 +498,8 @@ def main_ours(args):
                                  "frac": batched["bytes_per_launch"] / sec / 1e9 / bw},
                 "cpu_baseline": cpu_baseline_batched(args.cpu_seconds) if not args.skip_cpu_batched else None,
             }
+        if adjoint is not None:
+            out["adjoint"] = adjoint
         print(json.dumps(out), flush=True)
     _barrier(torch)
     if world > 1:
@@ -512,6 +560,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--skip-cpu-batched", action="store_true")
+    ap.add_argument("--skip-adjoint", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

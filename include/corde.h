@@ -145,6 +145,29 @@ int rod_get_plan(rod_handle h, int* plan);
 /* Number of kernel launches the last rod_step enqueued. */
 int rod_last_launch_count(rod_handle h);
 
+/* Forward rollout recorded for the adjoint: n_steps time steps with the drive last given
+ * to rod_set_input held constant, storing the state every ckpt_every steps (checkpoints
+ * kept by the handle) and, if pos_traj is not NULL, the node positions after every step
+ * into pos_traj [n_steps][n_elements][4] (device memory; .w = inverse mass).  When every
+ * rod has at most 512 nodes the launches use the adjoint's kernel layout.  The handle's
+ * state advances to step n_steps.  (Not in the paper: this and rod_adjoint provide the
+ * gradients of a loss on the trajectory.) */
+int rod_rollout(rod_handle h, int n_steps, int ckpt_every, float* pos_traj, void* stream);
+
+/* Reverse-mode gradient of a loss L(trajectory) through the last rod_rollout (hand-written
+ * adjoint of the step of Fig. 5, checkpoint-and-recompute).  Input dL_dpos_traj
+ * [n_steps][n_elements][4] device array: dL/d(position after step t) in .xyz (or NULL for
+ * zero).  Outputs, [n_elements][4] device arrays, any may be NULL:
+ *  dL_dK      per-joint stiffness (K1, K2, K3, 0) of joint i (frames i, i+1)
+ *  dL_duhat   per-joint intrinsic Darboux vector (x, y, z, 0)
+ *  dL_dvel0, dL_dpos0   initial node velocities / positions (xyz, 0)
+ *  dL_dquat0  initial frames (x, y, z, w components), dL_domega0 initial body angular velocities
+ * Rods of at most 512 nodes; shared memory bounds the constraint iterations (about 20
+ * for 256-node rods).  The material, drive and state set between rod_rollout and
+ * rod_adjoint must not change.  CORDE_ERR_UNSUPPORTED when the limits are exceeded. */
+int rod_adjoint(rod_handle h, const float* dL_dpos_traj, float* dL_dK, float* dL_duhat, float* dL_dvel0,
+                float* dL_dpos0, float* dL_dquat0, float* dL_domega0, void* stream);
+
 /* Empty-barrier floor (synchronous): ns per barrier over n_iters back-to-back barriers
  * of one scope in a single launch.  The paper's multi-block kernel pays an inter-block
  * barrier per data exchange (Section 2.2, Fig. 5); these floors are the reference for a

@@ -1,0 +1,30 @@
+"""``torch.autograd.Function`` over the rod rollout and its hand-written CUDA adjoint.
+
+``RodRollout.apply(batch, n_steps, ckpt_every, K, uhat, vel0, pos0)`` sets the per-joint
+stiffness ``K`` and intrinsic Darboux vectors ``uhat`` ([n_elem, 4] device tensors, the
+per-joint layout of ``rod_set_material``) and the initial velocities / positions
+([n_elem, 4]), runs ``rod_rollout`` and returns the node trajectory [n_steps, n_elem, 4].
+The backward pass calls ``rod_adjoint``.  The frames and angular velocities start from the
+batch's state at the time of the call.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import corde
+
+
+class RodRollout(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, batch, n_steps, ckpt_every, K, uhat, vel0, pos0):
+        mat = torch.cat([K.detach(), uhat.detach()], dim=1).contiguous()
+        corde.rod_set_material(batch.handle, mat)
+        corde.rod_set_state(batch.handle, pos4=pos0.detach().contiguous(), vel4=vel0.detach().contiguous())
+        traj = batch.rollout(int(n_steps), int(ckpt_every))
+        ctx.batch = batch
+        return traj
+
+    @staticmethod
+    def backward(ctx, g_traj):
+        g = ctx.batch.adjoint(g_traj.contiguous())
+        return None, None, None, g["K"], g["uhat"], g["vel0"], g["pos0"]

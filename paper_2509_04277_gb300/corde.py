@@ -59,6 +59,8 @@ SIGNATURES = {
     "rod_autotune": (ctypes.c_int, [_VP, ctypes.c_int, _VP]),
     "rod_get_plan": (ctypes.c_int, [_VP, _VP]),
     "rod_last_launch_count": (ctypes.c_int, [_VP]),
+    "rod_rollout": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP, _VP]),
+    "rod_adjoint": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "rod_barrier_floor": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_double), _VP]),
     "rod_destroy": (None, [_VP]),
@@ -181,6 +183,16 @@ def rod_last_launch_count(h) -> int:
 
 def rod_destroy(h):
     load().rod_destroy(h)
+
+
+def rod_rollout(h, n_steps, ckpt_every, pos_traj=None, stream=None):
+    _check(load().rod_rollout(h, int(n_steps), int(ckpt_every), _ptr(pos_traj), _stream(stream)), "rod_rollout")
+
+
+def rod_adjoint(h, dL_dpos_traj=None, dL_dK=None, dL_duhat=None, dL_dvel0=None, dL_dpos0=None, dL_dquat0=None,
+                dL_domega0=None, stream=None):
+    _check(load().rod_adjoint(h, _ptr(dL_dpos_traj), _ptr(dL_dK), _ptr(dL_duhat), _ptr(dL_dvel0), _ptr(dL_dpos0),
+                              _ptr(dL_dquat0), _ptr(dL_domega0), _stream(stream)), "rod_adjoint")
 
 
 def rod_barrier_floor(scope, threads=128, cluster=1, n_iters=100000, stream=None) -> float:
@@ -316,3 +328,23 @@ class RodBatch:
 
     def last_launch_count(self) -> int:
         return rod_last_launch_count(self.handle)
+
+    def rollout(self, n_steps, ckpt_every, record=True, stream=None):
+        """Recorded forward rollout; returns the position trajectory (torch, device,
+        [n_steps, n_elem, 4]) or None."""
+        import torch
+
+        traj = torch.empty((n_steps, self.n_elem, 4), dtype=torch.float32, device="cuda") if record else None
+        rod_rollout(self.handle, n_steps, ckpt_every, traj, stream)
+        return traj
+
+    def adjoint(self, dL_dpos_traj, stream=None) -> dict:
+        """Gradients of the loss through the last rollout (torch device tensors [n_elem, 4])."""
+        import torch
+
+        out = {k: torch.zeros((self.n_elem, 4), dtype=torch.float32, device="cuda")
+               for k in ("K", "uhat", "vel0", "pos0", "quat0", "omega0")}
+        g = None if dL_dpos_traj is None else dL_dpos_traj.contiguous()
+        rod_adjoint(self.handle, g, out["K"], out["uhat"], out["vel0"], out["pos0"], out["quat0"], out["omega0"],
+                    stream)
+        return out

@@ -1,0 +1,439 @@
+// Hand-written adjoint of the multi-step rollout (reverse-mode differentiation through
+// the step of Fig. 5), with checkpoint-and-recompute.
+//
+// One thread block per rod, two elements per thread (the step kernel's <2, NT> layout).
+// The forward rollout (rod_rollout) stores a checkpoint every K steps.  The reverse
+// kernel walks the segments backwards: it recomputes the K states of a segment into
+// scratch memory, then for each step (last to first) recomputes that step once more with
+// the velocities before every constraint half-sweep kept in shared memory, and applies
+// the transposed Jacobian of the step:
+//   r' = r + dt v2, q' = normalize(q + dt/2 q (x) (0, omega1))       (position update)
+//   v2 = P(r, v1): 2 n_iters half-sweeps of distance impulses          (constraints)
+//   v1 = damp (v + dt (w F + g)), omega1 = damp (omega + dt J^-1 (tau - omega x J omega))
+//   F, tau = elastic forces / torques of Eq. 2, 3, 8 (second derivatives of the energies)
+// Gradients flow to the initial positions and velocities and, accumulated over all
+// steps, to the per-joint stiffness (K1, K2, K3) and intrinsic Darboux vectors u-hat.
+#include "corde_step.cuh"
+#include "corde_variants.cuh"
+
+namespace corde {
+namespace {
+
+__device__ __forceinline__ float4 qmul4(float4 a, float4 b) {
+  return make_float4(a.w * b.x + a.x * b.w + a.y * b.z - a.z * b.y, a.w * b.y - a.x * b.z + a.y * b.w + a.z * b.x,
+                     a.w * b.z + a.x * b.y - a.y * b.x + a.z * b.w, a.w * b.w - a.x * b.x - a.y * b.y - a.z * b.z);
+}
+__device__ __forceinline__ float4 pure(float3 v) { return make_float4(v.x, v.y, v.z, 0.f); }
+__device__ __forceinline__ float4 add4(float4 a, float4 b) { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
+__device__ __forceinline__ float4 scale4(float s, float4 a) { return make_float4(s * a.x, s * a.y, s * a.z, s * a.w); }
+__device__ __forceinline__ float dot4(float4 a, float4 b) { return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w; }
+__device__ __forceinline__ float4 zero4() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+
+// VJP of joint_torques: given the adjoints of (ta, tb), the adjoints of qa, qb, K, u-hat.
+__device__ __forceinline__ void joint_torques_vjp(float4 qa, float4 qb, float4 uh, float4 K, float two_over_l,
+                                                  float3 ta_bar, float3 tb_bar, float4& qa_bar, float4& qb_bar,
+                                                  float3& K_bar, float3& uh_bar) {
+  const float dw = dot4(qa, qb);
+  const float3 dv = im_conj_mul(qa, qb);
+  const float3 u = two_over_l * dv;
+  const float3 du = f3(u.x - uh.x, u.y - uh.y, u.z - uh.z);
+  const float3 m = f3(2.f * K.x * du.x, 2.f * K.y * du.y, 2.f * K.z * du.z);
+  const float3 cv_bar = 0.5f * (ta_bar + tb_bar);
+  const float3 diff = ta_bar - tb_bar;
+  const float dw_bar = 0.5f * dot3(m, diff);
+  const float3 m_bar = 0.5f * dw * diff + cross3(cv_bar, dv);
+  float3 dv_bar = cross3(m, cv_bar);
+  K_bar = f3(2.f * du.x * m_bar.x, 2.f * du.y * m_bar.y, 2.f * du.z * m_bar.z);
+  const float3 u_bar = f3(2.f * K.x * m_bar.x, 2.f * K.y * m_bar.y, 2.f * K.z * m_bar.z);
+  uh_bar = -u_bar;
+  dv_bar += two_over_l * u_bar;
+  // dv = Im(conj(qa) (x) qb): d/dqb = qa (x) (0, .), d/dqa = -qb (x) (0, .); dw = qa . qb
+  qa_bar = add4(scale4(dw_bar, qb), scale4(-1.f, qmul4(qb, pure(dv_bar))));
+  qb_bar = add4(scale4(dw_bar, qa), qmul4(qa, pure(dv_bar)));
+}
+
+// VJP of rotate_inv(q, v) = v + 2 u x (u x v - w v) (u, w: vector and real part of q).
+__device__ __forceinline__ void rotate_inv_vjp(float4 q, float3 v, float3 o_bar, float3& v_bar, float4& q_bar) {
+  const float3 u = f3(q.x, q.y, q.z);
+  const float3 s = cross3(u, v) - q.w * v;
+  const float3 z_bar = 2.f * o_bar;
+  float3 u_bar = cross3(s, z_bar);
+  const float3 s_bar = cross3(z_bar, u);
+  u_bar += cross3(v, s_bar);
+  v_bar = o_bar + cross3(s_bar, u) - q.w * s_bar;
+  q_bar = make_float4(u_bar.x, u_bar.y, u_bar.z, -dot3(v, s_bar));
+}
+
+// VJP of director3.
+__device__ __forceinline__ float4 director3_vjp(float4 q, float3 a) {
+  return make_float4(2.f * (q.z * a.x - q.w * a.y) - 4.f * q.x * a.z, 2.f * (q.w * a.x + q.z * a.y) - 4.f * q.y * a.z,
+                     2.f * (q.x * a.x + q.y * a.y), 2.f * (q.y * a.x - q.x * a.y));
+}
+
+// VJP of segment_forces.
+__device__ __forceinline__ void segment_forces_vjp(float3 ra, float3 rb, float4 q, const RodDev& R, bool extensible,
+                                                   float3 fa_bar, float3 fb_bar, float3 tq_bar, float3& ra_bar,
+                                                   float3& rb_bar, float4& q_bar) {
+  const float3 e = rb - ra;
+  const float ee = dot3(e, e);
+  const float il = rsqrtf(ee);
+  const float3 t = il * e;
+  const float3 d3 = director3(q);
+  const float c = dot3(t, d3);
+  const float k = R.lKp;
+  const float3 f_bar = fb_bar - fa_bar;
+  const float3 g = d3 - c * t;
+  float il_bar = k * dot3(g, f_bar);
+  float3 d3_bar = (k * il) * f_bar;
+  const float c_bar = -k * il * dot3(t, f_bar);
+  float3 t_bar = (-k * il * c) * f_bar;
+  t_bar += c_bar * d3;
+  d3_bar += c_bar * t;
+  float ee_bar = 0.f;
+  if (extensible) {
+    const float len = ee * il;
+    const float3 fs_bar = fa_bar - fb_bar;
+    t_bar += (R.Ks * (len * R.inv_l0 - 1.f)) * fs_bar;
+    const float len_bar = R.Ks * R.inv_l0 * dot3(t, fs_bar);
+    ee_bar += il * len_bar;
+    il_bar += ee * len_bar;
+  }
+  // torque l0 Kp (-t_b.y, t_b.x, 0), t_b = R(q)^T t
+  const float3 tb_bar = f3(k * tq_bar.y, -k * tq_bar.x, 0.f);
+  float3 t_bar2;
+  float4 q_bar_rot;
+  rotate_inv_vjp(q, t, tb_bar, t_bar2, q_bar_rot);
+  t_bar += t_bar2;
+  q_bar = add4(q_bar_rot, director3_vjp(q, d3_bar));
+  // t = il e, il = ee^(-1/2), ee = e . e
+  float3 e_bar = il * t_bar;
+  il_bar += dot3(e, t_bar);
+  ee_bar += -0.5f * il * il * il * il_bar;
+  e_bar += (2.f * ee_bar) * e;
+  ra_bar = -e_bar;
+  rb_bar = e_bar;
+}
+
+// Adjoint of one distance constraint (pre-update velocities va, vb): with
+// g = s d and dg/dd = M = -(1/(dt W)) [(1 - l0/L) I + (l0/L) n n^T], returns
+// d_bar = M (-wa va_bar + wb vb_bar); the caller applies va_bar -= dt d_bar,
+// vb_bar += dt d_bar, ra_bar -= d_bar, rb_bar += d_bar.
+__device__ __forceinline__ float3 constraint_vjp(float3 ra, float3 va, float3 rb, float3 vb, float wa, float wb,
+                                                 float3 va_bar, float3 vb_bar, float l0, float dt) {
+  const float3 d = f3(__fmaf_rn(dt, __fsub_rn(vb.x, va.x), __fsub_rn(rb.x, ra.x)),
+                      __fmaf_rn(dt, __fsub_rn(vb.y, va.y), __fsub_rn(rb.y, ra.y)),
+                      __fmaf_rn(dt, __fsub_rn(vb.z, va.z), __fsub_rn(rb.z, ra.z)));
+  const float dd = __fmaf_rn(d.x, d.x, __fmaf_rn(d.y, d.y, __fmul_rn(d.z, d.z)));
+  const float il = rsqrtf(dd);
+  const float3 n = il * d;
+  const float3 g_bar = f3(__fmaf_rn(wb, vb_bar.x, -__fmul_rn(wa, va_bar.x)),
+                          __fmaf_rn(wb, vb_bar.y, -__fmul_rn(wa, va_bar.y)),
+                          __fmaf_rn(wb, vb_bar.z, -__fmul_rn(wa, va_bar.z)));
+  const float rho = l0 * il;
+  const float inv = -__frcp_rn(__fmul_rn(dt, wa + wb));
+  return inv * ((1.f - rho) * g_bar + (rho * dot3(n, g_bar)) * n);
+}
+
+template <int EPT, int NT>
+__device__ __forceinline__ void reverse_step(const RodDev& R, const int t, const float3 (&r)[EPT],
+                                             const float4 (&q)[EPT], const float3 (&om)[EPT], const float (&w)[EPT],
+                                             const float3 (&om1)[EPT], const float4 (&qo)[EPT],
+                                             const StepNeighbours& nb, const float4* par_u, const float4* par_k,
+                                             float4* halo, int& xc, const float4* sweep_v, float3 (&rb)[EPT],
+                                             float3 (&vb)[EPT], float4 (&qb)[EPT], float3 (&ob)[EPT],
+                                             float3 (&Kb)[EPT], float3 (&ub)[EPT]) {
+  const int e0 = t * EPT;
+  const int n = R.n;
+  const bool inext = (R.flags & F_INEXT) != 0;
+  const bool clamp = (R.flags & F_CLAMP) != 0;
+  const float dt = R.dt;
+  const float half_dt = 0.5f * dt;
+
+  // ---- position update: r' = r + dt v2, q' = normalize(q + dt/2 q (x) (0, omega1))
+  float3 vb2[EPT], ob1[EPT];
+  float4 qbi[EPT];
+#pragma unroll
+  for (int e = 0; e < EPT; ++e) {
+    const int i = e0 + e;
+    vb2[e] = vb[e] + dt * rb[e];
+    ob1[e] = ob[e];
+    qbi[e] = zero4();
+    if (i <= n - 2) {
+      const float4 a = q[e];
+      const float3 o = om1[e];
+      const float dx = a.w * o.x + a.y * o.z - a.z * o.y;
+      const float dy = a.w * o.y + a.z * o.x - a.x * o.z;
+      const float dz = a.w * o.z + a.x * o.y - a.y * o.x;
+      const float dwq = -(a.x * o.x + a.y * o.y + a.z * o.z);
+      const float4 p = make_float4(a.x + half_dt * dx, a.y + half_dt * dy, a.z + half_dt * dz, a.w + half_dt * dwq);
+      const float inv = rsqrtf(dot4(p, p));
+      const float4 pb = scale4(inv, add4(qb[e], scale4(-dot4(qo[e], qb[e]), qo[e])));
+      qbi[e] = add4(pb, scale4(half_dt, qmul4(pb, make_float4(-o.x, -o.y, -o.z, 0.f))));
+      ob1[e] += half_dt * im_conj_mul(a, pb);
+    }
+  }
+
+  // ---- constraint half-sweeps in reverse order (odd, then even, last iteration first)
+  if (inext) {
+    for (int it = R.n_iters - 1; it >= 0; --it) {
+      float4* hb = halo + (xc & 1) * kHaloSlots * NT;
+      ++xc;
+      hb[t] = make_float4(vb2[0].x, vb2[0].y, vb2[0].z, 0.f);
+      hb[NT + t] = make_float4(vb2[EPT - 1].x, vb2[EPT - 1].y, vb2[EPT - 1].z, 0.f);
+      block_sync<NT>();
+      const float4* sv = sweep_v + (2 * it + 1) * EPT * NT;
+#pragma unroll
+      for (int k = 0; k + 1 < EPT / 2; ++k) {
+        const int a = 2 * k + 1, b = 2 * k + 2;
+        if (e0 + b <= n - 1 && w[a] + w[b] > 0.f) {
+          const float3 db = constraint_vjp(r[a], f3(sv[a * NT + t]), r[b], f3(sv[b * NT + t]), w[a], w[b], vb2[a],
+                                           vb2[b], R.l0, dt);
+          vb2[a] -= dt * db;
+          vb2[b] += dt * db;
+          rb[a] -= db;
+          rb[b] += db;
+        }
+      }
+      if (t + 1 < NT && e0 + EPT <= n - 1 && w[EPT - 1] + nb.w_next > 0.f) {
+        const float3 db = constraint_vjp(r[EPT - 1], f3(sv[(EPT - 1) * NT + t]), nb.r_next, f3(sv[t + 1]),
+                                         w[EPT - 1], nb.w_next, vb2[EPT - 1], f3(hb[t + 1]), R.l0, dt);
+        vb2[EPT - 1] -= dt * db;
+        rb[EPT - 1] -= db;
+      }
+      if (t > 0 && e0 <= n - 1 && nb.w_prev + w[0] > 0.f) {
+        const float3 db = constraint_vjp(nb.r_prev, f3(sv[(EPT - 1) * NT + t - 1]), r[0], f3(sv[t]), nb.w_prev,
+                                         w[0], f3(hb[NT + t - 1]), vb2[0], R.l0, dt);
+        vb2[0] += dt * db;
+        rb[0] += db;
+      }
+      sv = sweep_v + (2 * it) * EPT * NT;
+#pragma unroll
+      for (int k = 0; k < EPT / 2; ++k) {
+        const int a = 2 * k, b = 2 * k + 1;
+        if (e0 + b <= n - 1 && w[a] + w[b] > 0.f) {
+          const float3 db = constraint_vjp(r[a], f3(sv[a * NT + t]), r[b], f3(sv[b * NT + t]), w[a], w[b], vb2[a],
+                                           vb2[b], R.l0, dt);
+          vb2[a] -= dt * db;
+          vb2[b] += dt * db;
+          rb[a] -= db;
+          rb[b] += db;
+        }
+      }
+    }
+  }
+
+  // ---- force integration: v1 = damp (v + dt (w F + g)), omega1 = damp (...)
+  float3 Fb[EPT], Tb[EPT];
+#pragma unroll
+  for (int e = 0; e < EPT; ++e) {
+    const int i = e0 + e;
+    if (w[e] > 0.f) {
+      Fb[e] = (R.damp * dt * w[e]) * vb2[e];
+      vb[e] = R.damp * vb2[e];
+    } else {
+      Fb[e] = zero3();
+      vb[e] = zero3();
+    }
+    const bool frame_dynamic = (i <= n - 2) && !(clamp && i == 0);
+    if (frame_dynamic) {
+      const float3 b = f3(R.Jinv1 * ob1[e].x, R.Jinv1 * ob1[e].y, R.Jinv3 * ob1[e].z);
+      Tb[e] = (R.damp * dt) * b;
+      const float3 o = om[e];
+      const float3 Jw = f3(R.J1 * o.x, R.J1 * o.y, R.J3 * o.z);
+      const float3 oxb = cross3(o, b);
+      const float3 Joxb = f3(R.J1 * oxb.x, R.J1 * oxb.y, R.J3 * oxb.z);
+      ob[e] = R.damp * (ob1[e] + dt * (Joxb - cross3(Jw, b)));
+    } else {
+      Tb[e] = zero3();
+      ob[e] = zero3();
+    }
+  }
+
+  // ---- elastic forces and torques (transposed)
+  float4* hb = halo + (xc & 1) * kHaloSlots * NT;
+  ++xc;
+  hb[t] = make_float4(Fb[0].x, Fb[0].y, Fb[0].z, 0.f);
+  hb[NT + t] = make_float4(Tb[0].x, Tb[0].y, Tb[0].z, 0.f);
+  block_sync<NT>();
+  float3 Fb_next = zero3(), Tb_next = zero3();
+  if (t + 1 < NT) {
+    Fb_next = f3(hb[t + 1]);
+    Tb_next = f3(hb[NT + t + 1]);
+  }
+  float3 r_carry = zero3();
+  float4 q_carry = zero4();
+#pragma unroll
+  for (int e = 0; e < EPT; ++e) {
+    const int j = e0 + e;
+    const float4 qn = (e + 1 < EPT) ? q[(e + 1) % EPT] : nb.q_next;
+    const float3 rn = (e + 1 < EPT) ? r[(e + 1) % EPT] : nb.r_next;
+    if (j <= n - 3) {
+      const float3 tbar_b = (e + 1 < EPT) ? Tb[(e + 1) % EPT] : Tb_next;
+      float4 qa_bar, qn_bar;
+      float3 K_bar, uh_bar;
+      joint_torques_vjp(q[e], qn, par_u[e * NT + t], par_k[e * NT + t], R.two_over_l, Tb[e], tbar_b, qa_bar, qn_bar,
+                        K_bar, uh_bar);
+      qbi[e] = add4(qbi[e], qa_bar);
+      if (e + 1 < EPT) {
+        qbi[(e + 1) % EPT] = add4(qbi[(e + 1) % EPT], qn_bar);
+      } else {
+        q_carry = qn_bar;
+      }
+      Kb[e] += K_bar;
+      ub[e] += uh_bar;
+    }
+    if (j <= n - 2) {
+      const float3 fbar_b = (e + 1 < EPT) ? Fb[(e + 1) % EPT] : Fb_next;
+      float3 ra_bar, rn_bar;
+      float4 q_bar;
+      segment_forces_vjp(r[e], rn, q[e], R, !inext, Fb[e], fbar_b, Tb[e], ra_bar, rn_bar, q_bar);
+      rb[e] += ra_bar;
+      if (e + 1 < EPT) {
+        rb[(e + 1) % EPT] += rn_bar;
+      } else {
+        r_carry = rn_bar;
+      }
+      qbi[e] = add4(qbi[e], q_bar);
+    }
+  }
+  hb = halo + (xc & 1) * kHaloSlots * NT;
+  ++xc;
+  hb[t] = make_float4(r_carry.x, r_carry.y, r_carry.z, 0.f);
+  hb[NT + t] = q_carry;
+  block_sync<NT>();
+  if (t > 0) {
+    rb[0] += f3(hb[t - 1]);
+    qbi[0] = add4(qbi[0], hb[NT + t - 1]);
+  }
+#pragma unroll
+  for (int e = 0; e < EPT; ++e) qb[e] = qbi[e];
+}
+
+// Reverse pass over the whole rollout of one rod per block.
+template <int NT>
+__global__ void __launch_bounds__(NT)
+adjoint_kernel(AdjointArgs a) {
+  constexpr int EPT = 2;
+  extern __shared__ float4 smem[];
+  float4* par_u = smem;
+  float4* par_k = smem + EPT * NT;
+  float4* halo = smem + 2 * EPT * NT;
+  float4* sweep_v = halo + 2 * kHaloSlots * NT;
+
+  const int rid = a.work[blockIdx.x];
+  const RodDev R = a.rods[rid];
+  const int t = threadIdx.x;
+  const int e0 = t * EPT;
+  const int64_t E = a.n_elem;
+  float3 v_drive = zero3(), w_drive = zero3();
+  if (a.drive != nullptr) {
+    v_drive = f3(a.drive[2 * rid]);
+    w_drive = f3(a.drive[2 * rid + 1]);
+  }
+
+  float3 r[EPT], v[EPT], om[EPT];
+  float4 q[EPT];
+  float w[EPT];
+  float3 rb[EPT], vb[EPT], ob[EPT], Kb[EPT], ub[EPT];
+  float4 qb[EPT];
+#pragma unroll
+  for (int e = 0; e < EPT; ++e) {
+    rb[e] = vb[e] = ob[e] = Kb[e] = ub[e] = zero3();
+    qb[e] = zero4();
+  }
+  int xc = 0;
+  const int n_seg = (a.n_steps + a.ckpt_every - 1) / a.ckpt_every;
+  bool params_loaded = false;
+  for (int seg = n_seg - 1; seg >= 0; --seg) {
+    const int t0 = seg * a.ckpt_every;
+    const int cnt = min(a.ckpt_every, a.n_steps - t0);
+    const float4* ck = a.ckpt + (int64_t)seg * 4 * E;
+    load_rod<EPT, NT>(R, t, ck, ck + E, ck + 2 * E, ck + 3 * E, a.u4, a.k4, r, v, q, om, w,
+                      params_loaded ? nullptr : par_u, par_k);
+    params_loaded = true;
+    // recompute the segment's states into scratch
+    for (int s = 0; s < cnt; ++s) {
+      float4* st = a.seg_states + (int64_t)s * 4 * E + R.off;
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) {
+        if (e0 + e < R.n) {
+          st[e0 + e] = make_float4(r[e].x, r[e].y, r[e].z, w[e]);
+          st[E + e0 + e] = make_float4(v[e].x, v[e].y, v[e].z, 0.f);
+          st[2 * E + e0 + e] = q[e];
+          st[3 * E + e0 + e] = make_float4(om[e].x, om[e].y, om[e].z, 0.f);
+        }
+      }
+      if (s + 1 < cnt)
+        step_body<EPT, NT, false>(R, t, r, v, q, om, w, par_u, par_k, halo, xc, v_drive, w_drive, nullptr, nullptr);
+    }
+    // reverse the segment's steps
+    for (int s = cnt - 1; s >= 0; --s) {
+      const float4* st = a.seg_states + (int64_t)s * 4 * E + R.off;
+      float3 r_in[EPT], om_in[EPT];
+      float4 q_in[EPT];
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) {
+        if (e0 + e < R.n) {
+          r[e] = f3(st[e0 + e]);
+          v[e] = f3(st[E + e0 + e]);
+          q[e] = st[2 * E + e0 + e];
+          om[e] = f3(st[3 * E + e0 + e]);
+        }
+        r_in[e] = r[e];
+        q_in[e] = q[e];
+        om_in[e] = om[e];
+      }
+      StepNeighbours nb;
+      step_body<EPT, NT, true>(R, t, r, v, q, om, w, par_u, par_k, halo, xc, v_drive, w_drive, sweep_v, &nb);
+      // loss gradient with respect to the positions after this step
+      if (a.dLdpos != nullptr) {
+        const float4* g = a.dLdpos + (int64_t)(t0 + s) * E + R.off;
+#pragma unroll
+        for (int e = 0; e < EPT; ++e)
+          if (e0 + e < R.n) rb[e] += f3(g[e0 + e]);
+      }
+      reverse_step<EPT, NT>(R, t, r_in, q_in, om_in, w, om, q, nb, par_u, par_k, halo, xc, sweep_v, rb, vb, qb, ob,
+                            Kb, ub);
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < EPT; ++e) {
+    const int i = e0 + e;
+    if (i < R.n) {
+      const int64_t o = R.off + i;
+      if (a.dpos0) a.dpos0[o] = make_float4(rb[e].x, rb[e].y, rb[e].z, 0.f);
+      if (a.dvel0) a.dvel0[o] = make_float4(vb[e].x, vb[e].y, vb[e].z, 0.f);
+      if (a.dquat0) a.dquat0[o] = qb[e];
+      if (a.domega0) a.domega0[o] = make_float4(ob[e].x, ob[e].y, ob[e].z, 0.f);
+      if (a.dK) a.dK[o] = make_float4(Kb[e].x, Kb[e].y, Kb[e].z, 0.f);
+      if (a.duhat) a.duhat[o] = make_float4(ub[e].x, ub[e].y, ub[e].z, 0.f);
+    }
+  }
+}
+
+template <int NT>
+cudaError_t launch_adjoint_nt(const AdjointArgs& a, int n_blocks, int smem, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(adjoint_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  adjoint_kernel<NT><<<n_blocks, NT, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int adjoint_smem_bytes(int nt, int n_iters) {
+  const int ept = 2;
+  return (2 * ept * nt + 2 * kHaloSlots * nt + 2 * (n_iters > 0 ? n_iters : 1) * ept * nt) * (int)sizeof(float4);
+}
+
+cudaError_t launch_adjoint(int nt, const AdjointArgs& a, int n_blocks, int smem, cudaStream_t s) {
+  switch (nt) {
+    case 32: return launch_adjoint_nt<32>(a, n_blocks, smem, s);
+    case 64: return launch_adjoint_nt<64>(a, n_blocks, smem, s);
+    case 128: return launch_adjoint_nt<128>(a, n_blocks, smem, s);
+    case 256: return launch_adjoint_nt<256>(a, n_blocks, smem, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace corde

@@ -93,6 +93,7 @@ struct corde_rods {
   int64_t n_elem = 0;
   std::vector<int> n_nodes, off;
   std::vector<int> flags;
+  std::vector<int> n_iters;
   std::vector<double> derived;  // [n_rods][16]
   RodDev* d_rods = nullptr;
   double* d_derived = nullptr;
@@ -102,6 +103,13 @@ struct corde_rods {
   std::vector<int> plan;  // variant index per rod
   std::vector<Bin> bins;
   int last_launches = 0;
+  // rollout / adjoint
+  float4* d_ckpt = nullptr;  // [n_ckpt][4][E]
+  size_t ckpt_cap = 0;       // float4 entries
+  float4* d_seg = nullptr;   // [K][4][E] scratch of the reverse pass
+  size_t seg_cap = 0;
+  int ro_steps = 0, ro_every = 0;
+  std::vector<Bin> adj_bins;  // variant = threads per block
 };
 
 namespace {
@@ -306,7 +314,8 @@ int build_bins(rod_handle h) {
   return CORDE_OK;
 }
 
-int launch_bins(rod_handle h, const std::vector<Bin>& bins, int n_steps, const float4* drive, cudaStream_t s) {
+int launch_bins(rod_handle h, const std::vector<Bin>& bins, int n_steps, const float4* drive, cudaStream_t s,
+                float4* traj = nullptr) {
   StepArgs a;
   a.rods = h->d_rods;
   a.x4 = h->d_x;
@@ -317,6 +326,8 @@ int launch_bins(rod_handle h, const std::vector<Bin>& bins, int n_steps, const f
   a.k4 = h->d_k;
   a.drive = drive;
   a.n_steps = n_steps;
+  a.traj = traj;
+  a.n_elem = h->n_elem;
   int launches = 0;
   for (const auto& b : bins) {
     a.work = b.d_work;
@@ -328,6 +339,35 @@ int launch_bins(rod_handle h, const std::vector<Bin>& bins, int n_steps, const f
     ++launches;
   }
   h->last_launches = launches;
+  return CORDE_OK;
+}
+
+// True if the kernel may dereference p (device, managed or mapped pinned host memory);
+// *dev receives the device address.
+bool device_accessible(const void* p, const void** dev) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) {
+    *dev = p;
+    return reinterpret_cast<uintptr_t>(p) % 16 == 0;
+  }
+  if (at.type == cudaMemoryTypeHost && at.devicePointer != nullptr) {
+    *dev = at.devicePointer;
+    return reinterpret_cast<uintptr_t>(at.devicePointer) % 16 == 0;
+  }
+  return false;
+}
+
+int ensure_capacity(float4** buf, size_t* cap, size_t need) {
+  if (*cap >= need) return CORDE_OK;
+  cudaFree(*buf);
+  *buf = nullptr;
+  *cap = 0;
+  CK(cudaMalloc(buf, need * sizeof(float4)));
+  *cap = need;
   return CORDE_OK;
 }
 
@@ -401,6 +441,8 @@ int rod_create(int n_rods, const RodParams* params, const float* pos, const floa
   h->n_elem = E;
   h->n_nodes = nn;
   h->off = off;
+  h->n_iters.resize(n_rods);
+  for (int r = 0; r < n_rods; ++r) h->n_iters[r] = params[r].inextensible ? params[r].n_iters : 0;
   const int64_t F = E - n_rods, J = E - 2 * (int64_t)n_rods;
   std::vector<int> elem_rod(E);
   for (int r = 0; r < n_rods; ++r)
@@ -482,19 +524,10 @@ int rod_step(rod_handle h, int n_steps, const float* drive, void* stream) {
   const float4* d = h->d_drive;
   if (drive) {
     // The kernel dereferences `drive`: accept device, managed or mapped pinned host memory.
-    cudaPointerAttributes at;
-    if (cudaPointerGetAttributes(&at, drive) != cudaSuccess) {
-      cudaGetLastError();
-      return fail(CORDE_ERR_ARG, "drive is not a device-accessible pointer");
-    }
-    if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) {
-      d = reinterpret_cast<const float4*>(drive);
-    } else if (at.type == cudaMemoryTypeHost && at.devicePointer != nullptr) {
-      d = reinterpret_cast<const float4*>(at.devicePointer);
-    } else {
-      return fail(CORDE_ERR_ARG, "drive must be device, managed or mapped pinned host memory");
-    }
-    if (reinterpret_cast<uintptr_t>(d) % 16 != 0) return fail(CORDE_ERR_ARG, "drive must be 16-byte aligned");
+    const void* dp = nullptr;
+    if (!device_accessible(drive, &dp))
+      return fail(CORDE_ERR_ARG, "drive must be 16-byte aligned device, managed or mapped pinned host memory");
+    d = reinterpret_cast<const float4*>(dp);
   }
   return launch_bins(h, h->bins, n_steps, d, (cudaStream_t)stream);
 }
@@ -680,6 +713,137 @@ int rod_autotune(rod_handle h, int n_steps, void* stream) {
   return build_bins(h);
 }
 
+// Bins of the adjoint layout: two elements per thread, the smallest power-of-two block
+// (>= 32 threads) holding the rod.  Bin.variant is the index of the matching <2, nt> step
+// variant, so that rod_rollout and the adjoint's recomputation run the same kernel code.
+static int build_adjoint_bins(rod_handle h) {
+  if (!h->adj_bins.empty()) return CORDE_OK;
+  for (int nt = 32; nt <= kAdjointMaxNodes / 2; nt *= 2) {
+    std::vector<int> rods;
+    for (int r = 0; r < h->n_rods; ++r) {
+      int need = 32;
+      while (2 * need < h->n_nodes[r]) need *= 2;
+      if (need == nt) rods.push_back(r);
+    }
+    if (rods.empty()) continue;
+    const int v = find_variant(2, nt);
+    if (v < 0) return fail(CORDE_ERR_UNSUPPORTED, "no <2, " + std::to_string(nt) + "> step variant");
+    Bin b{v, (int)rods.size(), nullptr};
+    CK(cudaMalloc(&b.d_work, rods.size() * sizeof(int)));
+    CK(cudaMemcpy(b.d_work, rods.data(), rods.size() * sizeof(int), cudaMemcpyHostToDevice));
+    h->adj_bins.push_back(b);
+  }
+  return CORDE_OK;
+}
+
+static bool adjoint_capable(rod_handle h) {
+  for (int r = 0; r < h->n_rods; ++r)
+    if (h->n_nodes[r] > kAdjointMaxNodes) return false;
+  return true;
+}
+
+int rod_rollout(rod_handle h, int n_steps, int ckpt_every, float* pos_traj, void* stream) {
+  if (int rc = check_handle(h)) return rc;
+  if (n_steps < 1 || ckpt_every < 1) return fail(CORDE_ERR_ARG, "n_steps and ckpt_every must be >= 1");
+  float4* traj = nullptr;
+  if (pos_traj) {
+    const void* dp = nullptr;
+    if (!device_accessible(pos_traj, &dp))
+      return fail(CORDE_ERR_ARG, "pos_traj must be 16-byte aligned device memory");
+    traj = reinterpret_cast<float4*>(const_cast<void*>(dp));
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t E = h->n_elem;
+  const int n_seg = (n_steps + ckpt_every - 1) / ckpt_every;
+  if (int rc = ensure_capacity(&h->d_ckpt, &h->ckpt_cap, (size_t)n_seg * 4 * E)) return rc;
+  const size_t b = (size_t)E * sizeof(float4);
+  const bool adj = adjoint_capable(h);
+  if (adj)
+    if (int rc = build_adjoint_bins(h)) return rc;
+  const std::vector<Bin>& bins = adj ? h->adj_bins : h->bins;
+  int launches = 0;
+  for (int seg = 0; seg < n_seg; ++seg) {
+    float4* ck = h->d_ckpt + (size_t)seg * 4 * E;
+    CK(cudaMemcpyAsync(ck, h->d_x, b, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(ck + E, h->d_v, b, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(ck + 2 * E, h->d_q, b, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(ck + 3 * E, h->d_o, b, cudaMemcpyDeviceToDevice, s));
+    const int t0 = seg * ckpt_every;
+    const int cnt = std::min(ckpt_every, n_steps - t0);
+    if (int rc = launch_bins(h, bins, cnt, h->d_drive, s, traj ? traj + (size_t)t0 * E : nullptr)) return rc;
+    launches += h->last_launches;
+  }
+  h->last_launches = launches;
+  h->ro_steps = n_steps;
+  h->ro_every = ckpt_every;
+  return CORDE_OK;
+}
+
+int rod_adjoint(rod_handle h, const float* dL_dpos_traj, float* dL_dK, float* dL_duhat, float* dL_dvel0,
+                float* dL_dpos0, float* dL_dquat0, float* dL_domega0, void* stream) {
+  if (int rc = check_handle(h)) return rc;
+  if (h->ro_steps < 1) return fail(CORDE_ERR_ARG, "rod_adjoint needs a preceding rod_rollout");
+  for (int r = 0; r < h->n_rods; ++r)
+    if (h->n_nodes[r] > kAdjointMaxNodes)
+      return fail(CORDE_ERR_UNSUPPORTED, "the adjoint kernel holds rods of at most " +
+                                             std::to_string(kAdjointMaxNodes) + " nodes");
+  const float* ptrs_in[1] = {dL_dpos_traj};
+  float* ptrs_out[6] = {dL_dK, dL_duhat, dL_dvel0, dL_dpos0, dL_dquat0, dL_domega0};
+  const void* dev_in = nullptr;
+  if (ptrs_in[0] && !device_accessible(ptrs_in[0], &dev_in))
+    return fail(CORDE_ERR_ARG, "dL_dpos_traj must be 16-byte aligned device memory");
+  float4* dev_out[6];
+  for (int k = 0; k < 6; ++k) {
+    dev_out[k] = nullptr;
+    if (ptrs_out[k]) {
+      const void* dp = nullptr;
+      if (!device_accessible(ptrs_out[k], &dp)) return fail(CORDE_ERR_ARG, "gradient outputs must be device memory");
+      dev_out[k] = reinterpret_cast<float4*>(const_cast<void*>(dp));
+    }
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t E = h->n_elem;
+  if (int rc = ensure_capacity(&h->d_seg, &h->seg_cap, (size_t)h->ro_every * 4 * E)) return rc;
+  if (int rc = build_adjoint_bins(h)) return rc;
+  int dev = 0, smem_max = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  AdjointArgs a;
+  a.rods = h->d_rods;
+  a.ckpt = h->d_ckpt;
+  a.seg_states = h->d_seg;
+  a.u4 = h->d_u;
+  a.k4 = h->d_k;
+  a.drive = h->d_drive;
+  a.dLdpos = reinterpret_cast<const float4*>(dev_in);
+  a.n_steps = h->ro_steps;
+  a.ckpt_every = h->ro_every;
+  a.n_elem = E;
+  a.dK = dev_out[0];
+  a.duhat = dev_out[1];
+  a.dvel0 = dev_out[2];
+  a.dpos0 = dev_out[3];
+  a.dquat0 = dev_out[4];
+  a.domega0 = dev_out[5];
+  int launches = 0;
+  for (const auto& b : h->adj_bins) {
+    int iters = 0;
+    for (int r = 0; r < h->n_rods; ++r) iters = std::max(iters, h->n_iters[r]);
+    const int nt = variants()[b.variant].nt;
+    const int smem = adjoint_smem_bytes(nt, iters);
+    if (smem > smem_max)
+      return fail(CORDE_ERR_UNSUPPORTED, "adjoint needs " + std::to_string(smem) + " B of shared memory per block; " +
+                                             std::to_string(smem_max) + " available (fewer constraint iterations " +
+                                             "or shorter rods)");
+    a.work = b.d_work;
+    cudaError_t e = launch_adjoint(nt, a, b.count, smem, s);
+    if (e != cudaSuccess) return fail(CORDE_ERR_CUDA, std::string("adjoint launch: ") + cudaGetErrorString(e));
+    ++launches;
+  }
+  h->last_launches = launches;
+  return CORDE_OK;
+}
+
 void rod_destroy(rod_handle h) {
   if (!h) return;
   cudaSetDevice(h->device);
@@ -688,6 +852,8 @@ void rod_destroy(rod_handle h) {
   cudaFree(h->d_rods); cudaFree(h->d_derived);
   cudaFree(h->d_x); cudaFree(h->d_v); cudaFree(h->d_q); cudaFree(h->d_o); cudaFree(h->d_u); cudaFree(h->d_k);
   cudaFree(h->d_drive); cudaFree(h->d_elem_rod);
+  cudaFree(h->d_ckpt); cudaFree(h->d_seg);
+  for (auto& b : h->adj_bins) cudaFree(b.d_work);
   delete h;
 }
 

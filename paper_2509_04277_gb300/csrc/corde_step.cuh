@@ -19,6 +19,9 @@
 // A step costs 2 + n_iters block barriers (the paper's single-block kernel uses two
 // __syncthreads per constraint iteration, one thread per element).  Neighbour data moves
 // through a ping-pong pair of shared-memory buffers, so one barrier per exchange suffices.
+//
+// The step body is a device function shared by the forward kernel and the adjoint's
+// recomputation, so both run the same arithmetic.
 #pragma once
 
 #include "corde_common.cuh"
@@ -50,8 +53,8 @@ __device__ __forceinline__ void joint_torques(float4 qa, float4 qb, float4 uh, f
 
 // Segment forces between nodes a and b and the penalty torque on frame q (Eq. 8, and
 // Eq. 2 when the rod is extensible).  Penalty: E = 1/2 l0 Kp |t - d3|^2 gives the force
-// l0 Kp (d3 - (t . d3) t) / |e| on node b (opposite on a) and the world torque
-// l0 Kp d3 x t on the frame.
+// l0 Kp (d3 - (t . d3) t) / |e| on node b (opposite on a) and the torque l0 Kp d3 x t,
+// which in the body frame (d3 = e_z) is l0 Kp (-t_b.y, t_b.x, 0) with t_b = R(q)^T t.
 __device__ __forceinline__ void segment_forces(float3 ra, float3 rb, float4 q, const RodDev& R, bool extensible,
                                                float3& fa, float3& fb, float3& tq) {
   const float3 e = rb - ra;
@@ -69,7 +72,8 @@ __device__ __forceinline__ void segment_forces(float3 ra, float3 rb, float4 q, c
     fa += fs;
     fb -= fs;
   }
-  tq = rotate_inv(q, R.lKp * cross3(d3, t));
+  const float3 tb = rotate_inv(q, t);
+  tq = f3(-R.lKp * tb.y, R.lKp * tb.x, 0.f);
 }
 
 // Velocity-impulse factor of one distance constraint (predictive: makes the segment
@@ -90,6 +94,13 @@ __device__ __forceinline__ float constraint_factor(float3 ra, float3 va, float3 
   return __fmul_rn(__fmul_rn(-C, il), __frcp_rn(__fmul_rn(dt, wsum)));
 }
 
+// Neighbour data of one step, kept by the adjoint's recomputation.
+struct StepNeighbours {
+  float3 r_next, r_prev;
+  float w_next, w_prev;
+  float4 q_next;
+};
+
 // Dynamic shared memory of a <EPT, NT> block: per-element joint parameters (u-hat and
 // K), element-major so that thread t's accesses are conflict-free, then the two
 // ping-pong exchange buffers of three float4 slots per thread.
@@ -99,12 +110,246 @@ constexpr int step_smem_bytes() {
   return (2 * EPT * NT + 2 * kHaloSlots * NT) * (int)sizeof(float4);
 }
 
+// One time step of the rod held by this block.  With STORE, the velocities before every
+// constraint half-sweep are written to sweep_v ([2 n_iters][EPT][NT]) and the neighbour
+// data to *nb (for the adjoint).
+template <int EPT, int NT, bool STORE>
+__device__ __forceinline__ void step_body(const RodDev& R, const int t, float3 (&r)[EPT], float3 (&v)[EPT],
+                                          float4 (&q)[EPT], float3 (&om)[EPT], const float (&w)[EPT],
+                                          const float4* par_u, const float4* par_k, float4* halo, int& xc,
+                                          const float3 v_drive, const float3 w_drive, float4* sweep_v,
+                                          StepNeighbours* nb) {
+  const int e0 = t * EPT;
+  const int n = R.n;
+  const bool inext = (R.flags & F_INEXT) != 0;
+  const bool clamp = (R.flags & F_CLAMP) != 0;
+  const float dt = R.dt;
+  const float half_dt = 0.5f * dt;
+
+  // ---- exchange 1: first element's position, inverse mass and frame to the left
+  // neighbour, last element's position and inverse mass to the right neighbour (the
+  // positions hold for the whole step: the constraint sweeps change velocities only)
+  float4* hb = halo + (xc & 1) * kHaloSlots * NT;
+  ++xc;
+  hb[t] = make_float4(r[0].x, r[0].y, r[0].z, w[0]);
+  hb[NT + t] = q[0];
+  hb[2 * NT + t] = make_float4(r[EPT - 1].x, r[EPT - 1].y, r[EPT - 1].z, w[EPT - 1]);
+  block_sync<NT>();
+  float3 r_next = zero3(), r_prev = zero3();
+  float w_next = 0.f, w_prev = 0.f;
+  float4 q_next = make_float4(0.f, 0.f, 0.f, 1.f);
+  if (t + 1 < NT) {
+    const float4 a = hb[t + 1];
+    r_next = f3(a);
+    w_next = a.w;
+    q_next = hb[NT + t + 1];
+  }
+  if (t > 0) {
+    const float4 a = hb[2 * NT + t - 1];
+    r_prev = f3(a);
+    w_prev = a.w;
+  }
+  if constexpr (STORE) {
+    nb->r_next = r_next;
+    nb->r_prev = r_prev;
+    nb->w_next = w_next;
+    nb->w_prev = w_prev;
+    nb->q_next = q_next;
+  }
+
+  // ---- elastic forces and torques
+  float3 F[EPT], tau[EPT];
+#pragma unroll
+  for (int e = 0; e < EPT; ++e) {
+    F[e] = zero3();
+    tau[e] = zero3();
+  }
+  float3 F_carry = zero3(), tau_carry = zero3();
+#pragma unroll
+  for (int e = 0; e < EPT; ++e) {
+    const int j = e0 + e;
+    const float4 qb = (e + 1 < EPT) ? q[(e + 1) % EPT] : q_next;
+    const float3 rb = (e + 1 < EPT) ? r[(e + 1) % EPT] : r_next;
+    if (j <= n - 3) {  // joint between frames j and j+1
+      float3 ta, tb;
+      joint_torques(q[e], qb, par_u[e * NT + t], par_k[e * NT + t], R.two_over_l, ta, tb);
+      tau[e] += ta;
+      if (e + 1 < EPT) {
+        tau[(e + 1) % EPT] += tb;
+      } else {
+        tau_carry = tb;
+      }
+    }
+    if (j <= n - 2) {  // segment between nodes j and j+1, frame j
+      float3 fa, fb, tq;
+      segment_forces(r[e], rb, q[e], R, !inext, fa, fb, tq);
+      F[e] += fa;
+      tau[e] += tq;
+      if (e + 1 < EPT) {
+        F[(e + 1) % EPT] += fb;
+      } else {
+        F_carry = fb;
+      }
+    }
+  }
+  // ---- exchange 2: carries to the right neighbour's first element
+  hb = halo + (xc & 1) * kHaloSlots * NT;
+  ++xc;
+  hb[t] = make_float4(F_carry.x, F_carry.y, F_carry.z, 0.f);
+  hb[NT + t] = make_float4(tau_carry.x, tau_carry.y, tau_carry.z, 0.f);
+  block_sync<NT>();
+  if (t > 0) {
+    F[0] += f3(hb[t - 1]);
+    tau[0] += f3(hb[NT + t - 1]);
+  }
+
+  // ---- integrate forces and torques into velocities
+#pragma unroll
+  for (int e = 0; e < EPT; ++e) {
+    const int i = e0 + e;
+    if (w[e] > 0.f) {
+      const float3 a = f3(w[e] * F[e].x + R.gx, w[e] * F[e].y + R.gy, w[e] * F[e].z + R.gz);
+      v[e] = R.damp * (v[e] + dt * a);
+    }
+    const bool frame_dynamic = (i <= n - 2) && !(clamp && i == 0);
+    if (frame_dynamic) {
+      const float3 o = om[e];
+      const float3 Jw = f3(R.J1 * o.x, R.J1 * o.y, R.J3 * o.z);
+      const float3 rhs = tau[e] - cross3(o, Jw);
+      const float3 on = f3(o.x + dt * R.Jinv1 * rhs.x, o.y + dt * R.Jinv1 * rhs.y, o.z + dt * R.Jinv3 * rhs.z);
+      om[e] = R.damp * on;
+    }
+  }
+  if (clamp && t == 0) {
+    v[0] = v_drive;
+    om[0] = w_drive;
+  }
+
+  // ---- distance-constraint iterations (inextensible rod), red-black
+  if (inext) {
+    for (int it = 0; it < R.n_iters; ++it) {
+      if constexpr (STORE) {
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) sweep_v[((2 * it) * EPT + e) * NT + t] = make_float4(v[e].x, v[e].y, v[e].z, 0.f);
+      }
+      // even segments (e0 + 2k, e0 + 2k + 1): local to the thread
+#pragma unroll
+      for (int k = 0; k < EPT / 2; ++k) {
+        const int a = 2 * k, b = 2 * k + 1;
+        const float ws = w[a] + w[b];
+        if (e0 + b <= n - 1 && ws > 0.f) {
+          float3 d;
+          const float s = constraint_factor(r[a], v[a], r[b], v[b], ws, R.l0, dt, d);
+          v[a] -= (w[a] * s) * d;
+          v[b] += (w[b] * s) * d;
+        }
+      }
+      if constexpr (STORE) {
+#pragma unroll
+        for (int e = 0; e < EPT; ++e)
+          sweep_v[((2 * it + 1) * EPT + e) * NT + t] = make_float4(v[e].x, v[e].y, v[e].z, 0.f);
+      }
+      // exchange 3: velocities of the first and last element
+      hb = halo + (xc & 1) * kHaloSlots * NT;
+      ++xc;
+      hb[t] = make_float4(v[0].x, v[0].y, v[0].z, 0.f);
+      hb[NT + t] = make_float4(v[EPT - 1].x, v[EPT - 1].y, v[EPT - 1].z, 0.f);
+      block_sync<NT>();
+      // odd segments inside the thread
+#pragma unroll
+      for (int k = 0; k + 1 < EPT / 2; ++k) {
+        const int a = 2 * k + 1, b = 2 * k + 2;
+        const float ws = w[a] + w[b];
+        if (e0 + b <= n - 1 && ws > 0.f) {
+          float3 d;
+          const float s = constraint_factor(r[a], v[a], r[b], v[b], ws, R.l0, dt, d);
+          v[a] -= (w[a] * s) * d;
+          v[b] += (w[b] * s) * d;
+        }
+      }
+      // odd segment across the right boundary: (my last, right neighbour's first)
+      if (t + 1 < NT && e0 + EPT <= n - 1) {
+        const float ws = w[EPT - 1] + w_next;
+        if (ws > 0.f) {
+          float3 d;
+          const float s = constraint_factor(r[EPT - 1], v[EPT - 1], r_next, f3(hb[t + 1]), ws, R.l0, dt, d);
+          v[EPT - 1] -= (w[EPT - 1] * s) * d;
+        }
+      }
+      // odd segment across the left boundary: (left neighbour's last, my first)
+      if (t > 0 && e0 <= n - 1) {
+        const float ws = w_prev + w[0];
+        if (ws > 0.f) {
+          float3 d;
+          const float s = constraint_factor(r_prev, f3(hb[NT + t - 1]), r[0], v[0], ws, R.l0, dt, d);
+          v[0] += (w[0] * s) * d;
+        }
+      }
+    }
+  }
+
+  // ---- integrate linear and angular velocities (semi-implicit Euler)
+#pragma unroll
+  for (int e = 0; e < EPT; ++e) {
+    const int i = e0 + e;
+    r[e] += dt * v[e];
+    if (i <= n - 2) {
+      const float4 a = q[e];
+      const float3 o = om[e];
+      // q (x) (0, omega)
+      const float dx = a.w * o.x + a.y * o.z - a.z * o.y;
+      const float dy = a.w * o.y + a.z * o.x - a.x * o.z;
+      const float dz = a.w * o.z + a.x * o.y - a.y * o.x;
+      const float dwq = -(a.x * o.x + a.y * o.y + a.z * o.z);
+      const float4 b = make_float4(a.x + half_dt * dx, a.y + half_dt * dy, a.z + half_dt * dz, a.w + half_dt * dwq);
+      const float inv = rsqrtf(b.x * b.x + b.y * b.y + b.z * b.z + b.w * b.w);
+      q[e] = make_float4(b.x * inv, b.y * inv, b.z * inv, b.w * inv);
+    }
+  }
+}
+
+// Loads the rod's elements owned by thread t (registers) and its joint parameters
+// (shared memory, read back only by the same thread).
+template <int EPT, int NT>
+__device__ __forceinline__ void load_rod(const RodDev& R, const int t, const float4* __restrict__ x4,
+                                         const float4* __restrict__ v4, const float4* __restrict__ q4,
+                                         const float4* __restrict__ o4, const float4* __restrict__ u4,
+                                         const float4* __restrict__ k4, float3 (&r)[EPT], float3 (&v)[EPT],
+                                         float4 (&q)[EPT], float3 (&om)[EPT], float (&w)[EPT], float4* par_u,
+                                         float4* par_k) {
+  const int e0 = t * EPT;
+#pragma unroll
+  for (int e = 0; e < EPT; ++e) {
+    const int i = e0 + e;
+    if (i < R.n) {
+      const float4 a = x4[R.off + i];
+      r[e] = f3(a);
+      w[e] = a.w;
+      v[e] = f3(v4[R.off + i]);
+      q[e] = q4[R.off + i];
+      om[e] = f3(o4[R.off + i]);
+      if (par_u != nullptr) {
+        par_u[e * NT + t] = u4[R.off + i];
+        par_k[e * NT + t] = k4[R.off + i];
+      }
+    } else {
+      r[e] = zero3();
+      v[e] = zero3();
+      om[e] = zero3();
+      q[e] = make_float4(0.f, 0.f, 0.f, 1.f);
+      w[e] = 0.f;
+    }
+  }
+}
+
+// n_steps time steps of one rod per block.  traj (optional): positions after every step,
+// [n_steps][n_elements] float4 with .w the inverse mass.
 template <int EPT, int NT>
 __global__ void __launch_bounds__(NT)
 step_kernel(const RodDev* __restrict__ rods, const int* __restrict__ work, float4* __restrict__ x4,
             float4* __restrict__ v4, float4* __restrict__ q4, float4* __restrict__ o4,
             const float4* __restrict__ u4, const float4* __restrict__ k4, const float4* __restrict__ drive,
-            int n_steps) {
+            int n_steps, float4* __restrict__ traj, int64_t n_elem) {
   static_assert(EPT % 2 == 0, "elements per thread must be even (red-black sweeps)");
   extern __shared__ float4 smem[];
   float4* par_u = smem;
@@ -115,214 +360,31 @@ step_kernel(const RodDev* __restrict__ rods, const int* __restrict__ work, float
   const RodDev R = rods[rid];
   const int t = threadIdx.x;
   const int e0 = t * EPT;
-  const int n = R.n;
-  const bool inext = (R.flags & F_INEXT) != 0;
-  const bool clamp = (R.flags & F_CLAMP) != 0;
-  const float dt = R.dt;
-  const float half_dt = 0.5f * dt;
 
   float3 r[EPT], v[EPT], om[EPT];
   float4 q[EPT];
   float w[EPT];
-#pragma unroll
-  for (int e = 0; e < EPT; ++e) {
-    const int i = e0 + e;
-    if (i < n) {
-      const float4 a = x4[R.off + i];
-      r[e] = f3(a);
-      w[e] = a.w;
-      v[e] = f3(v4[R.off + i]);
-      q[e] = q4[R.off + i];
-      om[e] = f3(o4[R.off + i]);
-      par_u[e * NT + t] = u4[R.off + i];
-      par_k[e * NT + t] = k4[R.off + i];
-    } else {
-      r[e] = zero3();
-      v[e] = zero3();
-      om[e] = zero3();
-      q[e] = make_float4(0.f, 0.f, 0.f, 1.f);
-      w[e] = 0.f;
-    }
-  }
+  load_rod<EPT, NT>(R, t, x4, v4, q4, o4, u4, k4, r, v, q, om, w, par_u, par_k);
   float3 v_drive = zero3(), w_drive = zero3();
   if (drive != nullptr) {
     v_drive = f3(drive[2 * rid]);
     w_drive = f3(drive[2 * rid + 1]);
   }
-  // Parameters are read back only by the thread that wrote them: no barrier needed.
 
   int xc = 0;  // exchange counter selects the ping-pong buffer
   for (int step = 0; step < n_steps; ++step) {
-    // ---- exchange 1: first element's position, inverse mass and frame to the left
-    // neighbour, last element's position and inverse mass to the right neighbour (the
-    // positions hold for the whole step: the constraint sweeps change velocities only)
-    float4* hb = halo + (xc & 1) * kHaloSlots * NT;
-    ++xc;
-    hb[t] = make_float4(r[0].x, r[0].y, r[0].z, w[0]);
-    hb[NT + t] = q[0];
-    hb[2 * NT + t] = make_float4(r[EPT - 1].x, r[EPT - 1].y, r[EPT - 1].z, w[EPT - 1]);
-    block_sync<NT>();
-    float3 r_next = zero3(), r_prev = zero3();
-    float w_next = 0.f, w_prev = 0.f;
-    float4 q_next = make_float4(0.f, 0.f, 0.f, 1.f);
-    if (t + 1 < NT) {
-      const float4 a = hb[t + 1];
-      r_next = f3(a);
-      w_next = a.w;
-      q_next = hb[NT + t + 1];
-    }
-    if (t > 0) {
-      const float4 a = hb[2 * NT + t - 1];
-      r_prev = f3(a);
-      w_prev = a.w;
-    }
-
-    // ---- elastic forces and torques
-    float3 F[EPT], tau[EPT];
+    step_body<EPT, NT, false>(R, t, r, v, q, om, w, par_u, par_k, halo, xc, v_drive, w_drive, nullptr, nullptr);
+    if (traj != nullptr) {
 #pragma unroll
-    for (int e = 0; e < EPT; ++e) {
-      F[e] = zero3();
-      tau[e] = zero3();
-    }
-    float3 F_carry = zero3(), tau_carry = zero3();
-#pragma unroll
-    for (int e = 0; e < EPT; ++e) {
-      const int j = e0 + e;
-      const float4 qb = (e + 1 < EPT) ? q[(e + 1) % EPT] : q_next;
-      const float3 rb = (e + 1 < EPT) ? r[(e + 1) % EPT] : r_next;
-      if (j <= n - 3) {  // joint between frames j and j+1
-        float3 ta, tb;
-        joint_torques(q[e], qb, par_u[e * NT + t], par_k[e * NT + t], R.two_over_l, ta, tb);
-        tau[e] += ta;
-        if (e + 1 < EPT) {
-          tau[(e + 1) % EPT] += tb;
-        } else {
-          tau_carry = tb;
-        }
-      }
-      if (j <= n - 2) {  // segment between nodes j and j+1, frame j
-        float3 fa, fb, tq;
-        segment_forces(r[e], rb, q[e], R, !inext, fa, fb, tq);
-        F[e] += fa;
-        tau[e] += tq;
-        if (e + 1 < EPT) {
-          F[(e + 1) % EPT] += fb;
-        } else {
-          F_carry = fb;
-        }
-      }
-    }
-    // ---- exchange 2: carries to the right neighbour's first element
-    hb = halo + (xc & 1) * kHaloSlots * NT;
-    ++xc;
-    hb[t] = make_float4(F_carry.x, F_carry.y, F_carry.z, 0.f);
-    hb[NT + t] = make_float4(tau_carry.x, tau_carry.y, tau_carry.z, 0.f);
-    block_sync<NT>();
-    if (t > 0) {
-      F[0] += f3(hb[t - 1]);
-      tau[0] += f3(hb[NT + t - 1]);
-    }
-
-    // ---- integrate forces and torques into velocities
-#pragma unroll
-    for (int e = 0; e < EPT; ++e) {
-      const int i = e0 + e;
-      if (w[e] > 0.f) {
-        const float3 a = f3(w[e] * F[e].x + R.gx, w[e] * F[e].y + R.gy, w[e] * F[e].z + R.gz);
-        v[e] = R.damp * (v[e] + dt * a);
-      }
-      const bool frame_dynamic = (i <= n - 2) && !(clamp && i == 0);
-      if (frame_dynamic) {
-        const float3 o = om[e];
-        const float3 Jw = f3(R.J1 * o.x, R.J1 * o.y, R.J3 * o.z);
-        const float3 rhs = tau[e] - cross3(o, Jw);
-        const float3 on = f3(o.x + dt * R.Jinv1 * rhs.x, o.y + dt * R.Jinv1 * rhs.y, o.z + dt * R.Jinv3 * rhs.z);
-        om[e] = R.damp * on;
-      }
-    }
-    if (clamp && t == 0) {
-      v[0] = v_drive;
-      om[0] = w_drive;
-    }
-
-    // ---- distance-constraint iterations (inextensible rod), red-black
-    if (inext) {
-      for (int it = 0; it < R.n_iters; ++it) {
-        // even segments (e0 + 2k, e0 + 2k + 1): local to the thread
-#pragma unroll
-        for (int k = 0; k < EPT / 2; ++k) {
-          const int a = 2 * k, b = 2 * k + 1;
-          const float ws = w[a] + w[b];
-          if (e0 + b <= n - 1 && ws > 0.f) {
-            float3 d;
-            const float s = constraint_factor(r[a], v[a], r[b], v[b], ws, R.l0, dt, d);
-            v[a] -= (w[a] * s) * d;
-            v[b] += (w[b] * s) * d;
-          }
-        }
-        // exchange 3: velocities of the first and last element
-        hb = halo + (xc & 1) * kHaloSlots * NT;
-        ++xc;
-        hb[t] = make_float4(v[0].x, v[0].y, v[0].z, 0.f);
-        hb[NT + t] = make_float4(v[EPT - 1].x, v[EPT - 1].y, v[EPT - 1].z, 0.f);
-        block_sync<NT>();
-        // odd segments inside the thread
-#pragma unroll
-        for (int k = 0; k + 1 < EPT / 2; ++k) {
-          const int a = 2 * k + 1, b = 2 * k + 2;
-          const float ws = w[a] + w[b];
-          if (e0 + b <= n - 1 && ws > 0.f) {
-            float3 d;
-            const float s = constraint_factor(r[a], v[a], r[b], v[b], ws, R.l0, dt, d);
-            v[a] -= (w[a] * s) * d;
-            v[b] += (w[b] * s) * d;
-          }
-        }
-        // odd segment across the right boundary: (my last, right neighbour's first)
-        if (t + 1 < NT && e0 + EPT <= n - 1) {
-          const float ws = w[EPT - 1] + w_next;
-          if (ws > 0.f) {
-            float3 d;
-            const float s = constraint_factor(r[EPT - 1], v[EPT - 1], r_next, f3(hb[t + 1]), ws, R.l0, dt, d);
-            v[EPT - 1] -= (w[EPT - 1] * s) * d;
-          }
-        }
-        // odd segment across the left boundary: (left neighbour's last, my first)
-        if (t > 0 && e0 <= n - 1) {
-          const float ws = w_prev + w[0];
-          if (ws > 0.f) {
-            float3 d;
-            const float s = constraint_factor(r_prev, f3(hb[NT + t - 1]), r[0], v[0], ws, R.l0, dt, d);
-            v[0] += (w[0] * s) * d;
-          }
-        }
-      }
-    }
-
-    // ---- integrate linear and angular velocities (semi-implicit Euler)
-#pragma unroll
-    for (int e = 0; e < EPT; ++e) {
-      const int i = e0 + e;
-      r[e] += dt * v[e];
-      if (i <= n - 2) {
-        const float4 a = q[e];
-        const float3 o = om[e];
-        // q (x) (0, omega)
-        const float dx = a.w * o.x + a.y * o.z - a.z * o.y;
-        const float dy = a.w * o.y + a.z * o.x - a.x * o.z;
-        const float dz = a.w * o.z + a.x * o.y - a.y * o.x;
-        const float dwq = -(a.x * o.x + a.y * o.y + a.z * o.z);
-        float4 b = make_float4(a.x + half_dt * dx, a.y + half_dt * dy, a.z + half_dt * dz, a.w + half_dt * dwq);
-        const float inv = rsqrtf(b.x * b.x + b.y * b.y + b.z * b.z + b.w * b.w);
-        q[e] = make_float4(b.x * inv, b.y * inv, b.z * inv, b.w * inv);
-      }
+      for (int e = 0; e < EPT; ++e)
+        if (e0 + e < R.n) traj[(int64_t)step * n_elem + R.off + e0 + e] = make_float4(r[e].x, r[e].y, r[e].z, w[e]);
     }
   }
 
 #pragma unroll
   for (int e = 0; e < EPT; ++e) {
     const int i = e0 + e;
-    if (i < n) {
+    if (i < R.n) {
       x4[R.off + i] = make_float4(r[e].x, r[e].y, r[e].z, w[e]);
       v4[R.off + i] = make_float4(v[e].x, v[e].y, v[e].z, 0.f);
       q4[R.off + i] = q[e];

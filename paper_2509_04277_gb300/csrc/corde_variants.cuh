@@ -17,6 +17,8 @@ struct StepArgs {
   const float4 *u4, *k4;
   const float4* drive;
   int n_steps;
+  float4* traj;    // optional: positions after every step, [n_steps][n_elem]
+  int64_t n_elem;
 };
 
 typedef cudaError_t (*StepLaunchFn)(const StepArgs& a, int n_blocks, cudaStream_t s);
@@ -28,6 +30,23 @@ struct StepVariant {
   StepLaunchFn launch;
   int capacity() const { return ept * nt; }
 };
+
+// Arguments of the reverse (adjoint) kernel; see corde_adjoint.cu.
+struct AdjointArgs {
+  const RodDev* rods;
+  const int* work;
+  const float4* ckpt;    // [n_ckpt][4][n_elem]: x4, v4, q4, o4 at steps 0, K, 2K, ...
+  float4* seg_states;    // scratch [K][4][n_elem]
+  const float4 *u4, *k4;
+  const float4* drive;
+  const float4* dLdpos;  // [n_steps][n_elem] or NULL
+  int n_steps, ckpt_every;
+  int64_t n_elem;
+  float4 *dpos0, *dvel0, *dquat0, *domega0, *dK, *duhat;
+};
+int adjoint_smem_bytes(int nt, int n_iters);
+cudaError_t launch_adjoint(int nt, const AdjointArgs& a, int n_blocks, int smem, cudaStream_t s);
+constexpr int kAdjointMaxNodes = 512;
 
 // Defined in the per-EPT instantiation units.
 extern const StepVariant kStepVariantsE2[];
