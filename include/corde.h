@@ -168,6 +168,32 @@ int rod_rollout(rod_handle h, int n_steps, int ckpt_every, float* pos_traj, void
 int rod_adjoint(rod_handle h, const float* dL_dpos_traj, float* dL_dK, float* dL_duhat, float* dL_dvel0,
                 float* dL_dpos0, float* dL_dquat0, float* dL_domega0, void* stream);
 
+/* Gradient of one rod's rollout without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call cudaMalloc where
+ * they need a gradient - a haptic or control loop under a real-time budget (an allocation
+ * can stall and synchronise the device), or an application whose device memory is
+ * owned by its own pool.  It runs the recorded rollout (as rod_rollout) and the reverse
+ * pass (as rod_adjoint) of a single rod described like rod_create's arguments, keeping
+ * every intermediate in one static 16 MiB array that is part of the library image (every
+ * GPU that loads the library holds it until the process exits).
+ *  params         one rod (host).  Inputs, device memory in rod_create's layouts: pos [N][3],
+ *                 quat [N-1][4], rest_quat, vel, omega, stiff_mul (NULL allowed as in
+ *                 rod_create), drive [8] or NULL (zero).
+ *  dL_dpos_traj   [n_steps][N][4] device, dL/d(position after step t), or NULL.
+ *  Outputs (device, [N][4] floats, NULL skips): pos_traj [n_steps][N][4] positions after
+ *                 every step; dL_dK, dL_duhat, dL_dvel0, dL_dpos0 as in rod_adjoint.
+ * Limits: N <= 512 and (ceil(n_steps / ckpt_every) + min(ckpt_every, n_steps)) * 64 * N
+ * bytes plus about 100 * N bytes must fit in 16 MiB; larger requests return CORDE_ERR_ARG
+ * with the size needed.  It calls no cudaMalloc, cudaFree or other allocating routine.
+ * The first call on each device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current: make that first call before any stream capture.  Every call
+ * shares the one array and overwrites it; calls that overlap on the GPU (other streams,
+ * other host threads) race and give wrong results.  Asynchronous on `stream`. */
+int rod_adjoint_noalloc(const RodParams* params, const float* pos, const float* quat, const float* rest_quat,
+                        const float* vel, const float* omega, const float* stiff_mul, const float* drive,
+                        int n_steps, int ckpt_every, const float* dL_dpos_traj, float* pos_traj, float* dL_dK,
+                        float* dL_duhat, float* dL_dvel0, float* dL_dpos0, void* stream);
+
 /* Empty-barrier floor (synchronous): ns per barrier over n_iters back-to-back barriers
  * of one scope in a single launch.  The paper's multi-block kernel pays an inter-block
  * barrier per data exchange (Section 2.2, Fig. 5); these floors are the reference for a

@@ -61,6 +61,8 @@ SIGNATURES = {
     "rod_last_launch_count": (ctypes.c_int, [_VP]),
     "rod_rollout": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP, _VP]),
     "rod_adjoint": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "rod_adjoint_noalloc": (ctypes.c_int, [ctypes.POINTER(RodParams), _VP, _VP, _VP, _VP, _VP, _VP, _VP,
+                                           ctypes.c_int, ctypes.c_int, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "rod_barrier_floor": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_double), _VP]),
     "rod_destroy": (None, [_VP]),
@@ -201,6 +203,17 @@ def rod_barrier_floor(scope, threads=128, cluster=1, n_iters=100000, stream=None
     _check(load().rod_barrier_floor(int(scope), int(threads), int(cluster), int(n_iters), ctypes.byref(ns),
                                     _stream(stream)), "rod_barrier_floor")
     return ns.value
+
+
+def rod_adjoint_noalloc(params, pos, quat, rest_quat=None, vel=None, omega=None, stiff_mul=None, drive=None,
+                        n_steps=1, ckpt_every=1, dL_dpos_traj=None, pos_traj=None, dL_dK=None, dL_duhat=None,
+                        dL_dvel0=None, dL_dpos0=None, stream=None):
+    """Rollout and reverse pass of one rod with no device allocation (all pointers are
+    caller-owned device buffers; intermediates live in the library's static array)."""
+    _check(load().rod_adjoint_noalloc(ctypes.byref(params), _ptr(pos), _ptr(quat), _ptr(rest_quat), _ptr(vel),
+                                      _ptr(omega), _ptr(stiff_mul), _ptr(drive), int(n_steps), int(ckpt_every),
+                                      _ptr(dL_dpos_traj), _ptr(pos_traj), _ptr(dL_dK), _ptr(dL_duhat),
+                                      _ptr(dL_dvel0), _ptr(dL_dpos0), _stream(stream)), "rod_adjoint_noalloc")
 
 
 # ------------------------------------------------------------------ convenience

@@ -858,3 +858,186 @@ void rod_destroy(rod_handle h) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------
+// Gradient entry point that allocates nothing.
+//
+// Some callers cannot call cudaMalloc at the point where they need a gradient: a haptic or
+// control loop running under a real-time budget (an allocation can stall for milliseconds
+// and may synchronise the device), an application whose device memory is owned by its own
+// pool or arena, or code that must not change the process's allocation state.  For them,
+// rod_adjoint_noalloc runs the recorded rollout and the reverse pass of one rod with every
+// intermediate (derived constants, packed state, checkpoints, per-segment states) in the
+// file-scope array below, which is part of the library image: every GPU that loads the
+// library holds these 16 MiB until the process exits.  The caller passes inputs and
+// outputs as device memory.
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+constexpr int kMaxDevices = 64;
+void* g_noalloc_base[kMaxDevices] = {};
+
+__global__ void noalloc_setup_kernel(RodParams p, int n, RodParams* P, int* off, int* work, int* elem_rod,
+                                     const float* drive_in, float4* drive) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) {
+    *P = p;
+    off[0] = 0;
+    work[0] = 0;
+    drive[0] = drive_in ? make_float4(drive_in[0], drive_in[1], drive_in[2], 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
+    drive[1] = drive_in ? make_float4(drive_in[4], drive_in[5], drive_in[6], 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  if (i < n) elem_rod[i] = 0;
+}
+
+bool device_readable(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+extern "C" int rod_adjoint_noalloc(const RodParams* params, const float* pos, const float* quat,
+                                   const float* rest_quat, const float* vel, const float* omega,
+                                   const float* stiff_mul, const float* drive, int n_steps, int ckpt_every,
+                                   const float* dL_dpos_traj, float* pos_traj, float* dL_dK, float* dL_duhat,
+                                   float* dL_dvel0, float* dL_dpos0, void* stream) {
+  if (!params || !pos || !quat) return fail(CORDE_ERR_ARG, "rod_adjoint_noalloc: need params, pos and quat");
+  std::string why;
+  if (!params_valid(*params, why)) return fail(CORDE_ERR_ARG, "rod_adjoint_noalloc: " + why);
+  const int N = params->n_nodes;
+  if (N > kAdjointMaxNodes)
+    return fail(CORDE_ERR_ARG, "rod_adjoint_noalloc: at most " + std::to_string(kAdjointMaxNodes) + " nodes");
+  if (n_steps < 1 || ckpt_every < 1) return fail(CORDE_ERR_ARG, "rod_adjoint_noalloc: n_steps, ckpt_every >= 1");
+  const float* ins[7] = {pos, quat, rest_quat, vel, omega, stiff_mul, drive};
+  for (const float* p : ins)
+    if (p && !device_readable(p)) return fail(CORDE_ERR_ARG, "rod_adjoint_noalloc: inputs must be device memory");
+  const void* dev_traj_in = nullptr;
+  if (dL_dpos_traj && !device_accessible(dL_dpos_traj, &dev_traj_in))
+    return fail(CORDE_ERR_ARG, "rod_adjoint_noalloc: dL_dpos_traj must be 16-byte aligned device memory");
+  float* outs[5] = {pos_traj, dL_dK, dL_duhat, dL_dvel0, dL_dpos0};
+  float4* dev_out[5];
+  for (int k = 0; k < 5; ++k) {
+    dev_out[k] = nullptr;
+    if (outs[k]) {
+      const void* dp = nullptr;
+      if (!device_accessible(outs[k], &dp))
+        return fail(CORDE_ERR_ARG, "rod_adjoint_noalloc: outputs must be 16-byte aligned device memory");
+      dev_out[k] = reinterpret_cast<float4*>(const_cast<void*>(dp));
+    }
+  }
+
+  // scratch layout
+  const int n_seg = (n_steps + ckpt_every - 1) / ckpt_every;
+  const int K = std::min(ckpt_every, n_steps);
+  size_t o = 0;
+  const size_t o_P = o; o = align256(o + sizeof(RodParams));
+  const size_t o_off = o; o = align256(o + sizeof(int));
+  const size_t o_work = o; o = align256(o + sizeof(int));
+  const size_t o_der = o; o = align256(o + 16 * sizeof(double));
+  const size_t o_rod = o; o = align256(o + sizeof(RodDev));
+  const size_t o_drv = o; o = align256(o + 2 * sizeof(float4));
+  const size_t o_er = o; o = align256(o + (size_t)N * sizeof(int));
+  const size_t o_state = o; o = align256(o + 6 * (size_t)N * sizeof(float4));
+  const size_t o_ckpt = o; o = align256(o + (size_t)n_seg * 4 * N * sizeof(float4));
+  const size_t o_seg = o; o = align256(o + (size_t)K * 4 * N * sizeof(float4));
+  if (o > kNoAllocScratchBytes)
+    return fail(CORDE_ERR_ARG, "rod_adjoint_noalloc: needs " + std::to_string(o) + " bytes of scratch, above the " +
+                                   std::to_string(kNoAllocScratchBytes) +
+                                   "-byte static limit (fewer steps, a smaller ckpt_every or a shorter rod)");
+
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return fail(CORDE_ERR_UNSUPPORTED, "rod_adjoint_noalloc: device index");
+  if (!g_noalloc_base[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(CORDE_ERR_CUDA, std::string("rod_adjoint_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    g_noalloc_base[dev] = p;
+  }
+  unsigned char* base = static_cast<unsigned char*>(g_noalloc_base[dev]);
+  RodParams* d_P = reinterpret_cast<RodParams*>(base + o_P);
+  int* d_off = reinterpret_cast<int*>(base + o_off);
+  int* d_work = reinterpret_cast<int*>(base + o_work);
+  double* d_der = reinterpret_cast<double*>(base + o_der);
+  RodDev* d_rod = reinterpret_cast<RodDev*>(base + o_rod);
+  float4* d_drv = reinterpret_cast<float4*>(base + o_drv);
+  int* d_er = reinterpret_cast<int*>(base + o_er);
+  float4* st = reinterpret_cast<float4*>(base + o_state);
+  float4 *x4 = st, *v4 = st + N, *q4 = st + 2 * N, *o4 = st + 3 * N, *u4 = st + 4 * N, *k4 = st + 5 * N;
+  float4* ckpt = reinterpret_cast<float4*>(base + o_ckpt);
+  float4* seg = reinterpret_cast<float4*>(base + o_seg);
+  cudaStream_t s = (cudaStream_t)stream;
+
+  noalloc_setup_kernel<<<(N + 255) / 256, 256, 0, s>>>(*params, N, d_P, d_off, d_work, d_er, drive, d_drv);
+  derive_kernel<<<1, 32, 0, s>>>(1, d_P, d_off, d_rod, d_der);
+  pack_kernel<<<(N + 255) / 256, 256, 0, s>>>(N, d_er, d_rod, d_P, d_der, pos, quat, rest_quat, vel, omega, stiff_mul,
+                                               x4, v4, q4, o4, u4, k4);
+  CK(cudaGetLastError());
+
+  // forward rollout in the adjoint's layout: two elements per thread
+  int nt = 32;
+  while (2 * nt < N) nt *= 2;
+  const int v = find_variant(2, nt);
+  if (v < 0) return fail(CORDE_ERR_UNSUPPORTED, "rod_adjoint_noalloc: no step variant");
+  StepArgs a;
+  a.rods = d_rod;
+  a.work = d_work;
+  a.x4 = x4;
+  a.v4 = v4;
+  a.q4 = q4;
+  a.o4 = o4;
+  a.u4 = u4;
+  a.k4 = k4;
+  a.drive = d_drv;
+  a.n_elem = N;
+  const size_t b = (size_t)N * sizeof(float4);
+  for (int sg = 0; sg < n_seg; ++sg) {
+    float4* ck = ckpt + (size_t)sg * 4 * N;
+    CK(cudaMemcpyAsync(ck, x4, b, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(ck + N, v4, b, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(ck + 2 * N, q4, b, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(ck + 3 * N, o4, b, cudaMemcpyDeviceToDevice, s));
+    const int t0 = sg * ckpt_every;
+    a.n_steps = std::min(ckpt_every, n_steps - t0);
+    a.traj = dev_out[0] ? dev_out[0] + (size_t)t0 * N : nullptr;
+    cudaError_t e = variants()[v].launch(a, 1, s);
+    if (e != cudaSuccess) return fail(CORDE_ERR_CUDA, std::string("rod_adjoint_noalloc: step: ") + cudaGetErrorString(e));
+  }
+
+  // reverse pass
+  const int iters = params->inextensible ? params->n_iters : 0;
+  int smem_max = 0;
+  CK(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  const int smem = adjoint_smem_bytes(nt, iters);
+  if (smem > smem_max) return fail(CORDE_ERR_UNSUPPORTED, "rod_adjoint_noalloc: shared memory");
+  AdjointArgs ad;
+  ad.rods = d_rod;
+  ad.work = d_work;
+  ad.ckpt = ckpt;
+  ad.seg_states = seg;
+  ad.u4 = u4;
+  ad.k4 = k4;
+  ad.drive = d_drv;
+  ad.dLdpos = reinterpret_cast<const float4*>(dev_traj_in);
+  ad.n_steps = n_steps;
+  ad.ckpt_every = ckpt_every;
+  ad.n_elem = N;
+  ad.dK = dev_out[1];
+  ad.duhat = dev_out[2];
+  ad.dvel0 = dev_out[3];
+  ad.dpos0 = dev_out[4];
+  ad.dquat0 = nullptr;
+  ad.domega0 = nullptr;
+  cudaError_t e = launch_adjoint(nt, ad, 1, smem, s);
+  if (e != cudaSuccess) return fail(CORDE_ERR_CUDA, std::string("rod_adjoint_noalloc: adjoint: ") + cudaGetErrorString(e));
+  return CORDE_OK;
+}
