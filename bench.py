@@ -330,6 +330,37 @@ def run_adjoint(args, torch, corde, W, n_rods=1):
             "adjoint_element_steps_per_s": el_steps / (adj_ms * 1e-3), "gradients_finite": finite}
 
 
+def run_pair(args, torch, corde, W):
+    """Catheter/guidewire pair, 2 x 512 elements, binding modes v0/v1/v2, 1, 10 and 50 time
+    steps per launch (about 1000 steps each), drives updated every launch."""
+    stream = torch.cuda.current_stream()
+    out = {}
+    for mode in (0, 1, 2):
+        for S in (1, 10, 50):
+            cat, gw = W.catheter_guidewire(512, seed=3, beta0=-100.25)
+            l0 = gw.length / 511
+            n_launch = max(20, 1000 // S)
+            dcs, dgs = W.pair_drives(3, n_launch + 5, S * gw.dt, l0, -100.25)
+            drv = torch.as_tensor(np.stack([dcs, dgs], axis=1).astype(np.float32), device="cuda").contiguous()
+            b = corde.RodBatch([cat, gw])
+            b.bind(0, 1, mode)
+            for k in range(5):
+                b.step(S, drive=drv[k])
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for k in range(n_launch):
+                b.step(S, drive=drv[5 + k])
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            out[f"v{mode}_{S}ts"] = round(ms * 1e3 / (n_launch * S), 4)
+            b.close()
+    return {"unit": "us/step", "workload": "2 x 512 inextensible rods (catheter r=1 mm E=2 GPa, guidewire "
+                                           "r=0.45 mm E=60 GPa), one thread block per pair", "us_per_step": out}
+
+
 def cpu_baseline_single(seconds=10.0):
     """The FP64 oracle as it stands, one host core, on the 512-element guidewire."""
     import oracle
@@ -419,6 +450,7 @@ def main_ours(args):
     corde.load()
     single = run_single_rod(args, torch, corde, W, rank)
     batched = run_batched(args, torch, corde, W, rank, world) if not args.skip_batched else None
+    pair = run_pair(args, torch, corde, W) if not args.skip_pair else None
     adjoint = None
     if not args.skip_adjoint:
         adjoint = {"single": run_adjoint(args, torch, corde, W, 1), "batched": run_adjoint(args, torch, corde, W, 256)}
@@ -500,6 +532,8 @@ def main_ours(args):
             }
         if adjoint is not None:
             out["adjoint"] = adjoint
+        if pair is not None:
+            out["pair"] = pair
         print(json.dumps(out), flush=True)
     _barrier(torch)
     if world > 1:
@@ -561,6 +595,7 @@ def main():
     ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--skip-cpu-batched", action="store_true")
     ap.add_argument("--skip-adjoint", action="store_true")
+    ap.add_argument("--skip-pair", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

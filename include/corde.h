@@ -94,10 +94,22 @@ int rod_create(int n_rods, const RodParams* params, const float* pos, const floa
 
 /* Advance every rod by n_steps time steps in one persistent launch per kernel variant
  * of the handle's plan (one launch for a single rod).  drive: [n_rods][8] device
- * pointer (v_x v_y v_z _ w_x w_y w_z _), the base velocity and body angular velocity
- * held for the whole call, or NULL to use the values last given to rod_set_input
- * (initially zero).  n_steps >= 0. */
+ * pointer (v_x v_y v_z beta w_x w_y w_z _), the base velocity and body angular velocity
+ * held for the whole call (beta: binding offset of an inner rod, see rod_bind), or NULL
+ * to use the values last given to rod_set_input (initially zero).  n_steps >= 0. */
 int rod_step(rod_handle h, int n_steps, const float* drive, void* stream);
+
+/* Bind rod `inner` (guidewire) inside rod `outer` (catheter) of the same handle as a pair
+ * stepped together in one thread block (Section 3.4).  mode 0: no interaction (v0);
+ * 1: one-way binding, the outer rod is not moved (v1); 2: two-way binding (v2).  Binding
+ * constraints are distance constraints of rest length zero (Section 2.1 "Constraints"),
+ * applied after every constraint iteration in two colors: inner node i is bound to the
+ * outer centreline point at arclength (i + beta) l0, where beta is slot 3 of the inner
+ * rod's drive row (its insertion relative to the outer rod, in segments; read once per
+ * rod_step).  Both rods must be inextensible with equal l0, dt and n_iters and at most
+ * 1024 nodes; a rod can be in one pair.  Pairs are not supported by rod_rollout and
+ * rod_adjoint.  Synchronous (rebuilds the launch plan). */
+int rod_bind(rod_handle h, int outer, int inner, int mode);
 
 /* Copy the drive input [n_rods][8] (host or device) into the handle. */
 int rod_set_input(rod_handle h, const float* drive, void* stream);

@@ -71,8 +71,10 @@ def lib():
             L.oracle_count_flops.argtypes = [_P, _D, _D, _D, ctypes.c_int]
             L.oracle_count_flops.restype = ctypes.c_int64
             L.oracle_step_batch.argtypes = [ctypes.c_int, _P, _D, _D, _D, _D, _D, ctypes.c_int]
+            L.oracle_step_pair.argtypes = [_P, _D, _D, _D, _D, _D, _D, _P, _D, _D, _D, _D, _D, _D, ctypes.c_int,
+                                           ctypes.c_double, ctypes.c_int]
             for name in ("oracle_derive", "oracle_darboux", "oracle_energy", "oracle_forces", "oracle_step",
-                         "oracle_rollout", "oracle_rollout_jvp", "oracle_step_batch"):
+                         "oracle_rollout", "oracle_rollout_jvp", "oracle_step_batch", "oracle_step_pair"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -237,3 +239,16 @@ def step_batch(rods, states, n_steps) -> int:
         no += n
         fo += n - 1
     return threads
+
+
+def step_pair(outer, s_outer, inner, s_inner, mode, beta, n_steps=1, drive_outer=None, drive_inner=None):
+    """Advance copies of an outer/inner rod pair (catheter, guidewire) with binding mode
+    0/1/2 and offset beta (inner node i at outer arclength (i + beta) l0)."""
+    so = {k: _arr(v).copy() for k, v in s_outer.items()}
+    si = {k: _arr(v).copy() for k, v in s_inner.items()}
+    _check(lib().oracle_step_pair(ctypes.byref(params(outer)), _ptr(_arr(outer.rest_quat)), _ptr(so["pos"]),
+                                  _ptr(so["quat"]), _ptr(so["vel"]), _ptr(so["omega"]), _ptr(_arr(drive_outer)),
+                                  ctypes.byref(params(inner)), _ptr(_arr(inner.rest_quat)), _ptr(si["pos"]),
+                                  _ptr(si["quat"]), _ptr(si["vel"]), _ptr(si["omega"]), _ptr(_arr(drive_inner)),
+                                  int(mode), float(beta), int(n_steps)), "oracle_step_pair")
+    return so, si

@@ -345,24 +345,23 @@ template <class T> static inline V3<T> torque_from_gradient(Q4<T> q, Q4<T> g) {
 
 // ------------------------------------------------------------------ the time step
 
-// One time step, Fig. 5 order.  drive = [v_x v_y v_z . w_x w_y w_z .] of the kinematic
-// base (node 0, frame 0).  f_ext (N x 3, world) and tau_ext (M x 3, body) are optional
-// external loads (the "apply external forces and torques" line).
+// Fig. 5, first lines: external forces and torques (gravity with the physical mass,
+// optional loads), Cosserat elastic forces and torques, and their integration into
+// velocities (points as particles, frames as rigid bodies), with Rayleigh damping applied
+// implicitly: x <- (x + dt a) / (1 + alpha dt).  drive = [v_x v_y v_z . w_x w_y w_z .]
+// of the kinematic base (node 0, frame 0).  f_ext (N x 3, world) and tau_ext (M x 3,
+// body) are optional external loads.
 template <class T>
-static void step(const OracleParams& p, const Derived& d, const Material<T>& mat, State<T>& s,
-                 const double* drive, const double* f_ext, const double* tau_ext) {
+static void integrate_forces(const OracleParams& p, const Derived& d, const Material<T>& mat, State<T>& s,
+                             const double* drive, const double* f_ext, const double* tau_ext) {
   const double dt = p.dt;
-  // External forces and torques: gravity with the physical mass, optional loads.
   std::vector<V3<T>> Fext(d.N), F;
   std::vector<Q4<T>> g;
   for (int i = 0; i < d.N; ++i) {
     Fext[i] = v3(T(d.m[i] * p.gravity[0]), T(d.m[i] * p.gravity[1]), T(d.m[i] * p.gravity[2]));
     if (f_ext) Fext[i] = Fext[i] + v3(T(f_ext[3 * i]), T(f_ext[3 * i + 1]), T(f_ext[3 * i + 2]));
   }
-  // Cosserat elastic forces and torques.
   elastic_gradients(p, d, mat, s, F, g);
-  // Integrate forces and torques into velocities (points as particles, frames as rigid
-  // bodies), Rayleigh damping applied implicitly: x <- (x + dt a) / (1 + alpha dt).
   const double damp = 1.0 / (1.0 + p.damping_alpha * dt);
   for (int i = 0; i < d.N; ++i) {
     if (d.w[i] == 0.0) continue;
@@ -383,30 +382,35 @@ static void step(const OracleParams& p, const Derived& d, const Material<T>& mat
     s.v[0] = v3(T(drive ? drive[0] : 0.0), T(drive ? drive[1] : 0.0), T(drive ? drive[2] : 0.0));
     if (d.M > 0) s.om[0] = v3(T(drive ? drive[4] : 0.0), T(drive ? drive[5] : 0.0), T(drive ? drive[6] : 0.0));
   }
-  // Constraint iterations (inextensible rod): distance constraints C_d, predictive
-  // impulses, red-black order.  lambda = -C / (dt (w_a + w_b)) with C = |d| - l0,
-  // d = (r_b + dt v_b) - (r_a + dt v_a), n = d / |d|.
-  if (p.inextensible) {
-    for (int it = 0; it < p.n_iters; ++it) {
-      for (int parity = 0; parity < 2; ++parity) {
-        for (int j = parity; j < d.M; j += 2) {
-          const int a = j, b = j + 1;
-          const double W = d.w[a] + d.w[b];
-          if (W == 0.0) continue;
-          V3<T> pa = s.r[a] + dt * s.v[a];
-          V3<T> pb = s.r[b] + dt * s.v[b];
-          V3<T> dd = pb - pa;
-          T len = norm(dd);
-          T C = len - T(d.l0);
-          V3<T> n = (T(1.0) / len) * dd;
-          T lam = -C / T(dt * W);
-          s.v[a] = s.v[a] - (T(d.w[a]) * lam) * n;
-          s.v[b] = s.v[b] + (T(d.w[b]) * lam) * n;
-        }
-      }
-    }
+}
+
+// One half-sweep of the distance constraints C_d (inextensible rod, Section 2.1
+// "Constraints"): every segment j with j % 2 == parity gets a predictive impulse,
+// lambda = -C / (dt (w_a + w_b)) with C = |d| - l0, d = (r_b + dt v_b) - (r_a + dt v_a),
+// n = d / |d|, v_a -= w_a lambda n, v_b += w_b lambda n.
+template <class T>
+static void distance_sweep(const OracleParams& p, const Derived& d, State<T>& s, int parity) {
+  const double dt = p.dt;
+  for (int j = parity; j < d.M; j += 2) {
+    const int a = j, b = j + 1;
+    const double W = d.w[a] + d.w[b];
+    if (W == 0.0) continue;
+    V3<T> pa = s.r[a] + dt * s.v[a];
+    V3<T> pb = s.r[b] + dt * s.v[b];
+    V3<T> dd = pb - pa;
+    T len = norm(dd);
+    T C = len - T(d.l0);
+    V3<T> n = (T(1.0) / len) * dd;
+    T lam = -C / T(dt * W);
+    s.v[a] = s.v[a] - (T(d.w[a]) * lam) * n;
+    s.v[b] = s.v[b] + (T(d.w[b]) * lam) * n;
   }
-  // Integrate linear and angular velocity (semi-implicit Euler).
+}
+
+// Fig. 5, last line: semi-implicit Euler integration of linear and angular velocity.
+template <class T>
+static void integrate_positions(const OracleParams& p, const Derived& d, State<T>& s) {
+  const double dt = p.dt;
   for (int i = 0; i < d.N; ++i) s.r[i] = s.r[i] + dt * s.v[i];
   for (int j = 0; j < d.M; ++j) {
     Q4<T> dq = qmul(s.q[j], qpure(s.om[j]));
@@ -414,6 +418,77 @@ static void step(const OracleParams& p, const Derived& d, const Material<T>& mat
     T nn = sqrt(qdot(qn, qn));
     s.q[j] = qscale(T(1.0) / nn, qn);
   }
+}
+
+// One time step of one rod, Fig. 5 order: forces, then n_iters iterations of the
+// red-black distance sweeps (even segments, then odd), then the position update.
+template <class T>
+static void step(const OracleParams& p, const Derived& d, const Material<T>& mat, State<T>& s,
+                 const double* drive, const double* f_ext, const double* tau_ext) {
+  integrate_forces(p, d, mat, s, drive, f_ext, tau_ext);
+  if (p.inextensible) {
+    for (int it = 0; it < p.n_iters; ++it) {
+      distance_sweep(p, d, s, 0);
+      distance_sweep(p, d, s, 1);
+    }
+  }
+  integrate_positions(p, d, s);
+}
+
+// One color of the binding constraints C_b (Section 2.1 "Constraints": distance
+// constraints of rest length zero that keep two rods together; Section 3.4: v1 one-way,
+// the outer rod is not moved; v2 two-way).  Inner node i with i % 2 == color is bound to
+// the outer rod's centreline point at arclength (i + beta) l0 (both rods share l0):
+// segment k = floor(i + beta), fraction a = (i + beta) - k, point p = (1-a) r_k + a r_{k+1}.
+// Predictive vector impulse making (r_i + dt v_i) - (p + dt v_p) vanish:
+// lambda = -d / (dt w_eff), w_eff = w_i (+ (1-a)^2 w_k + a^2 w_{k+1} in v2).
+template <class T>
+static void binding_color(const OracleParams& po, const Derived& dout, State<T>& so, const Derived& din,
+                          State<T>& si, int mode, double beta, int color) {
+  const double dt = po.dt;
+  const double kb = std::floor(beta);
+  const double a = beta - kb;
+  for (int i = color; i < din.N; i += 2) {
+    const double kk = (double)i + kb;
+    if (kk < 0.0 || kk > (double)(dout.N - 2)) continue;
+    const int k = (int)kk;
+    const double wi = din.w[i];
+    const double wk = mode == 2 ? dout.w[k] : 0.0, wk1 = mode == 2 ? dout.w[k + 1] : 0.0;
+    const double weff = wi + (1.0 - a) * (1.0 - a) * wk + a * a * wk1;
+    if (weff == 0.0) continue;
+    V3<T> pc = (1.0 - a) * so.r[k] + a * so.r[k + 1];
+    V3<T> vc = (1.0 - a) * so.v[k] + a * so.v[k + 1];
+    V3<T> dd = (si.r[i] + dt * si.v[i]) - (pc + dt * vc);
+    V3<T> lam = (-1.0 / (dt * weff)) * dd;
+    si.v[i] = si.v[i] + wi * lam;
+    if (mode == 2) {
+      so.v[k] = so.v[k] - ((1.0 - a) * wk) * lam;
+      so.v[k + 1] = so.v[k + 1] - (a * wk1) * lam;
+    }
+  }
+}
+
+// One time step of an outer/inner rod pair (catheter and guidewire, Section 3.4): both
+// rods' forces, then per constraint iteration both rods' distance sweeps followed by the
+// two binding colors (mode 0: none), then both position updates.
+template <class T>
+static void step_pair(const OracleParams& po, const Derived& dout, const Material<T>& mo, State<T>& so,
+                      const double* drive_o, const OracleParams& pi, const Derived& din, const Material<T>& mi,
+                      State<T>& si, const double* drive_i, int mode, double beta) {
+  integrate_forces(po, dout, mo, so, drive_o, nullptr, nullptr);
+  integrate_forces(pi, din, mi, si, drive_i, nullptr, nullptr);
+  for (int it = 0; it < po.n_iters; ++it) {
+    distance_sweep(po, dout, so, 0);
+    distance_sweep(po, dout, so, 1);
+    distance_sweep(pi, din, si, 0);
+    distance_sweep(pi, din, si, 1);
+    if (mode != 0) {
+      binding_color(po, dout, so, din, si, mode, beta, 0);
+      binding_color(po, dout, so, din, si, mode, beta, 1);
+    }
+  }
+  integrate_positions(po, dout, so);
+  integrate_positions(pi, din, si);
 }
 
 // ------------------------------------------------------------------ marshalling
@@ -613,6 +688,30 @@ int oracle_rollout_jvp(const OracleParams* p, const double* rest_quat, const dou
       if (dtraj) { dtraj[o] = s.r[i].x.d; dtraj[o + 1] = s.r[i].y.d; dtraj[o + 2] = s.r[i].z.d; }
     }
   }
+  return 0;
+}
+
+// n_steps time steps of an outer/inner rod pair with binding mode 0, 1 or 2 (v0/v1/v2 of
+// Section 3.4) and binding offset beta (inner node i sits at outer arclength (i + beta) l0).
+// Both rods must be inextensible with the same l0, dt and n_iters.  State arrays of both
+// rods are advanced in place; drives are 8 doubles each or NULL.
+int oracle_step_pair(const OracleParams* po, const double* rest_o, double* pos_o, double* quat_o, double* vel_o,
+                     double* om_o, const double* drive_o, const OracleParams* pi, const double* rest_i,
+                     double* pos_i, double* quat_i, double* vel_i, double* om_i, const double* drive_i, int mode,
+                     double beta, int n_steps) {
+  if (!valid(po) || !valid(pi) || mode < 0 || mode > 2 || n_steps < 0) return -1;
+  if (!po->inextensible || !pi->inextensible || po->n_iters != pi->n_iters || po->dt != pi->dt) return -1;
+  Derived dout = derive(*po), din = derive(*pi);
+  if (std::fabs(dout.l0 - din.l0) > 1e-12 * dout.l0) return -1;
+  Material<double> mo, mi;
+  load_material(dout, rest_o, nullptr, mo);
+  load_material(din, rest_i, nullptr, mi);
+  State<double> so, si;
+  load_state(dout, pos_o, quat_o, vel_o, om_o, so);
+  load_state(din, pos_i, quat_i, vel_i, om_i, si);
+  for (int k = 0; k < n_steps; ++k) step_pair(*po, dout, mo, so, drive_o, *pi, din, mi, si, drive_i, mode, beta);
+  store_state(dout, so, pos_o, quat_o, vel_o, om_o);
+  store_state(din, si, pos_i, quat_i, vel_i, om_i);
   return 0;
 }
 

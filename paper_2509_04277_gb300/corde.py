@@ -49,6 +49,7 @@ SIGNATURES = {
                                   ctypes.POINTER(_VP)]),
     "rod_step": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP]),
     "rod_set_input": (ctypes.c_int, [_VP, _VP, _VP]),
+    "rod_bind": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "rod_get_state": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "rod_set_state": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "rod_info": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64)]),
@@ -132,6 +133,10 @@ def rod_create(params, pos, quat, rest_quat=None, vel=None, omega=None, stiff_mu
 
 def rod_step(h, n_steps, drive=None, stream=None):
     _check(load().rod_step(h, int(n_steps), _ptr(drive), _stream(stream)), "rod_step")
+
+
+def rod_bind(h, outer, inner, mode):
+    _check(load().rod_bind(h, int(outer), int(inner), int(mode)), "rod_bind")
 
 
 def rod_set_input(h, drive, stream=None):
@@ -332,6 +337,9 @@ class RodBatch:
         out = np.zeros((self.n_rods, 2), dtype=np.int32)
         rod_get_plan(self.handle, out)
         return out
+
+    def bind(self, outer, inner, mode):
+        rod_bind(self.handle, outer, inner, mode)
 
     def set_plan(self, ept, nt):
         rod_set_plan(self.handle, ept, nt)

@@ -94,6 +94,7 @@ struct corde_rods {
   std::vector<int> n_nodes, off;
   std::vector<int> flags;
   std::vector<int> n_iters;
+  std::vector<double> dt;
   std::vector<double> derived;  // [n_rods][16]
   RodDev* d_rods = nullptr;
   double* d_derived = nullptr;
@@ -110,6 +111,14 @@ struct corde_rods {
   size_t seg_cap = 0;
   int ro_steps = 0, ro_every = 0;
   std::vector<Bin> adj_bins;  // variant = threads per block
+  // catheter/guidewire pairs
+  std::vector<int4> pairs;     // (outer, inner, mode, 0)
+  std::vector<char> paired;    // per rod
+  struct PairBin {
+    int ept, nt, count;
+    int4* d_pairs;
+  };
+  std::vector<PairBin> pair_bins;
 };
 
 namespace {
@@ -303,7 +312,7 @@ int build_bins(rod_handle h) {
   for (size_t vi = 0; vi < vs.size(); ++vi) {
     std::vector<int> rods;
     for (int r = 0; r < h->n_rods; ++r)
-      if (h->plan[r] == (int)vi) rods.push_back(r);
+      if (h->plan[r] == (int)vi && !(r < (int)h->paired.size() && h->paired[r])) rods.push_back(r);
     if (rods.empty()) continue;
     std::stable_sort(rods.begin(), rods.end(), [&](int a, int b) { return h->n_nodes[a] > h->n_nodes[b]; });
     Bin b{(int)vi, (int)rods.size(), nullptr};
@@ -442,7 +451,11 @@ int rod_create(int n_rods, const RodParams* params, const float* pos, const floa
   h->n_nodes = nn;
   h->off = off;
   h->n_iters.resize(n_rods);
-  for (int r = 0; r < n_rods; ++r) h->n_iters[r] = params[r].inextensible ? params[r].n_iters : 0;
+  h->dt.resize(n_rods);
+  for (int r = 0; r < n_rods; ++r) {
+    h->n_iters[r] = params[r].inextensible ? params[r].n_iters : 0;
+    h->dt[r] = params[r].dt;
+  }
   const int64_t F = E - n_rods, J = E - 2 * (int64_t)n_rods;
   std::vector<int> elem_rod(E);
   for (int r = 0; r < n_rods; ++r)
@@ -529,7 +542,28 @@ int rod_step(rod_handle h, int n_steps, const float* drive, void* stream) {
       return fail(CORDE_ERR_ARG, "drive must be 16-byte aligned device, managed or mapped pinned host memory");
     d = reinterpret_cast<const float4*>(dp);
   }
-  return launch_bins(h, h->bins, n_steps, d, (cudaStream_t)stream);
+  if (int rc = launch_bins(h, h->bins, n_steps, d, (cudaStream_t)stream)) return rc;
+  if (!h->pair_bins.empty()) {
+    StepArgs a;
+    a.rods = h->d_rods;
+    a.work = nullptr;
+    a.x4 = h->d_x;
+    a.v4 = h->d_v;
+    a.q4 = h->d_q;
+    a.o4 = h->d_o;
+    a.u4 = h->d_u;
+    a.k4 = h->d_k;
+    a.drive = d;
+    a.n_steps = n_steps;
+    a.traj = nullptr;
+    a.n_elem = h->n_elem;
+    for (const auto& pb : h->pair_bins) {
+      cudaError_t e = launch_pair(pb.ept, pb.nt, a, pb.d_pairs, pb.count, (cudaStream_t)stream);
+      if (e != cudaSuccess) return fail(CORDE_ERR_CUDA, std::string("pair launch: ") + cudaGetErrorString(e));
+      ++h->last_launches;
+    }
+  }
+  return CORDE_OK;
 }
 
 int rod_set_input(rod_handle h, const float* drive, void* stream) {
@@ -673,7 +707,7 @@ int rod_autotune(rod_handle h, int n_steps, void* stream) {
     std::vector<int> rods;
     int nmax = 0;
     for (int r = 0; r < h->n_rods; ++r)
-      if (cls[r] == c) {
+      if (cls[r] == c && !(r < (int)h->paired.size() && h->paired[r])) {
         rods.push_back(r);
         nmax = std::max(nmax, h->n_nodes[r]);
       }
@@ -713,6 +747,57 @@ int rod_autotune(rod_handle h, int n_steps, void* stream) {
   return build_bins(h);
 }
 
+// Pair kernel layout: two elements per thread up to 512 nodes per rod, four up to 1024,
+// the smallest power-of-two group (>= 32 threads) holding the longer rod.
+static int pair_layout(int n, int* ept, int* nt) {
+  *ept = n <= 512 ? 2 : 4;
+  *nt = 32;
+  while (*nt * *ept < n) *nt *= 2;
+  return *nt <= 256 ? CORDE_OK : CORDE_ERR_UNSUPPORTED;
+}
+
+static int build_pair_bins(rod_handle h) {
+  for (auto& pb : h->pair_bins) cudaFree(pb.d_pairs);
+  h->pair_bins.clear();
+  for (int ept : {2, 4})
+    for (int nt = 32; nt <= 256; nt *= 2) {
+      std::vector<int4> ps;
+      for (const int4& p : h->pairs) {
+        int e = 0, t = 0;
+        pair_layout(std::max(h->n_nodes[p.x], h->n_nodes[p.y]), &e, &t);
+        if (e == ept && t == nt) ps.push_back(p);
+      }
+      if (ps.empty()) continue;
+      corde_rods::PairBin pb{ept, nt, (int)ps.size(), nullptr};
+      CK(cudaMalloc(&pb.d_pairs, ps.size() * sizeof(int4)));
+      CK(cudaMemcpy(pb.d_pairs, ps.data(), ps.size() * sizeof(int4), cudaMemcpyHostToDevice));
+      h->pair_bins.push_back(pb);
+    }
+  return CORDE_OK;
+}
+
+int rod_bind(rod_handle h, int outer, int inner, int mode) {
+  if (int rc = check_handle(h)) return rc;
+  if (outer < 0 || inner < 0 || outer >= h->n_rods || inner >= h->n_rods || outer == inner)
+    return fail(CORDE_ERR_ARG, "rod_bind: bad rod indices");
+  if (mode < 0 || mode > 2) return fail(CORDE_ERR_ARG, "rod_bind: mode must be 0, 1 or 2");
+  if (h->paired.empty()) h->paired.assign(h->n_rods, 0);
+  if (h->paired[outer] || h->paired[inner]) return fail(CORDE_ERR_ARG, "rod_bind: rod already in a pair");
+  const double* a = &h->derived[16 * (size_t)outer];
+  const double* b = &h->derived[16 * (size_t)inner];
+  if (h->n_iters[outer] != h->n_iters[inner] || h->n_iters[outer] == 0)
+    return fail(CORDE_ERR_ARG, "rod_bind: both rods must be inextensible with the same n_iters");
+  if (h->dt[outer] != h->dt[inner]) return fail(CORDE_ERR_ARG, "rod_bind: both rods must share dt");
+  if (std::fabs(a[0] - b[0]) > 1e-9 * a[0]) return fail(CORDE_ERR_ARG, "rod_bind: both rods must share l0");
+  int e = 0, t = 0;
+  if (pair_layout(std::max(h->n_nodes[outer], h->n_nodes[inner]), &e, &t) != CORDE_OK)
+    return fail(CORDE_ERR_UNSUPPORTED, "rod_bind: rods of at most 1024 nodes");
+  h->pairs.push_back(make_int4(outer, inner, mode, 0));
+  h->paired[outer] = h->paired[inner] = 1;
+  if (int rc = build_bins(h)) return rc;
+  return build_pair_bins(h);
+}
+
 // Bins of the adjoint layout: two elements per thread, the smallest power-of-two block
 // (>= 32 threads) holding the rod.  Bin.variant is the index of the matching <2, nt> step
 // variant, so that rod_rollout and the adjoint's recomputation run the same kernel code.
@@ -745,6 +830,7 @@ static bool adjoint_capable(rod_handle h) {
 int rod_rollout(rod_handle h, int n_steps, int ckpt_every, float* pos_traj, void* stream) {
   if (int rc = check_handle(h)) return rc;
   if (n_steps < 1 || ckpt_every < 1) return fail(CORDE_ERR_ARG, "n_steps and ckpt_every must be >= 1");
+  if (!h->pairs.empty()) return fail(CORDE_ERR_UNSUPPORTED, "rod_rollout: bound pairs are not supported");
   float4* traj = nullptr;
   if (pos_traj) {
     const void* dp = nullptr;
@@ -783,6 +869,7 @@ int rod_adjoint(rod_handle h, const float* dL_dpos_traj, float* dL_dK, float* dL
                 float* dL_dpos0, float* dL_dquat0, float* dL_domega0, void* stream) {
   if (int rc = check_handle(h)) return rc;
   if (h->ro_steps < 1) return fail(CORDE_ERR_ARG, "rod_adjoint needs a preceding rod_rollout");
+  if (!h->pairs.empty()) return fail(CORDE_ERR_UNSUPPORTED, "rod_adjoint: bound pairs are not supported");
   for (int r = 0; r < h->n_rods; ++r)
     if (h->n_nodes[r] > kAdjointMaxNodes)
       return fail(CORDE_ERR_UNSUPPORTED, "the adjoint kernel holds rods of at most " +
@@ -854,6 +941,7 @@ void rod_destroy(rod_handle h) {
   cudaFree(h->d_drive); cudaFree(h->d_elem_rod);
   cudaFree(h->d_ckpt); cudaFree(h->d_seg);
   for (auto& b : h->adj_bins) cudaFree(b.d_work);
+  for (auto& pb : h->pair_bins) cudaFree(pb.d_pairs);
   delete h;
 }
 

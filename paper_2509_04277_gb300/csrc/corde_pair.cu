@@ -1,0 +1,192 @@
+// Catheter/guidewire pair in one thread block (Section 3.4): the outer rod (catheter)
+// on threads [0, NT), the inner rod (guidewire) on threads [NT, 2 NT), stepped in
+// lockstep by the shared step body, with the binding constraints C_b (Section 2.1
+// "Constraints": distance constraints of rest length zero) applied after every
+// iteration's odd distance sweep.
+//
+// Binding reading: both rods share the rest segment length l0; inner node i is bound to
+// the outer centreline point at arclength (i + beta) l0 - segment k = floor(i + beta),
+// fraction a = (i + beta) - k - when 0 <= k <= N_outer - 2.  beta, the inner rod's
+// insertion relative to the outer rod in segments, is a per-launch input (slot 3 of the
+// inner rod's drive row).  Mode 1 (v1, one-way): the outer rod is not moved by binding.
+// Mode 2 (v2, two-way): the impulse is shared by inverse mass.  Mode 0 (v0): no binding.
+// The impulses are applied in two colors (even inner nodes, then odd), so that within a
+// color no two constraints touch the same outer node; the outer rod's velocities are
+// staged in shared memory for the inner threads to read (and, in v2, to update).
+#include "corde_step.cuh"
+#include "corde_variants.cuh"
+
+namespace corde {
+namespace {
+
+template <int SYNC_NT>
+struct PairHook {
+  int group;       // 0 outer, 1 inner
+  int t;           // thread index within the group
+  int mode;        // 0, 1, 2
+  int k0;          // floor(beta)
+  float alpha;     // beta - k0
+  int n_out;       // outer nodes
+  int n_in;        // inner nodes
+  float dt;
+  float4* out_r;   // [capacity] outer positions and inverse masses (once per step)
+  float4* out_v;   // [capacity] outer velocities (every iteration)
+
+  template <int EPT>
+  __device__ __forceinline__ void before_iterations(const float3 (&r)[EPT], const float (&w)[EPT]) const {
+    if (mode == 0 || group != 0) return;
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) {
+      const int i = t * EPT + e;
+      if (i < n_out) out_r[i] = make_float4(r[e].x, r[e].y, r[e].z, w[e]);
+    }
+  }
+
+  template <int EPT>
+  __device__ __forceinline__ void after_odd(const float3 (&r)[EPT], float3 (&v)[EPT], const float (&w)[EPT]) const {
+    if (mode == 0) return;
+    if (group == 0) {
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) {
+        const int i = t * EPT + e;
+        if (i < n_out) out_v[i] = make_float4(v[e].x, v[e].y, v[e].z, 0.f);
+      }
+    }
+    block_sync<SYNC_NT>();
+    for (int color = 0; color < 2; ++color) {
+      if (group == 1) {
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) {
+          const int i = t * EPT + e;  // EPT is even: node parity = e parity
+          if ((e & 1) != color || i >= n_in) continue;
+          const int k = i + k0;
+          if (k < 0 || k > n_out - 2) continue;
+          const float4 rk = out_r[k], rk1 = out_r[k + 1];
+          const float a = alpha, b = 1.f - alpha;
+          const float wk = mode == 2 ? rk.w : 0.f, wk1 = mode == 2 ? rk1.w : 0.f;
+          const float weff = w[e] + b * b * wk + a * a * wk1;
+          if (!(weff > 0.f)) continue;
+          const float4 vk = out_v[k], vk1 = out_v[k + 1];
+          const float3 pc = f3(b * rk.x + a * rk1.x, b * rk.y + a * rk1.y, b * rk.z + a * rk1.z);
+          const float3 vc = f3(b * vk.x + a * vk1.x, b * vk.y + a * vk1.y, b * vk.z + a * vk1.z);
+          const float3 d = (r[e] - pc) + dt * (v[e] - vc);
+          const float3 lam = (-1.f / (dt * weff)) * d;
+          v[e] += w[e] * lam;
+          if (mode == 2) {
+            const float3 dk = (b * wk) * lam, dk1 = (a * wk1) * lam;
+            out_v[k] = make_float4(vk.x - dk.x, vk.y - dk.y, vk.z - dk.z, 0.f);
+            out_v[k + 1] = make_float4(vk1.x - dk1.x, vk1.y - dk1.y, vk1.z - dk1.z, 0.f);
+          }
+        }
+      }
+      if (mode == 2) block_sync<SYNC_NT>();
+    }
+    if (mode == 2 && group == 0) {
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) {
+        const int i = t * EPT + e;
+        if (i < n_out) v[e] = f3(out_v[i]);
+      }
+    }
+  }
+};
+
+template <int EPT, int NT>
+constexpr int pair_smem_bytes() {
+  return (2 * (2 * EPT * NT + 2 * kHaloSlots * NT) + 2 * EPT * NT) * (int)sizeof(float4);
+}
+
+template <int EPT, int NT>
+__global__ void __launch_bounds__(2 * NT)
+pair_kernel(const RodDev* __restrict__ rods, const int4* __restrict__ pairs, float4* __restrict__ x4,
+            float4* __restrict__ v4, float4* __restrict__ q4, float4* __restrict__ o4,
+            const float4* __restrict__ u4, const float4* __restrict__ k4, const float4* __restrict__ drive,
+            int n_steps) {
+  extern __shared__ float4 smem[];
+  const int group = threadIdx.x / NT;
+  const int t = threadIdx.x - group * NT;
+  const int4 pr = pairs[blockIdx.x];  // (outer rod, inner rod, mode, 0)
+  const int rid = group == 0 ? pr.x : pr.y;
+  const RodDev R = rods[rid];
+  float4* gs = smem + group * (2 * EPT * NT + 2 * kHaloSlots * NT);
+  float4* par_u = gs;
+  float4* par_k = gs + EPT * NT;
+  float4* halo = gs + 2 * EPT * NT;
+  float4* out_r = smem + 2 * (2 * EPT * NT + 2 * kHaloSlots * NT);
+  float4* out_v = out_r + EPT * NT;
+
+  float3 r[EPT], v[EPT], om[EPT];
+  float4 q[EPT];
+  float w[EPT];
+  load_rod<EPT, NT>(R, t, x4, v4, q4, o4, u4, k4, r, v, q, om, w, par_u, par_k);
+  float3 v_drive = zero3(), w_drive = zero3();
+  float beta = 0.f;
+  if (drive != nullptr) {
+    const float4 d0 = drive[2 * rid];
+    v_drive = f3(d0);
+    w_drive = f3(drive[2 * rid + 1]);
+    beta = drive[2 * pr.y].w;
+  }
+  PairHook<2 * NT> hook;
+  hook.group = group;
+  hook.t = t;
+  hook.mode = pr.z;
+  hook.k0 = (int)floorf(beta);
+  hook.alpha = beta - floorf(beta);
+  hook.n_out = rods[pr.x].n;
+  hook.n_in = rods[pr.y].n;
+  hook.dt = R.dt;
+  hook.out_r = out_r;
+  hook.out_v = out_v;
+
+  int xc = 0;
+  for (int step = 0; step < n_steps; ++step)
+    step_body<EPT, NT, false, 2 * NT, PairHook<2 * NT>>(R, t, r, v, q, om, w, par_u, par_k, halo, xc, v_drive,
+                                                        w_drive, nullptr, nullptr, hook);
+  const int e0 = t * EPT;
+#pragma unroll
+  for (int e = 0; e < EPT; ++e) {
+    const int i = e0 + e;
+    if (i < R.n) {
+      x4[R.off + i] = make_float4(r[e].x, r[e].y, r[e].z, w[e]);
+      v4[R.off + i] = make_float4(v[e].x, v[e].y, v[e].z, 0.f);
+      q4[R.off + i] = q[e];
+      o4[R.off + i] = make_float4(om[e].x, om[e].y, om[e].z, 0.f);
+    }
+  }
+}
+
+template <int EPT, int NT>
+cudaError_t launch_pair_t(const StepArgs& a, const int4* pairs, int n_pairs, cudaStream_t s) {
+  constexpr int smem = pair_smem_bytes<EPT, NT>();
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(pair_kernel<EPT, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+  }
+  pair_kernel<EPT, NT><<<n_pairs, 2 * NT, smem, s>>>(a.rods, pairs, a.x4, a.v4, a.q4, a.o4, a.u4, a.k4, a.drive,
+                                                      a.n_steps);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_pair(int ept, int nt, const StepArgs& a, const int4* pairs, int n_pairs, cudaStream_t s) {
+  if (ept == 2) {
+    switch (nt) {
+      case 32: return launch_pair_t<2, 32>(a, pairs, n_pairs, s);
+      case 64: return launch_pair_t<2, 64>(a, pairs, n_pairs, s);
+      case 128: return launch_pair_t<2, 128>(a, pairs, n_pairs, s);
+      case 256: return launch_pair_t<2, 256>(a, pairs, n_pairs, s);
+    }
+  } else if (ept == 4) {
+    switch (nt) {
+      case 32: return launch_pair_t<4, 32>(a, pairs, n_pairs, s);
+      case 64: return launch_pair_t<4, 64>(a, pairs, n_pairs, s);
+      case 128: return launch_pair_t<4, 128>(a, pairs, n_pairs, s);
+      case 256: return launch_pair_t<4, 256>(a, pairs, n_pairs, s);
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace corde

@@ -94,6 +94,16 @@ __device__ __forceinline__ float constraint_factor(float3 ra, float3 va, float3 
   return __fmul_rn(__fmul_rn(-C, il), __frcp_rn(__fmul_rn(dt, wsum)));
 }
 
+// Hook into the constraint loop of step_body: before_iterations() once per step before
+// the sweeps, after_odd() after every iteration's odd sweep.  The plain rod needs none;
+// the catheter/guidewire pair applies its binding constraints there.
+struct NoHook {
+  template <int EPT>
+  __device__ __forceinline__ void before_iterations(const float3 (&)[EPT], const float (&)[EPT]) const {}
+  template <int EPT>
+  __device__ __forceinline__ void after_odd(const float3 (&)[EPT], float3 (&)[EPT], const float (&)[EPT]) const {}
+};
+
 // Neighbour data of one step, kept by the adjoint's recomputation.
 struct StepNeighbours {
   float3 r_next, r_prev;
@@ -110,15 +120,16 @@ constexpr int step_smem_bytes() {
   return (2 * EPT * NT + 2 * kHaloSlots * NT) * (int)sizeof(float4);
 }
 
-// One time step of the rod held by this block.  With STORE, the velocities before every
-// constraint half-sweep are written to sweep_v ([2 n_iters][EPT][NT]) and the neighbour
-// data to *nb (for the adjoint).
-template <int EPT, int NT, bool STORE>
+// One time step of the rod held by NT threads (thread t of the group).  SYNC_NT threads
+// take part in every barrier: NT for one rod per block, more when several rods share a
+// block in lockstep.  With STORE, the velocities before every constraint half-sweep are
+// written to sweep_v ([2 n_iters][EPT][NT]) and the neighbour data to *nb (adjoint).
+template <int EPT, int NT, bool STORE, int SYNC_NT = NT, class Hook = NoHook>
 __device__ __forceinline__ void step_body(const RodDev& R, const int t, float3 (&r)[EPT], float3 (&v)[EPT],
                                           float4 (&q)[EPT], float3 (&om)[EPT], const float (&w)[EPT],
                                           const float4* par_u, const float4* par_k, float4* halo, int& xc,
                                           const float3 v_drive, const float3 w_drive, float4* sweep_v,
-                                          StepNeighbours* nb) {
+                                          StepNeighbours* nb, const Hook& hook = Hook()) {
   const int e0 = t * EPT;
   const int n = R.n;
   const bool inext = (R.flags & F_INEXT) != 0;
@@ -134,7 +145,7 @@ __device__ __forceinline__ void step_body(const RodDev& R, const int t, float3 (
   hb[t] = make_float4(r[0].x, r[0].y, r[0].z, w[0]);
   hb[NT + t] = q[0];
   hb[2 * NT + t] = make_float4(r[EPT - 1].x, r[EPT - 1].y, r[EPT - 1].z, w[EPT - 1]);
-  block_sync<NT>();
+  block_sync<SYNC_NT>();
   float3 r_next = zero3(), r_prev = zero3();
   float w_next = 0.f, w_prev = 0.f;
   float4 q_next = make_float4(0.f, 0.f, 0.f, 1.f);
@@ -197,7 +208,7 @@ __device__ __forceinline__ void step_body(const RodDev& R, const int t, float3 (
   ++xc;
   hb[t] = make_float4(F_carry.x, F_carry.y, F_carry.z, 0.f);
   hb[NT + t] = make_float4(tau_carry.x, tau_carry.y, tau_carry.z, 0.f);
-  block_sync<NT>();
+  block_sync<SYNC_NT>();
   if (t > 0) {
     F[0] += f3(hb[t - 1]);
     tau[0] += f3(hb[NT + t - 1]);
@@ -227,6 +238,7 @@ __device__ __forceinline__ void step_body(const RodDev& R, const int t, float3 (
 
   // ---- distance-constraint iterations (inextensible rod), red-black
   if (inext) {
+    hook.template before_iterations<EPT>(r, w);
     for (int it = 0; it < R.n_iters; ++it) {
       if constexpr (STORE) {
 #pragma unroll
@@ -254,7 +266,7 @@ __device__ __forceinline__ void step_body(const RodDev& R, const int t, float3 (
       ++xc;
       hb[t] = make_float4(v[0].x, v[0].y, v[0].z, 0.f);
       hb[NT + t] = make_float4(v[EPT - 1].x, v[EPT - 1].y, v[EPT - 1].z, 0.f);
-      block_sync<NT>();
+      block_sync<SYNC_NT>();
       // odd segments inside the thread
 #pragma unroll
       for (int k = 0; k + 1 < EPT / 2; ++k) {
@@ -285,6 +297,7 @@ __device__ __forceinline__ void step_body(const RodDev& R, const int t, float3 (
           v[0] += (w[0] * s) * d;
         }
       }
+      hook.template after_odd<EPT>(r, v, w);
     }
   }
 

@@ -48,6 +48,10 @@ int adjoint_smem_bytes(int nt, int n_iters);
 cudaError_t launch_adjoint(int nt, const AdjointArgs& a, int n_blocks, int smem, cudaStream_t s);
 constexpr int kAdjointMaxNodes = 512;
 
+// Catheter/guidewire pairs (corde_pair.cu): pairs[i] = (outer rod, inner rod, mode, 0);
+// ept in {2, 4}, nt (threads per rod) in {32, ..., 256}.
+cudaError_t launch_pair(int ept, int nt, const StepArgs& a, const int4* pairs, int n_pairs, cudaStream_t s);
+
 // Defined in the per-EPT instantiation units.
 extern const StepVariant kStepVariantsE2[];
 extern const int kNumStepVariantsE2;

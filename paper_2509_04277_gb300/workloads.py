@@ -280,3 +280,32 @@ def random_directions(seed: int, n_dirs: int, size: int) -> np.ndarray:
     """Seeded unit directions for directional-derivative checks."""
     d = rng(seed).standard_normal((n_dirs, size))
     return d / np.linalg.norm(d, axis=1, keepdims=True)
+
+
+def catheter_guidewire(n: int = 512, seed: int = 3, beta0: float = -100.25):
+    """The 2 x n catheter/guidewire pair (Section 3.4): both rods 1.5 m long with n nodes
+    (shared segment length), along +x; the guidewire runs inside the catheter, its node i
+    at the catheter arclength (i + beta0) l0 (beta0 < 0: the guidewire base lies behind the
+    catheter base and its proximal part is outside).  Returns (catheter, guidewire)."""
+    cat = catheter(n, seed=seed)
+    gw = guidewire(n, seed=seed + 1)
+    l0 = gw.length / (n - 1)
+    base = (beta0 * l0, 0.0, 0.0)
+    gw2 = straight_rod(n, gw.length, base=base, seg_sigma=1e-3, ang_sigma=1e-3, seed=seed + 1,
+                       radius=gw.radius, E_bend=gw.E_bend, E_stretch=gw.E_stretch, G=gw.G, density=gw.density,
+                       dt=gw.dt, n_iters=gw.n_iters, inextensible=True, clamp=1, damping_alpha=0.0)
+    return cat, gw2
+
+
+def pair_drives(seed: int, n_launches: int, launch_dt: float, l0: float, beta0: float):
+    """Seeded insertion/twist drives of the catheter and guidewire bases (1 kHz samples,
+    zero-order hold per launch) and the binding offset beta of every launch: beta0 plus
+    the guidewire's base displacement relative to the catheter's, in segments (prefix
+    sums of the held velocities).  Returns (drive_catheter, drive_guidewire), each
+    [n_launches, 8]; beta is in slot 3 of the guidewire rows."""
+    dc = sinusoid_drive(seed, n_launches, launch_dt)
+    dg = sinusoid_drive(seed + 7, n_launches, launch_dt)
+    rel = (dg[:, 0] - dc[:, 0]) * launch_dt
+    disp = np.concatenate([[0.0], np.cumsum(rel)[:-1]])
+    dg[:, 3] = beta0 + disp / l0
+    return dc, dg

@@ -381,3 +381,63 @@ def test_flop_count_linear_in_elements():
     a = oracle.count_flops(W.guidewire(64), 2)
     b = oracle.count_flops(W.guidewire(128), 2)
     assert 1.9 < b / a < 2.05
+
+
+# ------------------------------------------------------------------ binding (catheter/guidewire)
+
+
+def test_binding_one_way_puts_inner_nodes_on_outer_centreline():
+    """v1 with a static outer rod: after one step every bound inner node sits exactly on
+    the outer rod's centreline point it is bound to (the last binding color leaves the
+    other color's constraints satisfied because the outer rod does not move)."""
+    cat, gw = W.catheter_guidewire(32, seed=82, beta0=-5.4)
+    so, si = oracle.state_of(cat), oracle.state_of(gw)
+    si["pos"][:, 1] += 1e-3  # lateral offset of the inner rod
+    beta = -5.4
+    so2, si2 = oracle.step_pair(cat, so, gw, si, 1, beta, 1)
+    k0 = int(np.floor(beta))
+    a = beta - k0
+    worst = 0.0
+    for i in range(32):
+        k = i + k0
+        if 0 <= k <= 30:
+            p = (1 - a) * so2["pos"][k] + a * so2["pos"][k + 1]
+            worst = max(worst, np.abs(si2["pos"][i] - p).max())
+    assert worst < 1e-12
+
+
+def test_binding_two_way_conserves_momentum():
+    """v2 on free rods without gravity: binding impulses are equal and opposite, so the
+    pair's total (inertial) momentum is unchanged by a step."""
+    cat, gw = W.catheter_guidewire(24, seed=83, beta0=-3.3)
+    for r in (cat, gw):
+        r.clamp = 0
+    so, si = oracle.state_of(cat), oracle.state_of(gw)
+    g = np.random.default_rng(4)
+    so["vel"] = g.standard_normal(so["vel"].shape) * 0.01
+    si["vel"] = g.standard_normal(si["vel"].shape) * 0.01
+    si["pos"][:, 2] += 5e-4
+
+    def momentum(rod, s):
+        d = oracle.derive(rod)
+        m = np.full(rod.n_nodes, d["mass_scale"] * d["m_interior"])
+        m[0] *= 0.5
+        m[-1] *= 0.5
+        return (m[:, None] * s["vel"]).sum(axis=0)
+
+    p0 = momentum(cat, so) + momentum(gw, si)
+    so2, si2 = oracle.step_pair(cat, so, gw, si, 2, -3.3, 1)
+    p1 = momentum(cat, so2) + momentum(gw, si2)
+    scale = np.abs(momentum(gw, si2) - momentum(gw, si)).max()
+    assert scale > 1e-6  # binding did act
+    np.testing.assert_allclose(p1, p0, atol=1e-12 * max(1.0, scale) + 1e-15)
+
+
+def test_binding_mode_zero_is_two_independent_rods():
+    cat, gw = W.catheter_guidewire(20, seed=84, beta0=-2.5)
+    so, si = oracle.state_of(cat), oracle.state_of(gw)
+    dc = np.array([0.01, 0, 0, 0, 0, 0, 1.0, 0])
+    dg = np.array([0.02, 0, 0, -2.5, 0, 0, -1.0, 0])
+    so2, si2 = oracle.step_pair(cat, so, gw, si, 0, -2.5, 5, drive_outer=dc, drive_inner=dg)
+    np.testing.assert_array_equal(so2["pos"], oracle.step(cat, so, 5, drive=dc)["pos"])
+    np.testing.assert_array_equal(si2["pos"], oracle.step(gw, si, 5, drive=dg)["pos"])
