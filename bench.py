@@ -151,7 +151,10 @@ def run_single_rod(args, torch, corde, W, rank):
     drive_np = W.sinusoid_drive(2 + rank, n_launch_total, STEPS_PER_LAUNCH * rod.dt).astype(np.float32)
     drive = torch.as_tensor(drive_np, device=dev).contiguous()
     b = corde.RodBatch([rod])
-    b.autotune(STEPS_PER_LAUNCH)
+    if args.no_autotune:
+        b.set_plan(2, 256)
+    else:
+        b.autotune(STEPS_PER_LAUNCH)
     plan = [int(x) for x in b.plan()[0]]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -247,7 +250,8 @@ def run_batched(args, torch, corde, W, rank, world):
     n_elem = b.n_elem
     S = args.batched_steps_per_launch
     n_launch = max(1, args.batched_steps // S)
-    b.autotune(S)
+    if not args.no_autotune:
+        b.autotune(S)
     plan = b.plan()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     b.step(S)
@@ -448,6 +452,14 @@ def main_ours(args):
     from paper_2509_04277_gb300 import workloads as W
 
     corde.load()
+    if args.only is not None:
+        part = {"single": lambda: run_single_rod(args, torch, corde, W, rank),
+                "batched": lambda: run_batched(args, torch, corde, W, rank, world),
+                "pair": lambda: run_pair(args, torch, corde, W),
+                "adjoint": lambda: run_adjoint(args, torch, corde, W, 1)}[args.only]()
+        if rank == 0:
+            print(json.dumps({"only": args.only, "result": part}, default=str), flush=True)
+        return
     single = run_single_rod(args, torch, corde, W, rank)
     batched = run_batched(args, torch, corde, W, rank, world) if not args.skip_batched else None
     pair = run_pair(args, torch, corde, W) if not args.skip_pair else None
@@ -596,6 +608,10 @@ def main():
     ap.add_argument("--skip-cpu-batched", action="store_true")
     ap.add_argument("--skip-adjoint", action="store_true")
     ap.add_argument("--skip-pair", action="store_true")
+    ap.add_argument("--only", choices=["single", "batched", "pair", "adjoint"], default=None,
+                    help="run one part only and print its raw result (profiling aid, not a bench line)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="fixed kernel plan (single rod <2, 256>, batch default plan)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
