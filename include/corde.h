@@ -154,7 +154,16 @@ int rod_set_plan(rod_handle h, int ept, int nt);
 int rod_autotune(rod_handle h, int n_steps, void* stream);
 int rod_get_plan(rod_handle h, int* plan);
 
-/* Number of kernel launches the last rod_step enqueued. */
+/* When one rod_step needs several kernel launches (rods of several length bins, bound
+ * pairs), rod_step captures them once into a CUDA graph whose kernels run concurrently
+ * and replays it (re-captured when n_steps or the plan changes; the drive is first copied
+ * into an internal buffer the graph reads).  mode 0: never use a graph; 1: when more than
+ * one launch is needed (default); 2: always.  The first rod_step after a change captures
+ * on an internal stream: do not call it inside a caller's own stream capture. */
+int rod_set_graph_mode(rod_handle h, int mode);
+
+/* Number of kernel launches the last rod_step enqueued (kernel nodes of the graph when
+ * the graph path ran). */
 int rod_last_launch_count(rod_handle h);
 
 /* Forward rollout recorded for the adjoint: n_steps time steps with the drive last given

@@ -60,6 +60,7 @@ SIGNATURES = {
     "rod_autotune": (ctypes.c_int, [_VP, ctypes.c_int, _VP]),
     "rod_get_plan": (ctypes.c_int, [_VP, _VP]),
     "rod_last_launch_count": (ctypes.c_int, [_VP]),
+    "rod_set_graph_mode": (ctypes.c_int, [_VP, ctypes.c_int]),
     "rod_rollout": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP, _VP]),
     "rod_adjoint": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "rod_adjoint_noalloc": (ctypes.c_int, [ctypes.POINTER(RodParams), _VP, _VP, _VP, _VP, _VP, _VP, _VP,
@@ -182,6 +183,10 @@ def rod_autotune(h, n_steps, stream=None):
 
 def rod_get_plan(h, out):
     _check(load().rod_get_plan(h, _ptr(out)), "rod_get_plan")
+
+
+def rod_set_graph_mode(h, mode):
+    _check(load().rod_set_graph_mode(h, int(mode)), "rod_set_graph_mode")
 
 
 def rod_last_launch_count(h) -> int:
@@ -346,6 +351,9 @@ class RodBatch:
 
     def autotune(self, n_steps, stream=None):
         rod_autotune(self.handle, n_steps, stream)
+
+    def set_graph_mode(self, mode):
+        rod_set_graph_mode(self.handle, mode)
 
     def last_launch_count(self) -> int:
         return rod_last_launch_count(self.handle)

@@ -100,6 +100,7 @@ struct corde_rods {
   double* d_derived = nullptr;
   float4 *d_x = nullptr, *d_v = nullptr, *d_q = nullptr, *d_o = nullptr, *d_u = nullptr, *d_k = nullptr;
   float4* d_drive = nullptr;
+  float4* d_drive_graph = nullptr;  // the drive the graph reads (copied in before each replay)
   int* d_elem_rod = nullptr;
   std::vector<int> plan;  // variant index per rod
   std::vector<Bin> bins;
@@ -119,6 +120,16 @@ struct corde_rods {
     int4* d_pairs;
   };
   std::vector<PairBin> pair_bins;
+  // CUDA graph of one rod_step (all bins forked onto parallel branches)
+  int graph_mode = 1;  // 0 never, 1 when a step needs more than one launch, 2 always
+  cudaGraphExec_t graph_exec = nullptr;
+  int graph_steps = -1;
+  const float4* graph_drive = nullptr;
+  int graph_launches = 0;
+  cudaStream_t cap_stream = nullptr;
+  std::vector<cudaStream_t> side;
+  cudaEvent_t fork_ev = nullptr;
+  std::vector<cudaEvent_t> join_ev;
 };
 
 namespace {
@@ -306,7 +317,14 @@ void free_bins(rod_handle h) {
 
 // Group rods by variant; each group's work list is sorted by decreasing length so that
 // the longest rods start first.
+void invalidate_graph(rod_handle h) {
+  if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+  h->graph_exec = nullptr;
+  h->graph_steps = -1;
+}
+
 int build_bins(rod_handle h) {
+  invalidate_graph(h);
   free_bins(h);
   const auto& vs = variants();
   for (size_t vi = 0; vi < vs.size(); ++vi) {
@@ -403,9 +421,100 @@ bool params_valid(const RodParams& p, std::string& why) {
   return true;
 }
 
+// Launches every bin and pair bin of one rod_step.  With branches, bin k goes to
+// branches[k] (for the forked graph capture); otherwise all go to s in order.
+int launch_all(rod_handle h, int n_steps, const float4* d, cudaStream_t s, const std::vector<cudaStream_t>* branches) {
+  int launches = 0;
+  size_t k = 0;
+  for (size_t b = 0; b < h->bins.size(); ++b, ++k) {
+    cudaStream_t sk = branches ? (*branches)[k] : s;
+    std::vector<Bin> one{h->bins[b]};
+    if (int rc = launch_bins(h, one, n_steps, d, sk)) return rc;
+    ++launches;
+  }
+  if (!h->pair_bins.empty()) {
+    StepArgs a;
+    a.rods = h->d_rods;
+    a.work = nullptr;
+    a.x4 = h->d_x;
+    a.v4 = h->d_v;
+    a.q4 = h->d_q;
+    a.o4 = h->d_o;
+    a.u4 = h->d_u;
+    a.k4 = h->d_k;
+    a.drive = d;
+    a.n_steps = n_steps;
+    a.traj = nullptr;
+    a.n_elem = h->n_elem;
+    for (const auto& pb : h->pair_bins) {
+      cudaStream_t sk = branches ? (*branches)[k] : s;
+      ++k;
+      cudaError_t e = launch_pair(pb.ept, pb.nt, a, pb.d_pairs, pb.count, sk);
+      if (e != cudaSuccess) return fail(CORDE_ERR_CUDA, std::string("pair launch: ") + cudaGetErrorString(e));
+      ++launches;
+    }
+  }
+  h->last_launches = launches;
+  return CORDE_OK;
+}
+
+// Captures one rod_step into a CUDA graph whose kernel nodes run concurrently (fork on
+// an event, one branch stream per bin, join), so that the bins fill the SMs together.
+int capture_graph(rod_handle h, int n_steps, const float4* d) {
+  invalidate_graph(h);
+  const size_t nb = h->bins.size() + h->pair_bins.size();
+  if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  if (!h->fork_ev) CK(cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming));
+  while (h->side.size() < nb) {
+    cudaStream_t st;
+    CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    h->side.push_back(st);
+    cudaEvent_t ev;
+    CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    h->join_ev.push_back(ev);
+  }
+  CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+  int rc = CORDE_OK;
+  cudaError_t e = cudaEventRecord(h->fork_ev, h->cap_stream);
+  for (size_t k = 0; k < nb && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(h->side[k], h->fork_ev, 0);
+  if (e == cudaSuccess) rc = launch_all(h, n_steps, d, h->cap_stream, &h->side);
+  for (size_t k = 0; k < nb && e == cudaSuccess && rc == CORDE_OK; ++k) {
+    e = cudaEventRecord(h->join_ev[k], h->side[k]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->cap_stream, h->join_ev[k], 0);
+  }
+  cudaGraph_t g = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &g);
+  if (rc != CORDE_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return fail(CORDE_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+  }
+  cudaError_t e3 = cudaGraphInstantiate(&h->graph_exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e3 != cudaSuccess) {
+    h->graph_exec = nullptr;
+    return fail(CORDE_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e3));
+  }
+  h->graph_steps = n_steps;
+  h->graph_drive = d;
+  h->graph_launches = (int)nb;
+  return CORDE_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+int rod_set_graph_mode(rod_handle h, int mode) {
+  if (int rc = check_handle(h)) return rc;
+  if (mode < 0 || mode > 2) return fail(CORDE_ERR_ARG, "graph mode must be 0, 1 or 2");
+  h->graph_mode = mode;
+  invalidate_graph(h);
+  return CORDE_OK;
+}
 
 const char* rod_strerror(int code) {
   switch (code) {
@@ -542,27 +651,17 @@ int rod_step(rod_handle h, int n_steps, const float* drive, void* stream) {
       return fail(CORDE_ERR_ARG, "drive must be 16-byte aligned device, managed or mapped pinned host memory");
     d = reinterpret_cast<const float4*>(dp);
   }
-  if (int rc = launch_bins(h, h->bins, n_steps, d, (cudaStream_t)stream)) return rc;
-  if (!h->pair_bins.empty()) {
-    StepArgs a;
-    a.rods = h->d_rods;
-    a.work = nullptr;
-    a.x4 = h->d_x;
-    a.v4 = h->d_v;
-    a.q4 = h->d_q;
-    a.o4 = h->d_o;
-    a.u4 = h->d_u;
-    a.k4 = h->d_k;
-    a.drive = d;
-    a.n_steps = n_steps;
-    a.traj = nullptr;
-    a.n_elem = h->n_elem;
-    for (const auto& pb : h->pair_bins) {
-      cudaError_t e = launch_pair(pb.ept, pb.nt, a, pb.d_pairs, pb.count, (cudaStream_t)stream);
-      if (e != cudaSuccess) return fail(CORDE_ERR_CUDA, std::string("pair launch: ") + cudaGetErrorString(e));
-      ++h->last_launches;
-    }
+  const int n_launch = (int)h->bins.size() + (int)h->pair_bins.size();
+  const bool use_graph = h->graph_mode == 2 || (h->graph_mode == 1 && n_launch > 1);
+  if (!use_graph) return launch_all(h, n_steps, d, (cudaStream_t)stream, nullptr);
+  if (!h->d_drive_graph) CK(cudaMalloc(&h->d_drive_graph, h->n_rods * 2 * sizeof(float4)));
+  CK(cudaMemcpyAsync(h->d_drive_graph, d, h->n_rods * 2 * sizeof(float4), cudaMemcpyDeviceToDevice,
+                     (cudaStream_t)stream));
+  if (!h->graph_exec || h->graph_steps != n_steps || h->graph_drive != h->d_drive_graph) {
+    if (int rc = capture_graph(h, n_steps, h->d_drive_graph)) return rc;
   }
+  CK(cudaGraphLaunch(h->graph_exec, (cudaStream_t)stream));
+  h->last_launches = h->graph_launches;
   return CORDE_OK;
 }
 
@@ -757,6 +856,7 @@ static int pair_layout(int n, int* ept, int* nt) {
 }
 
 static int build_pair_bins(rod_handle h) {
+  invalidate_graph(h);
   for (auto& pb : h->pair_bins) cudaFree(pb.d_pairs);
   h->pair_bins.clear();
   for (int ept : {2, 4})
@@ -938,10 +1038,15 @@ void rod_destroy(rod_handle h) {
   free_bins(h);
   cudaFree(h->d_rods); cudaFree(h->d_derived);
   cudaFree(h->d_x); cudaFree(h->d_v); cudaFree(h->d_q); cudaFree(h->d_o); cudaFree(h->d_u); cudaFree(h->d_k);
-  cudaFree(h->d_drive); cudaFree(h->d_elem_rod);
+  cudaFree(h->d_drive); cudaFree(h->d_elem_rod); cudaFree(h->d_drive_graph);
   cudaFree(h->d_ckpt); cudaFree(h->d_seg);
   for (auto& b : h->adj_bins) cudaFree(b.d_work);
   for (auto& pb : h->pair_bins) cudaFree(pb.d_pairs);
+  if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+  for (auto st : h->side) cudaStreamDestroy(st);
+  for (auto ev : h->join_ev) cudaEventDestroy(ev);
+  if (h->fork_ev) cudaEventDestroy(h->fork_ev);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   delete h;
 }
 
