@@ -155,7 +155,7 @@ def run_single_rod(args, torch, corde, W, rank):
         b.set_plan(2, 256)
     else:
         b.autotune(STEPS_PER_LAUNCH)
-    plan = [int(x) for x in b.plan()[0]]
+    plan = [int(x) for x in b.plan()[0][:2]]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def bench_step(k, events=None):
@@ -285,7 +285,7 @@ def run_batched(args, torch, corde, W, rank, world):
         "seconds": total_s,
         "element_steps_per_s": el_steps / total_s,
         "ms_per_launch": float(np.mean(ms)),
-        "plan": sorted({(int(a), int(c)) for a, c in plan}),
+        "plan": sorted({(int(a), int(c), int(k)) for a, c, k in plan}),
         "max_len_err": float(diag[:, 0].max()),
         "diag_rc": rc,
         "flops_per_launch": flops_per_el_step(10) * n_elem * S,
@@ -365,6 +365,35 @@ def run_pair(args, torch, corde, W):
             b.close()
     return {"unit": "us/step", "workload": "2 x 512 inextensible rods (catheter r=1 mm E=2 GPa, guidewire "
                                            "r=0.45 mm E=60 GPa), one thread block per pair", "us_per_step": out}
+
+
+def run_long_rods(args, torch, corde, W):
+    """Latency per step against rod length (the paper's near-constant-time claim for rods
+    spread over several SMs, Fig. 7): guidewire-like rods of 512 ... 8192 nodes (L grows
+    with N at the guidewire's segment length), 10 steps per launch; rods above 2048 nodes
+    run on a thread-block cluster."""
+    stream = torch.cuda.current_stream()
+    out = {}
+    for n in (512, 1024, 2048, 3072, 4096, 8192, 16384):
+        rod = W.guidewire(n, seed=7)
+        b = corde.RodBatch([rod])
+        if n <= 2048:
+            b.autotune(STEPS_PER_LAUNCH)
+        plan = [int(x) for x in b.plan()[0]]
+        for _ in range(20):
+            b.step(STEPS_PER_LAUNCH)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(100):
+            b.step(STEPS_PER_LAUNCH)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[str(n)] = {"us_per_step": round(e0.elapsed_time(e1) * 1e3 / (100 * STEPS_PER_LAUNCH), 4),
+                       "plan": plan}
+        b.close()
+    return out
 
 
 def cpu_baseline_single(seconds=10.0):
@@ -458,6 +487,7 @@ def main_ours(args):
         part = {"single": lambda: run_single_rod(args, torch, corde, W, rank),
                 "batched": lambda: run_batched(args, torch, corde, W, rank, world),
                 "pair": lambda: run_pair(args, torch, corde, W),
+                "long": lambda: run_long_rods(args, torch, corde, W),
                 "adjoint": lambda: run_adjoint(args, torch, corde, W, 1)}[args.only]()
         if rank == 0:
             print(json.dumps({"only": args.only, "result": part}, default=str), flush=True)
@@ -465,6 +495,7 @@ def main_ours(args):
     single = run_single_rod(args, torch, corde, W, rank)
     batched = run_batched(args, torch, corde, W, rank, world) if not args.skip_batched else None
     pair = run_pair(args, torch, corde, W) if not args.skip_pair else None
+    long_rods = run_long_rods(args, torch, corde, W) if not args.skip_long else None
     adjoint = None
     if not args.skip_adjoint:
         adjoint = {"single": run_adjoint(args, torch, corde, W, 1), "batched": run_adjoint(args, torch, corde, W, 256)}
@@ -554,6 +585,9 @@ def main_ours(args):
             out["adjoint"] = adjoint
         if pair is not None:
             out["pair"] = pair
+        if long_rods is not None:
+            out["long_rods"] = {"unit": "us/step", "steps_per_launch": STEPS_PER_LAUNCH,
+                                "by_nodes": long_rods}
         print(json.dumps(out), flush=True)
     _barrier(torch)
     if world > 1:
@@ -616,7 +650,8 @@ def main():
     ap.add_argument("--skip-cpu-batched", action="store_true")
     ap.add_argument("--skip-adjoint", action="store_true")
     ap.add_argument("--skip-pair", action="store_true")
-    ap.add_argument("--only", choices=["single", "batched", "pair", "adjoint"], default=None,
+    ap.add_argument("--skip-long", action="store_true")
+    ap.add_argument("--only", choices=["single", "batched", "pair", "adjoint", "long"], default=None,
                     help="run one part only and print its raw result (profiling aid, not a bench line)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="fixed kernel plan (single rod <2, 256>, batch default plan)")

@@ -145,12 +145,18 @@ int rod_set_material(rod_handle h, const float* per_joint, void* stream);
  * Returns CORDE_ERR_NONFINITE if any rod holds a non-finite value. */
 int rod_diagnostics(rod_handle h, double* out);
 
-/* Kernel variants: elements per thread (ept) and threads per block (nt).  rod_set_plan
- * forces one variant for every rod whose length it can hold (ept = 0 restores the
- * default plan); rod_autotune times the variants that hold each length bin on the
- * current state (state is saved and restored) and keeps the fastest per bin.
- * rod_get_plan writes [n_rods][2] ints (ept, nt).  Autotune is synchronous. */
+/* Kernel variants: elements per thread (ept) and threads per block (nt).  A rod of at
+ * most 2048 nodes runs in one thread block; a longer one (up to 32768 nodes) is spread
+ * over a cluster of `cluster` blocks that exchange border elements through distributed
+ * shared memory and synchronise with cluster barriers (the GB300 form of the paper's
+ * multi-block kernel, Section 2.2).  rod_set_plan forces one block variant for every rod
+ * it can hold (ept = 0 restores the default plan); rod_set_plan_cluster forces a cluster
+ * variant (ept, nt) in {(2,256), (4,256), (4,512)}, cluster 2..16, for every rod it can
+ * hold; rod_autotune times the block variants that hold each length bin on the current
+ * state (saved and restored) and keeps the fastest per bin.  rod_get_plan writes
+ * [n_rods][3] ints (ept, nt, cluster; cluster 0 = one block).  Synchronous. */
 int rod_set_plan(rod_handle h, int ept, int nt);
+int rod_set_plan_cluster(rod_handle h, int ept, int nt, int cluster);
 int rod_autotune(rod_handle h, int n_steps, void* stream);
 int rod_get_plan(rod_handle h, int* plan);
 

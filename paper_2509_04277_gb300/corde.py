@@ -57,6 +57,7 @@ SIGNATURES = {
     "rod_set_material": (ctypes.c_int, [_VP, _VP, _VP]),
     "rod_diagnostics": (ctypes.c_int, [_VP, _VP]),
     "rod_set_plan": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
+    "rod_set_plan_cluster": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "rod_autotune": (ctypes.c_int, [_VP, ctypes.c_int, _VP]),
     "rod_get_plan": (ctypes.c_int, [_VP, _VP]),
     "rod_last_launch_count": (ctypes.c_int, [_VP]),
@@ -175,6 +176,10 @@ def rod_diagnostics(h, out):
 
 def rod_set_plan(h, ept, nt):
     _check(load().rod_set_plan(h, int(ept), int(nt)), "rod_set_plan")
+
+
+def rod_set_plan_cluster(h, ept, nt, cluster):
+    _check(load().rod_set_plan_cluster(h, int(ept), int(nt), int(cluster)), "rod_set_plan_cluster")
 
 
 def rod_autotune(h, n_steps, stream=None):
@@ -339,9 +344,13 @@ class RodBatch:
         return rc, out
 
     def plan(self) -> np.ndarray:
-        out = np.zeros((self.n_rods, 2), dtype=np.int32)
+        """[n_rods, 3] (elements per thread, threads per block, blocks per rod; 0 = one block)."""
+        out = np.zeros((self.n_rods, 3), dtype=np.int32)
         rod_get_plan(self.handle, out)
         return out
+
+    def set_plan_cluster(self, ept, nt, cluster):
+        rod_set_plan_cluster(self.handle, ept, nt, cluster)
 
     def bind(self, outer, inner, mode):
         rod_bind(self.handle, outer, inner, mode)

@@ -341,6 +341,7 @@ adjoint_kernel(AdjointArgs a) {
     rb[e] = vb[e] = ob[e] = Kb[e] = ub[e] = zero3();
     qb[e] = zero4();
   }
+  const BlockHalo<NT, NT> H{t};
   int xc = 0;
   const int n_seg = (a.n_steps + a.ckpt_every - 1) / a.ckpt_every;
   bool params_loaded = false;
@@ -348,7 +349,7 @@ adjoint_kernel(AdjointArgs a) {
     const int t0 = seg * a.ckpt_every;
     const int cnt = min(a.ckpt_every, a.n_steps - t0);
     const float4* ck = a.ckpt + (int64_t)seg * 4 * E;
-    load_rod<EPT, NT>(R, t, ck, ck + E, ck + 2 * E, ck + 3 * E, a.u4, a.k4, r, v, q, om, w,
+    load_rod<EPT, NT>(R, t, t, ck, ck + E, ck + 2 * E, ck + 3 * E, a.u4, a.k4, r, v, q, om, w,
                       params_loaded ? nullptr : par_u, par_k);
     params_loaded = true;
     // recompute the segment's states into scratch
@@ -364,7 +365,7 @@ adjoint_kernel(AdjointArgs a) {
         }
       }
       if (s + 1 < cnt)
-        step_body<EPT, NT, false>(R, t, r, v, q, om, w, par_u, par_k, halo, xc, v_drive, w_drive, nullptr, nullptr);
+        step_body<EPT, NT, false>(R, H, r, v, q, om, w, par_u, par_k, halo, xc, v_drive, w_drive, nullptr, nullptr);
     }
     // reverse the segment's steps
     for (int s = cnt - 1; s >= 0; --s) {
@@ -384,7 +385,7 @@ adjoint_kernel(AdjointArgs a) {
         om_in[e] = om[e];
       }
       StepNeighbours nb;
-      step_body<EPT, NT, true>(R, t, r, v, q, om, w, par_u, par_k, halo, xc, v_drive, w_drive, sweep_v, &nb);
+      step_body<EPT, NT, true>(R, H, r, v, q, om, w, par_u, par_k, halo, xc, v_drive, w_drive, sweep_v, &nb);
       // loss gradient with respect to the positions after this step
       if (a.dLdpos != nullptr) {
         const float4* g = a.dLdpos + (int64_t)(t0 + s) * E + R.off;

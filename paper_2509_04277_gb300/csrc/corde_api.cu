@@ -51,10 +51,35 @@ const std::vector<StepVariant>& variants() {
   return v;
 }
 
-int max_capacity() {
+int max_block_capacity() {
   int c = 0;
   for (const auto& v : variants()) c = std::max(c, v.capacity());
   return c;
+}
+
+int max_capacity() {
+  int c = max_block_capacity();
+  for (int i = 0; i < kNumClusterVariants; ++i) c = std::max(c, kClusterVariants[i].capacity(kMaxCluster));
+  return c;
+}
+
+int find_cluster_variant(int ept, int nt) {
+  for (int i = 0; i < kNumClusterVariants; ++i)
+    if (kClusterVariants[i].ept == ept && kClusterVariants[i].nt == nt) return i;
+  return -1;
+}
+
+// Default plan of a rod longer than one block holds: 1024 nodes per block (4 elements x
+// 256 threads) over the fewest blocks, 2048 per block beyond 16 blocks.
+void default_cluster_plan(int n, int* variant, int* C) {
+  int v = find_cluster_variant(4, 256);
+  int c = (n + 1023) / 1024;
+  if (c > kMaxCluster) {
+    v = find_cluster_variant(4, 512);
+    c = (n + 2047) / 2048;
+  }
+  *variant = v;
+  *C = std::max(2, c);
 }
 
 int find_variant(int ept, int nt) {
@@ -80,9 +105,10 @@ int default_variant(int n) {
 }
 
 struct Bin {
-  int variant;
+  int variant;  // block variant index, or cluster variant index when cluster > 0
   int count;
   int* d_work;
+  int cluster = 0;  // blocks per rod (0: one block per rod)
 };
 
 }  // namespace
@@ -102,7 +128,8 @@ struct corde_rods {
   float4* d_drive = nullptr;
   float4* d_drive_graph = nullptr;  // the drive the graph reads (copied in before each replay)
   int* d_elem_rod = nullptr;
-  std::vector<int> plan;  // variant index per rod
+  std::vector<int> plan;          // variant index per rod (block or cluster table)
+  std::vector<int> plan_cluster;  // blocks per rod; 0: one block
   std::vector<Bin> bins;
   int last_launches = 0;
   // rollout / adjoint
@@ -326,14 +353,20 @@ void invalidate_graph(rod_handle h) {
 int build_bins(rod_handle h) {
   invalidate_graph(h);
   free_bins(h);
-  const auto& vs = variants();
-  for (size_t vi = 0; vi < vs.size(); ++vi) {
+  std::vector<std::pair<int, int>> keys;
+  for (int r = 0; r < h->n_rods; ++r) {
+    if (r < (int)h->paired.size() && h->paired[r]) continue;
+    std::pair<int, int> k{h->plan_cluster[r], h->plan[r]};
+    if (std::find(keys.begin(), keys.end(), k) == keys.end()) keys.push_back(k);
+  }
+  std::sort(keys.begin(), keys.end());
+  for (const auto& k : keys) {
     std::vector<int> rods;
     for (int r = 0; r < h->n_rods; ++r)
-      if (h->plan[r] == (int)vi && !(r < (int)h->paired.size() && h->paired[r])) rods.push_back(r);
-    if (rods.empty()) continue;
+      if (h->plan_cluster[r] == k.first && h->plan[r] == k.second && !(r < (int)h->paired.size() && h->paired[r]))
+        rods.push_back(r);
     std::stable_sort(rods.begin(), rods.end(), [&](int a, int b) { return h->n_nodes[a] > h->n_nodes[b]; });
-    Bin b{(int)vi, (int)rods.size(), nullptr};
+    Bin b{k.second, (int)rods.size(), nullptr, k.first};
     CK(cudaMalloc(&b.d_work, rods.size() * sizeof(int)));
     CK(cudaMemcpy(b.d_work, rods.data(), rods.size() * sizeof(int), cudaMemcpyHostToDevice));
     h->bins.push_back(b);
@@ -358,11 +391,20 @@ int launch_bins(rod_handle h, const std::vector<Bin>& bins, int n_steps, const f
   int launches = 0;
   for (const auto& b : bins) {
     a.work = b.d_work;
-    const StepVariant& v = variants()[b.variant];
-    cudaError_t e = v.launch(a, b.count, s);
-    if (e != cudaSuccess)
-      return fail(CORDE_ERR_CUDA, std::string("step launch (ept=") + std::to_string(v.ept) +
-                                      ", nt=" + std::to_string(v.nt) + "): " + cudaGetErrorString(e));
+    if (b.cluster > 0) {
+      const ClusterVariant& v = kClusterVariants[b.variant];
+      cudaError_t e = v.launch(a, b.count, b.cluster, s);
+      if (e != cudaSuccess)
+        return fail(CORDE_ERR_CUDA, std::string("cluster step launch (ept=") + std::to_string(v.ept) + ", nt=" +
+                                        std::to_string(v.nt) + ", cluster=" + std::to_string(b.cluster) +
+                                        "): " + cudaGetErrorString(e));
+    } else {
+      const StepVariant& v = variants()[b.variant];
+      cudaError_t e = v.launch(a, b.count, s);
+      if (e != cudaSuccess)
+        return fail(CORDE_ERR_CUDA, std::string("step launch (ept=") + std::to_string(v.ept) +
+                                        ", nt=" + std::to_string(v.nt) + "): " + cudaGetErrorString(e));
+    }
     ++launches;
   }
   h->last_launches = launches;
@@ -622,7 +664,14 @@ int rod_create(int n_rods, const RodParams* params, const float* pos, const floa
       break;
     }
     h->plan.resize(n_rods);
-    for (int r = 0; r < n_rods; ++r) h->plan[r] = default_variant(nn[r]);
+    h->plan_cluster.assign(n_rods, 0);
+    for (int r = 0; r < n_rods; ++r) {
+      if (nn[r] <= max_block_capacity()) {
+        h->plan[r] = default_variant(nn[r]);
+      } else {
+        default_cluster_plan(nn[r], &h->plan[r], &h->plan_cluster[r]);
+      }
+    }
     rc = build_bins(h);
   } while (0);
   cleanup_staging();
@@ -748,21 +797,47 @@ int rod_diagnostics(rod_handle h, double* out) {
 int rod_set_plan(rod_handle h, int ept, int nt) {
   if (int rc = check_handle(h)) return rc;
   if (ept == 0) {
-    for (int r = 0; r < h->n_rods; ++r) h->plan[r] = default_variant(h->n_nodes[r]);
+    for (int r = 0; r < h->n_rods; ++r) {
+      h->plan_cluster[r] = 0;
+      if (h->n_nodes[r] <= max_block_capacity()) {
+        h->plan[r] = default_variant(h->n_nodes[r]);
+      } else {
+        default_cluster_plan(h->n_nodes[r], &h->plan[r], &h->plan_cluster[r]);
+      }
+    }
     return build_bins(h);
   }
   const int v = find_variant(ept, nt);
   if (v < 0) return fail(CORDE_ERR_ARG, "no compiled variant with ept=" + std::to_string(ept) + ", nt=" + std::to_string(nt));
   for (int r = 0; r < h->n_rods; ++r)
-    if (variants()[v].capacity() >= h->n_nodes[r]) h->plan[r] = v;
+    if (variants()[v].capacity() >= h->n_nodes[r]) {
+      h->plan[r] = v;
+      h->plan_cluster[r] = 0;
+    }
+  return build_bins(h);
+}
+
+int rod_set_plan_cluster(rod_handle h, int ept, int nt, int cluster) {
+  if (int rc = check_handle(h)) return rc;
+  const int v = find_cluster_variant(ept, nt);
+  if (v < 0 || cluster < 2 || cluster > kMaxCluster)
+    return fail(CORDE_ERR_ARG, "no cluster variant with ept=" + std::to_string(ept) + ", nt=" + std::to_string(nt) +
+                                   ", cluster=" + std::to_string(cluster));
+  for (int r = 0; r < h->n_rods; ++r)
+    if (kClusterVariants[v].capacity(cluster) >= h->n_nodes[r]) {
+      h->plan[r] = v;
+      h->plan_cluster[r] = cluster;
+    }
   return build_bins(h);
 }
 
 int rod_get_plan(rod_handle h, int* plan) {
   if (!h || !plan) return fail(CORDE_ERR_ARG, "NULL argument");
   for (int r = 0; r < h->n_rods; ++r) {
-    plan[2 * r] = variants()[h->plan[r]].ept;
-    plan[2 * r + 1] = variants()[h->plan[r]].nt;
+    const int C = h->plan_cluster[r];
+    plan[3 * r] = C > 0 ? kClusterVariants[h->plan[r]].ept : variants()[h->plan[r]].ept;
+    plan[3 * r + 1] = C > 0 ? kClusterVariants[h->plan[r]].nt : variants()[h->plan[r]].nt;
+    plan[3 * r + 2] = C;
   }
   return CORDE_OK;
 }
@@ -799,14 +874,14 @@ int rod_autotune(rod_handle h, int n_steps, void* stream) {
     int c = 5;
     while ((1 << c) < h->n_nodes[r]) ++c;
     cls[r] = c;
-    max_cls = std::max(max_cls, c);
+    if (h->plan_cluster[r] == 0) max_cls = std::max(max_cls, c);
   }
   int rc = CORDE_OK;
   for (int c = 5; c <= max_cls && rc == CORDE_OK; ++c) {
     std::vector<int> rods;
     int nmax = 0;
     for (int r = 0; r < h->n_rods; ++r)
-      if (cls[r] == c && !(r < (int)h->paired.size() && h->paired[r])) {
+      if (cls[r] == c && h->plan_cluster[r] == 0 && !(r < (int)h->paired.size() && h->paired[r])) {
         rods.push_back(r);
         nmax = std::max(nmax, h->n_nodes[r]);
       }

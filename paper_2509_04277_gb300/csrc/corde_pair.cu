@@ -118,7 +118,7 @@ pair_kernel(const RodDev* __restrict__ rods, const int4* __restrict__ pairs, flo
   float3 r[EPT], v[EPT], om[EPT];
   float4 q[EPT];
   float w[EPT];
-  load_rod<EPT, NT>(R, t, x4, v4, q4, o4, u4, k4, r, v, q, om, w, par_u, par_k);
+  load_rod<EPT, NT>(R, t, t, x4, v4, q4, o4, u4, k4, r, v, q, om, w, par_u, par_k);
   float3 v_drive = zero3(), w_drive = zero3();
   float beta = 0.f;
   if (drive != nullptr) {
@@ -139,10 +139,11 @@ pair_kernel(const RodDev* __restrict__ rods, const int4* __restrict__ pairs, flo
   hook.out_r = out_r;
   hook.out_v = out_v;
 
+  const BlockHalo<NT, 2 * NT> H{t};
   int xc = 0;
   for (int step = 0; step < n_steps; ++step)
-    step_body<EPT, NT, false, 2 * NT, PairHook<2 * NT>>(R, t, r, v, q, om, w, par_u, par_k, halo, xc, v_drive,
-                                                        w_drive, nullptr, nullptr, hook);
+    step_body<EPT, NT, false>(R, H, r, v, q, om, w, par_u, par_k, halo, xc, v_drive, w_drive, nullptr, nullptr,
+                              hook);
   const int e0 = t * EPT;
 #pragma unroll
   for (int e = 0; e < EPT; ++e) {

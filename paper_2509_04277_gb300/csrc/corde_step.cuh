@@ -24,6 +24,8 @@
 // recomputation, so both run the same arithmetic.
 #pragma once
 
+#include <cooperative_groups.h>
+
 #include "corde_common.cuh"
 
 namespace corde {
@@ -36,6 +38,43 @@ __device__ __forceinline__ void block_sync() {
     __syncthreads();
   }
 }
+
+// Neighbour access and barrier of a rod held by one thread block (t = thread of the rod;
+// SYNC_NT threads take part in each barrier: NT, or more when several rods share the block
+// in lockstep).  Exchange buffers hold `slots` x NT float4, slot-major.
+template <int NT, int SYNC_NT>
+struct BlockHalo {
+  int t;
+  __device__ __forceinline__ int tg() const { return t; }
+  __device__ __forceinline__ bool has_next() const { return t + 1 < NT; }
+  __device__ __forceinline__ bool has_prev() const { return t > 0; }
+  __device__ __forceinline__ float4 next(const float4* hb, int slot) const { return hb[slot * NT + t + 1]; }
+  __device__ __forceinline__ float4 prev(const float4* hb, int slot) const { return hb[slot * NT + t - 1]; }
+  __device__ __forceinline__ void sync() const { block_sync<SYNC_NT>(); }
+};
+
+// A rod spread over the C thread blocks of a cluster (block c holds threads c NT ...
+// c NT + NT - 1 of the rod): the neighbours of a block's first and last thread live in
+// the adjacent blocks, whose exchange buffers are read through distributed shared
+// memory; the barrier is the cluster barrier (release / acquire).
+template <int NT>
+struct ClusterHalo {
+  int t, c, C;
+  __device__ __forceinline__ int tg() const { return c * NT + t; }
+  __device__ __forceinline__ bool has_next() const { return t + 1 < NT || c + 1 < C; }
+  __device__ __forceinline__ bool has_prev() const { return t > 0 || c > 0; }
+  __device__ __forceinline__ float4 next(const float4* hb, int slot) const {
+    if (t + 1 < NT) return hb[slot * NT + t + 1];
+    const float4* remote = cooperative_groups::this_cluster().map_shared_rank(hb, c + 1);
+    return remote[slot * NT];
+  }
+  __device__ __forceinline__ float4 prev(const float4* hb, int slot) const {
+    if (t > 0) return hb[slot * NT + t - 1];
+    const float4* remote = cooperative_groups::this_cluster().map_shared_rank(hb, c - 1);
+    return remote[slot * NT + NT - 1];
+  }
+  __device__ __forceinline__ void sync() const { cooperative_groups::this_cluster().sync(); }
+};
 
 // Bend/twist torques of the joint between frames a and b (Eq. 3): with
 // D = conj(qa) (x) qb, u = (2/l) Im(D) and m = 2 K (u - u-hat), the body torques are
@@ -76,22 +115,32 @@ __device__ __forceinline__ void segment_forces(float3 ra, float3 rb, float4 q, c
   tq = f3(-R.lKp * tb.y, R.lKp * tb.x, 0.f);
 }
 
-// Velocity-impulse factor of one distance constraint (predictive: makes the segment
-// length l0 after the update).  d = (r_b + dt v_b) - (r_a + dt v_a) is formed as
-// (r_b - r_a) + dt (v_b - v_a): the node difference is exact for neighbouring nodes,
-// whereas r + dt v would round dt v against |r|.  Returns s = lambda / |d| with
-// lambda = -(|d| - l0) / (dt (wa + wb)); the caller applies va -= wa s d, vb += wb s d.
+// Impulse of one distance constraint (predictive: makes the segment length l0 after the
+// update).  With e = r_b - r_a (fixed during the sweeps of a step) and
+// d = (r_b + dt v_b) - (r_a + dt v_a) = e + dt (v_b - v_a) (the node difference is exact
+// for neighbouring nodes, whereas r + dt v would round dt v against |r|), returns
+// g = lambda n = -(|d| - l0) / (dt (w_a + w_b)) d / |d|; the caller applies
+// v_a -= w_a g, v_b += w_b g.  inv_dtW = 1 / (dt (w_a + w_b)) is computed once per step.
 // Explicit round-to-nearest intrinsics make the two threads that share a boundary
 // constraint compute bit-identical impulses.
-__device__ __forceinline__ float constraint_factor(float3 ra, float3 va, float3 rb, float3 vb, float wsum, float l0,
-                                                   float dt, float3& d) {
-  d = f3(__fmaf_rn(dt, __fsub_rn(vb.x, va.x), __fsub_rn(rb.x, ra.x)),
-         __fmaf_rn(dt, __fsub_rn(vb.y, va.y), __fsub_rn(rb.y, ra.y)),
-         __fmaf_rn(dt, __fsub_rn(vb.z, va.z), __fsub_rn(rb.z, ra.z)));
+__device__ __forceinline__ float3 constraint_impulse(float3 e, float3 va, float3 vb, float inv_dtW, float l0,
+                                                     float dt) {
+  const float3 d = f3(__fmaf_rn(dt, __fsub_rn(vb.x, va.x), e.x), __fmaf_rn(dt, __fsub_rn(vb.y, va.y), e.y),
+                      __fmaf_rn(dt, __fsub_rn(vb.z, va.z), e.z));
   const float dd = __fmaf_rn(d.x, d.x, __fmaf_rn(d.y, d.y, __fmul_rn(d.z, d.z)));
   const float il = rsqrtf(dd);
-  const float C = __fsub_rn(__fmul_rn(dd, il), l0);
-  return __fmul_rn(__fmul_rn(-C, il), __frcp_rn(__fmul_rn(dt, wsum)));
+  const float s = __fmul_rn(__fmul_rn(__fsub_rn(l0, __fmul_rn(dd, il)), il), inv_dtW);
+  return f3(__fmul_rn(s, d.x), __fmul_rn(s, d.y), __fmul_rn(s, d.z));
+}
+
+// Per-step data of one constraint: e = r_b - r_a and 1 / (dt (w_a + w_b)), or 0 when the
+// constraint does not exist or joins two kinematic nodes.
+__device__ __forceinline__ float3 segment_vector(float3 ra, float3 rb) {
+  return f3(__fsub_rn(rb.x, ra.x), __fsub_rn(rb.y, ra.y), __fsub_rn(rb.z, ra.z));
+}
+__device__ __forceinline__ float inv_dt_wsum(bool exists, float wa, float wb, float dt) {
+  const float ws = __fadd_rn(wa, wb);
+  return (exists && ws > 0.f) ? __frcp_rn(__fmul_rn(dt, ws)) : 0.f;
 }
 
 // Hook into the constraint loop of step_body: before_iterations() once per step before
@@ -120,17 +169,18 @@ constexpr int step_smem_bytes() {
   return (2 * EPT * NT + 2 * kHaloSlots * NT) * (int)sizeof(float4);
 }
 
-// One time step of the rod held by NT threads (thread t of the group).  SYNC_NT threads
-// take part in every barrier: NT for one rod per block, more when several rods share a
-// block in lockstep.  With STORE, the velocities before every constraint half-sweep are
-// written to sweep_v ([2 n_iters][EPT][NT]) and the neighbour data to *nb (adjoint).
-template <int EPT, int NT, bool STORE, int SYNC_NT = NT, class Hook = NoHook>
-__device__ __forceinline__ void step_body(const RodDev& R, const int t, float3 (&r)[EPT], float3 (&v)[EPT],
+// One time step of the rod; H (BlockHalo or ClusterHalo) gives the thread's place in the
+// rod, its neighbours' exchange slots and the barrier.  With STORE, the velocities before
+// every constraint half-sweep are written to sweep_v ([2 n_iters][EPT][NT]) and the
+// neighbour data to *nb (for the adjoint).
+template <int EPT, int NT, bool STORE, class Halo, class Hook = NoHook>
+__device__ __forceinline__ void step_body(const RodDev& R, const Halo& H, float3 (&r)[EPT], float3 (&v)[EPT],
                                           float4 (&q)[EPT], float3 (&om)[EPT], const float (&w)[EPT],
                                           const float4* par_u, const float4* par_k, float4* halo, int& xc,
                                           const float3 v_drive, const float3 w_drive, float4* sweep_v,
                                           StepNeighbours* nb, const Hook& hook = Hook()) {
-  const int e0 = t * EPT;
+  const int t = H.t;
+  const int e0 = H.tg() * EPT;
   const int n = R.n;
   const bool inext = (R.flags & F_INEXT) != 0;
   const bool clamp = (R.flags & F_CLAMP) != 0;
@@ -145,18 +195,19 @@ __device__ __forceinline__ void step_body(const RodDev& R, const int t, float3 (
   hb[t] = make_float4(r[0].x, r[0].y, r[0].z, w[0]);
   hb[NT + t] = q[0];
   hb[2 * NT + t] = make_float4(r[EPT - 1].x, r[EPT - 1].y, r[EPT - 1].z, w[EPT - 1]);
-  block_sync<SYNC_NT>();
+  H.sync();
   float3 r_next = zero3(), r_prev = zero3();
   float w_next = 0.f, w_prev = 0.f;
   float4 q_next = make_float4(0.f, 0.f, 0.f, 1.f);
-  if (t + 1 < NT) {
-    const float4 a = hb[t + 1];
+  const bool has_next = H.has_next(), has_prev = H.has_prev();
+  if (has_next) {
+    const float4 a = H.next(hb, 0);
     r_next = f3(a);
     w_next = a.w;
-    q_next = hb[NT + t + 1];
+    q_next = H.next(hb, 1);
   }
-  if (t > 0) {
-    const float4 a = hb[2 * NT + t - 1];
+  if (has_prev) {
+    const float4 a = H.prev(hb, 2);
     r_prev = f3(a);
     w_prev = a.w;
   }
@@ -208,10 +259,10 @@ __device__ __forceinline__ void step_body(const RodDev& R, const int t, float3 (
   ++xc;
   hb[t] = make_float4(F_carry.x, F_carry.y, F_carry.z, 0.f);
   hb[NT + t] = make_float4(tau_carry.x, tau_carry.y, tau_carry.z, 0.f);
-  block_sync<SYNC_NT>();
-  if (t > 0) {
-    F[0] += f3(hb[t - 1]);
-    tau[0] += f3(hb[NT + t - 1]);
+  H.sync();
+  if (has_prev) {
+    F[0] += f3(H.prev(hb, 0));
+    tau[0] += f3(H.prev(hb, 1));
   }
 
   // ---- integrate forces and torques into velocities
@@ -231,7 +282,7 @@ __device__ __forceinline__ void step_body(const RodDev& R, const int t, float3 (
       om[e] = R.damp * on;
     }
   }
-  if (clamp && t == 0) {
+  if (clamp && e0 == 0) {
     v[0] = v_drive;
     om[0] = w_drive;
   }
@@ -239,6 +290,26 @@ __device__ __forceinline__ void step_body(const RodDev& R, const int t, float3 (
   // ---- distance-constraint iterations (inextensible rod), red-black
   if (inext) {
     hook.template before_iterations<EPT>(r, w);
+    // constraint geometry of this step (positions and masses do not change in the sweeps)
+    constexpr int NE = EPT / 2, NO = EPT / 2 > 1 ? EPT / 2 - 1 : 1;
+    float3 e_even[NE], e_odd[NO];
+    float i_even[NE], i_odd[NO];
+#pragma unroll
+    for (int k = 0; k < NE; ++k) {
+      e_even[k] = segment_vector(r[2 * k], r[2 * k + 1]);
+      i_even[k] = inv_dt_wsum(e0 + 2 * k + 1 <= n - 1, w[2 * k], w[2 * k + 1], dt);
+    }
+#pragma unroll
+    for (int k = 0; k < NO; ++k) {
+      const bool ex = EPT / 2 > 1 && e0 + 2 * k + 2 <= n - 1;
+      e_odd[k] = ex ? segment_vector(r[(2 * k + 1) % EPT], r[(2 * k + 2) % EPT]) : zero3();
+      i_odd[k] = inv_dt_wsum(ex, w[(2 * k + 1) % EPT], w[(2 * k + 2) % EPT], dt);
+    }
+    const float3 e_right = segment_vector(r[EPT - 1], r_next);
+    const float i_right = inv_dt_wsum(has_next && e0 + EPT <= n - 1, w[EPT - 1], w_next, dt);
+    const float3 e_left = segment_vector(r_prev, r[0]);
+    const float i_left = inv_dt_wsum(has_prev && e0 <= n - 1, w_prev, w[0], dt);
+
     for (int it = 0; it < R.n_iters; ++it) {
       if constexpr (STORE) {
 #pragma unroll
@@ -246,14 +317,11 @@ __device__ __forceinline__ void step_body(const RodDev& R, const int t, float3 (
       }
       // even segments (e0 + 2k, e0 + 2k + 1): local to the thread
 #pragma unroll
-      for (int k = 0; k < EPT / 2; ++k) {
-        const int a = 2 * k, b = 2 * k + 1;
-        const float ws = w[a] + w[b];
-        if (e0 + b <= n - 1 && ws > 0.f) {
-          float3 d;
-          const float s = constraint_factor(r[a], v[a], r[b], v[b], ws, R.l0, dt, d);
-          v[a] -= (w[a] * s) * d;
-          v[b] += (w[b] * s) * d;
+      for (int k = 0; k < NE; ++k) {
+        if (i_even[k] != 0.f) {
+          const float3 g = constraint_impulse(e_even[k], v[2 * k], v[2 * k + 1], i_even[k], R.l0, dt);
+          v[2 * k] -= w[2 * k] * g;
+          v[2 * k + 1] += w[2 * k + 1] * g;
         }
       }
       if constexpr (STORE) {
@@ -266,36 +334,26 @@ __device__ __forceinline__ void step_body(const RodDev& R, const int t, float3 (
       ++xc;
       hb[t] = make_float4(v[0].x, v[0].y, v[0].z, 0.f);
       hb[NT + t] = make_float4(v[EPT - 1].x, v[EPT - 1].y, v[EPT - 1].z, 0.f);
-      block_sync<SYNC_NT>();
+      H.sync();
       // odd segments inside the thread
 #pragma unroll
       for (int k = 0; k + 1 < EPT / 2; ++k) {
-        const int a = 2 * k + 1, b = 2 * k + 2;
-        const float ws = w[a] + w[b];
-        if (e0 + b <= n - 1 && ws > 0.f) {
-          float3 d;
-          const float s = constraint_factor(r[a], v[a], r[b], v[b], ws, R.l0, dt, d);
-          v[a] -= (w[a] * s) * d;
-          v[b] += (w[b] * s) * d;
+        if (i_odd[k] != 0.f) {
+          const int a = 2 * k + 1, b = 2 * k + 2;
+          const float3 g = constraint_impulse(e_odd[k], v[a], v[b], i_odd[k], R.l0, dt);
+          v[a] -= w[a] * g;
+          v[b] += w[b] * g;
         }
       }
       // odd segment across the right boundary: (my last, right neighbour's first)
-      if (t + 1 < NT && e0 + EPT <= n - 1) {
-        const float ws = w[EPT - 1] + w_next;
-        if (ws > 0.f) {
-          float3 d;
-          const float s = constraint_factor(r[EPT - 1], v[EPT - 1], r_next, f3(hb[t + 1]), ws, R.l0, dt, d);
-          v[EPT - 1] -= (w[EPT - 1] * s) * d;
-        }
+      if (i_right != 0.f) {
+        const float3 g = constraint_impulse(e_right, v[EPT - 1], f3(H.next(hb, 0)), i_right, R.l0, dt);
+        v[EPT - 1] -= w[EPT - 1] * g;
       }
       // odd segment across the left boundary: (left neighbour's last, my first)
-      if (t > 0 && e0 <= n - 1) {
-        const float ws = w_prev + w[0];
-        if (ws > 0.f) {
-          float3 d;
-          const float s = constraint_factor(r_prev, f3(hb[NT + t - 1]), r[0], v[0], ws, R.l0, dt, d);
-          v[0] += (w[0] * s) * d;
-        }
+      if (i_left != 0.f) {
+        const float3 g = constraint_impulse(e_left, f3(H.prev(hb, 1)), v[0], i_left, R.l0, dt);
+        v[0] += w[0] * g;
       }
       hook.template after_odd<EPT>(r, v, w);
     }
@@ -321,16 +379,16 @@ __device__ __forceinline__ void step_body(const RodDev& R, const int t, float3 (
   }
 }
 
-// Loads the rod's elements owned by thread t (registers) and its joint parameters
-// (shared memory, read back only by the same thread).
+// Loads the rod's elements owned by thread tg of the rod (registers) and their joint
+// parameters (shared memory slot t, read back only by the same thread).
 template <int EPT, int NT>
-__device__ __forceinline__ void load_rod(const RodDev& R, const int t, const float4* __restrict__ x4,
+__device__ __forceinline__ void load_rod(const RodDev& R, const int t, const int tg, const float4* __restrict__ x4,
                                          const float4* __restrict__ v4, const float4* __restrict__ q4,
                                          const float4* __restrict__ o4, const float4* __restrict__ u4,
                                          const float4* __restrict__ k4, float3 (&r)[EPT], float3 (&v)[EPT],
                                          float4 (&q)[EPT], float3 (&om)[EPT], float (&w)[EPT], float4* par_u,
                                          float4* par_k) {
-  const int e0 = t * EPT;
+  const int e0 = tg * EPT;
 #pragma unroll
   for (int e = 0; e < EPT; ++e) {
     const int i = e0 + e;
@@ -377,16 +435,17 @@ step_kernel(const RodDev* __restrict__ rods, const int* __restrict__ work, float
   float3 r[EPT], v[EPT], om[EPT];
   float4 q[EPT];
   float w[EPT];
-  load_rod<EPT, NT>(R, t, x4, v4, q4, o4, u4, k4, r, v, q, om, w, par_u, par_k);
+  load_rod<EPT, NT>(R, t, t, x4, v4, q4, o4, u4, k4, r, v, q, om, w, par_u, par_k);
   float3 v_drive = zero3(), w_drive = zero3();
   if (drive != nullptr) {
     v_drive = f3(drive[2 * rid]);
     w_drive = f3(drive[2 * rid + 1]);
   }
 
+  const BlockHalo<NT, NT> H{t};
   int xc = 0;  // exchange counter selects the ping-pong buffer
   for (int step = 0; step < n_steps; ++step) {
-    step_body<EPT, NT, false>(R, t, r, v, q, om, w, par_u, par_k, halo, xc, v_drive, w_drive, nullptr, nullptr);
+    step_body<EPT, NT, false>(R, H, r, v, q, om, w, par_u, par_k, halo, xc, v_drive, w_drive, nullptr, nullptr);
     if (traj != nullptr) {
 #pragma unroll
       for (int e = 0; e < EPT; ++e)

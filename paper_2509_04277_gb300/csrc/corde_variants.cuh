@@ -52,6 +52,19 @@ constexpr int kAdjointMaxNodes = 512;
 // ept in {2, 4}, nt (threads per rod) in {32, ..., 256}.
 cudaError_t launch_pair(int ept, int nt, const StepArgs& a, const int4* pairs, int n_pairs, cudaStream_t s);
 
+// Long rods over a thread-block cluster (corde_cluster.cu): C blocks of NT threads, EPT
+// elements per thread, one rod per cluster; launch(args, n_rods, C, stream).
+typedef cudaError_t (*ClusterLaunchFn)(const StepArgs& a, int n_rods, int C, cudaStream_t s);
+struct ClusterVariant {
+  int ept;
+  int nt;
+  ClusterLaunchFn launch;
+  int capacity(int C) const { return ept * nt * C; }
+};
+extern const ClusterVariant kClusterVariants[];
+extern const int kNumClusterVariants;
+constexpr int kMaxCluster = 16;
+
 // Defined in the per-EPT instantiation units.
 extern const StepVariant kStepVariantsE2[];
 extern const int kNumStepVariantsE2;

@@ -115,7 +115,7 @@ def test_every_variant_matches_oracle(corde, plan):
     rod = W.guidewire(n, seed=300 + plan[0] * 1000 + plan[1])
     b = corde.RodBatch([rod])
     b.set_plan(*plan)
-    assert tuple(b.plan()[0]) == plan
+    assert tuple(b.plan()[0][:2]) == plan
     b.close()
     _one_step_parity(corde, torch, rod, n_checks=2, drive=np.array([0.01, 0, 0, 0, 0, 0, 1.0, 0]), plan=plan)
 
