@@ -168,6 +168,33 @@ int rod_get_plan(rod_handle h, int* plan);
  * on an internal stream: do not call it inside a caller's own stream capture. */
 int rod_set_graph_mode(rod_handle h, int mode);
 
+/* Mailbox of running launches (Section 2.2 and 3.1: the haptic thread writes the device's
+ * state into the running kernel and reads the force feedback back, at a rate higher than
+ * the kernel launches, through pinned memory while the kernel runs).  While enabled,
+ * every rod_step launch polls the input every `period` steps (one non-blocking read of a
+ * seqlock in mapped pinned host memory by the thread owning the rod's base; a torn or
+ * unchanged input is skipped, nothing waits) and writes, every `period` steps, the base
+ * and tip node's position and velocity to two feedback records per rod.  Each input a
+ * rod picks up is logged as (global step, input sequence number), up to log_capacity
+ * entries, so a run can be replayed exactly.
+ *  rod_mailbox_enable   allocates the mapped buffers (synchronous); not with bound pairs.
+ *  rod_mailbox_write    host-side seqlock write of [n_rods][8] drive rows (as rod_step's
+ *                       drive); safe while kernels run; the k-th write gets sequence 2k.
+ *  rod_mailbox_read     consistent copy of the records: out [n_rods][2][8] 32-bit words
+ *                       (seq, step, x, y, z, vx, vy, vz as float bits); record 0 the base,
+ *                       1 the tip; seq 0 means not written yet.  Safe while kernels run.
+ *  rod_mailbox_log      copies min(count, capacity) (step, seq) pairs to out [capacity][2],
+ *                       returns the count and clears the log (synchronous).
+ *  rod_mailbox_disable  frees the mailbox (synchronous).
+ * With the mailbox enabled rod_step launches directly (no graph).  rod_steps_done: steps
+ * taken by rod_step on this handle (the log's step index). */
+int rod_mailbox_enable(rod_handle h, int period, int log_capacity);
+int rod_mailbox_write(rod_handle h, const float* drive);
+int rod_mailbox_read(rod_handle h, unsigned* out);
+int rod_mailbox_log(rod_handle h, int* out, int capacity, int* count);
+int rod_mailbox_disable(rod_handle h);
+int64_t rod_steps_done(rod_handle h);
+
 /* Number of kernel launches the last rod_step enqueued (kernel nodes of the graph when
  * the graph path ran). */
 int rod_last_launch_count(rod_handle h);

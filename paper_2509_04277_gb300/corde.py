@@ -62,6 +62,12 @@ SIGNATURES = {
     "rod_get_plan": (ctypes.c_int, [_VP, _VP]),
     "rod_last_launch_count": (ctypes.c_int, [_VP]),
     "rod_set_graph_mode": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "rod_mailbox_enable": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
+    "rod_mailbox_write": (ctypes.c_int, [_VP, _VP]),
+    "rod_mailbox_read": (ctypes.c_int, [_VP, _VP]),
+    "rod_mailbox_log": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "rod_mailbox_disable": (ctypes.c_int, [_VP]),
+    "rod_steps_done": (ctypes.c_int64, [_VP]),
     "rod_rollout": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP, _VP]),
     "rod_adjoint": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "rod_adjoint_noalloc": (ctypes.c_int, [ctypes.POINTER(RodParams), _VP, _VP, _VP, _VP, _VP, _VP, _VP,
@@ -192,6 +198,38 @@ def rod_get_plan(h, out):
 
 def rod_set_graph_mode(h, mode):
     _check(load().rod_set_graph_mode(h, int(mode)), "rod_set_graph_mode")
+
+
+def rod_mailbox_enable(h, period, log_capacity=65536):
+    _check(load().rod_mailbox_enable(h, int(period), int(log_capacity)), "rod_mailbox_enable")
+
+
+def rod_mailbox_write(h, drive):
+    d = np.ascontiguousarray(drive, dtype=np.float32)
+    _check(load().rod_mailbox_write(h, d.ctypes.data), "rod_mailbox_write")
+
+
+def rod_mailbox_read(h, n_rods):
+    """[n_rods, 2] records: dict arrays seq, step (int) and pos, vel ([n_rods, 2, 3] float32)."""
+    raw = np.zeros((n_rods, 2, 8), dtype=np.uint32)
+    _check(load().rod_mailbox_read(h, raw.ctypes.data), "rod_mailbox_read")
+    return {"seq": raw[..., 0].astype(np.int64), "step": raw[..., 1].astype(np.int64),
+            "pos": raw[..., 2:5].view(np.float32), "vel": raw[..., 5:8].view(np.float32)}
+
+
+def rod_mailbox_log(h, capacity=65536):
+    out = np.zeros((capacity, 2), dtype=np.int32)
+    n = ctypes.c_int()
+    _check(load().rod_mailbox_log(h, out.ctypes.data, int(capacity), ctypes.byref(n)), "rod_mailbox_log")
+    return out[:min(n.value, capacity)].copy(), n.value
+
+
+def rod_mailbox_disable(h):
+    _check(load().rod_mailbox_disable(h), "rod_mailbox_disable")
+
+
+def rod_steps_done(h) -> int:
+    return int(load().rod_steps_done(h))
 
 
 def rod_last_launch_count(h) -> int:

@@ -147,6 +147,13 @@ struct corde_rods {
     int4* d_pairs;
   };
   std::vector<PairBin> pair_bins;
+  // mailbox of running launches
+  int mb_period = 0;
+  void* mb_in_host = nullptr;   // 16-byte seqlock header + [n_rods][8] floats, mapped pinned
+  void* mb_out_host = nullptr;  // [n_rods][2][8] words, mapped pinned
+  MailboxDev mb_dev = {};
+  unsigned mb_host_seq = 0;
+  long long steps_done = 0;
   // CUDA graph of one rod_step (all bins forked onto parallel branches)
   int graph_mode = 1;  // 0 never, 1 when a step needs more than one launch, 2 always
   cudaGraphExec_t graph_exec = nullptr;
@@ -375,8 +382,8 @@ int build_bins(rod_handle h) {
 }
 
 int launch_bins(rod_handle h, const std::vector<Bin>& bins, int n_steps, const float4* drive, cudaStream_t s,
-                float4* traj = nullptr) {
-  StepArgs a;
+                float4* traj = nullptr, const MailboxDev* mb = nullptr) {
+  StepArgs a = {};
   a.rods = h->d_rods;
   a.x4 = h->d_x;
   a.v4 = h->d_v;
@@ -388,6 +395,7 @@ int launch_bins(rod_handle h, const std::vector<Bin>& bins, int n_steps, const f
   a.n_steps = n_steps;
   a.traj = traj;
   a.n_elem = h->n_elem;
+  if (mb) a.mb = *mb;
   int launches = 0;
   for (const auto& b : bins) {
     a.work = b.d_work;
@@ -475,7 +483,7 @@ int launch_all(rod_handle h, int n_steps, const float4* d, cudaStream_t s, const
     ++launches;
   }
   if (!h->pair_bins.empty()) {
-    StepArgs a;
+    StepArgs a = {};
     a.rods = h->d_rods;
     a.work = nullptr;
     a.x4 = h->d_x;
@@ -700,8 +708,16 @@ int rod_step(rod_handle h, int n_steps, const float* drive, void* stream) {
       return fail(CORDE_ERR_ARG, "drive must be 16-byte aligned device, managed or mapped pinned host memory");
     d = reinterpret_cast<const float4*>(dp);
   }
+  if (h->mb_period > 0) {
+    MailboxDev mb = h->mb_dev;
+    mb.step0 = h->steps_done;
+    if (int rc = launch_bins(h, h->bins, n_steps, d, (cudaStream_t)stream, nullptr, &mb)) return rc;
+    h->steps_done += n_steps;
+    return CORDE_OK;
+  }
   const int n_launch = (int)h->bins.size() + (int)h->pair_bins.size();
   const bool use_graph = h->graph_mode == 2 || (h->graph_mode == 1 && n_launch > 1);
+  h->steps_done += n_steps;
   if (!use_graph) return launch_all(h, n_steps, d, (cudaStream_t)stream, nullptr);
   if (!h->d_drive_graph) CK(cudaMalloc(&h->d_drive_graph, h->n_rods * 2 * sizeof(float4)));
   CK(cudaMemcpyAsync(h->d_drive_graph, d, h->n_rods * 2 * sizeof(float4), cudaMemcpyDeviceToDevice,
@@ -956,6 +972,7 @@ int rod_bind(rod_handle h, int outer, int inner, int mode) {
   if (outer < 0 || inner < 0 || outer >= h->n_rods || inner >= h->n_rods || outer == inner)
     return fail(CORDE_ERR_ARG, "rod_bind: bad rod indices");
   if (mode < 0 || mode > 2) return fail(CORDE_ERR_ARG, "rod_bind: mode must be 0, 1 or 2");
+  if (h->mb_period > 0) return fail(CORDE_ERR_UNSUPPORTED, "rod_bind: not with a mailbox enabled");
   if (h->paired.empty()) h->paired.assign(h->n_rods, 0);
   if (h->paired[outer] || h->paired[inner]) return fail(CORDE_ERR_ARG, "rod_bind: rod already in a pair");
   const double* a = &h->derived[16 * (size_t)outer];
@@ -1106,6 +1123,111 @@ int rod_adjoint(rod_handle h, const float* dL_dpos_traj, float* dL_dK, float* dL
   return CORDE_OK;
 }
 
+static void mailbox_free(rod_handle h) {
+  if (h->mb_in_host) cudaFreeHost(h->mb_in_host);
+  if (h->mb_out_host) cudaFreeHost(h->mb_out_host);
+  cudaFree(h->mb_dev.log);
+  cudaFree(h->mb_dev.log_count);
+  h->mb_in_host = h->mb_out_host = nullptr;
+  h->mb_dev = MailboxDev{};
+  h->mb_period = 0;
+}
+
+int rod_mailbox_enable(rod_handle h, int period, int log_capacity) {
+  if (int rc = check_handle(h)) return rc;
+  if (period < 1 || log_capacity < 1) return fail(CORDE_ERR_ARG, "rod_mailbox_enable: period and log_capacity >= 1");
+  if (!h->pairs.empty()) return fail(CORDE_ERR_UNSUPPORTED, "rod_mailbox_enable: not with bound pairs");
+  CK(cudaDeviceSynchronize());
+  mailbox_free(h);
+  const size_t in_bytes = 16 + (size_t)h->n_rods * 8 * sizeof(float);
+  const size_t out_bytes = (size_t)h->n_rods * 16 * sizeof(unsigned);
+  CK(cudaHostAlloc(&h->mb_in_host, in_bytes, cudaHostAllocMapped | cudaHostAllocPortable));
+  CK(cudaHostAlloc(&h->mb_out_host, out_bytes, cudaHostAllocMapped | cudaHostAllocPortable));
+  std::memset(h->mb_in_host, 0, in_bytes);
+  std::memset(h->mb_out_host, 0, out_bytes);
+  void *din = nullptr, *dout = nullptr;
+  CK(cudaHostGetDevicePointer(&din, h->mb_in_host, 0));
+  CK(cudaHostGetDevicePointer(&dout, h->mb_out_host, 0));
+  h->mb_dev.in_seq = reinterpret_cast<const unsigned*>(din);
+  h->mb_dev.in_drive = reinterpret_cast<const float*>(static_cast<char*>(din) + 16);
+  h->mb_dev.out = reinterpret_cast<unsigned*>(dout);
+  CK(cudaMalloc(&h->mb_dev.log, (size_t)log_capacity * sizeof(int2)));
+  CK(cudaMalloc(&h->mb_dev.log_count, sizeof(int)));
+  CK(cudaMemset(h->mb_dev.log_count, 0, sizeof(int)));
+  h->mb_dev.log_cap = log_capacity;
+  h->mb_dev.period = period;
+  h->mb_period = period;
+  h->mb_host_seq = 0;
+  invalidate_graph(h);
+  return CORDE_OK;
+}
+
+int rod_mailbox_disable(rod_handle h) {
+  if (int rc = check_handle(h)) return rc;
+  CK(cudaDeviceSynchronize());
+  mailbox_free(h);
+  return CORDE_OK;
+}
+
+int rod_mailbox_write(rod_handle h, const float* drive) {
+  if (!h || !drive) return fail(CORDE_ERR_ARG, "rod_mailbox_write: NULL argument");
+  if (h->mb_period <= 0) return fail(CORDE_ERR_ARG, "rod_mailbox_write: mailbox not enabled");
+  unsigned* seq = static_cast<unsigned*>(h->mb_in_host);
+  unsigned* payload = reinterpret_cast<unsigned*>(static_cast<char*>(h->mb_in_host) + 16);
+  const unsigned s0 = h->mb_host_seq;
+  __atomic_store_n(seq, s0 + 1u, __ATOMIC_RELAXED);  // odd: the payload is being written
+  __atomic_thread_fence(__ATOMIC_SEQ_CST);
+  for (int k = 0; k < h->n_rods * 8; ++k) {
+    unsigned bits;
+    std::memcpy(&bits, &drive[k], sizeof(bits));
+    __atomic_store_n(&payload[k], bits, __ATOMIC_RELAXED);
+  }
+  __atomic_thread_fence(__ATOMIC_SEQ_CST);
+  __atomic_store_n(seq, s0 + 2u, __ATOMIC_RELEASE);
+  h->mb_host_seq = s0 + 2u;
+  return CORDE_OK;
+}
+
+int rod_mailbox_read(rod_handle h, unsigned* out) {
+  if (!h || !out) return fail(CORDE_ERR_ARG, "rod_mailbox_read: NULL argument");
+  if (h->mb_period <= 0) return fail(CORDE_ERR_ARG, "rod_mailbox_read: mailbox not enabled");
+  const unsigned* rec = static_cast<const unsigned*>(h->mb_out_host);
+  for (int k = 0; k < 2 * h->n_rods; ++k) {
+    const unsigned* r = rec + 8 * k;
+    unsigned* o = out + 8 * k;
+    bool ok = false;
+    for (int attempt = 0; attempt < 10000 && !ok; ++attempt) {
+      const unsigned s1 = __atomic_load_n(&r[0], __ATOMIC_ACQUIRE);
+      if (s1 & 1u) continue;
+      for (int j = 1; j < 8; ++j) o[j] = __atomic_load_n(&r[j], __ATOMIC_RELAXED);
+      __atomic_thread_fence(__ATOMIC_SEQ_CST);
+      const unsigned s2 = __atomic_load_n(&r[0], __ATOMIC_RELAXED);
+      if (s1 == s2) {
+        o[0] = s1;
+        ok = true;
+      }
+    }
+    if (!ok) return fail(CORDE_ERR_CUDA, "rod_mailbox_read: no consistent record after 10000 attempts");
+  }
+  return CORDE_OK;
+}
+
+int rod_mailbox_log(rod_handle h, int* out, int capacity, int* count) {
+  if (int rc = check_handle(h)) return rc;
+  if (!count || (capacity > 0 && !out)) return fail(CORDE_ERR_ARG, "rod_mailbox_log: NULL argument");
+  if (h->mb_period <= 0) return fail(CORDE_ERR_ARG, "rod_mailbox_log: mailbox not enabled");
+  CK(cudaDeviceSynchronize());
+  int n = 0;
+  CK(cudaMemcpy(&n, h->mb_dev.log_count, sizeof(int), cudaMemcpyDeviceToHost));
+  *count = n;
+  const int m = std::min(std::min(n, capacity), h->mb_dev.log_cap);
+  if (m > 0) CK(cudaMemcpy(out, h->mb_dev.log, (size_t)m * sizeof(int2), cudaMemcpyDeviceToHost));
+  CK(cudaMemset(h->mb_dev.log_count, 0, sizeof(int)));
+  return CORDE_OK;
+}
+
+int64_t rod_steps_done(rod_handle h) { return h ? h->steps_done : -1; }
+
 void rod_destroy(rod_handle h) {
   if (!h) return;
   cudaSetDevice(h->device);
@@ -1122,6 +1244,7 @@ void rod_destroy(rod_handle h) {
   for (auto ev : h->join_ev) cudaEventDestroy(ev);
   if (h->fork_ev) cudaEventDestroy(h->fork_ev);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  mailbox_free(h);
   delete h;
 }
 
@@ -1256,7 +1379,7 @@ extern "C" int rod_adjoint_noalloc(const RodParams* params, const float* pos, co
   while (2 * nt < N) nt *= 2;
   const int v = find_variant(2, nt);
   if (v < 0) return fail(CORDE_ERR_UNSUPPORTED, "rod_adjoint_noalloc: no step variant");
-  StepArgs a;
+  StepArgs a = {};
   a.rods = d_rod;
   a.work = d_work;
   a.x4 = x4;

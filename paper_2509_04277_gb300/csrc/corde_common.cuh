@@ -21,6 +21,48 @@ struct RodDev {
 };
 static_assert(sizeof(RodDev) == 80, "RodDev layout");
 
+// Mailbox of a running launch, in mapped pinned host memory (Section 2.2: the haptic thread
+// writes the device state into the running kernel and reads the feedback back at a rate
+// higher than the kernel launches).  Disabled when period == 0.
+//  in_seq / in_drive: seqlock word and [n_rods][8] drive rows written by the host;
+//  out: [n_rods][2] records of 8 words (seq, step, x, y, z, vx, vy, vz): record 0 the
+//       base node, record 1 the tip node, each under its own seqlock;
+//  log: (global step, input seq) of every input a rod picked up, *log_count entries.
+struct MailboxDev {
+  const unsigned* in_seq;
+  const float* in_drive;
+  unsigned* out;
+  int2* log;
+  int* log_count;
+  int log_cap;
+  int period;
+  long long step0;  // global index of the launch's first step
+};
+
+// System-scope loads/stores/fences for memory shared with the host while a kernel runs.
+__device__ __forceinline__ unsigned ld_acquire_sys(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.sys.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned ld_relaxed_sys(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.relaxed.sys.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ float ld_relaxed_sys_f(const float* p) {
+  float v;
+  asm volatile("ld.relaxed.sys.f32 %0, [%1];" : "=f"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_sys(unsigned* p, unsigned v) {
+  asm volatile("st.relaxed.sys.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_release_sys(unsigned* p, unsigned v) {
+  asm volatile("st.release.sys.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void fence_acq_rel_sys() { asm volatile("fence.acq_rel.sys;" ::: "memory"); }
+
 // ---------------------------------------------------------------- float3 helpers
 
 __device__ __forceinline__ float3 f3(float x, float y, float z) { return make_float3(x, y, z); }

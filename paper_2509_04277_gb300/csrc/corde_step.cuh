@@ -413,43 +413,94 @@ __device__ __forceinline__ void load_rod(const RodDev& R, const int t, const int
   }
 }
 
-// n_steps time steps of one rod per block.  traj (optional): positions after every step,
-// [n_steps][n_elements] float4 with .w the inverse mass.
-template <int EPT, int NT>
-__global__ void __launch_bounds__(NT)
-step_kernel(const RodDev* __restrict__ rods, const int* __restrict__ work, float4* __restrict__ x4,
-            float4* __restrict__ v4, float4* __restrict__ q4, float4* __restrict__ o4,
-            const float4* __restrict__ u4, const float4* __restrict__ k4, const float4* __restrict__ drive,
-            int n_steps, float4* __restrict__ traj, int64_t n_elem) {
-  static_assert(EPT % 2 == 0, "elements per thread must be even (red-black sweeps)");
-  extern __shared__ float4 smem[];
+// One non-blocking read attempt of the drive mailbox (seqlock: the host makes the word odd
+// while it writes).  Returns true, with the drive row of rod `rid`, for a new consistent
+// input; a torn or unchanged input is skipped (read again at the next poll).
+__device__ __forceinline__ bool mailbox_poll(const MailboxDev& mb, int rid, unsigned& last, float3& vd, float3& wd) {
+  const unsigned s1 = ld_acquire_sys(mb.in_seq);
+  if ((s1 & 1u) || s1 == last || s1 == 0u) return false;
+  float d[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) d[k] = ld_relaxed_sys_f(mb.in_drive + 8 * (int64_t)rid + k);
+  fence_acq_rel_sys();
+  if (ld_relaxed_sys(mb.in_seq) != s1) return false;
+  vd = f3(d[0], d[1], d[2]);
+  wd = f3(d[4], d[5], d[6]);
+  last = s1;
+  return true;
+}
+
+__device__ __forceinline__ void mailbox_log(const MailboxDev& mb, long long step, unsigned seq) {
+  const int k = atomicAdd(mb.log_count, 1);
+  if (k < mb.log_cap) mb.log[k] = make_int2((int)step, (int)seq);
+}
+
+// Seqlock write of one feedback record (seq, step, position, velocity).
+__device__ __forceinline__ void mailbox_write(unsigned* rec, unsigned& seq, long long step, float3 r, float3 v) {
+  st_relaxed_sys(rec, seq + 1u);
+  fence_acq_rel_sys();
+  st_relaxed_sys(rec + 1, (unsigned)step);
+  st_relaxed_sys(rec + 2, __float_as_uint(r.x));
+  st_relaxed_sys(rec + 3, __float_as_uint(r.y));
+  st_relaxed_sys(rec + 4, __float_as_uint(r.z));
+  st_relaxed_sys(rec + 5, __float_as_uint(v.x));
+  st_relaxed_sys(rec + 6, __float_as_uint(v.y));
+  st_relaxed_sys(rec + 7, __float_as_uint(v.z));
+  seq += 2u;
+  st_release_sys(rec, seq);
+}
+
+// The launch of one rod by the threads described by H: load, n_steps steps (with the
+// optional trajectory output and mailbox), store.
+template <int EPT, int NT, class Halo>
+__device__ __forceinline__ void run_rod(const RodDev& R, const Halo& H, const int rid, const float4* __restrict__ x4in,
+                                        float4* __restrict__ x4, float4* __restrict__ v4, float4* __restrict__ q4,
+                                        float4* __restrict__ o4, const float4* __restrict__ u4,
+                                        const float4* __restrict__ k4, const float4* __restrict__ drive, int n_steps,
+                                        float4* __restrict__ traj, int64_t n_elem, const MailboxDev& mb, float4* smem) {
   float4* par_u = smem;
   float4* par_k = smem + EPT * NT;
   float4* halo = smem + 2 * EPT * NT;
-
-  const int rid = work[blockIdx.x];
-  const RodDev R = rods[rid];
-  const int t = threadIdx.x;
-  const int e0 = t * EPT;
-
+  const int t = H.t;
+  const int e0 = H.tg() * EPT;
   float3 r[EPT], v[EPT], om[EPT];
   float4 q[EPT];
   float w[EPT];
-  load_rod<EPT, NT>(R, t, t, x4, v4, q4, o4, u4, k4, r, v, q, om, w, par_u, par_k);
+  load_rod<EPT, NT>(R, t, H.tg(), x4in, v4, q4, o4, u4, k4, r, v, q, om, w, par_u, par_k);
   float3 v_drive = zero3(), w_drive = zero3();
   if (drive != nullptr) {
     v_drive = f3(drive[2 * rid]);
     w_drive = f3(drive[2 * rid + 1]);
   }
+  const bool owns_base = e0 == 0;
+  const bool owns_tip = e0 <= R.n - 1 && R.n - 1 < e0 + EPT;
+  unsigned mb_last = 0u, seq_base = 0u, seq_tip = 0u;
+  unsigned* rec_base = nullptr;
+  unsigned* rec_tip = nullptr;
+  if (mb.period > 0) {
+    rec_base = mb.out + 16 * (int64_t)rid;
+    rec_tip = rec_base + 8;
+    if (owns_base) seq_base = ld_relaxed_sys(rec_base) & ~1u;
+    if (owns_tip) seq_tip = ld_relaxed_sys(rec_tip) & ~1u;
+  }
 
-  const BlockHalo<NT, NT> H{t};
   int xc = 0;  // exchange counter selects the ping-pong buffer
   for (int step = 0; step < n_steps; ++step) {
+    if (mb.period > 0 && owns_base && step % mb.period == 0)
+      if (mailbox_poll(mb, rid, mb_last, v_drive, w_drive)) mailbox_log(mb, mb.step0 + step, mb_last);
     step_body<EPT, NT, false>(R, H, r, v, q, om, w, par_u, par_k, halo, xc, v_drive, w_drive, nullptr, nullptr);
     if (traj != nullptr) {
 #pragma unroll
       for (int e = 0; e < EPT; ++e)
         if (e0 + e < R.n) traj[(int64_t)step * n_elem + R.off + e0 + e] = make_float4(r[e].x, r[e].y, r[e].z, w[e]);
+    }
+    if (mb.period > 0 && (step + 1) % mb.period == 0) {
+      if (owns_base) mailbox_write(rec_base, seq_base, mb.step0 + step + 1, r[0], v[0]);
+      if (owns_tip) {
+#pragma unroll
+        for (int e = 0; e < EPT; ++e)
+          if (e0 + e == R.n - 1) mailbox_write(rec_tip, seq_tip, mb.step0 + step + 1, r[e], v[e]);
+      }
     }
   }
 
@@ -463,6 +514,22 @@ step_kernel(const RodDev* __restrict__ rods, const int* __restrict__ work, float
       o4[R.off + i] = make_float4(om[e].x, om[e].y, om[e].z, 0.f);
     }
   }
+}
+
+// n_steps time steps of one rod per block.  traj (optional): positions after every step,
+// [n_steps][n_elements] float4 with .w the inverse mass.
+template <int EPT, int NT>
+__global__ void __launch_bounds__(NT)
+step_kernel(const RodDev* __restrict__ rods, const int* __restrict__ work, float4* __restrict__ x4,
+            float4* __restrict__ v4, float4* __restrict__ q4, float4* __restrict__ o4,
+            const float4* __restrict__ u4, const float4* __restrict__ k4, const float4* __restrict__ drive,
+            int n_steps, float4* __restrict__ traj, int64_t n_elem, MailboxDev mb) {
+  static_assert(EPT % 2 == 0, "elements per thread must be even (red-black sweeps)");
+  extern __shared__ float4 smem[];
+  const int rid = work[blockIdx.x];
+  const RodDev R = rods[rid];
+  const BlockHalo<NT, NT> H{(int)threadIdx.x};
+  run_rod<EPT, NT>(R, H, rid, x4, x4, v4, q4, o4, u4, k4, drive, n_steps, traj, n_elem, mb, smem);
 }
 
 }  // namespace corde

@@ -19,6 +19,7 @@ struct StepArgs {
   int n_steps;
   float4* traj;    // optional: positions after every step, [n_steps][n_elem]
   int64_t n_elem;
+  MailboxDev mb;   // mailbox of the launch (period 0: none)
 };
 
 typedef cudaError_t (*StepLaunchFn)(const StepArgs& a, int n_blocks, cudaStream_t s);
