@@ -119,28 +119,49 @@ __device__ __forceinline__ void segment_forces(float3 ra, float3 rb, float4 q, c
 // update).  With e = r_b - r_a (fixed during the sweeps of a step) and
 // d = (r_b + dt v_b) - (r_a + dt v_a) = e + dt (v_b - v_a) (the node difference is exact
 // for neighbouring nodes, whereas r + dt v would round dt v against |r|), returns
-// g = lambda n = -(|d| - l0) / (dt (w_a + w_b)) d / |d|; the caller applies
-// v_a -= w_a g, v_b += w_b g.  inv_dtW = 1 / (dt (w_a + w_b)) is computed once per step.
-// Explicit round-to-nearest intrinsics make the two threads that share a boundary
-// constraint compute bit-identical impulses.
+// g = lambda n = -(|d| - l0) / (dt (w_a + w_b)) d / |d| = (l0 / |d| - 1) inv_dtW d;
+// the caller applies v_a -= w_a g, v_b += w_b g.  inv_dtW = 1 / (dt (w_a + w_b)) is
+// computed once per step (0 for a constraint that does not exist: then e is a safe
+// non-zero vector and g = 0).
 __device__ __forceinline__ float3 constraint_impulse(float3 e, float3 va, float3 vb, float inv_dtW, float l0,
                                                      float dt) {
   const float3 d = f3(__fmaf_rn(dt, __fsub_rn(vb.x, va.x), e.x), __fmaf_rn(dt, __fsub_rn(vb.y, va.y), e.y),
                       __fmaf_rn(dt, __fsub_rn(vb.z, va.z), e.z));
   const float dd = __fmaf_rn(d.x, d.x, __fmaf_rn(d.y, d.y, __fmul_rn(d.z, d.z)));
-  const float il = rsqrtf(dd);
-  const float s = __fmul_rn(__fmul_rn(__fsub_rn(l0, __fmul_rn(dd, il)), il), inv_dtW);
+  const float s = __fmul_rn(__fmaf_rn(l0, rsqrtf(dd), -1.f), inv_dtW);
   return f3(__fmul_rn(s, d.x), __fmul_rn(s, d.y), __fmul_rn(s, d.z));
 }
 
-// Per-step data of one constraint: e = r_b - r_a and 1 / (dt (w_a + w_b)), or 0 when the
-// constraint does not exist or joins two kinematic nodes.
+// Two independent constraints in the two lanes of packed FP32x2 operations (Blackwell
+// fma/mul/add.f32x2): lane x and lane y each compute exactly what constraint_impulse
+// computes for them (round-to-nearest per lane), with half the instructions.
+struct Vec3x2 {
+  float2 x, y, z;
+};
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ Vec3x2 constraint_impulse2(const Vec3x2& e, const Vec3x2& va, const Vec3x2& vb,
+                                                      float2 inv_dtW, float l0, float dt) {
+  const float2 dt2 = make_float2(dt, dt);
+  const float2 dx = __ffma2_rn(dt2, __fadd2_rn(vb.x, neg2(va.x)), e.x);
+  const float2 dy = __ffma2_rn(dt2, __fadd2_rn(vb.y, neg2(va.y)), e.y);
+  const float2 dz = __ffma2_rn(dt2, __fadd2_rn(vb.z, neg2(va.z)), e.z);
+  const float2 dd = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+  const float2 il = make_float2(rsqrtf(dd.x), rsqrtf(dd.y));
+  const float2 sv = __fmul2_rn(__ffma2_rn(make_float2(l0, l0), il, make_float2(-1.f, -1.f)), inv_dtW);
+  return Vec3x2{__fmul2_rn(sv, dx), __fmul2_rn(sv, dy), __fmul2_rn(sv, dz)};
+}
+
+// Per-step data of one constraint: e = r_b - r_a and 1 / (dt (w_a + w_b)); a constraint
+// that does not exist (or joins two kinematic nodes) gets 0 and a safe e.
 __device__ __forceinline__ float3 segment_vector(float3 ra, float3 rb) {
   return f3(__fsub_rn(rb.x, ra.x), __fsub_rn(rb.y, ra.y), __fsub_rn(rb.z, ra.z));
 }
 __device__ __forceinline__ float inv_dt_wsum(bool exists, float wa, float wb, float dt) {
   const float ws = __fadd_rn(wa, wb);
   return (exists && ws > 0.f) ? __frcp_rn(__fmul_rn(dt, ws)) : 0.f;
+}
+__device__ __forceinline__ float3 safe_segment(float inv, float3 e, float l0) {
+  return inv != 0.f ? e : f3(0.f, 0.f, l0);
 }
 
 // Hook into the constraint loop of step_body: before_iterations() once per step before
@@ -296,32 +317,54 @@ __device__ __forceinline__ void step_body(const RodDev& R, const Halo& H, float3
     float i_even[NE], i_odd[NO];
 #pragma unroll
     for (int k = 0; k < NE; ++k) {
-      e_even[k] = segment_vector(r[2 * k], r[2 * k + 1]);
       i_even[k] = inv_dt_wsum(e0 + 2 * k + 1 <= n - 1, w[2 * k], w[2 * k + 1], dt);
+      e_even[k] = safe_segment(i_even[k], segment_vector(r[2 * k], r[2 * k + 1]), R.l0);
     }
 #pragma unroll
     for (int k = 0; k < NO; ++k) {
       const bool ex = EPT / 2 > 1 && e0 + 2 * k + 2 <= n - 1;
-      e_odd[k] = ex ? segment_vector(r[(2 * k + 1) % EPT], r[(2 * k + 2) % EPT]) : zero3();
       i_odd[k] = inv_dt_wsum(ex, w[(2 * k + 1) % EPT], w[(2 * k + 2) % EPT], dt);
+      e_odd[k] = safe_segment(i_odd[k], segment_vector(r[(2 * k + 1) % EPT], r[(2 * k + 2) % EPT]), R.l0);
     }
-    const float3 e_right = segment_vector(r[EPT - 1], r_next);
+    // the two boundary constraints, right (my last, next first) in lane x and left
+    // (previous last, my first) in lane y
     const float i_right = inv_dt_wsum(has_next && e0 + EPT <= n - 1, w[EPT - 1], w_next, dt);
-    const float3 e_left = segment_vector(r_prev, r[0]);
     const float i_left = inv_dt_wsum(has_prev && e0 <= n - 1, w_prev, w[0], dt);
+    const float3 e_r = safe_segment(i_right, segment_vector(r[EPT - 1], r_next), R.l0);
+    const float3 e_l = safe_segment(i_left, segment_vector(r_prev, r[0]), R.l0);
+    const Vec3x2 e_bnd{make_float2(e_r.x, e_l.x), make_float2(e_r.y, e_l.y), make_float2(e_r.z, e_l.z)};
+    const float2 i_bnd = make_float2(i_right, i_left);
+    const float2 w_bnd = make_float2(-w[EPT - 1], w[0]);
 
     for (int it = 0; it < R.n_iters; ++it) {
       if constexpr (STORE) {
 #pragma unroll
         for (int e = 0; e < EPT; ++e) sweep_v[((2 * it) * EPT + e) * NT + t] = make_float4(v[e].x, v[e].y, v[e].z, 0.f);
       }
-      // even segments (e0 + 2k, e0 + 2k + 1): local to the thread
+      // even segments (e0 + 2k, e0 + 2k + 1): local to the thread, two per packed op
+      if constexpr (NE == 1) {
+        const float3 g = constraint_impulse(e_even[0], v[0], v[1], i_even[0], R.l0, dt);
+        v[0] -= w[0] * g;
+        v[1] += w[1] * g;
+      } else {
 #pragma unroll
-      for (int k = 0; k < NE; ++k) {
-        if (i_even[k] != 0.f) {
-          const float3 g = constraint_impulse(e_even[k], v[2 * k], v[2 * k + 1], i_even[k], R.l0, dt);
-          v[2 * k] -= w[2 * k] * g;
-          v[2 * k + 1] += w[2 * k + 1] * g;
+        for (int k = 0; k + 1 < NE; k += 2) {
+          const int a0 = 2 * k, b0 = 2 * k + 1, a1 = 2 * k + 2, b1 = 2 * k + 3;
+          const Vec3x2 ep{make_float2(e_even[k].x, e_even[k + 1].x), make_float2(e_even[k].y, e_even[k + 1].y),
+                          make_float2(e_even[k].z, e_even[k + 1].z)};
+          const Vec3x2 va{make_float2(v[a0].x, v[a1].x), make_float2(v[a0].y, v[a1].y), make_float2(v[a0].z, v[a1].z)};
+          const Vec3x2 vb{make_float2(v[b0].x, v[b1].x), make_float2(v[b0].y, v[b1].y), make_float2(v[b0].z, v[b1].z)};
+          const Vec3x2 g = constraint_impulse2(ep, va, vb, make_float2(i_even[k], i_even[k + 1]), R.l0, dt);
+          v[a0] -= w[a0] * f3(g.x.x, g.y.x, g.z.x);
+          v[a1] -= w[a1] * f3(g.x.y, g.y.y, g.z.y);
+          v[b0] += w[b0] * f3(g.x.x, g.y.x, g.z.x);
+          v[b1] += w[b1] * f3(g.x.y, g.y.y, g.z.y);
+        }
+        if constexpr (NE % 2 == 1) {
+          const int a = EPT - 2, b = EPT - 1;
+          const float3 g = constraint_impulse(e_even[NE - 1], v[a], v[b], i_even[NE - 1], R.l0, dt);
+          v[a] -= w[a] * g;
+          v[b] += w[b] * g;
         }
       }
       if constexpr (STORE) {
@@ -338,22 +381,25 @@ __device__ __forceinline__ void step_body(const RodDev& R, const Halo& H, float3
       // odd segments inside the thread
 #pragma unroll
       for (int k = 0; k + 1 < EPT / 2; ++k) {
-        if (i_odd[k] != 0.f) {
-          const int a = 2 * k + 1, b = 2 * k + 2;
-          const float3 g = constraint_impulse(e_odd[k], v[a], v[b], i_odd[k], R.l0, dt);
-          v[a] -= w[a] * g;
-          v[b] += w[b] * g;
-        }
+        const int a = 2 * k + 1, b = 2 * k + 2;
+        const float3 g = constraint_impulse(e_odd[k], v[a], v[b], i_odd[k], R.l0, dt);
+        v[a] -= w[a] * g;
+        v[b] += w[b] * g;
       }
-      // odd segment across the right boundary: (my last, right neighbour's first)
-      if (i_right != 0.f) {
-        const float3 g = constraint_impulse(e_right, v[EPT - 1], f3(H.next(hb, 0)), i_right, R.l0, dt);
-        v[EPT - 1] -= w[EPT - 1] * g;
-      }
-      // odd segment across the left boundary: (left neighbour's last, my first)
-      if (i_left != 0.f) {
-        const float3 g = constraint_impulse(e_left, f3(H.prev(hb, 1)), v[0], i_left, R.l0, dt);
-        v[0] += w[0] * g;
+      // odd segments across the two thread boundaries, in one packed evaluation
+      {
+        const float3 vn = has_next ? f3(H.next(hb, 0)) : zero3();
+        const float3 vp = has_prev ? f3(H.prev(hb, 1)) : zero3();
+        const Vec3x2 va{make_float2(v[EPT - 1].x, vp.x), make_float2(v[EPT - 1].y, vp.y),
+                        make_float2(v[EPT - 1].z, vp.z)};
+        const Vec3x2 vb{make_float2(vn.x, v[0].x), make_float2(vn.y, v[0].y), make_float2(vn.z, v[0].z)};
+        const Vec3x2 g = constraint_impulse2(e_bnd, va, vb, i_bnd, R.l0, dt);
+        // right: v_last -= w_last g.x ; left: v_first += w_first g.y
+        const float2 nx = __ffma2_rn(w_bnd, g.x, make_float2(v[EPT - 1].x, v[0].x));
+        const float2 ny = __ffma2_rn(w_bnd, g.y, make_float2(v[EPT - 1].y, v[0].y));
+        const float2 nz = __ffma2_rn(w_bnd, g.z, make_float2(v[EPT - 1].z, v[0].z));
+        v[EPT - 1] = f3(nx.x, ny.x, nz.x);
+        v[0] = f3(nx.y, ny.y, nz.y);
       }
       hook.template after_odd<EPT>(r, v, w);
     }
