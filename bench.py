@@ -396,6 +396,46 @@ def run_long_rods(args, torch, corde, W):
     return out
 
 
+def run_tube(args, torch, corde, W):
+    """Guidewire insertion into a curved vessel (contact constraints with Coulomb friction
+    against an analytic tube): 512 nodes, vessel centreline radius 0.5 m, inner radius
+    2 mm, mu = 0.1, base pushed at 5 cm/s; 10 steps per launch, 100 launches timed after
+    300 steps of settling (the wire then presses on the outer wall), beside the same
+    rod without the vessel."""
+    stream = torch.cuda.current_stream()
+    drive = torch.as_tensor(np.array([[0.05, 0, 0, 0, 0, 0, 2.0, 0]], np.float32), device="cuda")
+    out = {}
+    for with_tube in (True, False):
+        rod, tube = W.vessel_guidewire(512, seed=11)
+        b = corde.RodBatch([rod])
+        if with_tube:
+            b.set_tube(0, tube)
+        b.autotune(STEPS_PER_LAUNCH)
+        for _ in range(30):
+            b.step(STEPS_PER_LAUNCH, drive=drive)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(100):
+            b.step(STEPS_PER_LAUNCH, drive=drive)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        key = "vessel" if with_tube else "free"
+        out[key] = {"us_per_step": round(e0.elapsed_time(e1) * 1e3 / (100 * STEPS_PER_LAUNCH), 4),
+                    "plan": [int(x) for x in b.plan()[0]]}
+        if with_tube:
+            pos = b.rod_state(b.state_numpy(), 0)["pos"]
+            off = np.hypot(np.hypot(pos[:, 0] - tube[0], pos[:, 1] - tube[1]) - tube[3], pos[:, 2] - tube[2])
+            allow = tube[4] - rod.radius
+            out[key]["nodes_on_wall"] = int(np.sum(off > allow * (1 - 1e-3)))
+            out[key]["max_offset_over_allow"] = round(float(off.max() / allow), 6)
+        b.close()
+    return {"unit": "us/step", "workload": "512-node guidewire in a curved vessel (Rc 0.5 m, Rt 2 mm, mu 0.1), "
+                                           "10 constraint iterations over distance and contact constraints",
+            **out}
+
+
 def cpu_baseline_single(seconds=10.0):
     """The FP64 oracle as it stands, one host core, on the 512-element guidewire."""
     import oracle
@@ -488,6 +528,7 @@ def main_ours(args):
                 "batched": lambda: run_batched(args, torch, corde, W, rank, world),
                 "pair": lambda: run_pair(args, torch, corde, W),
                 "long": lambda: run_long_rods(args, torch, corde, W),
+                "tube": lambda: run_tube(args, torch, corde, W),
                 "adjoint": lambda: run_adjoint(args, torch, corde, W, 1)}[args.only]()
         if rank == 0:
             print(json.dumps({"only": args.only, "result": part}, default=str), flush=True)
@@ -496,6 +537,7 @@ def main_ours(args):
     batched = run_batched(args, torch, corde, W, rank, world) if not args.skip_batched else None
     pair = run_pair(args, torch, corde, W) if not args.skip_pair else None
     long_rods = run_long_rods(args, torch, corde, W) if not args.skip_long else None
+    tube = run_tube(args, torch, corde, W) if not args.skip_tube else None
     adjoint = None
     if not args.skip_adjoint:
         adjoint = {"single": run_adjoint(args, torch, corde, W, 1), "batched": run_adjoint(args, torch, corde, W, 256)}
@@ -588,6 +630,8 @@ def main_ours(args):
         if long_rods is not None:
             out["long_rods"] = {"unit": "us/step", "steps_per_launch": STEPS_PER_LAUNCH,
                                 "by_nodes": long_rods}
+        if tube is not None:
+            out["vessel_contact"] = tube
         print(json.dumps(out), flush=True)
     _barrier(torch)
     if world > 1:
@@ -651,7 +695,8 @@ def main():
     ap.add_argument("--skip-adjoint", action="store_true")
     ap.add_argument("--skip-pair", action="store_true")
     ap.add_argument("--skip-long", action="store_true")
-    ap.add_argument("--only", choices=["single", "batched", "pair", "adjoint", "long"], default=None,
+    ap.add_argument("--skip-tube", action="store_true")
+    ap.add_argument("--only", choices=["single", "batched", "pair", "adjoint", "long", "tube"], default=None,
                     help="run one part only and print its raw result (profiling aid, not a bench line)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="fixed kernel plan (single rod <2, 256>, batch default plan)")

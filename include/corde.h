@@ -111,6 +111,21 @@ int rod_step(rod_handle h, int n_steps, const float* drive, void* stream);
  * rod_adjoint.  Synchronous (rebuilds the launch plan). */
 int rod_bind(rod_handle h, int outer, int inner, int mode);
 
+/* Collision with an analytic vessel for rod `rod` (contact constraints C_c with Coulomb
+ * friction, Section 2.1 "Constraints", iterated with the distance constraints as in
+ * Section 3.3; an analytic tube stands in for the paper's vessel meshes).
+ * tube: 8 host doubles (cx, cy, cz, Rc, Rt, mu, enable, 0): the vessel centreline is the
+ * circle of radius Rc about (cx, cy) in the plane z = cz, its inner radius Rt > rod radius,
+ * mu >= 0 the friction coefficient; enable = 0 removes the vessel.  Every constraint
+ * iteration, after the distance sweeps, each dynamic node with predicted centreline offset
+ * |(r - c) + dt v| > Rt - radius gets the normal velocity change that puts it on the wall
+ * and a tangential velocity cut of at most mu times that change.
+ * Errors: CORDE_ERR_ARG for a bad index, NULL tube, Rc <= 0, Rt <= rod radius or mu < 0;
+ * CORDE_ERR_UNSUPPORTED for an extensible rod (n_iters = 0: no constraint iterations) or a
+ * rod bound in a pair (rod_bind likewise refuses rods inside a vessel).  rod_adjoint
+ * refuses handles with a vessel (contact is not differentiated).  Synchronous. */
+int rod_set_tube(rod_handle h, int rod, const double* tube);
+
 /* Copy the drive input [n_rods][8] (host or device) into the handle. */
 int rod_set_input(rod_handle h, const float* drive, void* stream);
 

@@ -71,10 +71,12 @@ def lib():
             L.oracle_count_flops.argtypes = [_P, _D, _D, _D, ctypes.c_int]
             L.oracle_count_flops.restype = ctypes.c_int64
             L.oracle_step_batch.argtypes = [ctypes.c_int, _P, _D, _D, _D, _D, _D, ctypes.c_int]
+            L.oracle_step_tube.argtypes = [_P, _D, _D, _D, _D, _D, _D, _D, ctypes.c_int]
             L.oracle_step_pair.argtypes = [_P, _D, _D, _D, _D, _D, _D, _P, _D, _D, _D, _D, _D, _D, ctypes.c_int,
                                            ctypes.c_double, ctypes.c_int]
             for name in ("oracle_derive", "oracle_darboux", "oracle_energy", "oracle_forces", "oracle_step",
-                         "oracle_rollout", "oracle_rollout_jvp", "oracle_step_batch", "oracle_step_pair"):
+                         "oracle_rollout", "oracle_rollout_jvp", "oracle_step_batch", "oracle_step_pair",
+                         "oracle_step_tube"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -252,3 +254,12 @@ def step_pair(outer, s_outer, inner, s_inner, mode, beta, n_steps=1, drive_outer
                                   _ptr(si["quat"]), _ptr(si["vel"]), _ptr(si["omega"]), _ptr(_arr(drive_inner)),
                                   int(mode), float(beta), int(n_steps)), "oracle_step_pair")
     return so, si
+
+
+def step_tube(rod, state, tube, n_steps=1, drive=None):
+    """Advance a copy of ``state`` inside an analytic vessel tube = [cx, cy, cz, Rc, Rt, mu]."""
+    s = {k: _arr(v).copy() for k, v in state.items()}
+    _check(lib().oracle_step_tube(ctypes.byref(params(rod)), _ptr(_arr(rod.rest_quat)), _ptr(s["pos"]),
+                                  _ptr(s["quat"]), _ptr(s["vel"]), _ptr(s["omega"]), _ptr(_arr(drive)),
+                                  _ptr(_arr(tube)), int(n_steps)), "oracle_step_tube")
+    return s

@@ -420,16 +420,53 @@ static void integrate_positions(const OracleParams& p, const Derived& d, State<T
   }
 }
 
+// Collision response against an analytic vessel (contact constraints C_c with Coulomb
+// friction, Section 2.1 "Constraints"; iterated with the distance constraints, Section
+// 3.3).  tube = [cx, cy, cz, Rc, Rt, mu]: the vessel centreline is the circle of radius Rc
+// about (cx, cy) in the plane z = cz, its inner radius Rt.  A dynamic node must keep its
+// predicted position p = r + dt v within Rt - r of the centreline.  With c the centreline
+// point nearest to p and delta = p - c, a violation |delta| > Rt - r changes the
+// normal velocity by dvn = -(|delta| - (Rt - r)) / dt along n = delta / |delta| and cuts
+// the tangential velocity v_t by at most mu |dvn| (Coulomb).
+template <class T>
+static void contact_sweep(const OracleParams& p, const Derived& d, State<T>& s, const double* tube) {
+  const double dt = p.dt;
+  const double allow = tube[4] - p.radius;
+  for (int i = 0; i < d.N; ++i) {
+    if (d.w[i] == 0.0) continue;
+    const V3<T> pr = s.r[i] + dt * s.v[i];
+    const T dx = pr.x - T(tube[0]), dy = pr.y - T(tube[1]);
+    const T rho = sqrt(dx * dx + dy * dy);
+    if (val(rho) == 0.0) continue;
+    const V3<T> c{T(tube[0]) + T(tube[3]) * dx / rho, T(tube[1]) + T(tube[3]) * dy / rho, T(tube[2])};
+    const V3<T> delta = pr - c;
+    const T dist = norm(delta);
+    if (!(val(dist) > allow)) continue;
+    const V3<T> n = (T(1.0) / dist) * delta;
+    const T dvn = -(dist - T(allow)) / T(dt);
+    const V3<T> vt = s.v[i] - dot(s.v[i], n) * n;
+    const T vtn = norm(vt);
+    T keep(1.0);
+    if (val(vtn) > 0.0) {
+      const T f = T(1.0) - T(tube[5]) * (val(dvn) < 0 ? -dvn : dvn) / vtn;
+      keep = val(f) > 0.0 ? f : T(0.0);
+    }
+    s.v[i] = (s.v[i] + dvn * n) - (T(1.0) - keep) * vt;
+  }
+}
+
 // One time step of one rod, Fig. 5 order: forces, then n_iters iterations of the
-// red-black distance sweeps (even segments, then odd), then the position update.
+// red-black distance sweeps (even segments, then odd) followed by the collision response
+// (when a vessel is given), then the position update.
 template <class T>
 static void step(const OracleParams& p, const Derived& d, const Material<T>& mat, State<T>& s,
-                 const double* drive, const double* f_ext, const double* tau_ext) {
+                 const double* drive, const double* f_ext, const double* tau_ext, const double* tube = nullptr) {
   integrate_forces(p, d, mat, s, drive, f_ext, tau_ext);
   if (p.inextensible) {
     for (int it = 0; it < p.n_iters; ++it) {
       distance_sweep(p, d, s, 0);
       distance_sweep(p, d, s, 1);
+      if (tube) contact_sweep(p, d, s, tube);
     }
   }
   integrate_positions(p, d, s);
@@ -688,6 +725,22 @@ int oracle_rollout_jvp(const OracleParams* p, const double* rest_quat, const dou
       if (dtraj) { dtraj[o] = s.r[i].x.d; dtraj[o + 1] = s.r[i].y.d; dtraj[o + 2] = s.r[i].z.d; }
     }
   }
+  return 0;
+}
+
+// n_steps time steps of one rod inside an analytic vessel tube = [cx, cy, cz, Rc, Rt, mu]
+// (see contact_sweep); otherwise as oracle_step.
+int oracle_step_tube(const OracleParams* p, const double* rest_quat, double* pos, double* quat, double* vel,
+                     double* omega, const double* drive, const double* tube, int n_steps) {
+  if (!valid(p) || !pos || !quat || !vel || !omega || !tube || n_steps < 0) return -1;
+  if (!(tube[3] > 0) || !(tube[4] > p->radius) || !(tube[5] >= 0)) return -1;
+  Derived d = derive(*p);
+  Material<double> mat;
+  load_material(d, rest_quat, nullptr, mat);
+  State<double> s;
+  load_state(d, pos, quat, vel, omega, s);
+  for (int k = 0; k < n_steps; ++k) step(*p, d, mat, s, drive, nullptr, nullptr, tube);
+  store_state(d, s, pos, quat, vel, omega);
   return 0;
 }
 

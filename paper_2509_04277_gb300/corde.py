@@ -50,6 +50,7 @@ SIGNATURES = {
     "rod_step": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP]),
     "rod_set_input": (ctypes.c_int, [_VP, _VP, _VP]),
     "rod_bind": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "rod_set_tube": (ctypes.c_int, [_VP, ctypes.c_int, _VP]),
     "rod_get_state": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "rod_set_state": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "rod_info": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64)]),
@@ -145,6 +146,14 @@ def rod_step(h, n_steps, drive=None, stream=None):
 
 def rod_bind(h, outer, inner, mode):
     _check(load().rod_bind(h, int(outer), int(inner), int(mode)), "rod_bind")
+
+
+def rod_set_tube(h, rod, tube, enable=True):
+    """tube = (cx, cy, cz, Rc, Rt, mu): analytic vessel of rod `rod` (enable=False removes it)."""
+    t = np.zeros(8, dtype=np.float64)
+    t[:6] = np.asarray(tube, dtype=np.float64)[:6]
+    t[6] = 1.0 if enable else 0.0
+    _check(load().rod_set_tube(h, int(rod), t.ctypes.data), "rod_set_tube")
 
 
 def rod_set_input(h, drive, stream=None):
@@ -392,6 +401,10 @@ class RodBatch:
 
     def bind(self, outer, inner, mode):
         rod_bind(self.handle, outer, inner, mode)
+
+    def set_tube(self, rod, tube, enable=True):
+        """Analytic vessel (cx, cy, cz, Rc, Rt, mu) for rod `rod`; enable=False removes it."""
+        rod_set_tube(self.handle, rod, tube, enable)
 
     def set_plan(self, ept, nt):
         rod_set_plan(self.handle, ept, nt)

@@ -142,6 +142,7 @@ struct corde_rods {
   // catheter/guidewire pairs
   std::vector<int4> pairs;     // (outer, inner, mode, 0)
   std::vector<char> paired;    // per rod
+  std::vector<char> tube;      // per rod: vessel contact enabled
   struct PairBin {
     int ept, nt, count;
     int4* d_pairs;
@@ -221,6 +222,8 @@ __global__ void derive_kernel(int n_rods, const RodParams* __restrict__ P, const
   R.J3 = (float)J3;
   R.Jinv1 = (float)(1.0 / J1);
   R.Jinv3 = (float)(1.0 / J3);
+  R.tube_cx = R.tube_cy = R.tube_cz = R.tube_rc = 0.f;
+  R.tube_allow = R.tube_mu = R.pad2 = R.pad3 = 0.f;
   rods[r] = R;
   double* d = derived + 16 * (size_t)r;
   d[0] = l0; d[1] = A; d[2] = I; d[3] = K1; d[4] = K1; d[5] = K3; d[6] = Ks; d[7] = Kp;
@@ -611,6 +614,7 @@ int rod_create(int n_rods, const RodParams* params, const float* pos, const floa
   h->off = off;
   h->n_iters.resize(n_rods);
   h->dt.resize(n_rods);
+  h->tube.assign(n_rods, 0);
   for (int r = 0; r < n_rods; ++r) {
     h->n_iters[r] = params[r].inextensible ? params[r].n_iters : 0;
     h->dt[r] = params[r].dt;
@@ -937,6 +941,38 @@ int rod_autotune(rod_handle h, int n_steps, void* stream) {
   return build_bins(h);
 }
 
+__global__ void set_tube_kernel(RodDev* rods, int r, float cx, float cy, float cz, float rc, float allow, float mu,
+                                int enable) {
+  RodDev& R = rods[r];
+  R.tube_cx = cx;
+  R.tube_cy = cy;
+  R.tube_cz = cz;
+  R.tube_rc = rc;
+  R.tube_allow = allow;
+  R.tube_mu = mu;
+  R.flags = enable ? (R.flags | F_TUBE) : (R.flags & ~F_TUBE);
+}
+
+int rod_set_tube(rod_handle h, int rod, const double* tube) {
+  if (int rc = check_handle(h)) return rc;
+  if (rod < 0 || rod >= h->n_rods || !tube) return fail(CORDE_ERR_ARG, "rod_set_tube: bad rod or NULL tube");
+  const double radius = h->derived[16 * (size_t)rod + 1] > 0 ? std::sqrt(h->derived[16 * (size_t)rod + 1] / kPi) : 0;
+  const int enable = tube[6] != 0.0;
+  if (enable && !(tube[3] > 0 && tube[4] > radius && tube[5] >= 0))
+    return fail(CORDE_ERR_ARG, "rod_set_tube: need rc > 0, inner radius > rod radius, mu >= 0");
+  if (enable && h->n_iters[rod] == 0)
+    return fail(CORDE_ERR_UNSUPPORTED, "rod_set_tube: contact runs in the constraint iterations of an inextensible rod");
+  if (enable && !h->paired.empty() && h->paired[rod])
+    return fail(CORDE_ERR_UNSUPPORTED, "rod_set_tube: not for a rod bound in a pair");
+  set_tube_kernel<<<1, 1>>>(h->d_rods, rod, (float)tube[0], (float)tube[1], (float)tube[2], (float)tube[3],
+                            (float)(tube[4] - radius), (float)tube[5], enable);
+  CK(cudaGetLastError());
+  CK(cudaDeviceSynchronize());
+  if (enable) h->tube[rod] = 1;
+  else h->tube[rod] = 0;
+  return CORDE_OK;
+}
+
 // Pair kernel layout: two elements per thread up to 512 nodes per rod, four up to 1024,
 // the smallest power-of-two group (>= 32 threads) holding the longer rod.
 static int pair_layout(int n, int* ept, int* nt) {
@@ -975,6 +1011,7 @@ int rod_bind(rod_handle h, int outer, int inner, int mode) {
   if (h->mb_period > 0) return fail(CORDE_ERR_UNSUPPORTED, "rod_bind: not with a mailbox enabled");
   if (h->paired.empty()) h->paired.assign(h->n_rods, 0);
   if (h->paired[outer] || h->paired[inner]) return fail(CORDE_ERR_ARG, "rod_bind: rod already in a pair");
+  if (h->tube[outer] || h->tube[inner]) return fail(CORDE_ERR_UNSUPPORTED, "rod_bind: not for a rod inside a vessel");
   const double* a = &h->derived[16 * (size_t)outer];
   const double* b = &h->derived[16 * (size_t)inner];
   if (h->n_iters[outer] != h->n_iters[inner] || h->n_iters[outer] == 0)
@@ -1062,6 +1099,8 @@ int rod_adjoint(rod_handle h, const float* dL_dpos_traj, float* dL_dK, float* dL
   if (int rc = check_handle(h)) return rc;
   if (h->ro_steps < 1) return fail(CORDE_ERR_ARG, "rod_adjoint needs a preceding rod_rollout");
   if (!h->pairs.empty()) return fail(CORDE_ERR_UNSUPPORTED, "rod_adjoint: bound pairs are not supported");
+  for (int r = 0; r < h->n_rods; ++r)
+    if (h->tube[r]) return fail(CORDE_ERR_UNSUPPORTED, "rod_adjoint: vessel contact is not differentiated");
   for (int r = 0; r < h->n_rods; ++r)
     if (h->n_nodes[r] > kAdjointMaxNodes)
       return fail(CORDE_ERR_UNSUPPORTED, "the adjoint kernel holds rods of at most " +

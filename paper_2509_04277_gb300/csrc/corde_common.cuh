@@ -6,7 +6,7 @@
 
 namespace corde {
 
-enum : int { F_INEXT = 1, F_CLAMP = 2 };
+enum : int { F_INEXT = 1, F_CLAMP = 2, F_TUBE = 4 };
 
 // Per-rod constants used by the step kernel (derived once at creation, FP64 -> FP32).
 struct RodDev {
@@ -18,8 +18,10 @@ struct RodDev {
   float Ks, inv_l0, damp, pad0;   // stretch stiffness, 1 / l0, 1 / (1 + alpha dt)
   float gx, gy, gz, pad1;         // gravity acceleration of a dynamic node (g / mass_scale)
   float J1, J3, Jinv1, Jinv3;     // inertial frame inertia diag (J1, J1, J3) and inverses
+  float tube_cx, tube_cy, tube_cz, tube_rc;  // vessel centreline: circle in the plane z = cz
+  float tube_allow, tube_mu, pad2, pad3;     // inner radius minus rod radius, Coulomb friction
 };
-static_assert(sizeof(RodDev) == 80, "RodDev layout");
+static_assert(sizeof(RodDev) == 112, "RodDev layout");
 
 // Mailbox of a running launch, in mapped pinned host memory (Section 2.2: the haptic thread
 // writes the device state into the running kernel and reads the feedback back at a rate

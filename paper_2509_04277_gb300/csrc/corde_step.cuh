@@ -164,6 +164,36 @@ __device__ __forceinline__ float3 safe_segment(float inv, float3 e, float l0) {
   return inv != 0.f ? e : f3(0.f, 0.f, l0);
 }
 
+// Contact of node (r, v) with the wall of an analytic vessel (collision constraint C_c with
+// Coulomb friction, Section 2.1 "Constraints"; a tube stands in for the vessel meshes):
+// the centreline is the circle of radius rc about (cx, cy) in the plane z = cz; the node
+// must stay within `allow` (inner radius minus rod radius) of it.  With p = r + dt v the
+// predicted position and c the centreline point nearest to p, delta = p - c is normal to
+// the centreline; if |delta| > allow the
+// normal velocity changes by dvn = -(|delta| - allow) / dt along n = delta / |delta| (the
+// predicted node lands on the wall) and the tangential velocity shrinks by at most
+// mu |dvn| (Coulomb).  Kinematic nodes (w = 0) are skipped.
+__device__ __forceinline__ void tube_contact(float3 r, float3& v, float w, const RodDev& R, float dt) {
+  if (!(w > 0.f)) return;
+  const float3 p = r + dt * v;  // predicted position; its closest centreline point
+  const float dx = p.x - R.tube_cx, dy = p.y - R.tube_cy;
+  const float rho2 = dx * dx + dy * dy;
+  if (!(rho2 > 0.f)) return;
+  const float k = 1.f - R.tube_rc * rsqrtf(rho2);
+  const float3 delta = f3(dx * k, dy * k, p.z - R.tube_cz);
+  const float d2 = dot3(delta, delta);
+  if (!(d2 > R.tube_allow * R.tube_allow)) return;
+  const float il = rsqrtf(d2);
+  const float3 n = il * delta;
+  const float dvn = -(d2 * il - R.tube_allow) / dt;
+  const float vn = dot3(v, n);
+  const float3 vt = v - vn * n;
+  const float vt2 = dot3(vt, vt);
+  float keep = 1.f;
+  if (vt2 > 0.f) keep = fmaxf(0.f, 1.f - R.tube_mu * fabsf(dvn) * rsqrtf(vt2));
+  v = v + dvn * n - (1.f - keep) * vt;
+}
+
 // Hook into the constraint loop of step_body: before_iterations() once per step before
 // the sweeps, after_odd() after every iteration's odd sweep.  The plain rod needs none;
 // the catheter/guidewire pair applies its binding constraints there.
@@ -400,6 +430,12 @@ __device__ __forceinline__ void step_body(const RodDev& R, const Halo& H, float3
         const float2 nz = __ffma2_rn(w_bnd, g.z, make_float2(v[EPT - 1].z, v[0].z));
         v[EPT - 1] = f3(nx.x, ny.x, nz.x);
         v[0] = f3(nx.y, ny.y, nz.y);
+      }
+      // collision response (analytic vessel), per node
+      if (R.flags & F_TUBE) {
+#pragma unroll
+        for (int e = 0; e < EPT; ++e)
+          if (e0 + e < n) tube_contact(r[e], v[e], w[e], R, dt);
       }
       hook.template after_odd<EPT>(r, v, w);
     }

@@ -309,3 +309,33 @@ def pair_drives(seed: int, n_launches: int, launch_dt: float, l0: float, beta0: 
     disp = np.concatenate([[0.0], np.cumsum(rel)[:-1]])
     dg[:, 3] = beta0 + disp / l0
     return dc, dg
+
+
+def vessel_guidewire(n: int = 512, seed: int = 11, rc: float = 0.5, rt: float = 2e-3, mu: float = 0.1,
+                     offset: float = 0.8):
+    """The guidewire inside a curved vessel (the insertion test of Section 3.3 with an
+    analytic tube in place of the phantom mesh): the vessel centreline is the circle of
+    radius rc about (0, rc) in the plane z = 0, tangent to +x at the origin; inner radius
+    rt, Coulomb friction mu.  The guidewire (straight at rest) starts as a polygon on the
+    circle of radius rc + offset (rt - r) (towards the outer wall) with segments of rest
+    length, frames along the segments, seeded segment tilts of 2e-5 rad; the wall holds it
+    bent, so it presses against the outer wall within a few steps.
+    Returns (rod, tube) with tube = [cx, cy, cz, Rc, Rt, mu]."""
+    rod = guidewire(n, seed=seed)
+    g = rng(seed + 17)
+    m = n - 1
+    l0 = rod.length / m
+    big_r = rc + offset * (rt - rod.radius)
+    dphi = 2.0 * math.asin(l0 / (2.0 * big_r))
+    phi_seg = (np.arange(m) + 0.5) * dphi  # chord j points along the tangent at its middle
+    align = Rotation.from_rotvec([0.0, math.pi / 2, 0.0])
+    frames = Rotation.from_rotvec(np.stack([np.zeros(m), np.zeros(m), phi_seg], axis=1)) * align
+    frames = frames * Rotation.from_rotvec(g.standard_normal((m, 3)) * 2e-5)
+    pos = np.zeros((n, 3))
+    pos[0] = (0.0, rc - big_r, 0.0)
+    pos[1:] = pos[0] + np.cumsum(l0 * frames.apply([0.0, 0.0, 1.0]), axis=0)
+    rod.pos = pos
+    rod.quat = _hemisphere_continuous(frames.as_quat())
+    rod.rest_quat = _hemisphere_continuous(np.tile(align.as_quat()[None, :], (m, 1)))
+    tube = np.array([0.0, rc, 0.0, rc, rt, mu])
+    return rod, tube

@@ -441,3 +441,77 @@ def test_binding_mode_zero_is_two_independent_rods():
     so2, si2 = oracle.step_pair(cat, so, gw, si, 0, -2.5, 5, drive_outer=dc, drive_inner=dg)
     np.testing.assert_array_equal(so2["pos"], oracle.step(cat, so, 5, drive=dc)["pos"])
     np.testing.assert_array_equal(si2["pos"], oracle.step(gw, si, 5, drive=dg)["pos"])
+
+
+# ------------------------------------------------------------------ vessel contact
+
+
+def _straight_tube_rod(mu, v, n=8):
+    """A short straight rod along +x inside a nearly straight tube (centreline radius 1 km
+    through the origin, tangent to +x), translating rigidly with velocity v."""
+    rod = _rod(n, length=0.05, clamp=0, n_iters=1, mass_scale=1.0, inertia_scale=1.0)
+    rod.quat = rod.rest_quat.copy()
+    rod.pos = np.zeros((n, 3))
+    rod.pos[:, 0] = np.linspace(0, 0.05, n)
+    st = oracle.state_of(rod)
+    st["vel"][:] = v
+    tube = np.array([0.0, 1000.0, 0.0, 1000.0, 2e-3, mu])
+    return rod, st, tube
+
+
+def test_vessel_contact_inactive_inside():
+    """Nodes well inside the vessel: the step is the step without a vessel."""
+    rod, st, tube = _straight_tube_rod(0.3, [0.01, 0.0, 0.0])
+    a = oracle.step_tube(rod, st, tube, 3)
+    b = oracle.step(rod, st, 3)
+    for k in a:
+        np.testing.assert_array_equal(a[k], b[k])
+
+
+def test_vessel_contact_puts_penetrating_nodes_on_the_wall():
+    """A rigid rod moving into the wall (+z) fast enough to cross it in one step: after
+    the step every node lies exactly at the allowed distance (inner radius minus rod
+    radius) from the centreline; the normal velocity is what lands it there."""
+    vz = 200.0  # crosses the 1 mm clearance in one 1e-5 s step
+    rod, st, tube = _straight_tube_rod(0.0, [0.0, 0.0, vz])
+    s = oracle.step_tube(rod, st, tube, 1)
+    allow = tube[4] - rod.radius
+    # distance to the (locally straight) centreline: |(y - y_c, z)| with y_c ~ x^2 / (2 Rc)
+    yc = 1000.0 - np.sqrt(1000.0**2 - s["pos"][:, 0] ** 2)
+    dist = np.sqrt((s["pos"][:, 1] - yc) ** 2 + s["pos"][:, 2] ** 2)
+    np.testing.assert_allclose(dist, allow, rtol=1e-9)
+
+
+def _wall_normal(pos, tube):
+    """Outward wall normal at each node: from the nearest centreline point to the node."""
+    dx, dy = pos[:, 0] - tube[0], pos[:, 1] - tube[1]
+    rho = np.hypot(dx, dy)
+    c = np.stack([tube[0] + tube[3] * dx / rho, tube[1] + tube[3] * dy / rho, np.full(len(pos), tube[2])], 1)
+    d = pos - c
+    return d / np.linalg.norm(d, axis=1, keepdims=True)
+
+
+def test_vessel_contact_coulomb_friction():
+    """Coulomb's law at the wall, per node, with n the wall normal at the node's predicted
+    position r + dt v (where the constraint is evaluated): the velocity change splits into a normal part dvn and a tangential part dvt
+    with |dvt| = mu |dvn| opposing the tangential velocity while sliding; mu = 0 leaves
+    the tangential velocity alone; a large mu stops it (sticking)."""
+    v0 = np.array([0.2, 0.0, 200.0])
+    for mu in (0.0, 1e-3, 10.0):
+        rod, st, tube = _straight_tube_rod(mu, v0)
+        s = oracle.step_tube(rod, st, tube, 1)
+        n = _wall_normal(st["pos"] + rod.dt * v0, tube)
+        dv = s["vel"] - v0
+        dvn = np.sum(dv * n, axis=1)
+        dvt = dv - dvn[:, None] * n
+        vt0 = v0 - np.sum(v0 * n, axis=1)[:, None] * n
+        assert np.all(dvn < -90.0)  # pushed back by ~ (200 dt - 1 mm) / dt = 100 m/s
+        if mu == 0.0:
+            assert np.all(np.linalg.norm(dvt, axis=1) < 1e-9 * np.abs(dvn))
+        elif mu == 1e-3:
+            np.testing.assert_allclose(np.linalg.norm(dvt, axis=1), mu * np.abs(dvn), rtol=1e-6)
+            cos = np.sum(dvt * vt0, axis=1) / (np.linalg.norm(dvt, axis=1) * np.linalg.norm(vt0, axis=1))
+            np.testing.assert_allclose(cos, -1.0, atol=1e-9)
+        else:
+            vt1 = s["vel"] - np.sum(s["vel"] * n, axis=1)[:, None] * n
+            assert np.all(np.linalg.norm(vt1, axis=1) < 1e-6 * np.linalg.norm(vt0, axis=1))
