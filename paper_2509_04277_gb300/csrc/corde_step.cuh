@@ -173,25 +173,29 @@ __device__ __forceinline__ float3 safe_segment(float inv, float3 e, float l0) {
 // normal velocity changes by dvn = -(|delta| - allow) / dt along n = delta / |delta| (the
 // predicted node lands on the wall) and the tangential velocity shrinks by at most
 // mu |dvn| (Coulomb).  Kinematic nodes (w = 0) are skipped.
-__device__ __forceinline__ void tube_contact(float3 r, float3& v, float w, const RodDev& R, float dt) {
-  if (!(w > 0.f)) return;
-  const float3 p = r + dt * v;  // predicted position; its closest centreline point
-  const float dx = p.x - R.tube_cx, dy = p.y - R.tube_cy;
-  const float rho2 = dx * dx + dy * dy;
-  if (!(rho2 > 0.f)) return;
-  const float k = 1.f - R.tube_rc * rsqrtf(rho2);
-  const float3 delta = f3(dx * k, dy * k, p.z - R.tube_cz);
-  const float d2 = dot3(delta, delta);
-  if (!(d2 > R.tube_allow * R.tube_allow)) return;
+__device__ __forceinline__ void tube_contact(float3 r, float3& v, float w, const RodDev& R, float dt,
+                                             float inv_dt) {
+  // offset of the predicted position from the vessel centre, radially (rho) and along z
+  const float px = fmaf(dt, v.x, r.x - R.tube_cx), py = fmaf(dt, v.y, r.y - R.tube_cy);
+  const float pz = fmaf(dt, v.z, r.z - R.tube_cz);
+  const float rho2 = fmaxf(fmaf(px, px, py * py), 1e-30f);
+  const float irho = rsqrtf(rho2);
+  const float s = fmaf(rho2, irho, -R.tube_rc);  // rho - rc: radial offset from the centreline
+  const float d2 = fmaxf(fmaf(s, s, pz * pz), 1e-30f);  // |delta|^2, delta = p - c
   const float il = rsqrtf(d2);
-  const float3 n = il * delta;
-  const float dvn = -(d2 * il - R.tube_allow) / dt;
+  const float a = s * irho * il;
+  const float3 n = f3(px * a, py * a, pz * il);  // delta / |delta|
+  // branch-free: a node out of contact (or kinematic) gets dvn = 0 and keep = 1, which
+  // leaves v unchanged exactly
+  const bool hit = (w > 0.f) && (d2 > R.tube_allow * R.tube_allow);
+  const float dvn = hit ? (R.tube_allow - d2 * il) * inv_dt : 0.f;
   const float vn = dot3(v, n);
   const float3 vt = v - vn * n;
-  const float vt2 = dot3(vt, vt);
-  float keep = 1.f;
-  if (vt2 > 0.f) keep = fmaxf(0.f, 1.f - R.tube_mu * fabsf(dvn) * rsqrtf(vt2));
-  v = v + dvn * n - (1.f - keep) * vt;
+  const float vt2 = fmaxf(dot3(vt, vt), 1e-30f);
+  const float keep = hit ? fmaxf(0.f, 1.f - R.tube_mu * fabsf(dvn) * rsqrtf(vt2)) : 1.f;
+  // v + dvn n - (1 - keep) vt  =  keep v + (dvn + (1 - keep) vn) n
+  const float c = fmaf(1.f - keep, vn, dvn);
+  v = f3(fmaf(keep, v.x, c * n.x), fmaf(keep, v.y, c * n.y), fmaf(keep, v.z, c * n.z));
 }
 
 // Hook into the constraint loop of step_body: before_iterations() once per step before
@@ -341,6 +345,7 @@ __device__ __forceinline__ void step_body(const RodDev& R, const Halo& H, float3
   // ---- distance-constraint iterations (inextensible rod), red-black
   if (inext) {
     hook.template before_iterations<EPT>(r, w);
+    const float inv_dt = 1.f / dt;
     // constraint geometry of this step (positions and masses do not change in the sweeps)
     constexpr int NE = EPT / 2, NO = EPT / 2 > 1 ? EPT / 2 - 1 : 1;
     float3 e_even[NE], e_odd[NO];
@@ -435,7 +440,7 @@ __device__ __forceinline__ void step_body(const RodDev& R, const Halo& H, float3
       if (R.flags & F_TUBE) {
 #pragma unroll
         for (int e = 0; e < EPT; ++e)
-          if (e0 + e < n) tube_contact(r[e], v[e], w[e], R, dt);
+          if (e0 + e < n) tube_contact(r[e], v[e], w[e], R, dt, inv_dt);
       }
       hook.template after_odd<EPT>(r, v, w);
     }
