@@ -72,11 +72,15 @@ def lib():
             L.oracle_count_flops.restype = ctypes.c_int64
             L.oracle_step_batch.argtypes = [ctypes.c_int, _P, _D, _D, _D, _D, _D, ctypes.c_int]
             L.oracle_step_tube.argtypes = [_P, _D, _D, _D, _D, _D, _D, _D, ctypes.c_int]
+            L.oracle_step_contact.argtypes = [_P, _D, _D, _D, _D, _D, _D, _D, _D, ctypes.c_int]
+            L.oracle_self_candidates.argtypes = [_P, _D, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+            L.oracle_self_contact_pass.argtypes = [_P, _D, _D, ctypes.c_double]
             L.oracle_step_pair.argtypes = [_P, _D, _D, _D, _D, _D, _D, _P, _D, _D, _D, _D, _D, _D, ctypes.c_int,
                                            ctypes.c_double, ctypes.c_int]
             for name in ("oracle_derive", "oracle_darboux", "oracle_energy", "oracle_forces", "oracle_step",
                          "oracle_rollout", "oracle_rollout_jvp", "oracle_step_batch", "oracle_step_pair",
-                         "oracle_step_tube"):
+                         "oracle_step_tube", "oracle_step_contact", "oracle_self_candidates",
+                         "oracle_self_contact_pass"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -263,3 +267,37 @@ def step_tube(rod, state, tube, n_steps=1, drive=None):
                                   _ptr(s["quat"]), _ptr(s["vel"]), _ptr(s["omega"]), _ptr(_arr(drive)),
                                   _ptr(_arr(tube)), int(n_steps)), "oracle_step_tube")
     return s
+
+
+def step_contact(rod, state, tube=None, self_mu=None, n_steps=1, drive=None):
+    """Advance a copy of ``state`` with contact: the vessel tube = [cx, cy, cz, Rc, Rt, mu]
+    (None: no vessel) and self-collision with friction ``self_mu`` (None: none)."""
+    s = {k: _arr(v).copy() for k, v in state.items()}
+    sp = None if self_mu is None else np.array([float(self_mu)])
+    _check(lib().oracle_step_contact(ctypes.byref(params(rod)), _ptr(_arr(rod.rest_quat)), _ptr(s["pos"]),
+                                     _ptr(s["quat"]), _ptr(s["vel"]), _ptr(s["omega"]), _ptr(_arr(drive)),
+                                     _ptr(_arr(tube)), _ptr(sp), int(n_steps)), "oracle_step_contact")
+    return s
+
+
+def self_candidates(rod, pos, cap=64):
+    """Self-collision candidate partners of every node of ``pos`` (list of ascending
+    index arrays) and the number of candidate pairs."""
+    pos = _arr(pos)
+    n = pos.shape[0]
+    counts = np.zeros(n, dtype=np.int32)
+    lst = np.zeros((n, cap), dtype=np.int32)
+    pairs = lib().oracle_self_candidates(ctypes.byref(params(rod)), _ptr(pos), counts.ctypes.data,
+                                         lst.ctypes.data, int(cap))
+    if pairs < 0:
+        raise RuntimeError("oracle_self_candidates failed")
+    return [lst[i, :min(counts[i], cap)].copy() for i in range(n)], int(pairs)
+
+
+def self_contact_pass(rod, pos, vel, mu):
+    """One Jacobi pass of the self-contact constraints: the velocities after it."""
+    pos = _arr(pos)
+    v = _arr(vel).copy()
+    _check(lib().oracle_self_contact_pass(ctypes.byref(params(rod)), _ptr(pos), _ptr(v),
+                                          float(mu)), "oracle_self_contact_pass")
+    return v

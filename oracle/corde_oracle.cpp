@@ -39,6 +39,7 @@
 //     swept red-black: even segments, then odd segments, per iteration.
 //   * "Clamped" / driven base: node 0 and frame 0 are kinematic (inverse mass 0); their
 //     velocities come from the drive input.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -455,18 +456,113 @@ static void contact_sweep(const OracleParams& p, const Derived& d, State<T>& s, 
   }
 }
 
+// Self-collision ("Collisions and self-collisions" and Section 2.1 "Constraints": contact
+// constraints C_c for self-collisions with Coulomb friction).  Every mass point carries a
+// sphere of the rod radius r; two mass points i, j at least min_sep apart along the rod
+// collide when their spheres overlap.  Detection runs once per step, on the positions the
+// constraint stage starts from: the candidate pairs are all pairs with |i - j| >= min_sep
+// and |r_i - r_j| < reach (reach = 3r: contact distance 2r plus a skin of r, so a pair
+// that comes into contact during the step is a candidate).  This is the definition the
+// GPU's bounding-sphere broad phase and sphere-sphere narrow phase must reproduce.
+//   min_sep = max(2, floor(2r / l0) + 1): the smallest index gap whose rest distance
+//   exceeds the contact distance (mass points closer along a straight rod always overlap).
+struct SelfContact {
+  double mu;       // Coulomb friction coefficient between strands
+  double contact;  // contact distance 2r
+  double reach;    // candidate distance 3r
+  int min_sep;     // smallest index gap considered
+};
+
+static SelfContact self_contact_of(const OracleParams& p, const Derived& d, double mu) {
+  SelfContact sc;
+  sc.mu = mu;
+  sc.contact = 2.0 * p.radius;
+  sc.reach = 3.0 * p.radius;
+  const int m = (int)std::floor(sc.contact / d.l0) + 1;
+  sc.min_sep = m > 2 ? m : 2;
+  return sc;
+}
+
+// Candidate partners of every mass point, ascending, by brute force over all pairs.
+template <class T>
+static void self_candidates(const SelfContact& sc, const Derived& d, const State<T>& s,
+                            std::vector<std::vector<int>>& cand) {
+  cand.assign(d.N, std::vector<int>());
+  for (int i = 0; i < d.N; ++i)
+    for (int j = i + sc.min_sep; j < d.N; ++j) {
+      const double dx = val(s.r[j].x) - val(s.r[i].x);
+      const double dy = val(s.r[j].y) - val(s.r[i].y);
+      const double dz = val(s.r[j].z) - val(s.r[i].z);
+      if (dx * dx + dy * dy + dz * dz < sc.reach * sc.reach) {
+        cand[i].push_back(j);
+        cand[j].push_back(i);
+      }
+    }
+  for (auto& c : cand) std::sort(c.begin(), c.end());
+}
+
+// One pass of the self-contact constraints (Jacobi: every impulse from the velocities the
+// pass starts with).  For a candidate pair (i, j) with predicted offset
+// delta = (r_j - r_i) + dt (v_j - v_i) shorter than the contact distance, the pair's
+// impulse J (applied +J to j, -J to i) makes the relative normal velocity separate the
+// predicted spheres exactly and cuts the relative tangential velocity u_t by at most
+// mu times that normal change (Coulomb):
+//   phi = 2r - |delta|,  n = delta / |delta|,  du_n = phi / dt,
+//   J = (du_n n - min(1, mu du_n / |u_t|) u_t) / (w_i + w_j).
+// A mass point touching several others takes the average of its pairs' velocity changes,
+// weighted by penetration depth (as the paper weights its collision response vectors):
+//   dv_i = -w_i sum_j phi_ij J_ij / sum_j phi_ij.
+template <class T>
+static void self_contact_sweep(const OracleParams& p, const Derived& d, State<T>& s, const SelfContact& sc,
+                               const std::vector<std::vector<int>>& cand) {
+  const double dt = p.dt;
+  std::vector<V3<T>> dv(d.N, V3<T>{T(0.0), T(0.0), T(0.0)});
+  for (int i = 0; i < d.N; ++i) {
+    if (d.w[i] == 0.0 || cand[i].empty()) continue;
+    V3<T> acc{T(0.0), T(0.0), T(0.0)};
+    T wphi(0.0);
+    for (int j : cand[i]) {
+      const double wsum = d.w[i] + d.w[j];
+      const V3<T> u = s.v[j] - s.v[i];
+      const V3<T> delta = (s.r[j] - s.r[i]) + dt * u;
+      const T dist = norm(delta);
+      if (!(val(dist) < sc.contact) || val(dist) == 0.0) continue;
+      const T phi = T(sc.contact) - dist;
+      const V3<T> n = (T(1.0) / dist) * delta;
+      const T dun = phi / T(dt);
+      const V3<T> ut = u - dot(u, n) * n;
+      const T utn = norm(ut);
+      T cut(0.0);
+      if (val(utn) > 0.0) {
+        const T f = T(sc.mu) * dun / utn;
+        cut = val(f) < 1.0 ? f : T(1.0);
+      }
+      const V3<T> J = (T(1.0) / T(wsum)) * (dun * n - cut * ut);
+      acc = acc + phi * J;
+      wphi = wphi + phi;
+    }
+    if (val(wphi) > 0.0) dv[i] = (-d.w[i] / wphi) * acc;
+  }
+  for (int i = 0; i < d.N; ++i) s.v[i] = s.v[i] + dv[i];
+}
+
 // One time step of one rod, Fig. 5 order: forces, then n_iters iterations of the
-// red-black distance sweeps (even segments, then odd) followed by the collision response
-// (when a vessel is given), then the position update.
+// red-black distance sweeps (even segments, then odd) followed by the collision
+// responses (the vessel when given, then self-contact when given), then the position
+// update.
 template <class T>
 static void step(const OracleParams& p, const Derived& d, const Material<T>& mat, State<T>& s,
-                 const double* drive, const double* f_ext, const double* tau_ext, const double* tube = nullptr) {
+                 const double* drive, const double* f_ext, const double* tau_ext, const double* tube = nullptr,
+                 const SelfContact* sc = nullptr) {
   integrate_forces(p, d, mat, s, drive, f_ext, tau_ext);
   if (p.inextensible) {
+    std::vector<std::vector<int>> cand;
+    if (sc) self_candidates(*sc, d, s, cand);
     for (int it = 0; it < p.n_iters; ++it) {
       distance_sweep(p, d, s, 0);
       distance_sweep(p, d, s, 1);
       if (tube) contact_sweep(p, d, s, tube);
+      if (sc) self_contact_sweep(p, d, s, *sc, cand);
     }
   }
   integrate_positions(p, d, s);
@@ -542,7 +638,8 @@ static void load_state(const Derived& d, const double* pos, const double* quat, 
     s.v[i] = vel ? v3(T(vel[3 * i]), T(vel[3 * i + 1]), T(vel[3 * i + 2])) : v3(T(0.0), T(0.0), T(0.0));
   }
   for (int j = 0; j < d.M; ++j) {
-    s.q[j] = Q4<T>{T(quat[4 * j + 3]), T(quat[4 * j]), T(quat[4 * j + 1]), T(quat[4 * j + 2])};
+    s.q[j] = quat ? Q4<T>{T(quat[4 * j + 3]), T(quat[4 * j]), T(quat[4 * j + 1]), T(quat[4 * j + 2])}
+                  : Q4<T>{T(1.0), T(0.0), T(0.0), T(0.0)};
     s.om[j] = omega ? v3(T(omega[3 * j]), T(omega[3 * j + 1]), T(omega[3 * j + 2])) : v3(T(0.0), T(0.0), T(0.0));
   }
 }
@@ -741,6 +838,63 @@ int oracle_step_tube(const OracleParams* p, const double* rest_quat, double* pos
   load_state(d, pos, quat, vel, omega, s);
   for (int k = 0; k < n_steps; ++k) step(*p, d, mat, s, drive, nullptr, nullptr, tube);
   store_state(d, s, pos, quat, vel, omega);
+  return 0;
+}
+
+// n_steps time steps of one rod with contact: the vessel tube = [cx, cy, cz, Rc, Rt, mu]
+// (NULL: none) and self-collision self = [mu] (NULL: none); otherwise as oracle_step.
+int oracle_step_contact(const OracleParams* p, const double* rest_quat, double* pos, double* quat, double* vel,
+                        double* omega, const double* drive, const double* tube, const double* self, int n_steps) {
+  if (!valid(p) || !pos || !quat || !vel || !omega || n_steps < 0 || !p->inextensible) return -1;
+  if (tube && (!(tube[3] > 0) || !(tube[4] > p->radius) || !(tube[5] >= 0))) return -1;
+  if (self && !(self[0] >= 0)) return -1;
+  Derived d = derive(*p);
+  Material<double> mat;
+  load_material(d, rest_quat, nullptr, mat);
+  State<double> s;
+  load_state(d, pos, quat, vel, omega, s);
+  SelfContact sc;
+  if (self) sc = self_contact_of(*p, d, self[0]);
+  for (int k = 0; k < n_steps; ++k) step(*p, d, mat, s, drive, nullptr, nullptr, tube, self ? &sc : nullptr);
+  store_state(d, s, pos, quat, vel, omega);
+  return 0;
+}
+
+// Self-collision candidates of the positions pos: counts[i] partners of node i, listed
+// ascending in list[i * cap ...] (at most cap kept); returns the number of pairs, or -1.
+int oracle_self_candidates(const OracleParams* p, const double* pos, int* counts, int* list, int cap) {
+  if (!valid(p) || !pos || !counts || cap < 0) return -1;
+  Derived d = derive(*p);
+  State<double> s;
+  load_state(d, pos, nullptr, nullptr, nullptr, s);
+  const SelfContact sc = self_contact_of(*p, d, 0.0);
+  std::vector<std::vector<int>> cand;
+  self_candidates(sc, d, s, cand);
+  int pairs = 0;
+  for (int i = 0; i < d.N; ++i) {
+    counts[i] = (int)cand[i].size();
+    pairs += counts[i];
+    for (int k = 0; k < counts[i] && k < cap; ++k) list[(size_t)i * cap + k] = cand[i][k];
+  }
+  return pairs / 2;
+}
+
+// One Jacobi pass of the self-contact constraints on (pos, vel) with friction mu (vel is
+// updated in place); the candidates are detected on pos.
+int oracle_self_contact_pass(const OracleParams* p, const double* pos, double* vel, double mu) {
+  if (!valid(p) || !pos || !vel || !(mu >= 0)) return -1;
+  Derived d = derive(*p);
+  State<double> s;
+  load_state(d, pos, nullptr, vel, nullptr, s);
+  const SelfContact sc = self_contact_of(*p, d, mu);
+  std::vector<std::vector<int>> cand;
+  self_candidates(sc, d, s, cand);
+  self_contact_sweep(*p, d, s, sc, cand);
+  for (int i = 0; i < d.N; ++i) {
+    vel[3 * i] = s.v[i].x;
+    vel[3 * i + 1] = s.v[i].y;
+    vel[3 * i + 2] = s.v[i].z;
+  }
   return 0;
 }
 

@@ -339,3 +339,69 @@ def vessel_guidewire(n: int = 512, seed: int = 11, rc: float = 0.5, rt: float = 
     rod.rest_quat = _hemisphere_continuous(np.tile(align.as_quat()[None, :], (m, 1)))
     tube = np.array([0.0, rc, 0.0, rc, rt, mu])
     return rod, tube
+
+
+def _chord_march(curve: np.ndarray, l0: float, n: int) -> np.ndarray:
+    """n points along a densely sampled polyline, consecutive points exactly l0 apart."""
+    out = np.zeros((n, 3))
+    out[0] = curve[0]
+    k = 0
+    for i in range(1, n):
+        p = out[i - 1]
+        while k + 1 < len(curve) and np.linalg.norm(curve[k + 1] - p) < l0:
+            k += 1
+        if k + 1 >= len(curve):
+            raise ValueError("curve too short for n points at this spacing")
+        # point on segment curve[k] -> curve[k+1] at distance l0 from p (the far root)
+        a, b = curve[k], curve[k + 1]
+        d = b - a
+        f = a - p
+        A, B, C = d @ d, 2 * (f @ d), f @ f - l0 * l0
+        s = (-B + math.sqrt(max(B * B - 4 * A * C, 0.0))) / (2 * A)
+        out[i] = a + s * d
+    return out
+
+
+def torus_knot(n: int = 512, seed: int = 21, gap: float = 1.05, spacing: float = 1.35):
+    """Knot-like self-collision configuration (stands in for the haptic knot tying of
+    Section 3.5): a guidewire (r = 0.45 mm, E = 60 GPa, straight at rest, base driven) laid
+    on a (2, q) torus knot - two strands twisted around each other along a ring, strand
+    separation 2 gap r - cut open at a seeded angle so that its two ends lie side by side.
+    Nodes sit on the curve exactly l0 = spacing r apart (spheres of neighbouring mass
+    points overlap, as the paper's knot needs); frames follow the segments by parallel
+    transport, with seeded tilts of 2e-5 rad.  The ring's core radius follows from n
+    (R = (n - 1) l0 / 4 pi) and q is the odd number giving a twist pitch near 20 mm
+    (q = 3, a trefoil, for small n)."""
+    rod = guidewire(n, seed=seed)
+    g = rng(seed + 31)
+    r = rod.radius
+    l0 = spacing * r
+    a = gap * r
+    R = (n - 1) * l0 / (4.0 * math.pi)
+    q = max(3, int(round(4.0 * math.pi * R / 0.02)))
+    if q % 2 == 0:
+        q += 1
+    phi0 = g.uniform(0.0, 2.0 * math.pi)
+    phi = phi0 + np.linspace(0.0, 4.0 * math.pi, 400 * n)
+    th = 0.5 * q * (phi - phi0)
+    rho = R + a * np.cos(th)
+    curve = np.stack([rho * np.cos(phi), rho * np.sin(phi), a * np.sin(th)], axis=1)
+    pos = _chord_march(curve, l0, n)
+    m = n - 1
+    t = np.diff(pos, axis=0) / l0
+    rots = []
+    cur = Rotation.align_vectors(t[0][None, :], np.array([[0.0, 0.0, 1.0]]))[0]
+    rots.append(cur)
+    for j in range(1, m):
+        ax = np.cross(t[j - 1], t[j])
+        s = np.linalg.norm(ax)
+        ang = math.atan2(s, float(t[j - 1] @ t[j]))
+        step = Rotation.from_rotvec(ax / s * ang) if s > 0 else Rotation.identity()
+        cur = step * cur
+        rots.append(cur)
+    frames = Rotation.concatenate(rots) * Rotation.from_rotvec(g.standard_normal((m, 3)) * 2e-5)
+    rod.length = l0 * m
+    rod.pos = pos - pos[0]
+    rod.quat = _hemisphere_continuous(frames.as_quat())
+    rod.rest_quat = np.tile(rots[0].as_quat()[None, :], (m, 1))
+    return rod

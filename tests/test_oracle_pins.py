@@ -515,3 +515,171 @@ def test_vessel_contact_coulomb_friction():
         else:
             vt1 = s["vel"] - np.sum(s["vel"] * n, axis=1)[:, None] * n
             assert np.all(np.linalg.norm(vt1, axis=1) < 1e-6 * np.linalg.norm(vt0, axis=1))
+
+
+# ------------------------------------------------------------------ self-collision
+
+RS = 0.45e-3  # rod radius of the self-contact pins
+
+
+def _free_rod(n, spacing=1.35):
+    """Unclamped rod parameters with l0 = spacing r (min index gap 2 for spacing > 1)."""
+    return _rod(n, length=(n - 1) * spacing * RS, radius=RS, clamp=0, n_iters=1)
+
+
+def _far_line(n):
+    pos = np.zeros((n, 3))
+    pos[:, 0] = np.arange(n) * 10 * RS
+    return pos
+
+
+def test_self_candidates_match_kdtree():
+    """Detection against an independent neighbour search (scipy's k-d tree): every pair
+    at least min_sep apart in index and closer than 3 r, listed ascending per node."""
+    from scipy.spatial import cKDTree
+
+    for rod in (W.torus_knot(64), W.torus_knot(512)):
+        pos = rod.pos
+        cand, pairs = oracle.self_candidates(rod, pos)
+        l0 = rod.length / (rod.n_nodes - 1)
+        m = max(2, int(np.floor(2 * rod.radius / l0)) + 1)
+        ref = {(i, j) for i, j in cKDTree(pos).query_pairs(3 * rod.radius) if j - i >= m}
+        got = {(i, int(j)) for i in range(len(cand)) for j in cand[i] if j > i}
+        assert got == ref and pairs == len(ref) and len(ref) > 100
+        assert all(np.all(np.diff(c) > 0) for c in cand)
+
+
+def test_self_contact_single_pair_lands_on_contact_distance():
+    """One overlapping pair (nodes 1 and 5): only they change; their predicted distance
+    becomes exactly 2 r and their momentum is conserved (equal masses)."""
+    rod = _free_rod(8)
+    pos = _far_line(8)
+    pos[5] = pos[1] + [0.0, 1.8 * RS, 0.3 * RS]
+    vel = np.random.default_rng(3).normal(size=(8, 3)) * 0.01
+    v2 = oracle.self_contact_pass(rod, pos, vel, 0.0)
+    assert set(np.flatnonzero(np.any(v2 != vel, axis=1))) == {1, 5}
+    delta = (pos[5] - pos[1]) + rod.dt * (v2[5] - v2[1])
+    assert np.linalg.norm(delta) == pytest.approx(2 * RS, rel=1e-12)
+    np.testing.assert_allclose(v2[1] + v2[5], vel[1] + vel[5], rtol=0, atol=1e-15)
+
+
+def test_self_contact_coulomb_friction():
+    """Relative tangential velocity of one colliding pair, with n the pair's normal at the
+    predicted positions: mu = 0 leaves it; a small mu cuts it by exactly mu du_n (sliding)
+    against its direction; a large mu stops it (sticking)."""
+    rod = _free_rod(8)
+    pos = _far_line(8)
+    pos[5] = pos[1] + [0.0, 2.2 * RS, 0.0]
+    vel = np.zeros((8, 3))
+    vel[5] = [0.05, -10.0, 0.0]  # closes the 0.2 r gap and 0.2 r more in one step
+    u0 = vel[5] - vel[1]
+    d0 = (pos[5] - pos[1]) + rod.dt * u0
+    n = d0 / np.linalg.norm(d0)
+    ut0 = u0 - (u0 @ n) * n
+    for mu in (0.0, 1e-3, 10.0):
+        v2 = oracle.self_contact_pass(rod, pos, vel, mu)
+        du = (v2[5] - v2[1]) - u0
+        dun = du @ n
+        dut = du - dun * n
+        assert dun > 0
+        if mu == 0.0:
+            assert np.linalg.norm(dut) < 1e-12 * dun
+        elif mu == 1e-3:
+            assert np.linalg.norm(dut) == pytest.approx(mu * dun, rel=1e-9)
+            assert (dut @ ut0) / (np.linalg.norm(dut) * np.linalg.norm(ut0)) == pytest.approx(-1.0, abs=1e-12)
+        else:
+            u1 = v2[5] - v2[1]
+            assert np.linalg.norm(u1 - (u1 @ n) * n) < 1e-12 * np.linalg.norm(ut0)
+
+
+def test_self_contact_symmetric_sandwich():
+    """Node 3 squeezed equally between nodes 1 and 5 from opposite sides: the
+    penetration-weighted mean of its two pair responses is zero, while 1 and 5 are pushed
+    apart symmetrically."""
+    rod = _free_rod(8)
+    pos = _far_line(8)
+    c = np.array([100 * RS, 5 * RS, 0.0])
+    pos[3] = c
+    pos[1] = c - [1.8 * RS, 0.0, 0.0]
+    pos[5] = c + [1.8 * RS, 0.0, 0.0]
+    v2 = oracle.self_contact_pass(rod, pos, np.zeros((8, 3)), 0.2)
+    np.testing.assert_allclose(v2[3], 0.0, atol=1e-15)
+    assert v2[1][0] < 0 < v2[5][0]
+    np.testing.assert_allclose(v2[1], -v2[5], rtol=1e-14)
+
+
+def test_self_contact_is_continuous_at_the_contact_distance():
+    """The response (normal part and, while sliding, the friction cut) vanishes linearly
+    as the predicted gap closes to 2 r - no jump when a pair enters or leaves contact -
+    and is exactly zero outside."""
+    rod = _free_rod(8)
+    ratios = []
+    for eps in (1e-2, 1e-3, 1e-4, -1e-3):
+        pos = _far_line(8)
+        pos[5] = pos[1] + [0.0, 2 * RS * (1 - eps), 0.0]
+        vel = np.zeros((8, 3))
+        vel[5] = [1.0, 0.0, 0.0]  # mu du_n = 0.3 * 90 eps m/s < 1 m/s: sliding throughout
+        v2 = oracle.self_contact_pass(rod, pos, vel, 0.3)
+        dv = np.linalg.norm(v2 - vel)
+        phi = 2 * RS - np.linalg.norm((pos[5] - pos[1]) + rod.dt * (vel[5] - vel[1]))
+        if eps < 0:
+            assert dv == 0.0
+        else:
+            ratios.append(dv / phi)
+    assert max(ratios) / min(ratios) < 1.01
+
+
+def test_self_contact_straight_rod_untouched():
+    """Neighbours closer than 2 r along a straight rod never collide (index gap rule),
+    and no other pair is in contact: the pass changes nothing."""
+    rod = _free_rod(20, spacing=0.8)
+    pos = np.zeros((20, 3))
+    pos[:, 0] = np.arange(20) * 0.8 * RS
+    vel = np.random.default_rng(4).normal(size=(20, 3)) * 1e-3
+    cand, pairs = oracle.self_candidates(rod, pos)
+    assert pairs > 0  # index gap 3 sits at 2.4 r < 3 r: candidates, not contacts
+    np.testing.assert_array_equal(oracle.self_contact_pass(rod, pos, vel, 0.5), vel)
+
+
+def test_self_collision_keeps_the_knot_from_passing_through_itself():
+    """The trefoil (64 nodes, straight at rest) driven for 200 steps: with self-collision
+    no two mass points come closer than 2 r (to 1 %), and the segments stay within 0.5 %
+    of their rest length (the contact pass closes each iteration, after the distance
+    sweeps); without it the strands pass through one another."""
+    rod = W.torus_knot(64)
+    drive = np.array([0.05, 0, 0, 0, 0, 0, 2.0, 0])
+    m = max(2, int(np.floor(2 * rod.radius / (rod.length / 63))) + 1)
+    idx = np.arange(64)
+    far = np.abs(idx[:, None] - idx[None, :]) >= m
+
+    def closest(p):
+        return (np.linalg.norm(p[:, None] - p[None, :], axis=2)[far]).min() / (2 * rod.radius)
+
+    with_sc = oracle.step_contact(rod, oracle.state_of(rod), self_mu=0.1, n_steps=200, drive=drive)
+    without = oracle.step_contact(rod, oracle.state_of(rod), n_steps=200, drive=drive)
+    assert closest(with_sc["pos"]) > 0.99
+    assert closest(without["pos"]) < 0.6
+    seg = np.linalg.norm(np.diff(with_sc["pos"], axis=0), axis=1)
+    assert np.abs(seg / (rod.length / 63) - 1).max() < 5e-3
+
+
+def test_self_contact_weighting_is_continuous_in_the_contact_set():
+    """A mass point touching two others takes the penetration-weighted mean of the two
+    responses: as the second overlap shrinks to zero its response tends to the response
+    of the first pair alone (a plain mean over the touching pairs would jump to half)."""
+    rod = _free_rod(8)
+    c = np.array([100 * RS, 5 * RS, 0.0])
+
+    def response(eps):
+        pos = _far_line(8)
+        pos[3] = c
+        pos[1] = c - [1.7 * RS, 0.0, 0.0]
+        pos[5] = c + [0.0, 2 * RS * (1 - eps), 0.0] if eps is not None else c + [0.0, 10 * RS, 0.0]
+        vel = np.zeros((8, 3))
+        vel[3] = [0.0, 0.0, 0.02]
+        return oracle.self_contact_pass(rod, pos, vel, 0.1)[3]
+
+    alone = response(None)
+    assert np.linalg.norm(alone - [0.0, 0.0, 0.02]) > 1e-3
+    errs = [np.linalg.norm(response(eps) - alone) for eps in (1e-2, 1e-3, 1e-4)]
+    assert errs[0] > errs[1] > errs[2] and errs[2] < 1e-3 * np.linalg.norm(alone)
