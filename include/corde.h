@@ -126,6 +126,31 @@ int rod_bind(rod_handle h, int outer, int inner, int mode);
  * refuses handles with a vessel (contact is not differentiated).  Synchronous. */
 int rod_set_tube(rod_handle h, int rod, const double* tube);
 
+/* Self-collision of rod `rod` (contact constraints C_c for self-collisions with Coulomb
+ * friction, Section 2.1 "Constraints"; bounding-sphere broad phase and sphere-sphere
+ * narrow phase of "Collisions and self-collisions").
+ * params: 2 host doubles (mu, enable): mu >= 0 the friction coefficient between strands;
+ * enable = 0 turns it off.  Every mass point carries a sphere of the rod radius r.  Once
+ * per step the pairs (i, j) with |i - j| >= max(2, floor(2 r / l0) + 1) and
+ * |r_i - r_j| < 3 r are found; in every constraint iteration, after the distance sweeps
+ * and the vessel contact, each pair whose predicted distance is below 2 r gets the
+ * impulse that separates the predicted spheres, with a tangential cut of at most mu times
+ * the normal change, and each mass point takes the penetration-weighted mean of its
+ * pairs' velocity changes (one Jacobi pass).  The rod then runs in its own kernel (one
+ * block, two elements per thread).
+ * Errors: CORDE_ERR_ARG for a bad index, NULL params or mu < 0; CORDE_ERR_UNSUPPORTED for
+ * an extensible rod, a rod of more than 1024 nodes, a rod bound in a pair, or a handle
+ * with a mailbox.  rod_rollout, rod_adjoint, rod_mailbox_enable and rod_bind refuse
+ * self-colliding rods.  Synchronous. */
+int rod_set_self_collision(rod_handle h, int rod, const double* params);
+
+/* Self-collision statistics of rod `rod` from its last launch, into 4 host ints:
+ * candidate pairs at the last detection, most candidates of one mass point, pairs whose
+ * spheres overlapped at the last detection, and an overflow flag: bit 0 when some mass
+ * point had more than 16 candidates, bit 1 when the rod had more than 3 N candidate pairs
+ * (the excess is dropped; sticky until rod_set_self_collision).  Synchronous. */
+int rod_self_collision_stats(rod_handle h, int rod, int* out);
+
 /* Copy the drive input [n_rods][8] (host or device) into the handle. */
 int rod_set_input(rod_handle h, const float* drive, void* stream);
 

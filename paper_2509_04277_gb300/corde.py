@@ -51,6 +51,8 @@ SIGNATURES = {
     "rod_set_input": (ctypes.c_int, [_VP, _VP, _VP]),
     "rod_bind": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "rod_set_tube": (ctypes.c_int, [_VP, ctypes.c_int, _VP]),
+    "rod_set_self_collision": (ctypes.c_int, [_VP, ctypes.c_int, _VP]),
+    "rod_self_collision_stats": (ctypes.c_int, [_VP, ctypes.c_int, _VP]),
     "rod_get_state": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "rod_set_state": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "rod_info": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64)]),
@@ -154,6 +156,19 @@ def rod_set_tube(h, rod, tube, enable=True):
     t[:6] = np.asarray(tube, dtype=np.float64)[:6]
     t[6] = 1.0 if enable else 0.0
     _check(load().rod_set_tube(h, int(rod), t.ctypes.data), "rod_set_tube")
+
+
+def rod_set_self_collision(h, rod, mu, enable=True):
+    """Self-collision of rod `rod` with strand friction mu (enable=False turns it off)."""
+    p = np.array([float(mu), 1.0 if enable else 0.0], dtype=np.float64)
+    _check(load().rod_set_self_collision(h, int(rod), p.ctypes.data), "rod_set_self_collision")
+
+
+def rod_self_collision_stats(h, rod) -> dict:
+    out = np.zeros(4, dtype=np.int32)
+    _check(load().rod_self_collision_stats(h, int(rod), out.ctypes.data), "rod_self_collision_stats")
+    return {"candidate_pairs": int(out[0]), "max_candidates": int(out[1]), "overlapping_pairs": int(out[2]),
+            "overflow": int(out[3])}
 
 
 def rod_set_input(h, drive, stream=None):
@@ -405,6 +420,12 @@ class RodBatch:
     def set_tube(self, rod, tube, enable=True):
         """Analytic vessel (cx, cy, cz, Rc, Rt, mu) for rod `rod`; enable=False removes it."""
         rod_set_tube(self.handle, rod, tube, enable)
+
+    def set_self_collision(self, rod, mu, enable=True):
+        rod_set_self_collision(self.handle, rod, mu, enable)
+
+    def self_collision_stats(self, rod) -> dict:
+        return rod_self_collision_stats(self.handle, rod)
 
     def set_plan(self, ept, nt):
         rod_set_plan(self.handle, ept, nt)

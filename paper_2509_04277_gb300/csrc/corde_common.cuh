@@ -6,20 +6,21 @@
 
 namespace corde {
 
-enum : int { F_INEXT = 1, F_CLAMP = 2, F_TUBE = 4 };
+enum : int { F_INEXT = 1, F_CLAMP = 2, F_TUBE = 4, F_SELF = 8 };
 
 // Per-rod constants used by the step kernel (derived once at creation, FP64 -> FP32).
 struct RodDev {
   int off;      // first global element of the rod
   int n;        // nodes N
-  int flags;    // F_INEXT | F_CLAMP
+  int flags;    // F_INEXT | F_CLAMP | F_TUBE | F_SELF
   int n_iters;  // constraint iterations per step
   float dt, l0, two_over_l, lKp;  // time step, rest length, 2 / l_j, l0 * Kp
-  float Ks, inv_l0, damp, pad0;   // stretch stiffness, 1 / l0, 1 / (1 + alpha dt)
-  float gx, gy, gz, pad1;         // gravity acceleration of a dynamic node (g / mass_scale)
+  float Ks, inv_l0, damp, self_dist;  // stretch stiffness, 1 / l0, 1 / (1 + alpha dt), 2 r
+  float gx, gy, gz, self_reach;       // gravity acceleration of a dynamic node (g / mass_scale), 3 r
   float J1, J3, Jinv1, Jinv3;     // inertial frame inertia diag (J1, J1, J3) and inverses
   float tube_cx, tube_cy, tube_cz, tube_rc;  // vessel centreline: circle in the plane z = cz
-  float tube_allow, tube_mu, pad2, pad3;     // inner radius minus rod radius, Coulomb friction
+  float tube_allow, tube_mu, self_mu, self_sep;  // inner radius minus rod radius, Coulomb friction;
+                                                 // self-contact friction, smallest index gap
 };
 static_assert(sizeof(RodDev) == 112, "RodDev layout");
 

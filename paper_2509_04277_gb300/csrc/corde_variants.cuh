@@ -20,6 +20,7 @@ struct StepArgs {
   float4* traj;    // optional: positions after every step, [n_steps][n_elem]
   int64_t n_elem;
   MailboxDev mb;   // mailbox of the launch (period 0: none)
+  int4* self_stats;  // self-collision statistics per rod (corde_self.cu), or NULL
 };
 
 typedef cudaError_t (*StepLaunchFn)(const StepArgs& a, int n_blocks, cudaStream_t s);
@@ -48,6 +49,11 @@ struct AdjointArgs {
 int adjoint_smem_bytes(int nt, int n_iters);
 cudaError_t launch_adjoint(int nt, const AdjointArgs& a, int n_blocks, int smem, cudaStream_t s);
 constexpr int kAdjointMaxNodes = 512;
+
+// Rods with self-collision (corde_self.cu): one rod per block, at most 1024 nodes.
+extern const StepVariant kSelfVariants[];
+extern const int kNumSelfVariants;
+constexpr int kSelfMaxNodes = 1024;
 
 // Catheter/guidewire pairs (corde_pair.cu): pairs[i] = (outer rod, inner rod, mode, 0);
 // ept in {2, 4}, nt (threads per rod) in {32, ..., 256}.
