@@ -145,10 +145,11 @@ int rod_set_tube(rod_handle h, int rod, const double* tube);
 int rod_set_self_collision(rod_handle h, int rod, const double* params);
 
 /* Self-collision statistics of rod `rod` from its last launch, into 4 host ints:
- * candidate pairs at the last detection, most candidates of one mass point, pairs whose
- * spheres overlapped at the last detection, and an overflow flag: bit 0 when some mass
- * point had more than 16 candidates, bit 1 when the rod had more than 3 N candidate pairs
- * (the excess is dropped; sticky until rod_set_self_collision).  Synchronous. */
+ * candidate pairs at the last detection, the most candidates j > i of one mass point i,
+ * pairs whose spheres overlapped at the last detection, and an overflow flag: bit 0 when
+ * some mass point had more than 16 candidates above it, bit 1 when the rod had more than
+ * 3 N candidate pairs, bit 2 when a mass point touched more than 16 others in one
+ * iteration (the excess is dropped; sticky until rod_set_self_collision).  Synchronous. */
 int rod_self_collision_stats(rod_handle h, int rod, int* out);
 
 /* Copy the drive input [n_rods][8] (host or device) into the handle. */

@@ -3,62 +3,63 @@
 // friction).
 //
 // Every mass point carries a sphere of the rod radius r.  Once per step, on the positions
-// the constraint stage starts from, the block finds every pair (i, j) with
-// |i - j| >= min_sep and |r_i - r_j| < 3 r (contact distance 2 r plus a skin of r):
+// the constraint stage starts from, the block finds every pair (i < j) with
+// j - i >= min_sep and |r_i - r_j| < 3 r (contact distance 2 r plus a skin of r):
 //   broad phase  - bounding spheres wrap groups of 8 neighbouring mass points (centre: the
 //                  group's middle point, radius: its farthest point); every sphere is
 //                  checked against all others, with the 3 r reach added, into a bit
 //                  matrix of overlapping group pairs;
-//   narrow phase - each mass point checks the points of every group overlapping its own
-//                  group (sphere-sphere distance test) and keeps its partners, ascending,
-//                  in a list of at most 16 in shared memory;
-//   compaction   - the pairs (i < j) get consecutive slots (a block prefix sum over the
-//                  points' counts of larger partners), and every list entry is replaced by
-//                  its pair's slot.
+//   narrow phase - each mass point i checks the points j > i of every group overlapping
+//                  its own (sphere-sphere distance test) and keeps them, ascending, in a
+//                  list of at most 16 in shared memory;
+//   compaction   - the pairs get consecutive slots, ordered by (i, j) (a block prefix sum
+//                  over the points' counts).
 // In every constraint iteration, after the distance sweeps (and the vessel contact), the
-// velocities are staged in shared memory, every pair is evaluated once, spread evenly
-// over the threads (Jacobi: all from the staged velocities), and each mass point sums its
-// pairs in ascending partner order.  For a pair with predicted offset
-// delta = (r_j - r_i) + dt (v_j - v_i) shorter than 2 r, phi = 2 r - |delta|,
-// n = delta / |delta|, du_n = phi / dt, relative tangential velocity u_t,
-//   J = (du_n n - min(1, mu du_n / |u_t|) u_t) / (w_i + w_j)        (+J on j, -J on i),
-// and a point takes the penetration-weighted mean of its pairs:
-//   dv_i = -w_i sum_j phi_ij J_ij / sum_j phi_ij.
+// velocities are staged in shared memory and (Jacobi: everything from the staged
+// velocities)
+//   1. every pair's predicted offset delta = (r_j - r_i) + dt (v_j - v_i) is tested and the
+//      pairs with |delta| < 2 r are listed;
+//   2. each listed pair gets phi = 2 r - |delta|, n = delta / |delta|, du_n = phi / dt, the
+//      relative tangential velocity u_t and
+//        J = (du_n n - min(1, mu du_n / |u_t|) u_t) / (w_i + w_j)   (+J on j, -J on i),
+//      and its slot is appended to both mass points' short lists;
+//   3. each mass point sums its pairs in ascending slot order (= ascending partner order,
+//      so the result does not depend on the order of step 2) and takes the
+//      penetration-weighted mean  dv_i = -w_i sum_j phi_ij J_ij / sum_j phi_ij.
 // No pair is lost to the broad phase: a pair within reach lies in groups whose spheres,
 // grown by the reach, overlap.  Rods of at most 1024 nodes (everything lives in shared
-// memory); a mass point with more than 16 partners keeps the first 16, and pairs beyond
-// 3 per mass point are dropped; either raises the overflow flag of the rod's statistics.
+// memory).  Beyond 16 larger partners of a point, 3 pairs per point, or 16 touching pairs
+// of a point, the excess is dropped and the overflow flag of the rod's statistics raised.
 #include "corde_step.cuh"
 #include "corde_variants.cuh"
 
 namespace corde {
 namespace {
 
-constexpr int kSelfGroup = 8;     // mass points per bounding sphere
-constexpr int kSelfMaxCand = 16;  // partners kept per mass point
+constexpr int kSelfGroup = 8;         // mass points per bounding sphere
+constexpr int kSelfMaxCand = 16;      // larger partners kept per mass point; touching pairs per point
 constexpr int kSelfPairsPerNode = 3;  // compacted pair capacity: 3 pairs per mass point
-constexpr unsigned short kSelfNone = 0xffffu;  // list entry dropped (pair capacity exceeded)
-constexpr unsigned short kSelfDown = 0x8000u;  // list entry flag: this point is the pair's larger index
 
 // Shared-memory layout of the self-collision area (bytes from its start).
 template <int EPT, int NT>
 struct SelfLayout {
   static constexpr int NN = EPT * NT;                                // node capacity
   static constexpr int NG = (NN + kSelfGroup - 1) / kSelfGroup;      // bounding spheres
-  static constexpr int NGW = (NG + 31) / 32;                         // words per bit row
+  static constexpr int NGH = (NG + 15) / 16;                         // 16-bit words per bit row
   static constexpr int NP = kSelfPairsPerNode * NN;                  // pair capacity
-  static_assert(NP < 0x8000, "pair slots must fit 15 bits");
+  static_assert(NP < 0x10000, "pair slots must fit 16 bits");
   static constexpr int off_r = 0;                                    // float4 [NN]: r, w
   static constexpr int off_v = off_r + NN * 16;                      // float4 [NN]: v
   static constexpr int off_pj = off_v + NN * 16;                     // float4 [NP]: phi J, phi
+  // (its first NN entries hold the predicted positions r + dt v, w during the touch test)
   static constexpr int off_g = off_pj + NP * 16;                     // float4 [NG]: centre, radius
-  static constexpr int off_bits = off_g + NG * 16;                   // unsigned [NG][NGW]
-  static constexpr int off_cnt = off_bits + ((NG * NGW * 4 + 15) / 16) * 16;  // int [NN]: partners
-  static constexpr int off_up = off_cnt + NN * 4;                    // int [NN]: first pair slot << 8 | up
-  static constexpr int off_pa = off_up + NN * 4;                     // ushort2 [NP]: (i, j), i < j
-  static constexpr int off_scan = off_pa + NP * 4;                   // int [NT / 32 + 1]: warp sums
-  static constexpr int off_stat = off_scan + ((NT / 32 + 1) * 4 + 15) / 16 * 16;  // int [4]
-  static constexpr int off_list = off_stat + 16;                     // uint16 [kSelfMaxCand][NN]
+  static constexpr int off_bits = off_g + NG * 16;                   // uint16 [NG][NGH]
+  static constexpr int off_nact = off_bits + ((NG * NGH * 2 + 15) / 16) * 16;  // int [NN]
+  static constexpr int off_pa = off_nact + NN * 4;                   // ushort2 [NP]: (i, j), i < j
+  static constexpr int off_act = off_pa + NP * 4;                    // uint16 [NP]: touching pairs
+  static constexpr int off_scan = off_act + ((NP * 2 + 15) / 16) * 16;  // int [NT / 32 + 1]
+  static constexpr int off_stat = off_scan + ((NT / 32 + 1) * 4 + 15) / 16 * 16;  // int [8]
+  static constexpr int off_list = off_stat + 32;  // uint16 [kSelfMaxCand][NN]: partners, then slots
   static constexpr int bytes = off_list + kSelfMaxCand * NN * 2;
 };
 
@@ -110,32 +111,39 @@ struct SelfHook {
   unsigned char* base;
   int t, n, min_sep;
   float dt, inv_dt, dist, reach, mu;
-  mutable int active;   // block-uniform: some pair exists this step
   mutable int n_pairs;  // compacted pairs this step (block-uniform)
 
   __device__ __forceinline__ float4* sr() const { return reinterpret_cast<float4*>(base + L::off_r); }
   __device__ __forceinline__ float4* sv() const { return reinterpret_cast<float4*>(base + L::off_v); }
   __device__ __forceinline__ float4* pj() const { return reinterpret_cast<float4*>(base + L::off_pj); }
   __device__ __forceinline__ float4* gs() const { return reinterpret_cast<float4*>(base + L::off_g); }
-  __device__ __forceinline__ unsigned* bits() const { return reinterpret_cast<unsigned*>(base + L::off_bits); }
-  __device__ __forceinline__ int* cnt() const { return reinterpret_cast<int*>(base + L::off_cnt); }
-  __device__ __forceinline__ int* up() const { return reinterpret_cast<int*>(base + L::off_up); }
+  __device__ __forceinline__ unsigned short* bits() const {
+    return reinterpret_cast<unsigned short*>(base + L::off_bits);
+  }
+  __device__ __forceinline__ int* nact() const { return reinterpret_cast<int*>(base + L::off_nact); }
   __device__ __forceinline__ ushort2* pa() const { return reinterpret_cast<ushort2*>(base + L::off_pa); }
+  __device__ __forceinline__ unsigned short* act() const {
+    return reinterpret_cast<unsigned short*>(base + L::off_act);
+  }
   __device__ __forceinline__ int* scan() const { return reinterpret_cast<int*>(base + L::off_scan); }
+  // stat: [0] pairs, [1] most larger partners, [2] overlapping pairs, [3] overflow, [4] touching
   __device__ __forceinline__ int* stat() const { return reinterpret_cast<int*>(base + L::off_stat); }
   __device__ __forceinline__ unsigned short* list() const {
     return reinterpret_cast<unsigned short*>(base + L::off_list);
   }
 
   // Detection: broad phase over bounding spheres, narrow phase over mass points, then the
-  // pairs (i < j) compacted into slots and every list entry turned into its pair's slot.
+  // pairs compacted into slots ordered by (i, j).
   template <int E>
   __device__ __forceinline__ void before_iterations(const float3 (&r)[E], const float (&w)[E]) const {
     float4* R4 = sr();
     const int e0 = t * EPT;
 #pragma unroll
     for (int e = 0; e < EPT; ++e)
-      if (e0 + e < n) R4[e0 + e] = make_float4(r[e].x, r[e].y, r[e].z, w[e]);
+      if (e0 + e < n) {
+        R4[e0 + e] = make_float4(r[e].x, r[e].y, r[e].z, w[e]);
+        nact()[e0 + e] = 0;
+      }
     if (t < 3) stat()[t] = 0;
     block_sync<NT>();
     const int ng = (n + kSelfGroup - 1) / kSelfGroup;
@@ -152,25 +160,26 @@ struct SelfHook {
       gs()[g] = make_float4(c.x, c.y, c.z, sqrtf(rad2));
     }
     block_sync<NT>();
-    const int nw = (ng + 31) / 32;
-    for (int task = t; task < ng * nw; task += NT) {
-      const int a = task / nw, wd = task - a * nw;
+    const int nh = (ng + 15) / 16;
+    for (int task = t; task < ng * nh; task += NT) {
+      const int a = task / nh, wd = task - a * nh;
       const float4 ca = gs()[a];
       unsigned word = 0u;
-#pragma unroll 8
-      for (int bb = 0; bb < 32; ++bb) {
-        const int b = min(wd * 32 + bb, ng - 1);
+#pragma unroll
+      for (int bb = 0; bb < 16; ++bb) {
+        const int b = min(wd * 16 + bb, ng - 1);
         const float4 cb = gs()[b];
         const float dx = cb.x - ca.x, dy = cb.y - ca.y, dz = cb.z - ca.z;
         const float lim = (ca.w + cb.w + reach) * 1.001f + 1e-6f;  // conservative against rounding
-        if (wd * 32 + bb < ng && dx * dx + dy * dy + dz * dz <= lim * lim) word |= 1u << bb;
+        // pairs (i < j) only: groups b >= a
+        if (wd * 16 + bb >= a && wd * 16 + bb < ng && dx * dx + dy * dy + dz * dz <= lim * lim) word |= 1u << bb;
       }
-      bits()[a * L::NGW + wd] = word;
+      bits()[a * L::NGH + wd] = (unsigned short)word;
     }
     block_sync<NT>();
     const float reach2 = reach * reach, dist2 = dist * dist;
     int n_up[EPT];
-    int my_up = 0;
+    int my_up = 0, st_max = 0, st_touch = 0, st_over = 0;
 #pragma unroll
     for (int e = 0; e < EPT; ++e) {
       const int i = e0 + e;
@@ -178,56 +187,60 @@ struct SelfHook {
       if (i >= n) continue;
       const float4 ri = R4[i];
       const int a = i / kSelfGroup;
-      int c = 0, ups = 0, touching = 0;
-      for (int wd = 0; wd < nw; ++wd) {
-        unsigned word = bits()[a * L::NGW + wd];
+      int c = 0, touching = 0;
+      for (int wd = a / 16; wd < nh; ++wd) {
+        unsigned word = bits()[a * L::NGH + wd];
         while (word) {
-          const int jb = (wd * 32 + __ffs(word) - 1) * kSelfGroup;
+          const int jb = (wd * 16 + __ffs(word) - 1) * kSelfGroup;
           word &= word - 1u;
+          unsigned hit = 0u;
 #pragma unroll
           for (int jj = 0; jj < kSelfGroup; ++jj) {
             const int j = jb + jj;
             const float4 rj = R4[min(j, n - 1)];
             const float dx = rj.x - ri.x, dy = rj.y - ri.y, dz = rj.z - ri.z;
             const float d2 = dx * dx + dy * dy + dz * dz;
-            if (j < n && abs(i - j) >= min_sep && d2 < reach2) {
-              if (c < kSelfMaxCand) {
-                list()[c * L::NN + i] = (unsigned short)j;
-                ups += j > i;
-              }
-              ++c;
-              touching += d2 < dist2;
-            }
+            const bool ok = j < n && j - i >= min_sep;
+            if (ok && d2 < reach2) hit |= 1u << jj;
+            if (ok && d2 < dist2) ++touching;
+          }
+          while (hit) {
+            const int j = jb + __ffs(hit) - 1;
+            hit &= hit - 1u;
+            if (c < kSelfMaxCand) list()[c * L::NN + i] = (unsigned short)j;
+            ++c;
           }
         }
       }
-      if (c > kSelfMaxCand) atomicOr(&stat()[3], 1);
-      const int kept = min(c, kSelfMaxCand);
-      cnt()[i] = kept;
-      n_up[e] = ups;
-      my_up += ups;
-      if (kept > 0) {
-        atomicAdd(&stat()[0], kept);
-        atomicMax(&stat()[1], c);
-        atomicAdd(&stat()[2], touching);
-      }
+      st_over |= c > kSelfMaxCand;
+      n_up[e] = min(c, kSelfMaxCand);
+      my_up += n_up[e];
+      st_max = max(st_max, c);
+      st_touch += touching;
     }
-    // compacted pair slots: node i owns slots [first_i, first_i + up_i) for its partners j > i
+    // statistics: one shared atomic per warp
+    const int w_up = __reduce_add_sync(0xffffffffu, my_up);
+    st_touch = __reduce_add_sync(0xffffffffu, st_touch);
+    st_max = __reduce_max_sync(0xffffffffu, st_max);
+    st_over = __reduce_or_sync(0xffffffffu, st_over);
+    if ((t & 31) == 0) {
+      if (w_up > 0) {
+        atomicAdd(&stat()[0], w_up);
+        atomicMax(&stat()[1], st_max);
+        atomicAdd(&stat()[2], st_touch);
+      }
+      if (st_over) atomicOr(&stat()[3], 1);
+    }
+    // compacted pair slots: point i owns [first_i, first_i + up_i), partners ascending
     int total = 0;
     int first = block_exclusive_scan<NT>(my_up, scan(), &total);
 #pragma unroll
     for (int e = 0; e < EPT; ++e) {
       const int i = e0 + e;
       if (i >= n) continue;
-      up()[i] = (first << 8) | n_up[e];
-      const int c = cnt()[i];
-      int k2 = 0;
-      for (int k = 0; k < c; ++k) {
-        const int j = list()[k * L::NN + i];
-        if (j > i) {
-          const int slot = first + k2++;
-          if (slot < L::NP) pa()[slot] = make_ushort2((unsigned short)i, (unsigned short)j);
-        }
+      for (int k = 0; k < n_up[e]; ++k) {
+        const int slot = first + k;
+        if (slot < L::NP) pa()[slot] = make_ushort2((unsigned short)i, list()[k * L::NN + i]);
       }
       first += n_up[e];
     }
@@ -236,94 +249,116 @@ struct SelfHook {
       total = L::NP;
     }
     n_pairs = total;
-    block_sync<NT>();
-    // list entries -> pair slots (partners below: find this point in the partner's slots)
-    int any = 0;
-#pragma unroll
-    for (int e = 0; e < EPT; ++e) {
-      const int i = e0 + e;
-      if (i >= n) continue;
-      const int c = cnt()[i];
-      const int fi = up()[i] >> 8;
-      int k2 = 0;
-      for (int k = 0; k < c; ++k) {
-        const int j = list()[k * L::NN + i];
-        int slot;
-        unsigned short flag = 0;
-        if (j > i) {
-          slot = fi + k2++;
-        } else {
-          const int uj = up()[j];
-          const int fj = uj >> 8, nj = uj & 0xff;
-          slot = L::NP;
-          for (int q = 0; q < nj; ++q)
-            if (fj + q < L::NP && pa()[fj + q].y == i) slot = fj + q;
-          flag = kSelfDown;
-        }
-        list()[k * L::NN + i] = slot < L::NP ? (unsigned short)(slot | flag) : kSelfNone;
-      }
-      any |= c > 0;
-    }
-    active = block_or<NT>(any);
   }
 
-  // Response: every pair evaluated once from the staged velocities (Jacobi), then each
-  // mass point takes the penetration-weighted mean of its pairs, in ascending partner order.
+  // Response (see the file header): touching pairs found, their impulses computed, and
+  // every mass point's pairs summed in ascending slot order.
   template <int E>
   __device__ __forceinline__ void after_odd(const float3 (&r)[E], float3 (&v)[E], const float (&w)[E]) const {
-    if (!active) return;
+    if (n_pairs == 0) return;  // block-uniform
     const int e0 = t * EPT;
     float4* V4 = sv();
+    float4* Q4 = pj();  // predicted positions, read by the touch test only
 #pragma unroll
     for (int e = 0; e < EPT; ++e)
-      if (e0 + e < n) V4[e0 + e] = make_float4(v[e].x, v[e].y, v[e].z, 0.f);
+      if (e0 + e < n) {
+        V4[e0 + e] = make_float4(v[e].x, v[e].y, v[e].z, 0.f);
+        Q4[e0 + e] = make_float4(fmaf(dt, v[e].x, r[e].x), fmaf(dt, v[e].y, r[e].y), fmaf(dt, v[e].z, r[e].z), w[e]);
+      }
+    if (t == 0) stat()[4] = 0;
     block_sync<NT>();
     const float4* R4 = sr();
     float4* P4 = pj();
     const float dist2 = dist * dist;
-    for (int p0 = 0; p0 < n_pairs; p0 += 2 * NT) {
+    const int lane = t & 31;
+    // 1. which pairs touch: predicted positions closer than 2 r (the exact offset of step 2
+    //    decides the impulse; a pair misjudged here within rounding of 2 r has phi = 0)
+    constexpr int PH = 4;
+    for (int p0 = 0; p0 < n_pairs; p0 += PH * NT) {
+      bool hit[PH];
+      float4 qi[PH], qj[PH];
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int p = p0 + h * NT + t;
-        if (p >= n_pairs) continue;
-        const ushort2 ij = pa()[p];
-        const float4 ri = R4[ij.x], rj = R4[ij.y];
-        const float3 u = f3(V4[ij.y]) - f3(V4[ij.x]);
-        const float3 delta = (f3(rj) - f3(ri)) + dt * u;
-        const float d2 = dot3(delta, delta);
-        const float wsum = ri.w + rj.w;
-        float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (d2 < dist2 && d2 > 0.f && wsum > 0.f) {
-          const float il = rsqrtf(d2);
-          const float phi = dist - d2 * il;
-          const float3 nrm = il * delta;
-          const float dun = phi * inv_dt;
-          const float3 ut = u - dot3(u, nrm) * nrm;
-          const float ut2 = dot3(ut, ut);
-          const float cut = ut2 > 0.f ? fminf(1.f, mu * dun * rsqrtf(ut2)) : 0.f;
-          const float3 J = (phi * __frcp_rn(wsum)) * (dun * nrm - cut * ut);
-          out = make_float4(J.x, J.y, J.z, phi);
+      for (int h = 0; h < PH; ++h) {
+        const ushort2 ij = pa()[min(p0 + h * NT + t, n_pairs - 1)];
+        qi[h] = Q4[ij.x];
+        qj[h] = Q4[ij.y];
+      }
+#pragma unroll
+      for (int h = 0; h < PH; ++h) {
+        const float3 delta = f3(qj[h]) - f3(qi[h]);
+        hit[h] = p0 + h * NT + t < n_pairs && dot3(delta, delta) < dist2 * 1.0001f && qi[h].w + qj[h].w > 0.f;
+      }
+      // one list append per warp for the whole pass
+      unsigned m[PH];
+      int tot = 0;
+#pragma unroll
+      for (int h = 0; h < PH; ++h) {
+        m[h] = __ballot_sync(0xffffffffu, hit[h]);
+        tot += __popc(m[h]);
+      }
+      if (tot > 0) {
+        int at = 0;
+        if (lane == 0) at = atomicAdd(&stat()[4], tot);
+        at = __shfl_sync(0xffffffffu, at, 0);
+        const unsigned below = (1u << lane) - 1u;
+#pragma unroll
+        for (int h = 0; h < PH; ++h) {
+          if (hit[h]) act()[at + __popc(m[h] & below)] = (unsigned short)(p0 + h * NT + t);
+          at += __popc(m[h]);
         }
-        P4[p] = out;
       }
     }
     block_sync<NT>();
+    // 2. impulses of the touching pairs
+    const int na = stat()[4];
+    for (int q = t; q < na; q += NT) {
+      const int p = act()[q];
+      const ushort2 ij = pa()[p];
+      const float4 ri = R4[ij.x], rj = R4[ij.y];
+      const float3 u = f3(V4[ij.y]) - f3(V4[ij.x]);
+      const float3 delta = (f3(rj) - f3(ri)) + dt * u;
+      const float d2 = dot3(delta, delta);
+      const float il = rsqrtf(d2);
+      const float phi = fmaxf(dist - d2 * il, 0.f);  // rounding at the contact distance
+      const float3 nrm = il * delta;
+      const float dun = phi * inv_dt;
+      const float3 ut = u - dot3(u, nrm) * nrm;
+      const float ut2 = dot3(ut, ut);
+      const float cut = ut2 > 0.f ? fminf(1.f, mu * dun * rsqrtf(ut2)) : 0.f;
+      const float3 J = (phi * __frcp_rn(ri.w + rj.w)) * (dun * nrm - cut * ut);
+      P4[p] = make_float4(J.x, J.y, J.z, phi);
+      const int ka = atomicAdd(&nact()[ij.x], 1);
+      if (ka < kSelfMaxCand) list()[ka * L::NN + ij.x] = (unsigned short)p;
+      const int kb = atomicAdd(&nact()[ij.y], 1);
+      if (kb < kSelfMaxCand) list()[kb * L::NN + ij.y] = (unsigned short)p;
+      if (ka >= kSelfMaxCand || kb >= kSelfMaxCand) atomicOr(&stat()[3], 4);
+    }
+    block_sync<NT>();
+    // 3. each mass point: its pairs in ascending slot order
 #pragma unroll
     for (int e = 0; e < EPT; ++e) {
       const int i = e0 + e;
-      if (i >= n || !(w[e] > 0.f)) continue;
-      const int c = cnt()[i];
+      if (i >= n) continue;
+      const int k = min(nact()[i], kSelfMaxCand);
+      if (k == 0) continue;
+      nact()[i] = 0;
+      if (!(w[e] > 0.f)) continue;
       float3 acc = zero3();
       float wphi = 0.f;
-      for (int k = 0; k < c; ++k) {
-        const unsigned short ent = list()[k * L::NN + i];
-        if (ent == kSelfNone) continue;
-        const float4 s = P4[ent & 0x7fff];
-        if (ent & kSelfDown) acc += f3(s);
-        else acc -= f3(s);
-        wphi += s.w;
+      int prev = -1;
+      for (int q = 0; q < k; ++q) {
+        int next = 0x7fffffff;
+        for (int m = 0; m < k; ++m) {
+          const int sl = list()[m * L::NN + i];
+          if (sl > prev && sl < next) next = sl;
+        }
+        prev = next;
+        const float4 s4 = P4[next];
+        if (pa()[next].x == i) acc -= f3(s4);
+        else acc += f3(s4);
+        wphi += s4.w;
       }
-      if (wphi > 0.f) v[e] += (w[e] / wphi) * acc;
+      if (wphi > 0.f) v[e] += (w[e] * __frcp_rn(wphi)) * acc;
     }
   }
 };
@@ -334,7 +369,7 @@ constexpr int self_smem_bytes() {
 }
 
 template <int EPT, int NT>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, 1)
 self_step_kernel(const RodDev* __restrict__ rods, const int* __restrict__ work, float4* __restrict__ x4,
                  float4* __restrict__ v4, float4* __restrict__ q4, float4* __restrict__ o4,
                  const float4* __restrict__ u4, const float4* __restrict__ k4, const float4* __restrict__ drive,
@@ -367,7 +402,6 @@ self_step_kernel(const RodDev* __restrict__ rods, const int* __restrict__ work, 
   hook.dist = R.self_dist;
   hook.reach = R.self_reach;
   hook.mu = R.self_mu;
-  hook.active = 0;
   hook.n_pairs = 0;
   if (t == 0) hook.stat()[3] = 0;  // overflow flag of this launch (read after the last barrier)
 
@@ -391,10 +425,10 @@ self_step_kernel(const RodDev* __restrict__ rods, const int* __restrict__ work, 
   if (t == 0 && stats != nullptr) {
     const int* st = hook.stat();
     int4 out = stats[rid];
-    out.x = st[0] / 2;  // candidate pairs at the last detection
-    out.y = st[1];      // most partners of one mass point
-    out.z = st[2] / 2;  // pairs whose spheres overlap at the last detection
-    out.w |= st[3];     // 1: a partner list overflowed, 2: the pair slots overflowed (sticky)
+    out.x = st[0];   // candidate pairs at the last detection
+    out.y = st[1];   // most larger partners of one mass point
+    out.z = st[2];   // pairs whose spheres overlap at the last detection
+    out.w |= st[3];  // 1: partner list, 2: pair slots, 4: touching pairs of a point overflowed (sticky)
     stats[rid] = out;
   }
 }

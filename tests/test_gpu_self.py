@@ -92,7 +92,7 @@ def test_self_detection_matches_oracle(corde):
     stats = b.self_collision_stats(0)
     cand, pairs = oracle.self_candidates(rod, st0["pos"])
     assert stats["candidate_pairs"] == pairs
-    assert stats["max_candidates"] == max(len(c) for c in cand)
+    assert stats["max_partners_above"] == max(int(np.sum(c > i)) for i, c in enumerate(cand))
     assert not stats["overflow"]
     assert stats["overlapping_pairs"] >= 0
     b.close()
