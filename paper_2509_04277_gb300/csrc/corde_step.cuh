@@ -606,7 +606,7 @@ __device__ __forceinline__ void run_rod(const RodDev& R, const Halo& H, const in
 // n_steps time steps of one rod per block.  traj (optional): positions after every step,
 // [n_steps][n_elements] float4 with .w the inverse mass.
 template <int EPT, int NT>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, NT >= 512 ? 1 : 512 / NT)
 step_kernel(const RodDev* __restrict__ rods, const int* __restrict__ work, float4* __restrict__ x4,
             float4* __restrict__ v4, float4* __restrict__ q4, float4* __restrict__ o4,
             const float4* __restrict__ u4, const float4* __restrict__ k4, const float4* __restrict__ drive,
