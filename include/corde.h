@@ -99,6 +99,17 @@ int rod_create(int n_rods, const RodParams* params, const float* pos, const floa
  * to use the values last given to rod_set_input (initially zero).  n_steps >= 0. */
 int rod_step(rod_handle h, int n_steps, const float* drive, void* stream);
 
+/* One haptic tick in one call (the haptic loop of Section 2.2: the input goes in, the
+ * kernel runs its steps, the state comes out for the host): as rod_step, and the kernels
+ * write the positions after the last step to pos_out, [n_elements][4] floats (x, y, z,
+ * inverse mass), in their epilogue.  drive and pos_out may be device memory or mapped
+ * pinned host memory (cudaHostAlloc: mapped by default under unified addressing); over a
+ * coherent CPU-GPU link the kernels then read the drive and write the positions across
+ * the link, with no separate copy.  Both must be 16-byte aligned (CORDE_ERR_ARG
+ * otherwise).  pos_out NULL: exactly rod_step.  Asynchronous on the stream: the positions
+ * are complete when the stream is. */
+int rod_step_io(rod_handle h, int n_steps, const float* drive, float* pos_out, void* stream);
+
 /* Bind rod `inner` (guidewire) inside rod `outer` (catheter) of the same handle as a pair
  * stepped together in one thread block (Section 3.4).  mode 0: no interaction (v0);
  * 1: one-way binding, the outer rod is not moved (v1); 2: two-way binding (v2).  Binding

@@ -48,6 +48,7 @@ SIGNATURES = {
     "rod_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(RodParams), _VP, _VP, _VP, _VP, _VP, _VP, _VP,
                                   ctypes.POINTER(_VP)]),
     "rod_step": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP]),
+    "rod_step_io": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP]),
     "rod_set_input": (ctypes.c_int, [_VP, _VP, _VP]),
     "rod_bind": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "rod_set_tube": (ctypes.c_int, [_VP, ctypes.c_int, _VP]),
@@ -144,6 +145,12 @@ def rod_create(params, pos, quat, rest_quat=None, vel=None, omega=None, stiff_mu
 
 def rod_step(h, n_steps, drive=None, stream=None):
     _check(load().rod_step(h, int(n_steps), _ptr(drive), _stream(stream)), "rod_step")
+
+
+def rod_step_io(h, n_steps, drive=None, pos_out=None, stream=None):
+    """rod_step that also writes the positions after the last step to pos_out
+    ([n_elements, 4] float32, device or pinned host memory)."""
+    _check(load().rod_step_io(h, int(n_steps), _ptr(drive), _ptr(pos_out), _stream(stream)), "rod_step_io")
 
 
 def rod_bind(h, outer, inner, mode):

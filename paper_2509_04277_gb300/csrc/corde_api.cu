@@ -163,6 +163,8 @@ struct corde_rods {
   cudaGraphExec_t graph_exec = nullptr;
   int graph_steps = -1;
   const float4* graph_drive = nullptr;
+  float4* graph_pos_out = nullptr;
+  float4* io_pos = nullptr;  // positions output of the launch being issued (rod_step_io)
   int graph_launches = 0;
   cudaStream_t cap_stream = nullptr;
   std::vector<cudaStream_t> side;
@@ -402,6 +404,7 @@ int launch_bins(rod_handle h, const std::vector<Bin>& bins, int n_steps, const f
   a.traj = traj;
   a.n_elem = h->n_elem;
   a.self_stats = h->d_self_stats;
+  a.pos_out = h->io_pos;
   if (mb) a.mb = *mb;
   int launches = 0;
   for (const auto& b : bins) {
@@ -508,6 +511,7 @@ int launch_all(rod_handle h, int n_steps, const float4* d, cudaStream_t s, const
     a.drive = d;
     a.n_steps = n_steps;
     a.traj = nullptr;
+    a.pos_out = h->io_pos;
     a.n_elem = h->n_elem;
     for (const auto& pb : h->pair_bins) {
       cudaStream_t sk = branches ? (*branches)[k] : s;
@@ -563,6 +567,7 @@ int capture_graph(rod_handle h, int n_steps, const float4* d) {
   }
   h->graph_steps = n_steps;
   h->graph_drive = d;
+  h->graph_pos_out = h->io_pos;
   h->graph_launches = (int)nb;
   return CORDE_OK;
 }
@@ -708,7 +713,7 @@ int rod_create(int n_rods, const RodParams* params, const float* pos, const floa
   return CORDE_OK;
 }
 
-int rod_step(rod_handle h, int n_steps, const float* drive, void* stream) {
+static int step_impl(rod_handle h, int n_steps, const float* drive, float4* pos_out, void* stream) {
   if (int rc = check_handle(h)) return rc;
   if (n_steps < 0) return fail(CORDE_ERR_ARG, "n_steps must be >= 0");
   if (n_steps == 0) {
@@ -735,14 +740,33 @@ int rod_step(rod_handle h, int n_steps, const float* drive, void* stream) {
   h->steps_done += n_steps;
   if (!use_graph) return launch_all(h, n_steps, d, (cudaStream_t)stream, nullptr);
   if (!h->d_drive_graph) CK(cudaMalloc(&h->d_drive_graph, h->n_rods * 2 * sizeof(float4)));
-  CK(cudaMemcpyAsync(h->d_drive_graph, d, h->n_rods * 2 * sizeof(float4), cudaMemcpyDeviceToDevice,
-                     (cudaStream_t)stream));
-  if (!h->graph_exec || h->graph_steps != n_steps || h->graph_drive != h->d_drive_graph) {
+  CK(cudaMemcpyAsync(h->d_drive_graph, d, h->n_rods * 2 * sizeof(float4), cudaMemcpyDefault, (cudaStream_t)stream));
+  if (!h->graph_exec || h->graph_steps != n_steps || h->graph_drive != h->d_drive_graph ||
+      h->graph_pos_out != pos_out) {
     if (int rc = capture_graph(h, n_steps, h->d_drive_graph)) return rc;
   }
   CK(cudaGraphLaunch(h->graph_exec, (cudaStream_t)stream));
   h->last_launches = h->graph_launches;
   return CORDE_OK;
+}
+
+int rod_step(rod_handle h, int n_steps, const float* drive, void* stream) {
+  return step_impl(h, n_steps, drive, nullptr, stream);
+}
+
+int rod_step_io(rod_handle h, int n_steps, const float* drive, float* pos_out, void* stream) {
+  if (int rc = check_handle(h)) return rc;
+  float4* po = nullptr;
+  if (pos_out) {
+    const void* dp = nullptr;
+    if (!device_accessible(pos_out, &dp))
+      return fail(CORDE_ERR_ARG, "pos_out must be 16-byte aligned device, managed or mapped pinned host memory");
+    po = reinterpret_cast<float4*>(const_cast<void*>(dp));
+  }
+  h->io_pos = po;
+  const int rc = step_impl(h, n_steps, drive, po, stream);
+  h->io_pos = nullptr;
+  return rc;
 }
 
 int rod_set_input(rod_handle h, const float* drive, void* stream) {

@@ -20,7 +20,8 @@ __global__ void __launch_bounds__(NT)
 cluster_step_kernel(const RodDev* __restrict__ rods, const int* __restrict__ work, float4* __restrict__ x4,
                     float4* __restrict__ v4, float4* __restrict__ q4, float4* __restrict__ o4,
                     const float4* __restrict__ u4, const float4* __restrict__ k4, const float4* __restrict__ drive,
-                    int n_steps, float4* __restrict__ traj, int64_t n_elem, int C, MailboxDev mb) {
+                    int n_steps, float4* __restrict__ traj, int64_t n_elem, int C, MailboxDev mb,
+                    float4* __restrict__ pos_out) {
   static_assert(EPT % 2 == 0, "elements per thread must be even (red-black sweeps)");
   extern __shared__ float4 smem[];
   cooperative_groups::cluster_group cluster = cooperative_groups::this_cluster();
@@ -28,7 +29,7 @@ cluster_step_kernel(const RodDev* __restrict__ rods, const int* __restrict__ wor
   const int rid = work[blockIdx.x / C];
   const RodDev R = rods[rid];
   const ClusterHalo<NT> H{(int)threadIdx.x, c, C};
-  run_rod<EPT, NT>(R, H, rid, x4, x4, v4, q4, o4, u4, k4, drive, n_steps, traj, n_elem, mb, smem);
+  run_rod<EPT, NT>(R, H, rid, x4, x4, v4, q4, o4, u4, k4, drive, n_steps, traj, n_elem, mb, smem, pos_out);
   // no block leaves while a neighbour may still read its exchange buffer
   cluster.sync();
 }
@@ -58,7 +59,7 @@ cudaError_t launch_cluster_t(const StepArgs& a, int n_rods, int C, cudaStream_t 
   cfg.attrs = at;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, cluster_step_kernel<EPT, NT>, a.rods, a.work, a.x4, a.v4, a.q4, a.o4, a.u4, a.k4,
-                            a.drive, a.n_steps, a.traj, a.n_elem, C, a.mb);
+                            a.drive, a.n_steps, a.traj, a.n_elem, C, a.mb, a.pos_out);
 }
 
 }  // namespace

@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(2 * NT)
 pair_kernel(const RodDev* __restrict__ rods, const int4* __restrict__ pairs, float4* __restrict__ x4,
             float4* __restrict__ v4, float4* __restrict__ q4, float4* __restrict__ o4,
             const float4* __restrict__ u4, const float4* __restrict__ k4, const float4* __restrict__ drive,
-            int n_steps) {
+            int n_steps, float4* __restrict__ pos_out) {
   extern __shared__ float4 smem[];
   const int group = threadIdx.x / NT;
   const int t = threadIdx.x - group * NT;
@@ -153,6 +153,7 @@ pair_kernel(const RodDev* __restrict__ rods, const int4* __restrict__ pairs, flo
       v4[R.off + i] = make_float4(v[e].x, v[e].y, v[e].z, 0.f);
       q4[R.off + i] = q[e];
       o4[R.off + i] = make_float4(om[e].x, om[e].y, om[e].z, 0.f);
+      if (pos_out != nullptr) pos_out[R.off + i] = make_float4(r[e].x, r[e].y, r[e].z, w[e]);
     }
   }
 }
@@ -165,7 +166,7 @@ cudaError_t launch_pair_t(const StepArgs& a, const int4* pairs, int n_pairs, cud
     if (e != cudaSuccess) return e;
   }
   pair_kernel<EPT, NT><<<n_pairs, 2 * NT, smem, s>>>(a.rods, pairs, a.x4, a.v4, a.q4, a.o4, a.u4, a.k4, a.drive,
-                                                      a.n_steps);
+                                                      a.n_steps, a.pos_out);
   return cudaGetLastError();
 }
 

@@ -373,7 +373,7 @@ __global__ void __launch_bounds__(NT, 1)
 self_step_kernel(const RodDev* __restrict__ rods, const int* __restrict__ work, float4* __restrict__ x4,
                  float4* __restrict__ v4, float4* __restrict__ q4, float4* __restrict__ o4,
                  const float4* __restrict__ u4, const float4* __restrict__ k4, const float4* __restrict__ drive,
-                 int n_steps, int4* __restrict__ stats) {
+                 int n_steps, int4* __restrict__ stats, float4* __restrict__ pos_out) {
   extern __shared__ float4 smem[];
   const int rid = work[blockIdx.x];
   const RodDev R = rods[rid];
@@ -419,6 +419,7 @@ self_step_kernel(const RodDev* __restrict__ rods, const int* __restrict__ work, 
       v4[R.off + i] = make_float4(v[e].x, v[e].y, v[e].z, 0.f);
       q4[R.off + i] = q[e];
       o4[R.off + i] = make_float4(om[e].x, om[e].y, om[e].z, 0.f);
+      if (pos_out != nullptr) pos_out[R.off + i] = make_float4(r[e].x, r[e].y, r[e].z, w[e]);
     }
   }
   block_sync<NT>();
@@ -442,7 +443,7 @@ cudaError_t launch_self_t(const StepArgs& a, int n_blocks, cudaStream_t s) {
     if (e != cudaSuccess) return e;
   }
   self_step_kernel<EPT, NT><<<n_blocks, NT, smem, s>>>(a.rods, a.work, a.x4, a.v4, a.q4, a.o4, a.u4, a.k4, a.drive,
-                                                        a.n_steps, a.self_stats);
+                                                        a.n_steps, a.self_stats, a.pos_out);
   return cudaGetLastError();
 }
 

@@ -544,7 +544,8 @@ __device__ __forceinline__ void run_rod(const RodDev& R, const Halo& H, const in
                                         float4* __restrict__ x4, float4* __restrict__ v4, float4* __restrict__ q4,
                                         float4* __restrict__ o4, const float4* __restrict__ u4,
                                         const float4* __restrict__ k4, const float4* __restrict__ drive, int n_steps,
-                                        float4* __restrict__ traj, int64_t n_elem, const MailboxDev& mb, float4* smem) {
+                                        float4* __restrict__ traj, int64_t n_elem, const MailboxDev& mb, float4* smem,
+                                        float4* __restrict__ pos_out) {
   float4* par_u = smem;
   float4* par_k = smem + EPT * NT;
   float4* halo = smem + 2 * EPT * NT;
@@ -599,24 +600,26 @@ __device__ __forceinline__ void run_rod(const RodDev& R, const Halo& H, const in
       v4[R.off + i] = make_float4(v[e].x, v[e].y, v[e].z, 0.f);
       q4[R.off + i] = q[e];
       o4[R.off + i] = make_float4(om[e].x, om[e].y, om[e].z, 0.f);
+      if (pos_out != nullptr) pos_out[R.off + i] = make_float4(r[e].x, r[e].y, r[e].z, w[e]);
     }
   }
 }
 
 // n_steps time steps of one rod per block.  traj (optional): positions after every step,
-// [n_steps][n_elements] float4 with .w the inverse mass.
+// [n_steps][n_elements] float4 with .w the inverse mass; pos_out (optional): positions after
+// the last step, [n_elements] float4 (device or mapped host memory).
 template <int EPT, int NT>
 __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : 512 / NT)
 step_kernel(const RodDev* __restrict__ rods, const int* __restrict__ work, float4* __restrict__ x4,
             float4* __restrict__ v4, float4* __restrict__ q4, float4* __restrict__ o4,
             const float4* __restrict__ u4, const float4* __restrict__ k4, const float4* __restrict__ drive,
-            int n_steps, float4* __restrict__ traj, int64_t n_elem, MailboxDev mb) {
+            int n_steps, float4* __restrict__ traj, int64_t n_elem, MailboxDev mb, float4* __restrict__ pos_out) {
   static_assert(EPT % 2 == 0, "elements per thread must be even (red-black sweeps)");
   extern __shared__ float4 smem[];
   const int rid = work[blockIdx.x];
   const RodDev R = rods[rid];
   const BlockHalo<NT, NT> H{(int)threadIdx.x};
-  run_rod<EPT, NT>(R, H, rid, x4, x4, v4, q4, o4, u4, k4, drive, n_steps, traj, n_elem, mb, smem);
+  run_rod<EPT, NT>(R, H, rid, x4, x4, v4, q4, o4, u4, k4, drive, n_steps, traj, n_elem, mb, smem, pos_out);
 }
 
 }  // namespace corde

@@ -12,7 +12,7 @@ static cudaError_t launch_step(const StepArgs& a, int n_blocks, cudaStream_t s) 
     if (e != cudaSuccess) return e;
   }
   step_kernel<EPT, NT><<<n_blocks, NT, smem, s>>>(a.rods, a.work, a.x4, a.v4, a.q4, a.o4, a.u4, a.k4, a.drive,
-                                                  a.n_steps, a.traj, a.n_elem, a.mb);
+                                                  a.n_steps, a.traj, a.n_elem, a.mb, a.pos_out);
   return cudaGetLastError();
 }
 

@@ -21,6 +21,7 @@ struct StepArgs {
   int64_t n_elem;
   MailboxDev mb;   // mailbox of the launch (period 0: none)
   int4* self_stats;  // self-collision statistics per rod (corde_self.cu), or NULL
+  float4* pos_out;   // optional: positions (r, w) after the launch, [n_elem] (device or mapped host)
 };
 
 typedef cudaError_t (*StepLaunchFn)(const StepArgs& a, int n_blocks, cudaStream_t s);
