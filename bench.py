@@ -647,6 +647,7 @@ def main_ours(args):
                                         f"{sm_mhz:.0f} MHz ({which} sm_max_mhz)",
                          "note": "one rod = one thread block on one of 152 SMs; latency-bound by design",
                          "kernel": "step_kernel<ept=%d, nt=%d>" % tuple(single["plan"]),
+                         "frac_of_one_sm": round(achieved / (fp32_peak / NUM_SMS), 6),
                          "kernel_us_per_launch": round(single["kernel_ms_avg"] * 1e3, 3),
                          "duration": "timed region / launches (includes launch gaps); one launch bracketed "
                                      "alone by events: %.3f us" % (single["kernel_ms_isolated"] * 1e3)},
