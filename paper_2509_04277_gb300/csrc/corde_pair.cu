@@ -19,7 +19,7 @@
 namespace corde {
 namespace {
 
-template <int SYNC_NT>
+template <int SYNC_NT, int EPT>
 struct PairHook {
   int group;       // 0 outer, 1 inner
   int t;           // thread index within the group
@@ -31,19 +31,56 @@ struct PairHook {
   float dt;
   float4* out_r;   // [capacity] outer positions and inverse masses (once per step)
   float4* out_v;   // [capacity] outer velocities (every iteration)
+  // per step, inner nodes only (positions and masses are fixed during the sweeps):
+  mutable float3 rp[EPT];   // node position minus its binding point on the outer centreline
+  mutable float inv[EPT];   // -1 / (dt w_eff), 0 when the node has no binding this step
+  mutable float sk[EPT], sk1[EPT];  // v2: (1 - a) w_k and a w_k+1, the outer nodes' shares
 
-  template <int EPT>
-  __device__ __forceinline__ void before_iterations(const float3 (&r)[EPT], const float (&w)[EPT]) const {
-    if (mode == 0 || group != 0) return;
+  template <int E>
+  __device__ __forceinline__ void before_iterations(const float3 (&r)[E], const float (&w)[E]) const {
+    if (mode == 0) return;
+    if (group == 0) {
 #pragma unroll
-    for (int e = 0; e < EPT; ++e) {
-      const int i = t * EPT + e;
-      if (i < n_out) out_r[i] = make_float4(r[e].x, r[e].y, r[e].z, w[e]);
+      for (int e = 0; e < EPT; ++e) {
+        const int i = t * EPT + e;
+        if (i < n_out) out_r[i] = make_float4(r[e].x, r[e].y, r[e].z, w[e]);
+      }
+    }
+    block_sync<SYNC_NT>();
+    if (group == 1) {
+      const float a = alpha, b = 1.f - alpha;
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) {
+        const int i = t * EPT + e;
+        const int k = i + k0;
+        inv[e] = 0.f;
+        rp[e] = zero3();
+        sk[e] = sk1[e] = 0.f;
+        if (i >= n_in || k < 0 || k > n_out - 2) continue;
+        const float4 rk = out_r[k], rk1 = out_r[k + 1];
+        const float wk = mode == 2 ? rk.w : 0.f, wk1 = mode == 2 ? rk1.w : 0.f;
+        const float weff = w[e] + b * b * wk + a * a * wk1;
+        if (!(weff > 0.f)) continue;
+        const float3 pc = f3(b * rk.x + a * rk1.x, b * rk.y + a * rk1.y, b * rk.z + a * rk1.z);
+        rp[e] = r[e] - pc;
+        inv[e] = -1.f / (dt * weff);
+        sk[e] = b * wk;
+        sk1[e] = a * wk1;
+      }
     }
   }
 
-  template <int EPT>
-  __device__ __forceinline__ void after_odd(const float3 (&r)[EPT], float3 (&v)[EPT], const float (&w)[EPT]) const {
+  // One inner node's binding: lambda = -(d) / (dt w_eff) with d the predicted offset from
+  // its binding point; the node moves by w lambda, in v2 the two outer nodes by their shares.
+  __device__ __forceinline__ float3 binding(int e, float3 ve, float3& vk, float3& vk1) const {
+    const float a = alpha, b = 1.f - alpha;
+    const float3 vc = f3(b * vk.x + a * vk1.x, b * vk.y + a * vk1.y, b * vk.z + a * vk1.z);
+    const float3 d = rp[e] + dt * (ve - vc);
+    return inv[e] * d;
+  }
+
+  template <int E>
+  __device__ __forceinline__ void after_odd(const float3 (&r)[E], float3 (&v)[E], const float (&w)[E]) const {
     if (mode == 0) return;
     if (group == 0) {
 #pragma unroll
@@ -53,35 +90,38 @@ struct PairHook {
       }
     }
     block_sync<SYNC_NT>();
+    if (mode == 1) {
+      // one-way: the outer rod does not move, so the two colors are independent and run
+      // together (the same result as in order)
+      if (group == 1) {
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) {
+          if (inv[e] == 0.f) continue;
+          const int k = t * EPT + e + k0;
+          float3 vk = f3(out_v[k]), vk1 = f3(out_v[k + 1]);
+          v[e] += w[e] * binding(e, v[e], vk, vk1);
+        }
+      }
+      return;
+    }
+#pragma unroll
     for (int color = 0; color < 2; ++color) {
       if (group == 1) {
 #pragma unroll
         for (int e = 0; e < EPT; ++e) {
-          const int i = t * EPT + e;  // EPT is even: node parity = e parity
-          if ((e & 1) != color || i >= n_in) continue;
-          const int k = i + k0;
-          if (k < 0 || k > n_out - 2) continue;
-          const float4 rk = out_r[k], rk1 = out_r[k + 1];
-          const float a = alpha, b = 1.f - alpha;
-          const float wk = mode == 2 ? rk.w : 0.f, wk1 = mode == 2 ? rk1.w : 0.f;
-          const float weff = w[e] + b * b * wk + a * a * wk1;
-          if (!(weff > 0.f)) continue;
-          const float4 vk = out_v[k], vk1 = out_v[k + 1];
-          const float3 pc = f3(b * rk.x + a * rk1.x, b * rk.y + a * rk1.y, b * rk.z + a * rk1.z);
-          const float3 vc = f3(b * vk.x + a * vk1.x, b * vk.y + a * vk1.y, b * vk.z + a * vk1.z);
-          const float3 d = (r[e] - pc) + dt * (v[e] - vc);
-          const float3 lam = (-1.f / (dt * weff)) * d;
+          if ((e & 1) != color || inv[e] == 0.f) continue;  // EPT is even: node parity = e parity
+          const int k = t * EPT + e + k0;
+          float3 vk = f3(out_v[k]), vk1 = f3(out_v[k + 1]);
+          const float3 lam = binding(e, v[e], vk, vk1);
           v[e] += w[e] * lam;
-          if (mode == 2) {
-            const float3 dk = (b * wk) * lam, dk1 = (a * wk1) * lam;
-            out_v[k] = make_float4(vk.x - dk.x, vk.y - dk.y, vk.z - dk.z, 0.f);
-            out_v[k + 1] = make_float4(vk1.x - dk1.x, vk1.y - dk1.y, vk1.z - dk1.z, 0.f);
-          }
+          const float3 dk = sk[e] * lam, dk1 = sk1[e] * lam;
+          out_v[k] = make_float4(vk.x - dk.x, vk.y - dk.y, vk.z - dk.z, 0.f);
+          out_v[k + 1] = make_float4(vk1.x - dk1.x, vk1.y - dk1.y, vk1.z - dk1.z, 0.f);
         }
       }
-      if (mode == 2) block_sync<SYNC_NT>();
+      block_sync<SYNC_NT>();
     }
-    if (mode == 2 && group == 0) {
+    if (group == 0) {
 #pragma unroll
       for (int e = 0; e < EPT; ++e) {
         const int i = t * EPT + e;
@@ -127,7 +167,7 @@ pair_kernel(const RodDev* __restrict__ rods, const int4* __restrict__ pairs, flo
     w_drive = f3(drive[2 * rid + 1]);
     beta = drive[2 * pr.y].w;
   }
-  PairHook<2 * NT> hook;
+  PairHook<2 * NT, EPT> hook;
   hook.group = group;
   hook.t = t;
   hook.mode = pr.z;
