@@ -48,6 +48,7 @@ extern "C" {
 #define CORDE_ERR_OOM (-3)         /* device allocation failed                         */
 #define CORDE_ERR_UNSUPPORTED (-4) /* rod longer than any kernel variant, or no GPU    */
 #define CORDE_ERR_NONFINITE (-5)   /* diagnostics found a non-finite state             */
+#define CORDE_ERR_BUSY (-6)        /* no consistent mailbox snapshot after many tries   */
 
 typedef struct corde_rods* rod_handle;
 
@@ -238,6 +239,17 @@ int rod_set_graph_mode(rod_handle h, int mode);
  *  rod_mailbox_log      copies min(count, capacity) (step, seq) pairs to out [capacity][2],
  *                       returns the count and clears the log (synchronous).
  *  rod_mailbox_disable  frees the mailbox (synchronous).
+ *  rod_mailbox_positions_enable  (enable != 0) every rod additionally publishes all its
+ *                       positions every `period` steps into mapped pinned host memory,
+ *                       into a ring of 4 snapshot slots, each under its own seqlock (the
+ *                       graphics/haptic thread pulls the whole rod while the kernel runs;
+ *                       a slot is rewritten only every 4th publication, so the host has
+ *                       3 periods to copy one); allocates 4 x n_elements x 16 B of
+ *                       mapped memory (synchronous); needs rod_mailbox_enable first.
+ *  rod_mailbox_positions  consistent copy of rod `rod`'s latest snapshot: out [N][4]
+ *                       floats (x, y, z, inverse mass), *step the global step it was
+ *                       taken after (-1: none yet).  Host-only and non-blocking for the
+ *                       device; a torn read is retried, CORDE_ERR_BUSY after 10000 tries.
  * With the mailbox enabled rod_step launches directly (no graph).  rod_steps_done: steps
  * taken by rod_step on this handle (the log's step index). */
 int rod_mailbox_enable(rod_handle h, int period, int log_capacity);
@@ -245,6 +257,8 @@ int rod_mailbox_write(rod_handle h, const float* drive);
 int rod_mailbox_read(rod_handle h, unsigned* out);
 int rod_mailbox_log(rod_handle h, int* out, int capacity, int* count);
 int rod_mailbox_disable(rod_handle h);
+int rod_mailbox_positions_enable(rod_handle h, int enable);
+int rod_mailbox_positions(rod_handle h, int rod, float* out, long long* step);
 int64_t rod_steps_done(rod_handle h);
 
 /* Number of kernel launches the last rod_step enqueued (kernel nodes of the graph when

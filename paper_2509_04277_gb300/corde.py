@@ -71,6 +71,8 @@ SIGNATURES = {
     "rod_mailbox_read": (ctypes.c_int, [_VP, _VP]),
     "rod_mailbox_log": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "rod_mailbox_disable": (ctypes.c_int, [_VP]),
+    "rod_mailbox_positions_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "rod_mailbox_positions": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP]),
     "rod_steps_done": (ctypes.c_int64, [_VP]),
     "rod_rollout": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP, _VP]),
     "rod_adjoint": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
@@ -257,6 +259,18 @@ def rod_mailbox_log(h, capacity=65536):
 
 def rod_mailbox_disable(h):
     _check(load().rod_mailbox_disable(h), "rod_mailbox_disable")
+
+
+def rod_mailbox_positions_enable(h, enable=True):
+    _check(load().rod_mailbox_positions_enable(h, 1 if enable else 0), "rod_mailbox_positions_enable")
+
+
+def rod_mailbox_positions(h, rod, out):
+    """Latest consistent position snapshot of rod `rod` into out ([N, 4] float32 host
+    array); returns the global step it was taken after (-1: none yet)."""
+    step = ctypes.c_longlong(0)
+    _check(load().rod_mailbox_positions(h, int(rod), _ptr(out), ctypes.addressof(step)), "rod_mailbox_positions")
+    return int(step.value)
 
 
 def rod_steps_done(h) -> int:

@@ -155,6 +155,7 @@ struct corde_rods {
   int mb_period = 0;
   void* mb_in_host = nullptr;   // 16-byte seqlock header + [n_rods][8] floats, mapped pinned
   void* mb_out_host = nullptr;  // [n_rods][2][8] words, mapped pinned
+  void* mb_pos_host = nullptr;  // [n_rods][4] seqlock words, then [n_elem] float4 positions, mapped pinned
   MailboxDev mb_dev = {};
   unsigned mb_host_seq = 0;
   long long steps_done = 0;
@@ -1284,6 +1285,8 @@ int rod_adjoint(rod_handle h, const float* dL_dpos_traj, float* dL_dK, float* dL
 static void mailbox_free(rod_handle h) {
   if (h->mb_in_host) cudaFreeHost(h->mb_in_host);
   if (h->mb_out_host) cudaFreeHost(h->mb_out_host);
+  if (h->mb_pos_host) cudaFreeHost(h->mb_pos_host);
+  h->mb_pos_host = nullptr;
   cudaFree(h->mb_dev.log);
   cudaFree(h->mb_dev.log_count);
   h->mb_in_host = h->mb_out_host = nullptr;
@@ -1320,6 +1323,59 @@ int rod_mailbox_enable(rod_handle h, int period, int log_capacity) {
   h->mb_host_seq = 0;
   invalidate_graph(h);
   return CORDE_OK;
+}
+
+int rod_mailbox_positions_enable(rod_handle h, int enable) {
+  if (int rc = check_handle(h)) return rc;
+  if (h->mb_period <= 0) return fail(CORDE_ERR_ARG, "rod_mailbox_positions_enable: mailbox not enabled");
+  CK(cudaDeviceSynchronize());
+  if (h->mb_pos_host) cudaFreeHost(h->mb_pos_host);
+  h->mb_pos_host = nullptr;
+  h->mb_dev.pos_seq = nullptr;
+  h->mb_dev.pos = nullptr;
+  if (!enable) return CORDE_OK;
+  const size_t hdr = (size_t)h->n_rods * 32 * sizeof(unsigned);
+  const size_t bytes = hdr + (size_t)kPosSlots * h->n_elem * sizeof(float4);
+  CK(cudaHostAlloc(&h->mb_pos_host, bytes, cudaHostAllocMapped | cudaHostAllocPortable));
+  std::memset(h->mb_pos_host, 0, bytes);
+  void* d = nullptr;
+  CK(cudaHostGetDevicePointer(&d, h->mb_pos_host, 0));
+  h->mb_dev.pos_seq = reinterpret_cast<unsigned*>(d);
+  h->mb_dev.pos = reinterpret_cast<float4*>(static_cast<char*>(d) + hdr);
+  h->mb_dev.n_elem = h->n_elem;
+  return CORDE_OK;
+}
+
+int rod_mailbox_positions(rod_handle h, int rod, float* out, long long* step) {
+  if (!h || !out || !step) return fail(CORDE_ERR_ARG, "rod_mailbox_positions: NULL argument");
+  if (!h->mb_pos_host) return fail(CORDE_ERR_ARG, "rod_mailbox_positions: position snapshots not enabled");
+  if (rod < 0 || rod >= h->n_rods) return fail(CORDE_ERR_ARG, "rod_mailbox_positions: bad rod");
+  const unsigned* hdr = static_cast<const unsigned*>(h->mb_pos_host) + 32 * (size_t)rod;
+  const size_t hbytes = (size_t)h->n_rods * 32 * sizeof(unsigned);
+  const size_t nf = 4 * (size_t)h->n_nodes[rod];
+  for (int attempt = 0; attempt < 10000; ++attempt) {
+    // newest complete publication p lives in slot p % kPosSlots under seq 2p + 2; the
+    // kernel rewrites that slot only kPosSlots publications later
+    const unsigned pubs = __atomic_load_n(&hdr[0], __ATOMIC_ACQUIRE);
+    if (pubs == 0u) {
+      *step = -1;
+      return CORDE_OK;
+    }
+    const unsigned p = pubs - 1u;
+    const unsigned* sh = hdr + 4 + 4 * (p % kPosSlots);
+    const unsigned s1 = __atomic_load_n(&sh[0], __ATOMIC_ACQUIRE);
+    if (s1 != 2u * p + 2u) continue;
+    const unsigned lo = __atomic_load_n(&sh[1], __ATOMIC_RELAXED), hi = __atomic_load_n(&sh[2], __ATOMIC_RELAXED);
+    const float* src = reinterpret_cast<const float*>(static_cast<const char*>(h->mb_pos_host) + hbytes) +
+                       4 * ((size_t)(p % kPosSlots) * h->n_elem + h->off[rod]);
+    std::memcpy(out, src, nf * sizeof(float));
+    __atomic_thread_fence(__ATOMIC_SEQ_CST);
+    if (__atomic_load_n(&sh[0], __ATOMIC_RELAXED) == s1) {
+      *step = (long long)(((unsigned long long)hi << 32) | lo);
+      return CORDE_OK;
+    }
+  }
+  return fail(CORDE_ERR_BUSY, "rod_mailbox_positions: no consistent snapshot after 10000 attempts");
 }
 
 int rod_mailbox_disable(rod_handle h) {

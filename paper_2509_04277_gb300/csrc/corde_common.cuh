@@ -7,6 +7,7 @@
 namespace corde {
 
 enum : int { F_INEXT = 1, F_CLAMP = 2, F_TUBE = 4, F_SELF = 8 };
+constexpr int kPosSlots = 4;  // ring of position snapshots per rod (mailbox)
 
 // Per-rod constants used by the step kernel (derived once at creation, FP64 -> FP32).
 struct RodDev {
@@ -30,7 +31,10 @@ static_assert(sizeof(RodDev) == 112, "RodDev layout");
 //  in_seq / in_drive: seqlock word and [n_rods][8] drive rows written by the host;
 //  out: [n_rods][2] records of 8 words (seq, step, x, y, z, vx, vy, vz): record 0 the
 //       base node, record 1 the tip node, each under its own seqlock;
-//  log: (global step, input seq) of every input a rod picked up, *log_count entries.
+//  log: (global step, input seq) of every input a rod picked up, *log_count entries;
+//  pos_seq / pos (optional): position snapshots published every period steps into a ring of
+//       kPosSlots slots per rod: pos_seq[rid][32] words = (publications, _, _, _) then per
+//       slot (seq, step low, step high, _); pos[slot][n_elem] = (x, y, z, inverse mass).
 struct MailboxDev {
   const unsigned* in_seq;
   const float* in_drive;
@@ -40,6 +44,9 @@ struct MailboxDev {
   int log_cap;
   int period;
   long long step0;  // global index of the launch's first step
+  unsigned* pos_seq;
+  float4* pos;
+  long long n_elem;  // elements of the handle (slot stride of pos)
 };
 
 // System-scope loads/stores/fences for memory shared with the host while a kernel runs.

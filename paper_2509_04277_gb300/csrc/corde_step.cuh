@@ -562,7 +562,7 @@ __device__ __forceinline__ void run_rod(const RodDev& R, const Halo& H, const in
   }
   const bool owns_base = e0 == 0;
   const bool owns_tip = e0 <= R.n - 1 && R.n - 1 < e0 + EPT;
-  unsigned mb_last = 0u, seq_base = 0u, seq_tip = 0u;
+  unsigned mb_last = 0u, seq_base = 0u, seq_tip = 0u, seq_pos = 0u;
   unsigned* rec_base = nullptr;
   unsigned* rec_tip = nullptr;
   if (mb.period > 0) {
@@ -570,6 +570,9 @@ __device__ __forceinline__ void run_rod(const RodDev& R, const Halo& H, const in
     rec_tip = rec_base + 8;
     if (owns_base) seq_base = ld_relaxed_sys(rec_base) & ~1u;
     if (owns_tip) seq_tip = ld_relaxed_sys(rec_tip) & ~1u;
+    // every thread keeps the publication count (it selects the ring slot); read before the
+    // first barrier, so before any publication of this launch
+    if (mb.pos != nullptr) seq_pos = ld_relaxed_sys(mb.pos_seq + 32 * (int64_t)rid);
   }
 
   int xc = 0;  // exchange counter selects the ping-pong buffer
@@ -588,6 +591,41 @@ __device__ __forceinline__ void run_rod(const RodDev& R, const Halo& H, const in
 #pragma unroll
         for (int e = 0; e < EPT; ++e)
           if (e0 + e == R.n - 1) mailbox_write(rec_tip, seq_tip, mb.step0 + step + 1, r[e], v[e]);
+      }
+      if (mb.pos != nullptr) {
+        // snapshot p of every position into ring slot p % kPosSlots, under the slot's
+        // seqlock (2p + 1 while the rod's threads write, barrier-ordered after the first
+        // thread's system-scope fence; 2p + 2 after), then the publication count p + 1
+        unsigned* hdr = mb.pos_seq + 32 * (int64_t)rid;
+        const int slot = (int)(seq_pos % kPosSlots);
+        unsigned* sh = hdr + 4 + 4 * slot;
+        if (owns_base) {
+          st_relaxed_sys(sh, 2u * seq_pos + 1u);
+          fence_acq_rel_sys();
+        }
+        H.sync();
+        // system-scope stores (volatile), each thread's made visible to the host before
+        // the barrier after which the first thread releases the slot
+        volatile float4* dst = mb.pos + slot * mb.n_elem + R.off;
+#pragma unroll
+        for (int e = 0; e < EPT; ++e)
+          if (e0 + e < R.n) {
+            dst[e0 + e].x = r[e].x;
+            dst[e0 + e].y = r[e].y;
+            dst[e0 + e].z = r[e].z;
+            dst[e0 + e].w = w[e];
+          }
+        fence_acq_rel_sys();
+        H.sync();
+        if (owns_base) {
+          fence_acq_rel_sys();
+          const long long s = mb.step0 + step + 1;
+          st_relaxed_sys(sh + 1, (unsigned)(s & 0xffffffffll));
+          st_relaxed_sys(sh + 2, (unsigned)(s >> 32));
+          st_release_sys(sh, 2u * seq_pos + 2u);
+          st_release_sys(hdr, seq_pos + 1u);
+        }
+        ++seq_pos;
       }
     }
   }

@@ -100,3 +100,44 @@ def test_mailbox_updates_a_running_kernel_and_replays_exactly(corde):
     corde.rod_mailbox_disable(a.handle)
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("n", [512, 3000])
+def test_mailbox_position_snapshots_are_whole_steps(corde, n):
+    """A free-falling straight rod (no clamp, gravity on: every node has the same height at
+    any step) published every 5 steps during a 20000-step launch: each snapshot the host
+    pulls while the kernel runs holds one step (all heights equal), steps increase, and
+    the last snapshot is the final state.  3000 nodes run on a cluster of blocks."""
+    import torch
+
+    rod = W.straight_rod(n, 1.0, seed=620, radius=1e-3, E_bend=50e9, E_stretch=50e9, G=20e9, density=6500.0,
+                         dt=1e-5, n_iters=4, inextensible=True, clamp=0, damping_alpha=0.0, gravity=(0.0, 0.0, -9.81))
+    a = corde.RodBatch([rod])
+    g_eff = 9.81 / a.derived()[0, 8]  # gravity acts on the inertial mass: g / mass_scale
+    dt, period = 1e-5, 5
+    corde.rod_mailbox_enable(a.handle, period, 64)
+    corde.rod_mailbox_positions_enable(a.handle)
+    out = np.zeros((n, 4), np.float32)
+    assert corde.rod_mailbox_positions(a.handle, 0, out) == -1
+    a.step(20000)  # asynchronous: the host pulls snapshots while it runs
+    steps, seen = [], 0
+    t0 = time.time()
+    while time.time() - t0 < 30.0:
+        s = corde.rod_mailbox_positions(a.handle, 0, out)
+        if s > 0 and (not steps or s != steps[-1]):
+            steps.append(s)
+            if s >= 50:
+                # heights of one step agree to rounding; one period moves them g dt^2 period s
+                spread = float(out[:, 2].max() - out[:, 2].min())
+                assert spread < 0.2 * g_eff * dt * dt * period * s, f"torn snapshot at step {s}"
+                seen += 1
+        if s == 20000:
+            break
+    torch.cuda.synchronize()
+    assert steps == sorted(steps) and all(k % 5 == 0 for k in steps)
+    assert seen >= 3
+    s = corde.rod_mailbox_positions(a.handle, 0, out)
+    assert s == 20000
+    np.testing.assert_array_equal(out, a.state_numpy()["pos4"])
+    corde.rod_mailbox_disable(a.handle)
+    a.close()
