@@ -325,7 +325,7 @@ struct SelfHook {
       const float3 ut = u - dot3(u, nrm) * nrm;
       const float ut2 = dot3(ut, ut);
       const float cut = ut2 > 0.f ? fminf(1.f, mu * dun * rsqrtf(ut2)) : 0.f;
-      const float3 J = (phi * __frcp_rn(ri.w + rj.w)) * (dun * nrm - cut * ut);
+      const float3 J = (phi * __fdividef(1.f, ri.w + rj.w)) * (dun * nrm - cut * ut);  // approximate reciprocal: ~2 ulp
       P4[p] = make_float4(J.x, J.y, J.z, phi);
       const int ka = atomicAdd(&nact()[ij.x], 1);
       if (ka < kSelfMaxCand) list()[ka * L::NN + ij.x] = (unsigned short)p;
@@ -358,7 +358,7 @@ struct SelfHook {
         else acc += f3(s4);
         wphi += s4.w;
       }
-      if (wphi > 0.f) v[e] += (w[e] * __frcp_rn(wphi)) * acc;
+      if (wphi > 0.f) v[e] += __fdividef(w[e], wphi) * acc;
     }
   }
 };
