@@ -298,10 +298,14 @@ def run_batched(args, torch, corde, W, rank, world):
     mine = [rods[i] for i in sharding.shard([r.n_nodes for r in rods], rank, world)] if world > 1 else rods
     b = corde.RodBatch(mine)
     n_elem = b.n_elem
-    S = args.batched_steps_per_launch
-    n_launch = max(1, args.batched_steps // S)
+    S = args.batched_steps_per_launch or 100
     if not args.no_autotune:
         b.autotune(S)
+    steps_autotuned = False
+    if args.batched_steps_per_launch is None and not args.no_autotune:
+        S = b.autotune_steps((10, 25, 50, 100, 200), 400)
+        steps_autotuned = True
+    n_launch = max(1, args.batched_steps // S)
     plan = b.plan()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     b.step(S)
@@ -328,6 +332,7 @@ def run_batched(args, torch, corde, W, rank, world):
         "n_rods": len(mine),
         "n_elements": n_elem,
         "steps_per_launch": S,
+        "steps_per_launch_autotuned": steps_autotuned,
         "launches": n_launch,
         "gpu_launches": launches,
         "seconds": total_s,
@@ -411,8 +416,28 @@ def run_pair(args, torch, corde, W):
             ms = e0.elapsed_time(e1)
             out[f"v{mode}_{S}ts"] = round(ms * 1e3 / (n_launch * S), 4)
             b.close()
+    # the oracle's pair step on one host core, a bounded sample per mode
+    import oracle
+
+    cpu = {}
+    for mode in (0, 1, 2):
+        cat, gw = W.catheter_guidewire(512, seed=3, beta0=-100.25)
+        so, si = oracle.state_of(cat), oracle.state_of(gw)
+        n, t0 = 0, time.perf_counter()
+        while time.perf_counter() - t0 < 1.0 or n == 0:
+            so, si = oracle.step_pair(cat, so, gw, si, mode, -100.25, 10)
+            n += 10
+        cpu[f"v{mode}"] = round((time.perf_counter() - t0) * 1e6 / n, 2)
+    flops_step = 2 * 512 * flops_per_el_step(10)  # the two rods' steps (binding not counted)
+    peak = NUM_SMS * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
+    frac = {k: round(flops_step / (v * 1e-6) / 1e12 / peak, 7) for k, v in out.items()}
     return {"unit": "us/step", "workload": "2 x 512 inextensible rods (catheter r=1 mm E=2 GPa, guidewire "
-                                           "r=0.45 mm E=60 GPa), one thread block per pair", "us_per_step": out}
+                                           "r=0.45 mm E=60 GPa), one thread block per pair", "us_per_step": out,
+            "roofline_alu": {"flops_per_step": flops_step, "peak_tflops": round(peak, 2),
+                             "frac_of_gpu": frac, "note": "one pair = one thread block on one SM: at most 1/152 "
+                                                          "of the GPU; x152 gives the fraction of that SM"},
+            "cpu_oracle_us_per_step": cpu,
+            "speedup_vs_oracle_1core_10ts": {f"v{m}": round(cpu[f"v{m}"] / out[f"v{m}_10ts"], 1) for m in (0, 1, 2)}}
 
 
 def run_long_rods(args, torch, corde, W):
@@ -702,7 +727,11 @@ def main_ours(args):
             "checks": {"max_len_err": single["diag"][0], "max_qnorm_err": single["diag"][1],
                        "nonfinite": single["diag"][2]},
             "paper_context": {"us_per_step_512_single_block_10tskl": 32.0, "hardware": "GeForce GTX 560 (Fermi)",
-                              "note": "host-visible time incl. launch and D2H; compare with e2e"},
+                              "note": "host-visible time incl. launch and D2H; compare with e2e",
+                              "speedups_vs_cpu": {"extensible_10tskl": 40.0, "inextensible": 15.11,
+                                                  "catheter_guidewire_2x512": 13.5},
+                              "haptic_rate_khz": [0.5, 1.0],
+                              "ours_vs_oracle_1core": round(cpu["value"] / value, 1) if cpu else None},
         }
         if batched is not None:
             bw = peaks.get("hbm_gbs", 6800.0)
@@ -712,7 +741,9 @@ def main_ours(args):
             out["batched"] = {
                 "element_steps_per_s": batched["element_steps_per_s"],
                 "n_rods": batched["n_rods"], "n_elements": batched["n_elements"],
-                "steps_per_launch": batched["steps_per_launch"], "launches": batched["launches"],
+                "steps_per_launch": batched["steps_per_launch"],
+                "steps_per_launch_autotuned": batched["steps_per_launch_autotuned"],
+                "launches": batched["launches"],
                 "gpu_launches": batched["gpu_launches"], "ms_per_launch": round(batched["ms_per_launch"], 4),
                 "plan": batched["plan"], "max_len_err": batched["max_len_err"],
                 "roofline_alu": {"achieved": batched["flops_per_launch"] / sec / 1e12, "peak": round(fp32_peak, 2),
@@ -789,7 +820,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--batched-steps", type=int, default=1000)
-    ap.add_argument("--batched-steps-per-launch", type=int, default=100)
+    ap.add_argument("--batched-steps-per-launch", type=int, default=None,
+                    help="steps per launch of the batch (default: autotuned among 10..200)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--skip-cpu-batched", action="store_true")

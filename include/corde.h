@@ -211,6 +211,15 @@ int rod_diagnostics(rod_handle h, double* out);
 int rod_set_plan(rod_handle h, int ept, int nt);
 int rod_set_plan_cluster(rod_handle h, int ept, int nt, int cluster);
 int rod_autotune(rod_handle h, int n_steps, void* stream);
+
+/* Pick the number of time steps per launch, among n_candidates values (each >= 1), with
+ * the shortest time per step for this handle's plan: a launch spreads its load, store and
+ * launch latency over its steps, while the host's next input waits for the launch.  Each
+ * candidate runs ceil(min_steps / candidate) launches from the same state (restored
+ * afterwards, with the step count); two passes over the candidates, the second counts.
+ * *best receives the winner.  Not with a mailbox.  Synchronous. */
+int rod_autotune_steps(rod_handle h, const int* candidates, int n_candidates, int min_steps, int* best,
+                       void* stream);
 int rod_get_plan(rod_handle h, int* plan);
 
 /* When one rod_step needs several kernel launches (rods of several length bins, bound

@@ -63,6 +63,7 @@ SIGNATURES = {
     "rod_set_plan": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
     "rod_set_plan_cluster": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "rod_autotune": (ctypes.c_int, [_VP, ctypes.c_int, _VP]),
+    "rod_autotune_steps": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, _VP, _VP]),
     "rod_get_plan": (ctypes.c_int, [_VP, _VP]),
     "rod_last_launch_count": (ctypes.c_int, [_VP]),
     "rod_set_graph_mode": (ctypes.c_int, [_VP, ctypes.c_int]),
@@ -223,6 +224,15 @@ def rod_set_plan_cluster(h, ept, nt, cluster):
 
 def rod_autotune(h, n_steps, stream=None):
     _check(load().rod_autotune(h, int(n_steps), _stream(stream)), "rod_autotune")
+
+
+def rod_autotune_steps(h, candidates, min_steps, stream=None) -> int:
+    """Steps per launch, among candidates, with the shortest time per step."""
+    c = np.ascontiguousarray(candidates, dtype=np.int32)
+    best = np.zeros(1, dtype=np.int32)
+    _check(load().rod_autotune_steps(h, c.ctypes.data, int(c.size), int(min_steps), best.ctypes.data,
+                                     _stream(stream)), "rod_autotune_steps")
+    return int(best[0])
 
 
 def rod_get_plan(h, out):
@@ -453,6 +463,9 @@ class RodBatch:
 
     def autotune(self, n_steps, stream=None):
         rod_autotune(self.handle, n_steps, stream)
+
+    def autotune_steps(self, candidates, min_steps, stream=None) -> int:
+        return rod_autotune_steps(self.handle, candidates, min_steps, stream)
 
     def set_graph_mode(self, mode):
         rod_set_graph_mode(self.handle, mode)

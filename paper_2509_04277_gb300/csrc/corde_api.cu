@@ -888,6 +888,75 @@ int rod_set_plan_cluster(rod_handle h, int ept, int nt, int cluster) {
   return build_bins(h);
 }
 
+int rod_autotune_steps(rod_handle h, const int* candidates, int n_candidates, int min_steps, int* best,
+                       void* stream) {
+  if (int rc = check_handle(h)) return rc;
+  if (!candidates || n_candidates < 1 || !best || min_steps < 1)
+    return fail(CORDE_ERR_ARG, "rod_autotune_steps: need candidates, min_steps >= 1 and best");
+  for (int k = 0; k < n_candidates; ++k)
+    if (candidates[k] < 1) return fail(CORDE_ERR_ARG, "rod_autotune_steps: candidates must be >= 1");
+  if (h->mb_period > 0) return fail(CORDE_ERR_UNSUPPORTED, "rod_autotune_steps: not with a mailbox enabled");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t b = (size_t)h->n_elem * sizeof(float4);
+  float4 *sx = nullptr, *sv = nullptr, *sq = nullptr, *so = nullptr;
+  CK(cudaMalloc(&sx, b));
+  CK(cudaMalloc(&sv, b));
+  CK(cudaMalloc(&sq, b));
+  CK(cudaMalloc(&so, b));
+  CK(cudaMemcpyAsync(sx, h->d_x, b, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(sv, h->d_v, b, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(sq, h->d_q, b, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(so, h->d_o, b, cudaMemcpyDeviceToDevice, s));
+  auto restore = [&]() {
+    cudaMemcpyAsync(h->d_x, sx, b, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(h->d_v, sv, b, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(h->d_q, sq, b, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(h->d_o, so, b, cudaMemcpyDeviceToDevice, s);
+  };
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const long long steps0 = h->steps_done;
+  int rc = CORDE_OK;
+  float best_us = 1e30f;
+  int best_n = candidates[0];
+  // two passes, the second one counts (clock ramp-up, graph capture per candidate)
+  for (int pass = 0; pass < 2 && rc == CORDE_OK; ++pass) {
+    best_us = 1e30f;
+    for (int k = 0; k < n_candidates && rc == CORDE_OK; ++k) {
+      const int S = candidates[k];
+      const int launches = (min_steps + S - 1) / S;
+      restore();
+      if ((rc = step_impl(h, S, nullptr, nullptr, s)) != CORDE_OK) break;  // warm-up (and graph capture)
+      restore();
+      cudaEventRecord(e0, s);
+      for (int l = 0; l < launches && rc == CORDE_OK; ++l) rc = step_impl(h, S, nullptr, nullptr, s);
+      cudaEventRecord(e1, s);
+      if (rc != CORDE_OK) break;
+      if (cudaEventSynchronize(e1) != cudaSuccess) {
+        rc = fail(CORDE_ERR_CUDA, "rod_autotune_steps: timing");
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      const float us_per_step = ms * 1e3f / (float)(launches * S);
+      if (us_per_step < best_us) {
+        best_us = us_per_step;
+        best_n = S;
+      }
+    }
+  }
+  restore();
+  cudaStreamSynchronize(s);
+  h->steps_done = steps0;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(sx); cudaFree(sv); cudaFree(sq); cudaFree(so);
+  if (rc != CORDE_OK) return rc;
+  *best = best_n;
+  return CORDE_OK;
+}
+
 int rod_get_plan(rod_handle h, int* plan) {
   if (!h || !plan) return fail(CORDE_ERR_ARG, "NULL argument");
   for (int r = 0; r < h->n_rods; ++r) {

@@ -267,3 +267,20 @@ def test_graph_path_matches_direct_launches(corde):
         np.testing.assert_array_equal(sa[k], sb[k])
     a.close()
     b.close()
+
+
+def test_autotune_steps_leaves_the_state_and_picks_a_candidate(corde):
+    rods = W.batched_rods(64, seed=45)
+    b = corde.RodBatch(rods)
+    b.step(7)
+    before = b.state_numpy()
+    done = corde.rod_steps_done(b.handle)
+    best = b.autotune_steps((5, 20, 50), 100)
+    assert best in (5, 20, 50)
+    assert corde.rod_steps_done(b.handle) == done
+    after = b.state_numpy()
+    for k in before:
+        np.testing.assert_array_equal(before[k], after[k])
+    with pytest.raises(corde.CordeError):
+        b.autotune_steps((0, 10), 100)
+    b.close()
