@@ -381,7 +381,15 @@ def run_adjoint(args, torch, corde, W, n_rods=1):
     finite = bool(all(torch.isfinite(v).all().item() for v in grads.values()))
     b.close()
     el_steps = sum(r.n_nodes for r in rods) * n_steps
+    # algorithmic DRAM bytes of the reverse pass: the loss gradient dL/dpos it reads
+    # (16 B per element-step) and the checkpoints it restarts from (64 B per element per
+    # checkpoint); the per-segment recomputed states stay L2-resident
+    adj_bytes = el_steps * 16.0 + sum(r.n_nodes for r in rods) * 64.0 * (n_steps // ckpt)
+    hbm = _peaks()[0].get("hbm_gbs", 6800.0)
     return {"n_rods": n_rods, "n_nodes": 256, "n_steps": n_steps, "ckpt_every": ckpt,
+            "roofline_hbm": {"bytes": adj_bytes, "achieved_gbs": round(adj_bytes / (adj_ms * 1e-3) / 1e9, 2),
+                             "peak_gbs": hbm, "frac": round(adj_bytes / (adj_ms * 1e-3) / 1e9 / hbm, 5),
+                             "note": "latency-bound like the forward: one block per rod"},
             "fwd_ms": round(fwd_ms, 4), "fwd_launches": fwd_launches, "rollout_recorded_ms": round(roll_ms, 4),
             "adjoint_ms": round(adj_ms, 4), "adjoint_over_fwd": round(adj_ms / fwd_ms, 3),
             "adjoint_over_recorded_rollout": round(adj_ms / roll_ms, 3),
