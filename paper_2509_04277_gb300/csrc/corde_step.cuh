@@ -412,8 +412,8 @@ __device__ __forceinline__ void step_body(const RodDev& R, const Halo& H, float3
       ++xc;
       hb[t] = make_float4(v[0].x, v[0].y, v[0].z, 0.f);
       hb[NT + t] = make_float4(v[EPT - 1].x, v[EPT - 1].y, v[EPT - 1].z, 0.f);
-      H.sync();
-      // odd segments inside the thread
+      // odd segments inside the thread: they move elements 1 .. EPT - 2 only, which the
+      // exchange and the boundary segments do not read, so they run while the barrier waits
 #pragma unroll
       for (int k = 0; k + 1 < EPT / 2; ++k) {
         const int a = 2 * k + 1, b = 2 * k + 2;
@@ -421,6 +421,7 @@ __device__ __forceinline__ void step_body(const RodDev& R, const Halo& H, float3
         v[a] -= w[a] * g;
         v[b] += w[b] * g;
       }
+      H.sync();
       // odd segments across the two thread boundaries, in one packed evaluation
       {
         const float3 vn = has_next ? f3(H.next(hb, 0)) : zero3();
