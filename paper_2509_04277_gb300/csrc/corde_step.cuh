@@ -250,6 +250,44 @@ __device__ __forceinline__ void step_body(const RodDev& R, const Halo& H, float3
   hb[t] = make_float4(r[0].x, r[0].y, r[0].z, w[0]);
   hb[NT + t] = q[0];
   hb[2 * NT + t] = make_float4(r[EPT - 1].x, r[EPT - 1].y, r[EPT - 1].z, w[EPT - 1]);
+
+  // ---- elastic forces and torques.  Joint j couples frames j and j + 1, segment j nodes
+  // j and j + 1 (with frame j); all but the thread's last joint and segment are local, and
+  // they run while the exchange barrier waits.
+  float3 F[EPT], tau[EPT];
+#pragma unroll
+  for (int e = 0; e < EPT; ++e) {
+    F[e] = zero3();
+    tau[e] = zero3();
+  }
+  float3 F_carry = zero3(), tau_carry = zero3();
+  auto joint_and_segment = [&](int e, float4 qb, float3 rb) {
+    const int j = e0 + e;
+    if (j <= n - 3) {
+      float3 ta, tb;
+      joint_torques(q[e], qb, par_u[e * NT + t], par_k[e * NT + t], R.two_over_l, ta, tb);
+      tau[e] += ta;
+      if (e + 1 < EPT) {
+        tau[(e + 1) % EPT] += tb;
+      } else {
+        tau_carry = tb;
+      }
+    }
+    if (j <= n - 2) {
+      float3 fa, fb, tq;
+      segment_forces(r[e], rb, q[e], R, !inext, fa, fb, tq);
+      F[e] += fa;
+      tau[e] += tq;
+      if (e + 1 < EPT) {
+        F[(e + 1) % EPT] += fb;
+      } else {
+        F_carry = fb;
+      }
+    }
+  };
+#pragma unroll
+  for (int e = 0; e + 1 < EPT; ++e) joint_and_segment(e, q[e + 1], r[e + 1]);
+
   H.sync();
   float3 r_next = zero3(), r_prev = zero3();
   float w_next = 0.f, w_prev = 0.f;
@@ -273,42 +311,8 @@ __device__ __forceinline__ void step_body(const RodDev& R, const Halo& H, float3
     nb->w_prev = w_prev;
     nb->q_next = q_next;
   }
-
-  // ---- elastic forces and torques
-  float3 F[EPT], tau[EPT];
-#pragma unroll
-  for (int e = 0; e < EPT; ++e) {
-    F[e] = zero3();
-    tau[e] = zero3();
-  }
-  float3 F_carry = zero3(), tau_carry = zero3();
-#pragma unroll
-  for (int e = 0; e < EPT; ++e) {
-    const int j = e0 + e;
-    const float4 qb = (e + 1 < EPT) ? q[(e + 1) % EPT] : q_next;
-    const float3 rb = (e + 1 < EPT) ? r[(e + 1) % EPT] : r_next;
-    if (j <= n - 3) {  // joint between frames j and j+1
-      float3 ta, tb;
-      joint_torques(q[e], qb, par_u[e * NT + t], par_k[e * NT + t], R.two_over_l, ta, tb);
-      tau[e] += ta;
-      if (e + 1 < EPT) {
-        tau[(e + 1) % EPT] += tb;
-      } else {
-        tau_carry = tb;
-      }
-    }
-    if (j <= n - 2) {  // segment between nodes j and j+1, frame j
-      float3 fa, fb, tq;
-      segment_forces(r[e], rb, q[e], R, !inext, fa, fb, tq);
-      F[e] += fa;
-      tau[e] += tq;
-      if (e + 1 < EPT) {
-        F[(e + 1) % EPT] += fb;
-      } else {
-        F_carry = fb;
-      }
-    }
-  }
+  // the thread's last joint and segment reach into the next thread's first element
+  joint_and_segment(EPT - 1, q_next, r_next);
   // ---- exchange 2: carries to the right neighbour's first element
   hb = halo + (xc & 1) * kHaloSlots * NT;
   ++xc;
