@@ -74,6 +74,8 @@ SIGNATURES = {
     "rod_mailbox_disable": (ctypes.c_int, [_VP]),
     "rod_mailbox_positions_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
     "rod_mailbox_positions": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP]),
+    "rod_mailbox_lockstep": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
+    "rod_mailbox_status": (ctypes.c_int, [_VP, _VP]),
     "rod_steps_done": (ctypes.c_int64, [_VP]),
     "rod_rollout": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP, _VP]),
     "rod_adjoint": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
@@ -281,6 +283,16 @@ def rod_mailbox_positions(h, rod, out):
     step = ctypes.c_longlong(0)
     _check(load().rod_mailbox_positions(h, int(rod), _ptr(out), ctypes.addressof(step)), "rod_mailbox_positions")
     return int(step.value)
+
+
+def rod_mailbox_lockstep(h, enable=True, timeout_us=1_000_000):
+    _check(load().rod_mailbox_lockstep(h, 1 if enable else 0, int(timeout_us)), "rod_mailbox_lockstep")
+
+
+def rod_mailbox_status(h) -> int:
+    out = np.zeros(1, dtype=np.uint32)
+    _check(load().rod_mailbox_status(h, out.ctypes.data), "rod_mailbox_status")
+    return int(out[0])
 
 
 def rod_steps_done(h) -> int:

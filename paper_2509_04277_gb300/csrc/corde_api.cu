@@ -1372,7 +1372,7 @@ int rod_mailbox_enable(rod_handle h, int period, int log_capacity) {
   CK(cudaDeviceSynchronize());
   mailbox_free(h);
   const size_t in_bytes = 16 + (size_t)h->n_rods * 8 * sizeof(float);
-  const size_t out_bytes = (size_t)h->n_rods * 16 * sizeof(unsigned);
+  const size_t out_bytes = (size_t)h->n_rods * 16 * sizeof(unsigned) + 16;  // records, then the status word
   CK(cudaHostAlloc(&h->mb_in_host, in_bytes, cudaHostAllocMapped | cudaHostAllocPortable));
   CK(cudaHostAlloc(&h->mb_out_host, out_bytes, cudaHostAllocMapped | cudaHostAllocPortable));
   std::memset(h->mb_in_host, 0, in_bytes);
@@ -1383,6 +1383,7 @@ int rod_mailbox_enable(rod_handle h, int period, int log_capacity) {
   h->mb_dev.in_seq = reinterpret_cast<const unsigned*>(din);
   h->mb_dev.in_drive = reinterpret_cast<const float*>(static_cast<char*>(din) + 16);
   h->mb_dev.out = reinterpret_cast<unsigned*>(dout);
+  h->mb_dev.status = reinterpret_cast<unsigned*>(dout) + (size_t)h->n_rods * 16;
   CK(cudaMalloc(&h->mb_dev.log, (size_t)log_capacity * sizeof(int2)));
   CK(cudaMalloc(&h->mb_dev.log_count, sizeof(int)));
   CK(cudaMemset(h->mb_dev.log_count, 0, sizeof(int)));
@@ -1391,6 +1392,29 @@ int rod_mailbox_enable(rod_handle h, int period, int log_capacity) {
   h->mb_period = period;
   h->mb_host_seq = 0;
   invalidate_graph(h);
+  return CORDE_OK;
+}
+
+int rod_mailbox_lockstep(rod_handle h, int enable, int timeout_us) {
+  if (int rc = check_handle(h)) return rc;
+  if (h->mb_period <= 0) return fail(CORDE_ERR_ARG, "rod_mailbox_lockstep: mailbox not enabled");
+  if (enable && timeout_us < 1) return fail(CORDE_ERR_ARG, "rod_mailbox_lockstep: timeout_us >= 1");
+  if (enable)
+    for (int r = 0; r < h->n_rods; ++r)
+      if (h->plan_cluster[r] > 0)
+        return fail(CORDE_ERR_UNSUPPORTED, "rod_mailbox_lockstep: single-block rods only (rod " + std::to_string(r) +
+                                               " runs on a cluster)");
+  CK(cudaDeviceSynchronize());
+  h->mb_dev.lockstep = enable ? 1 : 0;
+  h->mb_dev.wait_ns = enable ? (unsigned long long)timeout_us * 1000ull : 0ull;
+  return CORDE_OK;
+}
+
+int rod_mailbox_status(rod_handle h, unsigned* status) {
+  if (!h || !status) return fail(CORDE_ERR_ARG, "rod_mailbox_status: NULL argument");
+  if (h->mb_period <= 0) return fail(CORDE_ERR_ARG, "rod_mailbox_status: mailbox not enabled");
+  unsigned* st = static_cast<unsigned*>(h->mb_out_host) + (size_t)h->n_rods * 16;
+  *status = __atomic_exchange_n(st, 0u, __ATOMIC_ACQ_REL);
   return CORDE_OK;
 }
 

@@ -47,6 +47,11 @@ struct MailboxDev {
   unsigned* pos_seq;
   float4* pos;
   long long n_elem;  // elements of the handle (slot stride of pos)
+  // lock-step (single-block rods): at every poll point wait for a new input, at most
+  // wait_ns of GPU time; a wait that runs out sets bit 0 of *status and ends the launch
+  int lockstep;
+  unsigned* status;
+  unsigned long long wait_ns;
 };
 
 // System-scope loads/stores/fences for memory shared with the host while a kernel runs.
@@ -72,6 +77,11 @@ __device__ __forceinline__ void st_release_sys(unsigned* p, unsigned v) {
   asm volatile("st.release.sys.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 __device__ __forceinline__ void fence_acq_rel_sys() { asm volatile("fence.acq_rel.sys;" ::: "memory"); }
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 // ---------------------------------------------------------------- float3 helpers
 

@@ -44,6 +44,7 @@ __device__ __forceinline__ void block_sync() {
 // in lockstep).  Exchange buffers hold `slots` x NT float4, slot-major.
 template <int NT, int SYNC_NT>
 struct BlockHalo {
+  static constexpr bool kCluster = false;
   int t;
   __device__ __forceinline__ int tg() const { return t; }
   __device__ __forceinline__ bool has_next() const { return t + 1 < NT; }
@@ -51,6 +52,14 @@ struct BlockHalo {
   __device__ __forceinline__ float4 next(const float4* hb, int slot) const { return hb[slot * NT + t + 1]; }
   __device__ __forceinline__ float4 prev(const float4* hb, int slot) const { return hb[slot * NT + t - 1]; }
   __device__ __forceinline__ void sync() const { block_sync<SYNC_NT>(); }
+  // block-wide OR of x (a barrier)
+  __device__ __forceinline__ int any(int x) const {
+    if constexpr (SYNC_NT == 32) {
+      return __any_sync(0xffffffffu, x);
+    } else {
+      return __syncthreads_or(x);
+    }
+  }
 };
 
 // A rod spread over the C thread blocks of a cluster (block c holds threads c NT ...
@@ -59,6 +68,7 @@ struct BlockHalo {
 // memory; the barrier is the cluster barrier (release / acquire).
 template <int NT>
 struct ClusterHalo {
+  static constexpr bool kCluster = true;
   int t, c, C;
   __device__ __forceinline__ int tg() const { return c * NT + t; }
   __device__ __forceinline__ bool has_next() const { return t + 1 < NT || c + 1 < C; }
@@ -527,6 +537,24 @@ __device__ __forceinline__ void mailbox_log(const MailboxDev& mb, long long step
   if (k < mb.log_cap) mb.log[k] = make_int2((int)step, (int)seq);
 }
 
+// Lock-step: wait for a new input, bounded by mb.wait_ns of GPU time (and an iteration
+// cap), backing off between reads.  Returns false, with bit 0 of the status set, when the
+// wait runs out.
+__device__ __forceinline__ bool mailbox_wait(const MailboxDev& mb, int rid, unsigned& last, float3& vd, float3& wd,
+                                             long long step) {
+  const unsigned long long t0 = global_ns();
+  for (int k = 0; k < (1 << 26); ++k) {
+    if (mailbox_poll(mb, rid, last, vd, wd)) {
+      mailbox_log(mb, step, last);
+      return true;
+    }
+    if (global_ns() - t0 > mb.wait_ns) break;
+    __nanosleep(256);
+  }
+  st_release_sys(mb.status, 1u);
+  return false;
+}
+
 // Seqlock write of one feedback record (seq, step, position, velocity).
 __device__ __forceinline__ void mailbox_write(unsigned* rec, unsigned& seq, long long step, float3 r, float3 v) {
   st_relaxed_sys(rec, seq + 1u);
@@ -582,8 +610,21 @@ __device__ __forceinline__ void run_rod(const RodDev& R, const Halo& H, const in
 
   int xc = 0;  // exchange counter selects the ping-pong buffer
   for (int step = 0; step < n_steps; ++step) {
-    if (mb.period > 0 && owns_base && step % mb.period == 0)
-      if (mailbox_poll(mb, rid, mb_last, v_drive, w_drive)) mailbox_log(mb, mb.step0 + step, mb_last);
+    if (mb.period > 0 && step % mb.period == 0) {
+      bool stop = false;
+      if constexpr (!Halo::kCluster) {
+        if (mb.lockstep) {
+          // lock-step: the base's thread waits (bounded) for the next input; the block
+          // waits at the OR below and leaves together if the wait ran out
+          int lost = 0;
+          if (owns_base) lost = !mailbox_wait(mb, rid, mb_last, v_drive, w_drive, mb.step0 + step);
+          stop = H.any(lost) != 0;
+        }
+      }
+      if (stop) break;
+      if (!mb.lockstep && owns_base && mailbox_poll(mb, rid, mb_last, v_drive, w_drive))
+        mailbox_log(mb, mb.step0 + step, mb_last);
+    }
     step_body<EPT, NT, false>(R, H, r, v, q, om, w, par_u, par_k, halo, xc, v_drive, w_drive, nullptr, nullptr);
     if (traj != nullptr) {
 #pragma unroll
@@ -609,8 +650,8 @@ __device__ __forceinline__ void run_rod(const RodDev& R, const Halo& H, const in
           fence_acq_rel_sys();
         }
         H.sync();
-        // system-scope stores (volatile), each thread's made visible to the host before
-        // the barrier after which the first thread releases the slot
+        // system-scope stores (volatile), ordered before the first thread's release by the
+        // barrier (release/acquire among the rod's threads) and its system-scope fence
         volatile float4* dst = mb.pos + slot * mb.n_elem + R.off;
 #pragma unroll
         for (int e = 0; e < EPT; ++e)
@@ -620,7 +661,6 @@ __device__ __forceinline__ void run_rod(const RodDev& R, const Halo& H, const in
             dst[e0 + e].z = r[e].z;
             dst[e0 + e].w = w[e];
           }
-        fence_acq_rel_sys();
         H.sync();
         if (owns_base) {
           fence_acq_rel_sys();

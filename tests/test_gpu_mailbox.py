@@ -141,3 +141,76 @@ def test_mailbox_position_snapshots_are_whole_steps(corde, n):
     np.testing.assert_array_equal(out, a.state_numpy()["pos4"])
     corde.rod_mailbox_disable(a.handle)
     a.close()
+
+
+def _wait_snapshot(corde, h, out, step, limit_s=10.0):
+    t0 = time.time()
+    while time.time() - t0 < limit_s:
+        if corde.rod_mailbox_positions(h, 0, out) >= step:
+            return True
+    return False
+
+
+def test_lockstep_each_input_drives_the_next_period_exactly(corde):
+    """Lock-step: one 200-step launch; the host writes drive k, waits for the snapshot after
+    steps 10 k .. 10 k + 9 and writes drive k + 1.  Every snapshot equals, bit for bit, the
+    positions of the same drives replayed as ordinary 10-step launches."""
+    import torch
+
+    rod = W.guidewire(512, seed=630)
+    a, b = corde.RodBatch([rod]), corde.RodBatch([rod])
+    corde.rod_mailbox_enable(a.handle, 10, 64)
+    corde.rod_mailbox_positions_enable(a.handle)
+    corde.rod_mailbox_lockstep(a.handle, True, 2_000_000)
+    drives = W.sinusoid_drive(631, 20, 10 * rod.dt).astype(np.float32)
+    base = corde.rod_steps_done(a.handle)
+    snaps = []
+    out = np.zeros((512, 4), np.float32)
+    a.step(200)  # asynchronous; waits for each input
+    for k in range(20):
+        corde.rod_mailbox_write(a.handle, drives[k].reshape(1, 8))
+        assert _wait_snapshot(corde, a.handle, out, base + 10 * (k + 1)), f"no snapshot for tick {k}"
+        snaps.append(out.copy())
+    torch.cuda.synchronize()
+    assert corde.rod_mailbox_status(a.handle) == 0
+    for k in range(20):
+        b.set_input(drives[k].reshape(1, 8))
+        b.step(10)
+        np.testing.assert_array_equal(snaps[k], b.state_numpy()["pos4"])
+    sa, sb = a.state_numpy(), b.state_numpy()
+    for key in sa:
+        np.testing.assert_array_equal(sa[key], sb[key])
+    corde.rod_mailbox_disable(a.handle)
+    a.close()
+    b.close()
+
+
+def test_lockstep_wait_runs_out_cleanly(corde):
+    """No input ever arrives: the launch's first wait runs out after 20 ms of GPU time, the
+    launch ends without stepping, the status reports it once, and the device stays usable."""
+    import torch
+
+    rod = W.guidewire(256, seed=640)
+    a = corde.RodBatch([rod])
+    before = a.state_numpy()
+    corde.rod_mailbox_enable(a.handle, 10, 64)
+    corde.rod_mailbox_lockstep(a.handle, True, 20_000)
+    t0 = time.time()
+    a.step(100)
+    torch.cuda.synchronize()
+    assert time.time() - t0 < 5.0
+    assert corde.rod_mailbox_status(a.handle) & 1
+    assert corde.rod_mailbox_status(a.handle) == 0
+    after = a.state_numpy()
+    for key in before:
+        np.testing.assert_array_equal(before[key], after[key])
+    corde.rod_mailbox_disable(a.handle)
+    a.step(10)  # the context is fine
+    torch.cuda.synchronize()
+    long_rod = corde.RodBatch([W.guidewire(3000, seed=641)])
+    corde.rod_mailbox_enable(long_rod.handle, 10, 64)
+    with pytest.raises(corde.CordeError):
+        corde.rod_mailbox_lockstep(long_rod.handle, True, 1000)
+    corde.rod_mailbox_disable(long_rod.handle)
+    long_rod.close()
+    a.close()
