@@ -490,13 +490,14 @@ bool params_valid(const RodParams& p, std::string& why) {
 
 // Launches every bin and pair bin of one rod_step.  With branches, bin k goes to
 // branches[k] (for the forked graph capture); otherwise all go to s in order.
-int launch_all(rod_handle h, int n_steps, const float4* d, cudaStream_t s, const std::vector<cudaStream_t>* branches) {
+int launch_all(rod_handle h, int n_steps, const float4* d, cudaStream_t s, const std::vector<cudaStream_t>* branches,
+               const MailboxDev* mb = nullptr) {
   int launches = 0;
   size_t k = 0;
   for (size_t b = 0; b < h->bins.size(); ++b, ++k) {
     cudaStream_t sk = branches ? (*branches)[k] : s;
     std::vector<Bin> one{h->bins[b]};
-    if (int rc = launch_bins(h, one, n_steps, d, sk)) return rc;
+    if (int rc = launch_bins(h, one, n_steps, d, sk, nullptr, mb)) return rc;
     ++launches;
   }
   if (!h->pair_bins.empty()) {
@@ -514,6 +515,7 @@ int launch_all(rod_handle h, int n_steps, const float4* d, cudaStream_t s, const
     a.traj = nullptr;
     a.pos_out = h->io_pos;
     a.n_elem = h->n_elem;
+    if (mb) a.mb = *mb;
     for (const auto& pb : h->pair_bins) {
       cudaStream_t sk = branches ? (*branches)[k] : s;
       ++k;
@@ -732,7 +734,7 @@ static int step_impl(rod_handle h, int n_steps, const float* drive, float4* pos_
   if (h->mb_period > 0) {
     MailboxDev mb = h->mb_dev;
     mb.step0 = h->steps_done;
-    if (int rc = launch_bins(h, h->bins, n_steps, d, (cudaStream_t)stream, nullptr, &mb)) return rc;
+    if (int rc = launch_all(h, n_steps, d, (cudaStream_t)stream, nullptr, &mb)) return rc;
     h->steps_done += n_steps;
     return CORDE_OK;
   }
@@ -1366,7 +1368,6 @@ static void mailbox_free(rod_handle h) {
 int rod_mailbox_enable(rod_handle h, int period, int log_capacity) {
   if (int rc = check_handle(h)) return rc;
   if (period < 1 || log_capacity < 1) return fail(CORDE_ERR_ARG, "rod_mailbox_enable: period and log_capacity >= 1");
-  if (!h->pairs.empty()) return fail(CORDE_ERR_UNSUPPORTED, "rod_mailbox_enable: not with bound pairs");
   for (int r = 0; r < h->n_rods; ++r)
     if (h->self[r]) return fail(CORDE_ERR_UNSUPPORTED, "rod_mailbox_enable: not with self-collision");
   CK(cudaDeviceSynchronize());

@@ -19,13 +19,14 @@
 namespace corde {
 namespace {
 
-template <int SYNC_NT, int EPT>
+template <int SYNC_NT, int EPT, bool DYN_BETA>
 struct PairHook {
   int group;       // 0 outer, 1 inner
   int t;           // thread index within the group
   int mode;        // 0, 1, 2
-  int k0;          // floor(beta)
-  float alpha;     // beta - k0
+  const float* beta_sh;  // binding offset beta (shared: the mailbox may change it between steps)
+  mutable int k0;        // floor(beta) of this step
+  mutable float alpha;   // beta - k0
   int n_out;       // outer nodes
   int n_in;        // inner nodes
   float dt;
@@ -39,6 +40,11 @@ struct PairHook {
   template <int E>
   __device__ __forceinline__ void before_iterations(const float3 (&r)[E], const float (&w)[E]) const {
     if (mode == 0) return;
+    if constexpr (DYN_BETA) {
+      const float beta = *beta_sh;  // written before this step's force-phase barriers
+      k0 = (int)floorf(beta);
+      alpha = beta - floorf(beta);
+    }
     if (group == 0) {
 #pragma unroll
       for (int e = 0; e < EPT; ++e) {
@@ -133,15 +139,18 @@ struct PairHook {
 
 template <int EPT, int NT>
 constexpr int pair_smem_bytes() {
-  return (2 * (2 * EPT * NT + 2 * kHaloSlots * NT) + 2 * EPT * NT) * (int)sizeof(float4);
+  // two rods' parameters and exchange slots, the outer rod's staged positions and
+  // velocities, and one slot for the binding offset
+  return (2 * (2 * EPT * NT + 2 * kHaloSlots * NT) + 2 * EPT * NT + 1) * (int)sizeof(float4);
 }
 
-template <int EPT, int NT>
+// MB: launched with the mailbox (inputs, and so beta, may change between steps).
+template <int EPT, int NT, bool MB>
 __global__ void __launch_bounds__(2 * NT)
 pair_kernel(const RodDev* __restrict__ rods, const int4* __restrict__ pairs, float4* __restrict__ x4,
             float4* __restrict__ v4, float4* __restrict__ q4, float4* __restrict__ o4,
             const float4* __restrict__ u4, const float4* __restrict__ k4, const float4* __restrict__ drive,
-            int n_steps, float4* __restrict__ pos_out) {
+            int n_steps, float4* __restrict__ pos_out, MailboxDev mb) {
   extern __shared__ float4 smem[];
   const int group = threadIdx.x / NT;
   const int t = threadIdx.x - group * NT;
@@ -154,6 +163,7 @@ pair_kernel(const RodDev* __restrict__ rods, const int4* __restrict__ pairs, flo
   float4* halo = gs + 2 * EPT * NT;
   float4* out_r = smem + 2 * (2 * EPT * NT + 2 * kHaloSlots * NT);
   float4* out_v = out_r + EPT * NT;
+  float& beta_sh = reinterpret_cast<float*>(out_v + EPT * NT)[0];
 
   float3 r[EPT], v[EPT], om[EPT];
   float4 q[EPT];
@@ -167,10 +177,11 @@ pair_kernel(const RodDev* __restrict__ rods, const int4* __restrict__ pairs, flo
     w_drive = f3(drive[2 * rid + 1]);
     beta = drive[2 * pr.y].w;
   }
-  PairHook<2 * NT, EPT> hook;
+  PairHook<2 * NT, EPT, MB> hook;
   hook.group = group;
   hook.t = t;
   hook.mode = pr.z;
+  hook.beta_sh = &beta_sh;
   hook.k0 = (int)floorf(beta);
   hook.alpha = beta - floorf(beta);
   hook.n_out = rods[pr.x].n;
@@ -181,9 +192,21 @@ pair_kernel(const RodDev* __restrict__ rods, const int4* __restrict__ pairs, flo
 
   const BlockHalo<NT, 2 * NT> H{t};
   int xc = 0;
-  for (int step = 0; step < n_steps; ++step)
-    step_body<EPT, NT, false>(R, H, r, v, q, om, w, par_u, par_k, halo, xc, v_drive, w_drive, nullptr, nullptr,
-                              hook);
+  if constexpr (MB) {
+    // beta is written by the inner rod's first thread only (here, and by its mailbox polls)
+    if (group == 1 && t == 0) beta_sh = beta;
+    RodMailbox<EPT> box(mb, R, rid, t * EPT);
+    for (int step = 0; step < n_steps; ++step) {
+      if (box.before_step(H, step, v_drive, w_drive, group == 1 ? &beta_sh : nullptr)) break;
+      step_body<EPT, NT, false>(R, H, r, v, q, om, w, par_u, par_k, halo, xc, v_drive, w_drive, nullptr, nullptr,
+                                hook);
+      box.after_step(H, step, r, v, w);
+    }
+  } else {
+    for (int step = 0; step < n_steps; ++step)
+      step_body<EPT, NT, false>(R, H, r, v, q, om, w, par_u, par_k, halo, xc, v_drive, w_drive, nullptr, nullptr,
+                                hook);
+  }
   const int e0 = t * EPT;
 #pragma unroll
   for (int e = 0; e < EPT; ++e) {
@@ -198,16 +221,22 @@ pair_kernel(const RodDev* __restrict__ rods, const int4* __restrict__ pairs, flo
   }
 }
 
-template <int EPT, int NT>
-cudaError_t launch_pair_t(const StepArgs& a, const int4* pairs, int n_pairs, cudaStream_t s) {
+template <int EPT, int NT, bool MB>
+cudaError_t launch_pair_mb(const StepArgs& a, const int4* pairs, int n_pairs, cudaStream_t s) {
   constexpr int smem = pair_smem_bytes<EPT, NT>();
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(pair_kernel<EPT, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = cudaFuncSetAttribute(pair_kernel<EPT, NT, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
   }
-  pair_kernel<EPT, NT><<<n_pairs, 2 * NT, smem, s>>>(a.rods, pairs, a.x4, a.v4, a.q4, a.o4, a.u4, a.k4, a.drive,
-                                                      a.n_steps, a.pos_out);
+  pair_kernel<EPT, NT, MB><<<n_pairs, 2 * NT, smem, s>>>(a.rods, pairs, a.x4, a.v4, a.q4, a.o4, a.u4, a.k4, a.drive,
+                                                          a.n_steps, a.pos_out, a.mb);
   return cudaGetLastError();
+}
+
+template <int EPT, int NT>
+cudaError_t launch_pair_t(const StepArgs& a, const int4* pairs, int n_pairs, cudaStream_t s) {
+  return a.mb.period > 0 ? launch_pair_mb<EPT, NT, true>(a, pairs, n_pairs, s)
+                         : launch_pair_mb<EPT, NT, false>(a, pairs, n_pairs, s);
 }
 
 }  // namespace

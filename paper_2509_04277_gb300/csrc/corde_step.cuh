@@ -518,7 +518,8 @@ __device__ __forceinline__ void load_rod(const RodDev& R, const int t, const int
 // One non-blocking read attempt of the drive mailbox (seqlock: the host makes the word odd
 // while it writes).  Returns true, with the drive row of rod `rid`, for a new consistent
 // input; a torn or unchanged input is skipped (read again at the next poll).
-__device__ __forceinline__ bool mailbox_poll(const MailboxDev& mb, int rid, unsigned& last, float3& vd, float3& wd) {
+__device__ __forceinline__ bool mailbox_poll(const MailboxDev& mb, int rid, unsigned& last, float3& vd, float3& wd,
+                                             float* slot3 = nullptr) {
   const unsigned s1 = ld_acquire_sys(mb.in_seq);
   if ((s1 & 1u) || s1 == last || s1 == 0u) return false;
   float d[8];
@@ -528,6 +529,7 @@ __device__ __forceinline__ bool mailbox_poll(const MailboxDev& mb, int rid, unsi
   if (ld_relaxed_sys(mb.in_seq) != s1) return false;
   vd = f3(d[0], d[1], d[2]);
   wd = f3(d[4], d[5], d[6]);
+  if (slot3 != nullptr) *slot3 = d[3];
   last = s1;
   return true;
 }
@@ -541,10 +543,10 @@ __device__ __forceinline__ void mailbox_log(const MailboxDev& mb, long long step
 // cap), backing off between reads.  Returns false, with bit 0 of the status set, when the
 // wait runs out.
 __device__ __forceinline__ bool mailbox_wait(const MailboxDev& mb, int rid, unsigned& last, float3& vd, float3& wd,
-                                             long long step) {
+                                             long long step, float* slot3 = nullptr) {
   const unsigned long long t0 = global_ns();
   for (int k = 0; k < (1 << 26); ++k) {
-    if (mailbox_poll(mb, rid, last, vd, wd)) {
+    if (mailbox_poll(mb, rid, last, vd, wd, slot3)) {
       mailbox_log(mb, step, last);
       return true;
     }
@@ -570,6 +572,102 @@ __device__ __forceinline__ void mailbox_write(unsigned* rec, unsigned& seq, long
   st_release_sys(rec, seq);
 }
 
+// Mailbox work of one rod inside a launch (Section 2.2: the haptic thread exchanges input
+// and feedback with the running kernel): before every `period`-th step the drive is polled
+// (or, in lock-step, waited for); after it the base/tip records and the position snapshot
+// are written.  H provides the barrier (and, for single blocks, the block-wide OR).
+template <int EPT>
+struct RodMailbox {
+  const MailboxDev& mb;  // the launch's parameter
+  const RodDev& R;
+  int rid, e0;
+  bool owns_base, owns_tip;
+  unsigned last = 0u, seq_base = 0u, seq_tip = 0u, seq_pos = 0u;
+  unsigned* rec_base = nullptr;
+  unsigned* rec_tip = nullptr;
+
+  __device__ __forceinline__ RodMailbox(const MailboxDev& m, const RodDev& R_, int rid_, int e0_)
+      : mb(m), R(R_), rid(rid_), e0(e0_) {
+    owns_base = e0 == 0;
+    owns_tip = e0 <= R.n - 1 && R.n - 1 < e0 + EPT;
+    if (mb.period > 0) {
+      rec_base = mb.out + 16 * (int64_t)rid;
+      rec_tip = rec_base + 8;
+      if (owns_base) seq_base = ld_relaxed_sys(rec_base) & ~1u;
+      if (owns_tip) seq_tip = ld_relaxed_sys(rec_tip) & ~1u;
+      // every thread keeps the publication count (it selects the ring slot); read before
+      // the first barrier, so before any publication of this launch
+      if (mb.pos != nullptr) seq_pos = ld_relaxed_sys(mb.pos_seq + 32 * (int64_t)rid);
+    }
+  }
+
+  // Before step `step`; true when the launch must stop (a lock-step wait ran out).  A new
+  // input replaces the drive (and *slot3, the drive row's slot 3, when given).
+  template <class Halo>
+  __device__ __forceinline__ bool before_step(const Halo& H, int step, float3& vd, float3& wd,
+                                              float* slot3 = nullptr) {
+    if (mb.period <= 0 || step % mb.period != 0) return false;
+    if constexpr (!Halo::kCluster) {
+      if (mb.lockstep) {
+        // lock-step: the base's thread waits (bounded) for the next input; the block waits
+        // at the OR and leaves together if the wait ran out
+        int lost = 0;
+        if (owns_base) lost = !mailbox_wait(mb, rid, last, vd, wd, mb.step0 + step, slot3);
+        return H.any(lost) != 0;
+      }
+    }
+    if (owns_base && mailbox_poll(mb, rid, last, vd, wd, slot3)) mailbox_log(mb, mb.step0 + step, last);
+    return false;
+  }
+
+  // After step `step`: feedback records and the position snapshot.
+  template <class Halo>
+  __device__ __forceinline__ void after_step(const Halo& H, int step, const float3 (&r)[EPT], const float3 (&v)[EPT],
+                                             const float (&w)[EPT]) {
+    if (mb.period <= 0 || (step + 1) % mb.period != 0) return;
+    if (owns_base) mailbox_write(rec_base, seq_base, mb.step0 + step + 1, r[0], v[0]);
+    if (owns_tip) {
+#pragma unroll
+      for (int e = 0; e < EPT; ++e)
+        if (e0 + e == R.n - 1) mailbox_write(rec_tip, seq_tip, mb.step0 + step + 1, r[e], v[e]);
+    }
+    if (mb.pos != nullptr) {
+      // snapshot p of every position into ring slot p % kPosSlots, under the slot's
+      // seqlock (2p + 1 while the rod's threads write, barrier-ordered after the first
+      // thread's system-scope fence; 2p + 2 after), then the publication count p + 1
+      unsigned* hdr = mb.pos_seq + 32 * (int64_t)rid;
+      const int slot = (int)(seq_pos % kPosSlots);
+      unsigned* sh = hdr + 4 + 4 * slot;
+      if (owns_base) {
+        st_relaxed_sys(sh, 2u * seq_pos + 1u);
+        fence_acq_rel_sys();
+      }
+      H.sync();
+      // system-scope stores (volatile), ordered before the first thread's release by the
+      // barrier (release/acquire among the rod's threads) and its system-scope fence
+      volatile float4* dst = mb.pos + slot * mb.n_elem + R.off;
+#pragma unroll
+      for (int e = 0; e < EPT; ++e)
+        if (e0 + e < R.n) {
+          dst[e0 + e].x = r[e].x;
+          dst[e0 + e].y = r[e].y;
+          dst[e0 + e].z = r[e].z;
+          dst[e0 + e].w = w[e];
+        }
+      H.sync();
+      if (owns_base) {
+        fence_acq_rel_sys();
+        const long long st = mb.step0 + step + 1;
+        st_relaxed_sys(sh + 1, (unsigned)(st & 0xffffffffll));
+        st_relaxed_sys(sh + 2, (unsigned)(st >> 32));
+        st_release_sys(sh, 2u * seq_pos + 2u);
+        st_release_sys(hdr, seq_pos + 1u);
+      }
+      ++seq_pos;
+    }
+  }
+};
+
 // The launch of one rod by the threads described by H: load, n_steps steps (with the
 // optional trajectory output and mailbox), store.
 template <int EPT, int NT, class Halo>
@@ -593,86 +691,18 @@ __device__ __forceinline__ void run_rod(const RodDev& R, const Halo& H, const in
     v_drive = f3(drive[2 * rid]);
     w_drive = f3(drive[2 * rid + 1]);
   }
-  const bool owns_base = e0 == 0;
-  const bool owns_tip = e0 <= R.n - 1 && R.n - 1 < e0 + EPT;
-  unsigned mb_last = 0u, seq_base = 0u, seq_tip = 0u, seq_pos = 0u;
-  unsigned* rec_base = nullptr;
-  unsigned* rec_tip = nullptr;
-  if (mb.period > 0) {
-    rec_base = mb.out + 16 * (int64_t)rid;
-    rec_tip = rec_base + 8;
-    if (owns_base) seq_base = ld_relaxed_sys(rec_base) & ~1u;
-    if (owns_tip) seq_tip = ld_relaxed_sys(rec_tip) & ~1u;
-    // every thread keeps the publication count (it selects the ring slot); read before the
-    // first barrier, so before any publication of this launch
-    if (mb.pos != nullptr) seq_pos = ld_relaxed_sys(mb.pos_seq + 32 * (int64_t)rid);
-  }
+  RodMailbox<EPT> box(mb, R, rid, e0);
 
   int xc = 0;  // exchange counter selects the ping-pong buffer
   for (int step = 0; step < n_steps; ++step) {
-    if (mb.period > 0 && step % mb.period == 0) {
-      bool stop = false;
-      if constexpr (!Halo::kCluster) {
-        if (mb.lockstep) {
-          // lock-step: the base's thread waits (bounded) for the next input; the block
-          // waits at the OR below and leaves together if the wait ran out
-          int lost = 0;
-          if (owns_base) lost = !mailbox_wait(mb, rid, mb_last, v_drive, w_drive, mb.step0 + step);
-          stop = H.any(lost) != 0;
-        }
-      }
-      if (stop) break;
-      if (!mb.lockstep && owns_base && mailbox_poll(mb, rid, mb_last, v_drive, w_drive))
-        mailbox_log(mb, mb.step0 + step, mb_last);
-    }
+    if (box.before_step(H, step, v_drive, w_drive)) break;
     step_body<EPT, NT, false>(R, H, r, v, q, om, w, par_u, par_k, halo, xc, v_drive, w_drive, nullptr, nullptr);
     if (traj != nullptr) {
 #pragma unroll
       for (int e = 0; e < EPT; ++e)
         if (e0 + e < R.n) traj[(int64_t)step * n_elem + R.off + e0 + e] = make_float4(r[e].x, r[e].y, r[e].z, w[e]);
     }
-    if (mb.period > 0 && (step + 1) % mb.period == 0) {
-      if (owns_base) mailbox_write(rec_base, seq_base, mb.step0 + step + 1, r[0], v[0]);
-      if (owns_tip) {
-#pragma unroll
-        for (int e = 0; e < EPT; ++e)
-          if (e0 + e == R.n - 1) mailbox_write(rec_tip, seq_tip, mb.step0 + step + 1, r[e], v[e]);
-      }
-      if (mb.pos != nullptr) {
-        // snapshot p of every position into ring slot p % kPosSlots, under the slot's
-        // seqlock (2p + 1 while the rod's threads write, barrier-ordered after the first
-        // thread's system-scope fence; 2p + 2 after), then the publication count p + 1
-        unsigned* hdr = mb.pos_seq + 32 * (int64_t)rid;
-        const int slot = (int)(seq_pos % kPosSlots);
-        unsigned* sh = hdr + 4 + 4 * slot;
-        if (owns_base) {
-          st_relaxed_sys(sh, 2u * seq_pos + 1u);
-          fence_acq_rel_sys();
-        }
-        H.sync();
-        // system-scope stores (volatile), ordered before the first thread's release by the
-        // barrier (release/acquire among the rod's threads) and its system-scope fence
-        volatile float4* dst = mb.pos + slot * mb.n_elem + R.off;
-#pragma unroll
-        for (int e = 0; e < EPT; ++e)
-          if (e0 + e < R.n) {
-            dst[e0 + e].x = r[e].x;
-            dst[e0 + e].y = r[e].y;
-            dst[e0 + e].z = r[e].z;
-            dst[e0 + e].w = w[e];
-          }
-        H.sync();
-        if (owns_base) {
-          fence_acq_rel_sys();
-          const long long s = mb.step0 + step + 1;
-          st_relaxed_sys(sh + 1, (unsigned)(s & 0xffffffffll));
-          st_relaxed_sys(sh + 2, (unsigned)(s >> 32));
-          st_release_sys(sh, 2u * seq_pos + 2u);
-          st_release_sys(hdr, seq_pos + 1u);
-        }
-        ++seq_pos;
-      }
-    }
+    box.after_step(H, step, r, v, w);
   }
 
 #pragma unroll

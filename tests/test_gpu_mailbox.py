@@ -214,3 +214,42 @@ def test_lockstep_wait_runs_out_cleanly(corde):
     corde.rod_mailbox_disable(long_rod.handle)
     long_rod.close()
     a.close()
+
+
+def test_lockstep_pair_with_moving_binding_offset(corde):
+    """A bound catheter/guidewire pair (v2) in lock-step: each tick's two drive rows (the
+    inner row's slot 3 is the binding offset, moving every tick) drive the next 10 steps;
+    both rods' snapshots equal ordinary 10-step launches with the same rows, bit for bit."""
+    import torch
+
+    cat, gw = W.catheter_guidewire(64, seed=650, beta0=-6.5)
+    a, b = corde.RodBatch([cat, gw]), corde.RodBatch([cat, gw])
+    a.bind(0, 1, 2)
+    b.bind(0, 1, 2)
+    corde.rod_mailbox_enable(a.handle, 10, 64)
+    corde.rod_mailbox_positions_enable(a.handle)
+    corde.rod_mailbox_lockstep(a.handle, True, 2_000_000)
+    dcs, dgs = W.pair_drives(651, 20, 10 * gw.dt, gw.length / 63, -6.5)
+    rows = np.stack([dcs, dgs], axis=1).astype(np.float32)
+    base = corde.rod_steps_done(a.handle)
+    out0, out1 = np.zeros((64, 4), np.float32), np.zeros((64, 4), np.float32)
+    snaps = []
+    a.step(200)
+    for k in range(20):
+        corde.rod_mailbox_write(a.handle, rows[k])
+        target = base + 10 * (k + 1)
+        assert _wait_snapshot(corde, a.handle, out0, target)
+        t0 = time.time()
+        while corde.rod_mailbox_positions(a.handle, 1, out1) < target and time.time() - t0 < 10.0:
+            pass
+        snaps.append((out0.copy(), out1.copy()))
+    torch.cuda.synchronize()
+    assert corde.rod_mailbox_status(a.handle) == 0
+    for k in range(20):
+        b.step(10, drive=torch.as_tensor(rows[k], device="cuda"))
+        st = b.state_numpy()["pos4"]
+        np.testing.assert_array_equal(snaps[k][0], st[:64])
+        np.testing.assert_array_equal(snaps[k][1], st[64:])
+    corde.rod_mailbox_disable(a.handle)
+    a.close()
+    b.close()
