@@ -196,6 +196,16 @@ def run_single_rod(args, torch, corde, W, rank):
     torch.cuda.synchronize()
     kern_ms = [s.elapsed_time(e) for s, e in ev]
     us_per_step = total_ms * 1e3 / (args.steps * LAUNCHES_PER_BENCH_STEP * STEPS_PER_LAUNCH)
+    # context, untimed: the same launches without launch overlap (each kernel is scheduled
+    # only after the previous one has ended)
+    b.set_launch_overlap(False)
+    e_a, e_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e_a.record(stream)
+    bench_step(args.warmup + args.steps - 1)
+    e_b.record(stream)
+    torch.cuda.synchronize()
+    no_overlap_us = e_a.elapsed_time(e_b) * 1e3 / (LAUNCHES_PER_BENCH_STEP * STEPS_PER_LAUNCH)
+    b.set_launch_overlap(True)
     rc, diag = b.diagnostics()
 
     # e2e: the haptic loop through the C ABI with host buffers.  One call per tick
@@ -301,6 +311,7 @@ def run_single_rod(args, torch, corde, W, rank):
     return {
         "floors": floors,
         "us_per_step": us_per_step,
+        "us_per_step_without_launch_overlap": no_overlap_us,
         "total_ms": total_ms,
         "kernel_ms_avg": total_ms / (args.steps * LAUNCHES_PER_BENCH_STEP),
         "kernel_ms_isolated": float(np.mean(kern_ms)),
@@ -765,6 +776,9 @@ def main_ours(args):
                          "duration": "timed region / launches (includes launch gaps); one launch bracketed "
                                      "alone by events: %.3f us" % (single["kernel_ms_isolated"] * 1e3)},
             "latency": {"us_per_step": round(value, 4), "barriers_per_step": 2 + single["n_iters"],
+                        "launch_overlap": "programmatic dependent launch (each launch waits in-kernel "
+                                          "for the previous one's writes)",
+                        "us_per_step_without_launch_overlap": round(single["us_per_step_without_launch_overlap"], 4),
                         "launch_rate_khz": round(1e3 / (value * STEPS_PER_LAUNCH), 2),
                         "haptic_1khz_realtime": bool(value * STEPS_PER_LAUNCH < 1000.0),
                         "floors_ns": {k: round(v, 2) for k, v in single["floors"].items()},

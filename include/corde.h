@@ -209,6 +209,14 @@ int rod_diagnostics(rod_handle h, double* out);
  * state (saved and restored) and keeps the fastest per bin.  rod_get_plan writes
  * [n_rods][3] ints (ept, nt, cluster; cluster 0 = one block).  Synchronous. */
 int rod_set_plan(rod_handle h, int ept, int nt);
+
+/* Launch overlap (on by default): the stepping kernels are launched with programmatic
+ * stream serialisation, so a launch is scheduled while the stream's previous stepping
+ * kernel still runs and starts stepping as soon as that kernel's writes are visible (each
+ * kernel waits for them before its first global access).  Results are bit for bit those
+ * of ordinary launches; enable = 0 switches it off (e.g. to time the launch gap).
+ * enable must be 0 or 1 (CORDE_ERR_ARG otherwise).  Host-side only. */
+int rod_set_launch_overlap(rod_handle h, int enable);
 int rod_set_plan_cluster(rod_handle h, int ept, int nt, int cluster);
 int rod_autotune(rod_handle h, int n_steps, void* stream);
 

@@ -61,6 +61,7 @@ SIGNATURES = {
     "rod_set_material": (ctypes.c_int, [_VP, _VP, _VP]),
     "rod_diagnostics": (ctypes.c_int, [_VP, _VP]),
     "rod_set_plan": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
+    "rod_set_launch_overlap": (ctypes.c_int, [_VP, ctypes.c_int]),
     "rod_set_plan_cluster": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "rod_autotune": (ctypes.c_int, [_VP, ctypes.c_int, _VP]),
     "rod_autotune_steps": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, _VP, _VP]),
@@ -218,6 +219,10 @@ def rod_diagnostics(h, out):
 
 def rod_set_plan(h, ept, nt):
     _check(load().rod_set_plan(h, int(ept), int(nt)), "rod_set_plan")
+
+
+def rod_set_launch_overlap(h, enable):
+    _check(load().rod_set_launch_overlap(h, int(enable)), "rod_set_launch_overlap")
 
 
 def rod_set_plan_cluster(h, ept, nt, cluster):
@@ -469,6 +474,9 @@ class RodBatch:
 
     def self_collision_stats(self, rod) -> dict:
         return rod_self_collision_stats(self.handle, rod)
+
+    def set_launch_overlap(self, enable: bool):
+        rod_set_launch_overlap(self.handle, 1 if enable else 0)
 
     def set_plan(self, ept, nt):
         rod_set_plan(self.handle, ept, nt)

@@ -133,6 +133,7 @@ struct corde_rods {
   std::vector<int> plan_cluster;  // blocks per rod; 0: one block
   std::vector<Bin> bins;
   int last_launches = 0;
+  int pdl = 1;  // stepping kernels launched with programmatic stream serialisation
   // rollout / adjoint
   float4* d_ckpt = nullptr;  // [n_ckpt][4][E]
   size_t ckpt_cap = 0;       // float4 entries
@@ -406,6 +407,7 @@ int launch_bins(rod_handle h, const std::vector<Bin>& bins, int n_steps, const f
   a.n_elem = h->n_elem;
   a.self_stats = h->d_self_stats;
   a.pos_out = h->io_pos;
+  a.pdl = h->pdl;
   if (mb) a.mb = *mb;
   int launches = 0;
   for (const auto& b : bins) {
@@ -515,6 +517,7 @@ int launch_all(rod_handle h, int n_steps, const float4* d, cudaStream_t s, const
     a.traj = nullptr;
     a.pos_out = h->io_pos;
     a.n_elem = h->n_elem;
+    a.pdl = h->pdl;
     if (mb) a.mb = *mb;
     for (const auto& pb : h->pair_bins) {
       cudaStream_t sk = branches ? (*branches)[k] : s;
@@ -874,6 +877,14 @@ int rod_set_plan(rod_handle h, int ept, int nt) {
       h->plan_cluster[r] = 0;
     }
   return build_bins(h);
+}
+
+int rod_set_launch_overlap(rod_handle h, int enable) {
+  if (int rc = check_handle(h)) return rc;
+  if (enable != 0 && enable != 1) return fail(CORDE_ERR_ARG, "rod_set_launch_overlap: enable must be 0 or 1");
+  if (h->pdl != enable) invalidate_graph(h);
+  h->pdl = enable;
+  return CORDE_OK;
 }
 
 int rod_set_plan_cluster(rod_handle h, int ept, int nt, int cluster) {
@@ -1690,6 +1701,7 @@ extern "C" int rod_adjoint_noalloc(const RodParams* params, const float* pos, co
   const int v = find_variant(2, nt);
   if (v < 0) return fail(CORDE_ERR_UNSUPPORTED, "rod_adjoint_noalloc: no step variant");
   StepArgs a = {};
+  a.pdl = 1;
   a.rods = d_rod;
   a.work = d_work;
   a.x4 = x4;

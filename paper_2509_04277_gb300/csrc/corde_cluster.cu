@@ -24,6 +24,7 @@ cluster_step_kernel(const RodDev* __restrict__ rods, const int* __restrict__ wor
                     float4* __restrict__ pos_out) {
   static_assert(EPT % 2 == 0, "elements per thread must be even (red-black sweeps)");
   extern __shared__ float4 smem[];
+  pdl_begin();
   cooperative_groups::cluster_group cluster = cooperative_groups::this_cluster();
   const int c = (int)cluster.block_rank();
   const int rid = work[blockIdx.x / C];
@@ -48,20 +49,8 @@ cudaError_t launch_cluster_t(const StepArgs& a, int n_rods, int C, cudaStream_t 
     cudaError_t e = cudaFuncSetAttribute(cluster_step_kernel<EPT, NT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
   }
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(n_rods * C);
-  cfg.blockDim = dim3(NT);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = C;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, cluster_step_kernel<EPT, NT>, a.rods, a.work, a.x4, a.v4, a.q4, a.o4, a.u4, a.k4,
-                            a.drive, a.n_steps, a.traj, a.n_elem, C, a.mb, a.pos_out);
+  return launch_kernel(cluster_step_kernel<EPT, NT>, dim3(n_rods * C), dim3(NT), smem, s, a.pdl, C, a.rods, a.work,
+                       a.x4, a.v4, a.q4, a.o4, a.u4, a.k4, a.drive, a.n_steps, a.traj, a.n_elem, C, a.mb, a.pos_out);
 }
 
 }  // namespace

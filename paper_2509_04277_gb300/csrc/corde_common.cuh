@@ -83,6 +83,17 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
+// Programmatic dependent launch.  A stepping kernel starts with this: it lets the stream's
+// next kernel be scheduled at once (that kernel only starts its own prologue early), then
+// waits until the stream's previous kernel has completed and its writes are visible.  Every
+// global access of the kernel comes after the wait, so the result does not depend on
+// whether the launch carried the programmatic-serialisation attribute (without it the wait
+// returns at once).
+__device__ __forceinline__ void pdl_begin() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // ---------------------------------------------------------------- float3 helpers
 
 __device__ __forceinline__ float3 f3(float x, float y, float z) { return make_float3(x, y, z); }

@@ -152,6 +152,7 @@ pair_kernel(const RodDev* __restrict__ rods, const int4* __restrict__ pairs, flo
             const float4* __restrict__ u4, const float4* __restrict__ k4, const float4* __restrict__ drive,
             int n_steps, float4* __restrict__ pos_out, MailboxDev mb) {
   extern __shared__ float4 smem[];
+  pdl_begin();
   const int group = threadIdx.x / NT;
   const int t = threadIdx.x - group * NT;
   const int4 pr = pairs[blockIdx.x];  // (outer rod, inner rod, mode, 0)
@@ -228,9 +229,8 @@ cudaError_t launch_pair_mb(const StepArgs& a, const int4* pairs, int n_pairs, cu
     cudaError_t e = cudaFuncSetAttribute(pair_kernel<EPT, NT, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
   }
-  pair_kernel<EPT, NT, MB><<<n_pairs, 2 * NT, smem, s>>>(a.rods, pairs, a.x4, a.v4, a.q4, a.o4, a.u4, a.k4, a.drive,
-                                                          a.n_steps, a.pos_out, a.mb);
-  return cudaGetLastError();
+  return launch_kernel(pair_kernel<EPT, NT, MB>, dim3(n_pairs), dim3(2 * NT), smem, s, a.pdl, 0, a.rods, pairs, a.x4,
+                       a.v4, a.q4, a.o4, a.u4, a.k4, a.drive, a.n_steps, a.pos_out, a.mb);
 }
 
 template <int EPT, int NT>

@@ -375,6 +375,7 @@ self_step_kernel(const RodDev* __restrict__ rods, const int* __restrict__ work, 
                  const float4* __restrict__ u4, const float4* __restrict__ k4, const float4* __restrict__ drive,
                  int n_steps, int4* __restrict__ stats, float4* __restrict__ pos_out) {
   extern __shared__ float4 smem[];
+  pdl_begin();
   const int rid = work[blockIdx.x];
   const RodDev R = rods[rid];
   const int t = threadIdx.x;
@@ -442,9 +443,8 @@ cudaError_t launch_self_t(const StepArgs& a, int n_blocks, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(self_step_kernel<EPT, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
   }
-  self_step_kernel<EPT, NT><<<n_blocks, NT, smem, s>>>(a.rods, a.work, a.x4, a.v4, a.q4, a.o4, a.u4, a.k4, a.drive,
-                                                        a.n_steps, a.self_stats, a.pos_out);
-  return cudaGetLastError();
+  return launch_kernel(self_step_kernel<EPT, NT>, dim3(n_blocks), dim3(NT), smem, s, a.pdl, 0, a.rods, a.work, a.x4,
+                       a.v4, a.q4, a.o4, a.u4, a.k4, a.drive, a.n_steps, a.self_stats, a.pos_out);
 }
 
 }  // namespace

@@ -729,6 +729,7 @@ step_kernel(const RodDev* __restrict__ rods, const int* __restrict__ work, float
             int n_steps, float4* __restrict__ traj, int64_t n_elem, MailboxDev mb, float4* __restrict__ pos_out) {
   static_assert(EPT % 2 == 0, "elements per thread must be even (red-black sweeps)");
   extern __shared__ float4 smem[];
+  pdl_begin();
   const int rid = work[blockIdx.x];
   const RodDev R = rods[rid];
   const BlockHalo<NT, NT> H{(int)threadIdx.x};

@@ -11,9 +11,8 @@ static cudaError_t launch_step(const StepArgs& a, int n_blocks, cudaStream_t s) 
     cudaError_t e = cudaFuncSetAttribute(step_kernel<EPT, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
   }
-  step_kernel<EPT, NT><<<n_blocks, NT, smem, s>>>(a.rods, a.work, a.x4, a.v4, a.q4, a.o4, a.u4, a.k4, a.drive,
-                                                  a.n_steps, a.traj, a.n_elem, a.mb, a.pos_out);
-  return cudaGetLastError();
+  return launch_kernel(step_kernel<EPT, NT>, dim3(n_blocks), dim3(NT), smem, s, a.pdl, 0, a.rods, a.work, a.x4,
+                       a.v4, a.q4, a.o4, a.u4, a.k4, a.drive, a.n_steps, a.traj, a.n_elem, a.mb, a.pos_out);
 }
 
 #define V(NT) {4, NT, step_smem_bytes<4, NT>(), &launch_step<4, NT>}

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <string>
+#include <utility>
 
 #include "corde_common.cuh"
 
@@ -22,7 +23,38 @@ struct StepArgs {
   MailboxDev mb;   // mailbox of the launch (period 0: none)
   int4* self_stats;  // self-collision statistics per rod (corde_self.cu), or NULL
   float4* pos_out;   // optional: positions (r, w) after the launch, [n_elem] (device or mapped host)
+  int pdl;           // 1: launch with programmatic stream serialisation (the kernel may start
+                     // before the stream's previous kernel ends; it waits in pdl_begin)
 };
+
+// Launches kernel<<<grid, block, smem, s>>>(args...), with the programmatic-serialisation
+// attribute when pdl != 0 and as clusters of `cluster` blocks along x when cluster > 0.
+template <class... KArgs, class... Args>
+cudaError_t launch_kernel(void (*kernel)(KArgs...), dim3 grid, dim3 block, int smem, cudaStream_t s, int pdl,
+                          int cluster, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = (size_t)smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[2];
+  int na = 0;
+  if (pdl) {
+    at[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[na].val.programmaticStreamSerializationAllowed = 1;
+    ++na;
+  }
+  if (cluster > 0) {
+    at[na].id = cudaLaunchAttributeClusterDimension;
+    at[na].val.clusterDim.x = (unsigned)cluster;
+    at[na].val.clusterDim.y = 1;
+    at[na].val.clusterDim.z = 1;
+    ++na;
+  }
+  cfg.attrs = at;
+  cfg.numAttrs = (unsigned)na;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 typedef cudaError_t (*StepLaunchFn)(const StepArgs& a, int n_blocks, cudaStream_t s);
 

@@ -218,7 +218,7 @@ def test_lockstep_wait_runs_out_cleanly(corde):
 
 def test_lockstep_pair_with_moving_binding_offset(corde):
     """A bound catheter/guidewire pair (v2) in lock-step: each tick's two drive rows (the
-    inner row's slot 3 is the binding offset, moving every tick) drive the next 10 steps;
+    inner row's slot 3 is the binding offset, 0.15 segments further each tick) drive the next 10 steps;
     both rods' snapshots equal ordinary 10-step launches with the same rows, bit for bit."""
     import torch
 
@@ -231,6 +231,7 @@ def test_lockstep_pair_with_moving_binding_offset(corde):
     corde.rod_mailbox_lockstep(a.handle, True, 2_000_000)
     dcs, dgs = W.pair_drives(651, 20, 10 * gw.dt, gw.length / 63, -6.5)
     rows = np.stack([dcs, dgs], axis=1).astype(np.float32)
+    rows[:, 1, 3] = -6.5 + 0.15 * np.arange(20)  # the binding point crosses three outer segments
     base = corde.rod_steps_done(a.handle)
     out0, out1 = np.zeros((64, 4), np.float32), np.zeros((64, 4), np.float32)
     snaps = []
