@@ -25,6 +25,7 @@
 #pragma once
 
 #include <cooperative_groups.h>
+#include <type_traits>
 
 #include "corde_common.cuh"
 
@@ -51,6 +52,22 @@ struct BlockHalo {
   __device__ __forceinline__ bool has_prev() const { return t > 0; }
   __device__ __forceinline__ float4 next(const float4* hb, int slot) const { return hb[slot * NT + t + 1]; }
   __device__ __forceinline__ float4 prev(const float4* hb, int slot) const { return hb[slot * NT + t - 1]; }
+  // three-float slots, one float per component (component c of slot s at float
+  // (3 s + c) NT + t): a neighbour's vector is three 32-bit loads, issued together
+  __device__ __forceinline__ void put3(float4* hb, int slot, float3 a) const {
+    float* f = reinterpret_cast<float*>(hb) + 3 * slot * NT + t;
+    f[0] = a.x;
+    f[NT] = a.y;
+    f[2 * NT] = a.z;
+  }
+  __device__ __forceinline__ float3 next3(const float4* hb, int slot) const {
+    const float* f = reinterpret_cast<const float*>(hb) + 3 * slot * NT + t + 1;
+    return f3(f[0], f[NT], f[2 * NT]);
+  }
+  __device__ __forceinline__ float3 prev3(const float4* hb, int slot) const {
+    const float* f = reinterpret_cast<const float*>(hb) + 3 * slot * NT + t - 1;
+    return f3(f[0], f[NT], f[2 * NT]);
+  }
   __device__ __forceinline__ void sync() const { block_sync<SYNC_NT>(); }
   // block-wide OR of x (a barrier)
   __device__ __forceinline__ int any(int x) const {
@@ -83,6 +100,12 @@ struct ClusterHalo {
     const float4* remote = cooperative_groups::this_cluster().map_shared_rank(hb, c - 1);
     return remote[slot * NT + NT - 1];
   }
+  // three-float slots: whole float4 slots here (one remote access per vector)
+  __device__ __forceinline__ void put3(float4* hb, int slot, float3 a) const {
+    hb[slot * NT + t] = make_float4(a.x, a.y, a.z, 0.f);
+  }
+  __device__ __forceinline__ float3 next3(const float4* hb, int slot) const { return f3(next(hb, slot)); }
+  __device__ __forceinline__ float3 prev3(const float4* hb, int slot) const { return f3(prev(hb, slot)); }
   __device__ __forceinline__ void sync() const { cooperative_groups::this_cluster().sync(); }
 };
 
@@ -326,12 +349,12 @@ __device__ __forceinline__ void step_body(const RodDev& R, const Halo& H, float3
   // ---- exchange 2: carries to the right neighbour's first element
   hb = halo + (xc & 1) * kHaloSlots * NT;
   ++xc;
-  hb[t] = make_float4(F_carry.x, F_carry.y, F_carry.z, 0.f);
-  hb[NT + t] = make_float4(tau_carry.x, tau_carry.y, tau_carry.z, 0.f);
+  H.put3(hb, 0, F_carry);
+  H.put3(hb, 1, tau_carry);
   H.sync();
   if (has_prev) {
-    F[0] += f3(H.prev(hb, 0));
-    tau[0] += f3(H.prev(hb, 1));
+    F[0] += H.prev3(hb, 0);
+    tau[0] += H.prev3(hb, 1);
   }
 
   // ---- integrate forces and torques into velocities
@@ -385,7 +408,8 @@ __device__ __forceinline__ void step_body(const RodDev& R, const Halo& H, float3
     const float2 i_bnd = make_float2(i_right, i_left);
     const float2 w_bnd = make_float2(-w[EPT - 1], w[0]);
 
-    for (int it = 0; it < R.n_iters; ++it) {
+    // one iteration; tube_on (a compile-time bool) adds the vessel contact
+    auto iteration = [&](int it, auto tube_on) {
       if constexpr (STORE) {
 #pragma unroll
         for (int e = 0; e < EPT; ++e) sweep_v[((2 * it) * EPT + e) * NT + t] = make_float4(v[e].x, v[e].y, v[e].z, 0.f);
@@ -424,8 +448,8 @@ __device__ __forceinline__ void step_body(const RodDev& R, const Halo& H, float3
       // exchange 3: velocities of the first and last element
       hb = halo + (xc & 1) * kHaloSlots * NT;
       ++xc;
-      hb[t] = make_float4(v[0].x, v[0].y, v[0].z, 0.f);
-      hb[NT + t] = make_float4(v[EPT - 1].x, v[EPT - 1].y, v[EPT - 1].z, 0.f);
+      H.put3(hb, 0, v[0]);
+      H.put3(hb, 1, v[EPT - 1]);
       // odd segments inside the thread: they move elements 1 .. EPT - 2 only, which the
       // exchange and the boundary segments do not read, so they run while the barrier waits
 #pragma unroll
@@ -438,8 +462,8 @@ __device__ __forceinline__ void step_body(const RodDev& R, const Halo& H, float3
       H.sync();
       // odd segments across the two thread boundaries, in one packed evaluation
       {
-        const float3 vn = has_next ? f3(H.next(hb, 0)) : zero3();
-        const float3 vp = has_prev ? f3(H.prev(hb, 1)) : zero3();
+        const float3 vn = has_next ? H.next3(hb, 0) : zero3();
+        const float3 vp = has_prev ? H.prev3(hb, 1) : zero3();
         const Vec3x2 va{make_float2(v[EPT - 1].x, vp.x), make_float2(v[EPT - 1].y, vp.y),
                         make_float2(v[EPT - 1].z, vp.z)};
         const Vec3x2 vb{make_float2(vn.x, v[0].x), make_float2(vn.y, v[0].y), make_float2(vn.z, v[0].z)};
@@ -452,12 +476,24 @@ __device__ __forceinline__ void step_body(const RodDev& R, const Halo& H, float3
         v[0] = f3(nx.y, ny.y, nz.y);
       }
       // collision response (analytic vessel), per node
-      if (R.flags & F_TUBE) {
+      if constexpr (decltype(tube_on)::value) {
 #pragma unroll
         for (int e = 0; e < EPT; ++e)
           if (e0 + e < n) tube_contact(r[e], v[e], w[e], R, dt, inv_dt);
       }
       hook.template after_odd<EPT>(r, v, w);
+    };
+    if (R.flags & F_TUBE) {
+      for (int it = 0; it < R.n_iters; ++it) iteration(it, std::true_type());
+    } else if constexpr (std::is_same<Hook, NoHook>::value && EPT == 2) {
+      // the plain rod: unrolled (ten iterations, the paper's count, run as one block of code)
+#pragma unroll 10
+      for (int it = 0; it < R.n_iters; ++it) iteration(it, std::false_type());
+    } else if constexpr (std::is_same<Hook, NoHook>::value) {
+#pragma unroll 2
+      for (int it = 0; it < R.n_iters; ++it) iteration(it, std::false_type());
+    } else {
+      for (int it = 0; it < R.n_iters; ++it) iteration(it, std::false_type());
     }
   }
 
