@@ -134,6 +134,36 @@ __device__ __forceinline__ float3 constraint_vjp(float3 ra, float3 va, float3 rb
   return inv * ((1.f - rho) * g_bar + (rho * dot3(n, g_bar)) * n);
 }
 
+// constraint_vjp in two parts.  The geometry (direction n and l0/L of the predicted
+// segment) depends only on the recorded velocities, so it is computed before the
+// exchange of the adjoint velocities; inv = -1/(dt W) is constant over a step, and 0
+// for a constraint that does not exist (its geometry is then a safe unit vector and the
+// returned d_bar is 0).  Same arithmetic as constraint_vjp.
+struct VjpGeo {
+  float3 n;
+  float rho;
+};
+__device__ __forceinline__ float vjp_inv(bool exists, float wa, float wb, float dt) {
+  return (exists && wa + wb > 0.f) ? -__frcp_rn(__fmul_rn(dt, wa + wb)) : 0.f;
+}
+__device__ __forceinline__ VjpGeo vjp_geo(float3 ra, float3 va, float3 rb, float3 vb, float inv, float l0,
+                                          float dt) {
+  float3 d = f3(__fmaf_rn(dt, __fsub_rn(vb.x, va.x), __fsub_rn(rb.x, ra.x)),
+                __fmaf_rn(dt, __fsub_rn(vb.y, va.y), __fsub_rn(rb.y, ra.y)),
+                __fmaf_rn(dt, __fsub_rn(vb.z, va.z), __fsub_rn(rb.z, ra.z)));
+  if (inv == 0.f) d = f3(0.f, 0.f, 1.f);
+  const float dd = __fmaf_rn(d.x, d.x, __fmaf_rn(d.y, d.y, __fmul_rn(d.z, d.z)));
+  const float il = rsqrtf(dd);
+  return VjpGeo{il * d, l0 * il};
+}
+__device__ __forceinline__ float3 vjp_apply(const VjpGeo& G, float inv, float wa, float wb, float3 va_bar,
+                                            float3 vb_bar) {
+  const float3 g_bar = f3(__fmaf_rn(wb, vb_bar.x, -__fmul_rn(wa, va_bar.x)),
+                          __fmaf_rn(wb, vb_bar.y, -__fmul_rn(wa, va_bar.y)),
+                          __fmaf_rn(wb, vb_bar.z, -__fmul_rn(wa, va_bar.z)));
+  return inv * ((1.f - G.rho) * g_bar + (G.rho * dot3(G.n, g_bar)) * G.n);
+}
+
 template <int EPT, int NT>
 __device__ __forceinline__ void reverse_step(const RodDev& R, const int t, const float3 (&r)[EPT],
                                              const float4 (&q)[EPT], const float3 (&om)[EPT], const float (&w)[EPT],
@@ -175,49 +205,71 @@ __device__ __forceinline__ void reverse_step(const RodDev& R, const int t, const
 
   // ---- constraint half-sweeps in reverse order (odd, then even, last iteration first)
   if (inext) {
+    const BlockHalo<NT, NT> H{t};
+    // -1 / (dt W) of every constraint the thread touches (constant over the step)
+    constexpr int NE = EPT / 2, NO = EPT / 2 - 1 > 0 ? EPT / 2 - 1 : 1;
+    float inv_e[NE], inv_o[NO];
+#pragma unroll
+    for (int k = 0; k < NE; ++k) inv_e[k] = vjp_inv(e0 + 2 * k + 1 <= n - 1, w[2 * k], w[2 * k + 1], dt);
+#pragma unroll
+    for (int k = 0; k < NO; ++k)
+      inv_o[k] = vjp_inv(EPT / 2 > 1 && e0 + 2 * k + 2 <= n - 1, w[(2 * k + 1) % EPT], w[(2 * k + 2) % EPT], dt);
+    const float inv_r = vjp_inv(t + 1 < NT && e0 + EPT <= n - 1, w[EPT - 1], nb.w_next, dt);
+    const float inv_l = vjp_inv(t > 0 && e0 <= n - 1, nb.w_prev, w[0], dt);
+    const int tn = min(t + 1, NT - 1), tp = max(t - 1, 0);  // in-range neighbour slots
+#pragma unroll 2
     for (int it = R.n_iters - 1; it >= 0; --it) {
-      float4* hb = halo + (xc & 1) * kHaloSlots * NT;
-      ++xc;
-      hb[t] = make_float4(vb2[0].x, vb2[0].y, vb2[0].z, 0.f);
-      hb[NT + t] = make_float4(vb2[EPT - 1].x, vb2[EPT - 1].y, vb2[EPT - 1].z, 0.f);
-      block_sync<NT>();
-      const float4* sv = sweep_v + (2 * it + 1) * EPT * NT;
+      // geometry of this iteration's constraints, from the recorded velocities
+      const float4* so = sweep_v + (2 * it + 1) * EPT * NT;  // before the odd half-sweep
+      const float4* se = sweep_v + (2 * it) * EPT * NT;      // before the even half-sweep
+      VjpGeo g_o[NO], g_e[NE];
 #pragma unroll
       for (int k = 0; k + 1 < EPT / 2; ++k) {
         const int a = 2 * k + 1, b = 2 * k + 2;
-        if (e0 + b <= n - 1 && w[a] + w[b] > 0.f) {
-          const float3 db = constraint_vjp(r[a], f3(sv[a * NT + t]), r[b], f3(sv[b * NT + t]), w[a], w[b], vb2[a],
-                                           vb2[b], R.l0, dt);
-          vb2[a] -= dt * db;
-          vb2[b] += dt * db;
-          rb[a] -= db;
-          rb[b] += db;
-        }
+        g_o[k] = vjp_geo(r[a], f3(so[a * NT + t]), r[b], f3(so[b * NT + t]), inv_o[k], R.l0, dt);
       }
-      if (t + 1 < NT && e0 + EPT <= n - 1 && w[EPT - 1] + nb.w_next > 0.f) {
-        const float3 db = constraint_vjp(r[EPT - 1], f3(sv[(EPT - 1) * NT + t]), nb.r_next, f3(sv[t + 1]),
-                                         w[EPT - 1], nb.w_next, vb2[EPT - 1], f3(hb[t + 1]), R.l0, dt);
+      const VjpGeo g_r = vjp_geo(r[EPT - 1], f3(so[(EPT - 1) * NT + t]), nb.r_next, f3(so[tn]), inv_r, R.l0, dt);
+      const VjpGeo g_l = vjp_geo(nb.r_prev, f3(so[(EPT - 1) * NT + tp]), r[0], f3(so[t]), inv_l, R.l0, dt);
+#pragma unroll
+      for (int k = 0; k < NE; ++k) {
+        const int a = 2 * k, b = 2 * k + 1;
+        g_e[k] = vjp_geo(r[a], f3(se[a * NT + t]), r[b], f3(se[b * NT + t]), inv_e[k], R.l0, dt);
+      }
+      // exchange of the adjoint velocities of the first and last element
+      float4* hb = halo + (xc & 1) * kHaloSlots * NT;
+      ++xc;
+      H.put3(hb, 0, vb2[0]);
+      H.put3(hb, 1, vb2[EPT - 1]);
+      // odd segments inside the thread (elements 1 .. EPT - 2: not exchanged)
+#pragma unroll
+      for (int k = 0; k + 1 < EPT / 2; ++k) {
+        const int a = 2 * k + 1, b = 2 * k + 2;
+        const float3 db = vjp_apply(g_o[k], inv_o[k], w[a], w[b], vb2[a], vb2[b]);
+        vb2[a] -= dt * db;
+        vb2[b] += dt * db;
+        rb[a] -= db;
+        rb[b] += db;
+      }
+      block_sync<NT>();
+      const float3 vn_bar = H.next3(hb, 0), vp_bar = H.prev3(hb, 1);  // read only where the constraint exists
+      {
+        const float3 db = vjp_apply(g_r, inv_r, w[EPT - 1], nb.w_next, vb2[EPT - 1], t + 1 < NT ? vn_bar : zero3());
         vb2[EPT - 1] -= dt * db;
         rb[EPT - 1] -= db;
       }
-      if (t > 0 && e0 <= n - 1 && nb.w_prev + w[0] > 0.f) {
-        const float3 db = constraint_vjp(nb.r_prev, f3(sv[(EPT - 1) * NT + t - 1]), r[0], f3(sv[t]), nb.w_prev,
-                                         w[0], f3(hb[NT + t - 1]), vb2[0], R.l0, dt);
+      {
+        const float3 db = vjp_apply(g_l, inv_l, nb.w_prev, w[0], t > 0 ? vp_bar : zero3(), vb2[0]);
         vb2[0] += dt * db;
         rb[0] += db;
       }
-      sv = sweep_v + (2 * it) * EPT * NT;
 #pragma unroll
-      for (int k = 0; k < EPT / 2; ++k) {
+      for (int k = 0; k < NE; ++k) {
         const int a = 2 * k, b = 2 * k + 1;
-        if (e0 + b <= n - 1 && w[a] + w[b] > 0.f) {
-          const float3 db = constraint_vjp(r[a], f3(sv[a * NT + t]), r[b], f3(sv[b * NT + t]), w[a], w[b], vb2[a],
-                                           vb2[b], R.l0, dt);
-          vb2[a] -= dt * db;
-          vb2[b] += dt * db;
-          rb[a] -= db;
-          rb[b] += db;
-        }
+        const float3 db = vjp_apply(g_e[k], inv_e[k], w[a], w[b], vb2[a], vb2[b]);
+        vb2[a] -= dt * db;
+        vb2[b] += dt * db;
+        rb[a] -= db;
+        rb[b] += db;
       }
     }
   }
