@@ -316,6 +316,19 @@ int rod_rollout(rod_handle h, int n_steps, int ckpt_every, float* pos_traj, void
 int rod_adjoint(rod_handle h, const float* dL_dpos_traj, float* dL_dK, float* dL_duhat, float* dL_dvel0,
                 float* dL_dpos0, float* dL_dquat0, float* dL_domega0, void* stream);
 
+/* Scratch budget of rod_adjoint's record mode (default 64 MiB).  Within a checkpoint
+ * segment the reverse pass needs every step's velocities before each constraint
+ * half-sweep.
+ *  - Record mode (the scratch fits in `bytes` and the block's shared memory holds two
+ *    copies of a step's sweeps): one forward pass over the segment keeps them in device
+ *    memory, 2 n_iters x 64 B per node and step plus 48 B per node and step of neighbour
+ *    data.  The reverse pass streams them back with asynchronous copies.
+ *  - Recompute mode (otherwise, and always with bytes = 0): every step is run forward
+ *    again before its reverse.
+ * Both modes give the same gradients bit for bit.  bytes >= 0 (CORDE_ERR_ARG otherwise).
+ * Host-side only. */
+int rod_set_adjoint_record_budget(rod_handle h, long long bytes);
+
 /* Gradient of one rod's rollout without any device allocation.  The paper has no
  * counterpart: this entry point exists for callers that cannot call cudaMalloc where
  * they need a gradient - a haptic or control loop under a real-time budget (an allocation

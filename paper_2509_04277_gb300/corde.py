@@ -62,6 +62,7 @@ SIGNATURES = {
     "rod_diagnostics": (ctypes.c_int, [_VP, _VP]),
     "rod_set_plan": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
     "rod_set_launch_overlap": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "rod_set_adjoint_record_budget": (ctypes.c_int, [_VP, ctypes.c_longlong]),
     "rod_set_plan_cluster": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "rod_autotune": (ctypes.c_int, [_VP, ctypes.c_int, _VP]),
     "rod_autotune_steps": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, _VP, _VP]),
@@ -219,6 +220,10 @@ def rod_diagnostics(h, out):
 
 def rod_set_plan(h, ept, nt):
     _check(load().rod_set_plan(h, int(ept), int(nt)), "rod_set_plan")
+
+
+def rod_set_adjoint_record_budget(h, n_bytes):
+    _check(load().rod_set_adjoint_record_budget(h, int(n_bytes)), "rod_set_adjoint_record_budget")
 
 
 def rod_set_launch_overlap(h, enable):
@@ -474,6 +479,9 @@ class RodBatch:
 
     def self_collision_stats(self, rod) -> dict:
         return rod_self_collision_stats(self.handle, rod)
+
+    def set_adjoint_record_budget(self, n_bytes: int):
+        rod_set_adjoint_record_budget(self.handle, n_bytes)
 
     def set_launch_overlap(self, enable: bool):
         rod_set_launch_overlap(self.handle, 1 if enable else 0)

@@ -134,6 +134,14 @@ __device__ __forceinline__ float3 constraint_vjp(float3 ra, float3 va, float3 rb
   return inv * ((1.f - rho) * g_bar + (rho * dot3(n, g_bar)) * n);
 }
 
+// Asynchronous 16-byte global -> shared copies (completed by cp_async_wait_all).
+__device__ __forceinline__ void cp_async16(float4* dst_smem, const float4* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // constraint_vjp in two parts.  The geometry (direction n and l0/L of the predicted
 // segment) depends only on the recorded velocities, so it is computed before the
 // exchange of the adjoint velocities; inv = -1/(dt W) is constant over a step, and 0
@@ -362,7 +370,7 @@ __device__ __forceinline__ void reverse_step(const RodDev& R, const int t, const
 }
 
 // Reverse pass over the whole rollout of one rod per block.
-template <int NT>
+template <int NT, bool RECORD>
 __global__ void __launch_bounds__(NT)
 adjoint_kernel(AdjointArgs a) {
   constexpr int EPT = 2;
@@ -371,6 +379,7 @@ adjoint_kernel(AdjointArgs a) {
   float4* par_k = smem + EPT * NT;
   float4* halo = smem + 2 * EPT * NT;
   float4* sweep_v = halo + 2 * kHaloSlots * NT;
+  const int64_t rec_stride = (int64_t)2 * a.rec_iters * EPT * NT;  // float4 per (step, block) record
 
   const int rid = a.work[blockIdx.x];
   const RodDev R = a.rods[rid];
@@ -404,8 +413,7 @@ adjoint_kernel(AdjointArgs a) {
     load_rod<EPT, NT>(R, t, t, ck, ck + E, ck + 2 * E, ck + 3 * E, a.u4, a.k4, r, v, q, om, w,
                       params_loaded ? nullptr : par_u, par_k);
     params_loaded = true;
-    // recompute the segment's states into scratch
-    for (int s = 0; s < cnt; ++s) {
+    auto put_state = [&](int s) {
       float4* st = a.seg_states + (int64_t)s * 4 * E + R.off;
 #pragma unroll
       for (int e = 0; e < EPT; ++e) {
@@ -416,8 +424,36 @@ adjoint_kernel(AdjointArgs a) {
           st[3 * E + e0 + e] = make_float4(om[e].x, om[e].y, om[e].z, 0.f);
         }
       }
-      if (s + 1 < cnt)
-        step_body<EPT, NT, false>(R, H, r, v, q, om, w, par_u, par_k, halo, xc, v_drive, w_drive, nullptr, nullptr);
+    };
+    auto rec_at = [&](int s) { return a.sweep_rec + ((int64_t)s * gridDim.x + blockIdx.x) * rec_stride; };
+    auto nb_at = [&](int s) { return a.nb_rec + (((int64_t)s * gridDim.x + blockIdx.x) * 3) * NT + t; };
+    // copies this thread's entries of step s's record into a shared buffer
+    auto fetch = [&](int s, float4* dst) {
+      const float4* src = rec_at(s);
+      const int n_ent = 2 * R.n_iters * EPT;
+      for (int k = 0; k < n_ent; ++k) cp_async16(dst + k * NT + t, src + k * NT + t);
+      cp_async_commit();
+    };
+    if constexpr (RECORD) {
+      // forward over the segment, keeping states 0 .. cnt, sweeps and neighbour data
+      for (int s = 0; s < cnt; ++s) {
+        put_state(s);
+        StepNeighbours nb;
+        step_body<EPT, NT, true>(R, H, r, v, q, om, w, par_u, par_k, halo, xc, v_drive, w_drive, rec_at(s), &nb);
+        float4* nr = nb_at(s);
+        nr[0] = make_float4(nb.r_next.x, nb.r_next.y, nb.r_next.z, nb.w_next);
+        nr[NT] = make_float4(nb.r_prev.x, nb.r_prev.y, nb.r_prev.z, nb.w_prev);
+        nr[2 * NT] = nb.q_next;
+      }
+      put_state(cnt);
+      fetch(cnt - 1, sweep_v + ((cnt - 1) & 1) * rec_stride);
+    } else {
+      // recompute the segment's states into scratch
+      for (int s = 0; s < cnt; ++s) {
+        put_state(s);
+        if (s + 1 < cnt)
+          step_body<EPT, NT, false>(R, H, r, v, q, om, w, par_u, par_k, halo, xc, v_drive, w_drive, nullptr, nullptr);
+      }
     }
     // reverse the segment's steps
     for (int s = cnt - 1; s >= 0; --s) {
@@ -437,7 +473,32 @@ adjoint_kernel(AdjointArgs a) {
         om_in[e] = om[e];
       }
       StepNeighbours nb;
-      step_body<EPT, NT, true>(R, H, r, v, q, om, w, par_u, par_k, halo, xc, v_drive, w_drive, sweep_v, &nb);
+      const float4* sweep = sweep_v;
+      if constexpr (RECORD) {
+        // the step's end state (frame and angular velocity after it), neighbour data and
+        // sweeps; the copy of step s - 1's sweeps starts once every thread is done with
+        // the buffer it reuses (step s + 1's)
+        const float4* sn = a.seg_states + (int64_t)(s + 1) * 4 * E + R.off;
+#pragma unroll
+        for (int e = 0; e < EPT; ++e)
+          if (e0 + e < R.n) {
+            q[e] = sn[2 * E + e0 + e];
+            om[e] = f3(sn[3 * E + e0 + e]);
+          }
+        const float4* nr = nb_at(s);
+        const float4 a0 = nr[0], a1 = nr[NT];
+        nb.r_next = f3(a0);
+        nb.w_next = a0.w;
+        nb.r_prev = f3(a1);
+        nb.w_prev = a1.w;
+        nb.q_next = nr[2 * NT];
+        cp_async_wait_all();
+        block_sync<NT>();
+        if (s > 0) fetch(s - 1, sweep_v + ((s - 1) & 1) * rec_stride);
+        sweep = sweep_v + (s & 1) * rec_stride;
+      } else {
+        step_body<EPT, NT, true>(R, H, r, v, q, om, w, par_u, par_k, halo, xc, v_drive, w_drive, sweep_v, &nb);
+      }
       // loss gradient with respect to the positions after this step
       if (a.dLdpos != nullptr) {
         const float4* g = a.dLdpos + (int64_t)(t0 + s) * E + R.off;
@@ -445,7 +506,7 @@ adjoint_kernel(AdjointArgs a) {
         for (int e = 0; e < EPT; ++e)
           if (e0 + e < R.n) rb[e] += f3(g[e0 + e]);
       }
-      reverse_step<EPT, NT>(R, t, r_in, q_in, om_in, w, om, q, nb, par_u, par_k, halo, xc, sweep_v, rb, vb, qb, ob,
+      reverse_step<EPT, NT>(R, t, r_in, q_in, om_in, w, om, q, nb, par_u, par_k, halo, xc, sweep, rb, vb, qb, ob,
                             Kb, ub);
     }
   }
@@ -464,19 +525,25 @@ adjoint_kernel(AdjointArgs a) {
   }
 }
 
+template <int NT, bool RECORD>
+cudaError_t launch_adjoint_mode(const AdjointArgs& a, int n_blocks, int smem, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(adjoint_kernel<NT, RECORD>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  adjoint_kernel<NT, RECORD><<<n_blocks, NT, smem, s>>>(a);
+  return cudaGetLastError();
+}
 template <int NT>
 cudaError_t launch_adjoint_nt(const AdjointArgs& a, int n_blocks, int smem, cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(adjoint_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
-  adjoint_kernel<NT><<<n_blocks, NT, smem, s>>>(a);
-  return cudaGetLastError();
+  return a.sweep_rec != nullptr ? launch_adjoint_mode<NT, true>(a, n_blocks, smem, s)
+                                : launch_adjoint_mode<NT, false>(a, n_blocks, smem, s);
 }
 
 }  // namespace
 
-int adjoint_smem_bytes(int nt, int n_iters) {
+int adjoint_smem_bytes(int nt, int n_iters, bool record) {
   const int ept = 2;
-  return (2 * ept * nt + 2 * kHaloSlots * nt + 2 * (n_iters > 0 ? n_iters : 1) * ept * nt) * (int)sizeof(float4);
+  const int sweep = 2 * (n_iters > 0 ? n_iters : 1) * ept * nt;
+  return (2 * ept * nt + 2 * kHaloSlots * nt + (record ? 2 : 1) * sweep) * (int)sizeof(float4);
 }
 
 cudaError_t launch_adjoint(int nt, const AdjointArgs& a, int n_blocks, int smem, cudaStream_t s) {

@@ -137,8 +137,13 @@ struct corde_rods {
   // rollout / adjoint
   float4* d_ckpt = nullptr;  // [n_ckpt][4][E]
   size_t ckpt_cap = 0;       // float4 entries
-  float4* d_seg = nullptr;   // [K][4][E] scratch of the reverse pass
+  float4* d_seg = nullptr;   // [K (+1)][4][E] scratch of the reverse pass
   size_t seg_cap = 0;
+  float4* d_sweep_rec = nullptr;  // record mode of the reverse pass: sweeps and neighbour data
+  size_t sweep_rec_cap = 0;
+  float4* d_nb_rec = nullptr;
+  size_t nb_rec_cap = 0;
+  long long adj_record_budget = 64ll << 20;
   int ro_steps = 0, ro_every = 0;
   std::vector<Bin> adj_bins;  // variant = threads per block
   // catheter/guidewire pairs
@@ -879,6 +884,13 @@ int rod_set_plan(rod_handle h, int ept, int nt) {
   return build_bins(h);
 }
 
+int rod_set_adjoint_record_budget(rod_handle h, long long bytes) {
+  if (int rc = check_handle(h)) return rc;
+  if (bytes < 0) return fail(CORDE_ERR_ARG, "rod_set_adjoint_record_budget: bytes must be >= 0");
+  h->adj_record_budget = bytes;
+  return CORDE_OK;
+}
+
 int rod_set_launch_overlap(rod_handle h, int enable) {
   if (int rc = check_handle(h)) return rc;
   if (enable != 0 && enable != 1) return fail(CORDE_ERR_ARG, "rod_set_launch_overlap: enable must be 0 or 1");
@@ -1323,11 +1335,34 @@ int rod_adjoint(rod_handle h, const float* dL_dpos_traj, float* dL_dK, float* dL
   }
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t E = h->n_elem;
-  if (int rc = ensure_capacity(&h->d_seg, &h->seg_cap, (size_t)h->ro_every * 4 * E)) return rc;
   if (int rc = build_adjoint_bins(h)) return rc;
   int dev = 0, smem_max = 0;
   CK(cudaGetDevice(&dev));
   CK(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  int iters = 0;
+  for (int r = 0; r < h->n_rods; ++r) iters = std::max(iters, h->n_iters[r]);
+  const int rec_iters = iters > 0 ? iters : 1;
+  // record mode per launch: two sweep buffers in shared memory and the scratch within budget
+  const size_t K = (size_t)h->ro_every;
+  std::vector<char> record(h->adj_bins.size(), 0);
+  size_t sweep_need = 0, nb_need = 0;
+  for (size_t i = 0; i < h->adj_bins.size(); ++i) {
+    const Bin& b = h->adj_bins[i];
+    const int nt = variants()[b.variant].nt;
+    const size_t sw = K * b.count * 2 * rec_iters * 2 * nt, nbn = K * b.count * 3 * nt;  // float4 entries
+    if (adjoint_smem_bytes(nt, iters, true) <= smem_max &&
+        (long long)((sw + nbn) * sizeof(float4)) <= h->adj_record_budget) {
+      record[i] = 1;
+      sweep_need = std::max(sweep_need, sw);
+      nb_need = std::max(nb_need, nbn);
+    }
+  }
+  const bool any_record = sweep_need > 0;
+  if (int rc = ensure_capacity(&h->d_seg, &h->seg_cap, (K + (any_record ? 1 : 0)) * 4 * E)) return rc;
+  if (any_record) {
+    if (int rc = ensure_capacity(&h->d_sweep_rec, &h->sweep_rec_cap, sweep_need)) return rc;
+    if (int rc = ensure_capacity(&h->d_nb_rec, &h->nb_rec_cap, nb_need)) return rc;
+  }
   AdjointArgs a;
   a.rods = h->d_rods;
   a.ckpt = h->d_ckpt;
@@ -1346,11 +1381,13 @@ int rod_adjoint(rod_handle h, const float* dL_dpos_traj, float* dL_dK, float* dL
   a.dquat0 = dev_out[4];
   a.domega0 = dev_out[5];
   int launches = 0;
-  for (const auto& b : h->adj_bins) {
-    int iters = 0;
-    for (int r = 0; r < h->n_rods; ++r) iters = std::max(iters, h->n_iters[r]);
+  for (size_t i = 0; i < h->adj_bins.size(); ++i) {
+    const Bin& b = h->adj_bins[i];
     const int nt = variants()[b.variant].nt;
-    const int smem = adjoint_smem_bytes(nt, iters);
+    const int smem = adjoint_smem_bytes(nt, iters, record[i] != 0);
+    a.sweep_rec = record[i] ? h->d_sweep_rec : nullptr;
+    a.nb_rec = record[i] ? h->d_nb_rec : nullptr;
+    a.rec_iters = rec_iters;
     if (smem > smem_max)
       return fail(CORDE_ERR_UNSUPPORTED, "adjoint needs " + std::to_string(smem) + " B of shared memory per block; " +
                                              std::to_string(smem_max) + " available (fewer constraint iterations " +
@@ -1558,6 +1595,7 @@ void rod_destroy(rod_handle h) {
   cudaFree(h->d_x); cudaFree(h->d_v); cudaFree(h->d_q); cudaFree(h->d_o); cudaFree(h->d_u); cudaFree(h->d_k);
   cudaFree(h->d_drive); cudaFree(h->d_elem_rod); cudaFree(h->d_drive_graph);
   cudaFree(h->d_ckpt); cudaFree(h->d_seg); cudaFree(h->d_self_stats);
+  cudaFree(h->d_sweep_rec); cudaFree(h->d_nb_rec);
   for (auto& b : h->adj_bins) cudaFree(b.d_work);
   for (auto& pb : h->pair_bins) cudaFree(pb.d_pairs);
   if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);

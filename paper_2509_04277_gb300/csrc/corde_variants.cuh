@@ -78,8 +78,18 @@ struct AdjointArgs {
   int n_steps, ckpt_every;
   int64_t n_elem;
   float4 *dpos0, *dvel0, *dquat0, *domega0, *dK, *duhat;
+  // Record mode (sweep_rec != NULL): the first pass over a checkpoint segment keeps, per
+  // step and block, the velocities before every constraint half-sweep
+  // (sweep_rec[(s gridDim + b) 2 rec_iters EPT NT ...]) and the neighbour data (nb_rec,
+  // 3 float4 per thread), and seg_states holds K + 1 states; the reverse pass then reads
+  // them instead of recomputing each step.  NULL: recompute mode.
+  float4* sweep_rec = nullptr;
+  float4* nb_rec = nullptr;
+  int rec_iters = 0;
 };
-int adjoint_smem_bytes(int nt, int n_iters);
+// Shared memory of the reverse kernel: parameters, exchange buffers and one (recompute
+// mode) or two (record mode: double-buffered copies) sweep-velocity buffers.
+int adjoint_smem_bytes(int nt, int n_iters, bool record = false);
 cudaError_t launch_adjoint(int nt, const AdjointArgs& a, int n_blocks, int smem, cudaStream_t s);
 constexpr int kAdjointMaxNodes = 512;
 

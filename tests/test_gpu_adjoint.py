@@ -228,3 +228,37 @@ def test_adjoint_requires_rollout_and_rejects_long_rods(corde):
         corde.rod_adjoint(b.handle)
     assert e.value.code == corde.CORDE_ERR_UNSUPPORTED
     b.close()
+
+
+def test_record_and_recompute_modes_give_identical_gradients(corde):
+    """The reverse pass either keeps each segment's sweep velocities from one forward pass
+    (record mode, the default when the scratch fits) or runs every step forward again
+    (recompute mode, budget 0).  Several rods of ragged lengths and different iteration
+    counts, a segment length that leaves a short last segment, and a 300-node rod whose
+    256-thread block has no room for two sweep buffers (recompute in both cases)."""
+    import dataclasses
+
+    import torch
+
+    rods = [dataclasses.replace(W.adjoint_rod(n, seed=970 + n), n_iters=it)
+            for n, it in ((7, 3), (33, 10), (100, 6), (256, 10))]
+    n_steps, ckpt = 47, 10
+    out = []
+    for budget in (64 << 20, 0):
+        for group in (rods, [W.adjoint_rod(300, seed=975)]):
+            b = corde.RodBatch(group)
+            b.set_adjoint_record_budget(budget)
+            traj = b.rollout(n_steps, ckpt)
+            g = torch.zeros_like(traj)
+            g[:, :, :3] = 1e-2 * torch.sin(traj[:, :, :3] * 37.0)
+            grads = b.adjoint(g)
+            out.append({k: v.cpu().numpy() for k, v in grads.items()})
+            b.close()
+    for a, c in ((out[0], out[2]), (out[1], out[3])):
+        for key in a:
+            assert np.isfinite(a[key]).all(), key
+            np.testing.assert_array_equal(a[key], c[key], err_msg=key)
+    h = corde.RodBatch(rods[:1])
+    with pytest.raises(corde.CordeError):
+        corde.rod_set_adjoint_record_budget(h.handle, -1)
+    h.close()
