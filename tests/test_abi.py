@@ -74,6 +74,8 @@ def test_argument_errors_are_reported_on_the_host(lib):
         corde.rod_create([good], None, quat)
     assert e.value.code == corde.CORDE_ERR_ARG
     assert lib.rod_step(None, 1, None, None) == corde.CORDE_ERR_ARG
+    assert lib.rod_set_launch_overlap(None, 1) == corde.CORDE_ERR_ARG
+    assert lib.rod_set_adjoint_record_budget(None, 0) == corde.CORDE_ERR_ARG
     assert lib.rod_strerror(corde.CORDE_ERR_NONFINITE) == b"non-finite state"
 
 
