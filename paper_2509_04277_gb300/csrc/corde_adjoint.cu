@@ -456,58 +456,111 @@ adjoint_kernel(AdjointArgs a) {
       }
     }
     // reverse the segment's steps
-    for (int s = cnt - 1; s >= 0; --s) {
-      const float4* st = a.seg_states + (int64_t)s * 4 * E + R.off;
-      float3 r_in[EPT], om_in[EPT];
-      float4 q_in[EPT];
+    if constexpr (RECORD) {
+      // Each step's inputs are loaded one step ahead, while the step before is reversed:
+      // the state before it, its neighbour data and the loss gradient after it.  The frame
+      // and angular velocity after step s are the state before step s + 1.
+      float3 pr[EPT], pom[EPT], pg[EPT];
+      float4 pq[EPT], pn0, pn1, pn2;
+      float4 nq[EPT];
+      float3 nom[EPT];
+      auto prefetch = [&](int s) {
+        const float4* st = a.seg_states + (int64_t)s * 4 * E + R.off;
 #pragma unroll
-      for (int e = 0; e < EPT; ++e) {
-        if (e0 + e < R.n) {
-          r[e] = f3(st[e0 + e]);
-          v[e] = f3(st[E + e0 + e]);
-          q[e] = st[2 * E + e0 + e];
-          om[e] = f3(st[3 * E + e0 + e]);
-        }
-        r_in[e] = r[e];
-        q_in[e] = q[e];
-        om_in[e] = om[e];
-      }
-      StepNeighbours nb;
-      const float4* sweep = sweep_v;
-      if constexpr (RECORD) {
-        // the step's end state (frame and angular velocity after it), neighbour data and
-        // sweeps; the copy of step s - 1's sweeps starts once every thread is done with
-        // the buffer it reuses (step s + 1's)
-        const float4* sn = a.seg_states + (int64_t)(s + 1) * 4 * E + R.off;
-#pragma unroll
-        for (int e = 0; e < EPT; ++e)
+        for (int e = 0; e < EPT; ++e) {
+          pg[e] = zero3();
           if (e0 + e < R.n) {
-            q[e] = sn[2 * E + e0 + e];
-            om[e] = f3(sn[3 * E + e0 + e]);
+            pr[e] = f3(st[e0 + e]);
+            pq[e] = st[2 * E + e0 + e];
+            pom[e] = f3(st[3 * E + e0 + e]);
+            if (a.dLdpos != nullptr) pg[e] = f3(a.dLdpos[(int64_t)(t0 + s) * E + R.off + e0 + e]);
           }
+        }
         const float4* nr = nb_at(s);
-        const float4 a0 = nr[0], a1 = nr[NT];
-        nb.r_next = f3(a0);
-        nb.w_next = a0.w;
-        nb.r_prev = f3(a1);
-        nb.w_prev = a1.w;
-        nb.q_next = nr[2 * NT];
+        pn0 = nr[0];
+        pn1 = nr[NT];
+        pn2 = nr[2 * NT];
+      };
+      {
+        const float4* sn = a.seg_states + (int64_t)cnt * 4 * E + R.off;
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) {
+          nq[e] = q[e];
+          nom[e] = om[e];
+          if (e0 + e < R.n) {
+            nq[e] = sn[2 * E + e0 + e];
+            nom[e] = f3(sn[3 * E + e0 + e]);
+          }
+        }
+      }
+      prefetch(cnt - 1);
+      for (int s = cnt - 1; s >= 0; --s) {
+        float3 r_in[EPT], om_in[EPT];
+        float4 q_in[EPT];
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) {
+          if (e0 + e < R.n) {
+            r[e] = pr[e];
+            q[e] = pq[e];
+            om[e] = pom[e];
+          }
+          r_in[e] = r[e];
+          q_in[e] = q[e];
+          om_in[e] = om[e];
+          if (a.dLdpos != nullptr && e0 + e < R.n) rb[e] += pg[e];  // loss gradient after this step
+          if (e0 + e < R.n) {
+            q[e] = nq[e];
+            om[e] = nom[e];
+          }
+          nq[e] = q_in[e];
+          nom[e] = om_in[e];
+        }
+        StepNeighbours nb;
+        nb.r_next = f3(pn0);
+        nb.w_next = pn0.w;
+        nb.r_prev = f3(pn1);
+        nb.w_prev = pn1.w;
+        nb.q_next = pn2;
+        // step s's sweeps; the copy of step s - 1's starts once every thread is done with
+        // the buffer it reuses (step s + 1's)
         cp_async_wait_all();
         block_sync<NT>();
-        if (s > 0) fetch(s - 1, sweep_v + ((s - 1) & 1) * rec_stride);
-        sweep = sweep_v + (s & 1) * rec_stride;
-      } else {
-        step_body<EPT, NT, true>(R, H, r, v, q, om, w, par_u, par_k, halo, xc, v_drive, w_drive, sweep_v, &nb);
+        if (s > 0) {
+          fetch(s - 1, sweep_v + ((s - 1) & 1) * rec_stride);
+          prefetch(s - 1);
+        }
+        reverse_step<EPT, NT>(R, t, r_in, q_in, om_in, w, om, q, nb, par_u, par_k, halo, xc,
+                              sweep_v + (s & 1) * rec_stride, rb, vb, qb, ob, Kb, ub);
       }
-      // loss gradient with respect to the positions after this step
-      if (a.dLdpos != nullptr) {
-        const float4* g = a.dLdpos + (int64_t)(t0 + s) * E + R.off;
+    } else {
+      for (int s = cnt - 1; s >= 0; --s) {
+        const float4* st = a.seg_states + (int64_t)s * 4 * E + R.off;
+        float3 r_in[EPT], om_in[EPT];
+        float4 q_in[EPT];
 #pragma unroll
-        for (int e = 0; e < EPT; ++e)
-          if (e0 + e < R.n) rb[e] += f3(g[e0 + e]);
+        for (int e = 0; e < EPT; ++e) {
+          if (e0 + e < R.n) {
+            r[e] = f3(st[e0 + e]);
+            v[e] = f3(st[E + e0 + e]);
+            q[e] = st[2 * E + e0 + e];
+            om[e] = f3(st[3 * E + e0 + e]);
+          }
+          r_in[e] = r[e];
+          q_in[e] = q[e];
+          om_in[e] = om[e];
+        }
+        StepNeighbours nb;
+        step_body<EPT, NT, true>(R, H, r, v, q, om, w, par_u, par_k, halo, xc, v_drive, w_drive, sweep_v, &nb);
+        // loss gradient with respect to the positions after this step
+        if (a.dLdpos != nullptr) {
+          const float4* g = a.dLdpos + (int64_t)(t0 + s) * E + R.off;
+#pragma unroll
+          for (int e = 0; e < EPT; ++e)
+            if (e0 + e < R.n) rb[e] += f3(g[e0 + e]);
+        }
+        reverse_step<EPT, NT>(R, t, r_in, q_in, om_in, w, om, q, nb, par_u, par_k, halo, xc, sweep_v, rb, vb, qb, ob,
+                              Kb, ub);
       }
-      reverse_step<EPT, NT>(R, t, r_in, q_in, om_in, w, om, q, nb, par_u, par_k, halo, xc, sweep, rb, vb, qb, ob,
-                            Kb, ub);
     }
   }
 #pragma unroll
