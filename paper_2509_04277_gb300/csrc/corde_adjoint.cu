@@ -533,30 +533,48 @@ adjoint_kernel(AdjointArgs a) {
                               sweep_v + (s & 1) * rec_stride, rb, vb, qb, ob, Kb, ub);
       }
     } else {
-      for (int s = cnt - 1; s >= 0; --s) {
+      // each step's state and loss gradient loaded one step ahead, as in record mode
+      float3 pr[EPT], pv[EPT], pom[EPT], pg[EPT];
+      float4 pq[EPT];
+      auto prefetch = [&](int s) {
         const float4* st = a.seg_states + (int64_t)s * 4 * E + R.off;
-        float3 r_in[EPT], om_in[EPT];
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) {
+          pg[e] = zero3();
+          if (e0 + e < R.n) {
+            pr[e] = f3(st[e0 + e]);
+            pv[e] = f3(st[E + e0 + e]);
+            pq[e] = st[2 * E + e0 + e];
+            pom[e] = f3(st[3 * E + e0 + e]);
+            if (a.dLdpos != nullptr) pg[e] = f3(a.dLdpos[(int64_t)(t0 + s) * E + R.off + e0 + e]);
+          }
+        }
+      };
+      prefetch(cnt - 1);
+      for (int s = cnt - 1; s >= 0; --s) {
+        float3 r_in[EPT], om_in[EPT], g_s[EPT];
         float4 q_in[EPT];
 #pragma unroll
         for (int e = 0; e < EPT; ++e) {
           if (e0 + e < R.n) {
-            r[e] = f3(st[e0 + e]);
-            v[e] = f3(st[E + e0 + e]);
-            q[e] = st[2 * E + e0 + e];
-            om[e] = f3(st[3 * E + e0 + e]);
+            r[e] = pr[e];
+            v[e] = pv[e];
+            q[e] = pq[e];
+            om[e] = pom[e];
           }
           r_in[e] = r[e];
           q_in[e] = q[e];
           om_in[e] = om[e];
+          g_s[e] = pg[e];
         }
+        if (s > 0) prefetch(s - 1);
         StepNeighbours nb;
         step_body<EPT, NT, true>(R, H, r, v, q, om, w, par_u, par_k, halo, xc, v_drive, w_drive, sweep_v, &nb);
         // loss gradient with respect to the positions after this step
         if (a.dLdpos != nullptr) {
-          const float4* g = a.dLdpos + (int64_t)(t0 + s) * E + R.off;
 #pragma unroll
           for (int e = 0; e < EPT; ++e)
-            if (e0 + e < R.n) rb[e] += f3(g[e0 + e]);
+            if (e0 + e < R.n) rb[e] += g_s[e];
         }
         reverse_step<EPT, NT>(R, t, r_in, q_in, om_in, w, om, q, nb, par_u, par_k, halo, xc, sweep_v, rb, vb, qb, ob,
                               Kb, ub);
