@@ -748,10 +748,10 @@ def main_ours(args):
                     "d2h_bytes_per_step": 512 * 16 * LAUNCHES_PER_BENCH_STEP,
                     "path": e2e_path,
                     "what": {"lockstep_persistent": "one persistent launch in lock-step (rod_step once; per tick "
-                                                    "rod_mailbox_write and rod_mailbox_positions): the host writes "
-                                                    "the drive, the kernel (waiting for it) runs 10 steps and "
-                                                    "publishes all 512 positions to pinned host memory, the host "
-                                                    "reads them; host wall clock",
+                                                    "rod_mailbox_write, then rod_mailbox_positions until the tick's "
+                                                    "snapshot): the host writes the drive, the kernel (waiting for "
+                                                    "it) runs 10 steps and publishes all 512 positions to pinned "
+                                                    "host memory, the host copies them; host wall clock",
                              "launch_per_tick": "per tick one rod_step_io call (the kernel reads the drive from "
                                                 "pinned host memory and writes the 512 positions to pinned host "
                                                 "memory) + stream sync; host wall clock"}[e2e_path],

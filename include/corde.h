@@ -287,6 +287,15 @@ int rod_mailbox_lockstep(rod_handle h, int enable, int timeout_us);
 /* Mailbox status word, cleared by the read: bit 0 = a lock-step wait ran out. */
 int rod_mailbox_status(rod_handle h, unsigned* status);
 int rod_mailbox_positions(rod_handle h, int rod, float* out, long long* step);
+/* One tick of a haptic loop in one call: writes drive (as rod_mailbox_write; NULL: no
+ * write), then spins on the host until rod `rod`'s newest position snapshot was taken
+ * after a global step >= target_step, and copies it as rod_mailbox_positions does (out
+ * [N][4] host floats, *step its step).  Only the snapshot header is polled while waiting.
+ * Errors: CORDE_ERR_ARG (NULL out or step, snapshots not enabled, bad rod, timeout_us <
+ * 0); CORDE_ERR_BUSY when timeout_us microseconds pass first or the mailbox status shows
+ * that a lock-step wait of the kernel ran out (the status word is left set). */
+int rod_mailbox_exchange(rod_handle h, const float* drive, int rod, long long target_step, float* out,
+                         long long timeout_us, long long* step);
 int64_t rod_steps_done(rod_handle h);
 
 /* Number of kernel launches the last rod_step enqueued (kernel nodes of the graph when

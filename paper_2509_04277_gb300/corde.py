@@ -76,6 +76,7 @@ SIGNATURES = {
     "rod_mailbox_disable": (ctypes.c_int, [_VP]),
     "rod_mailbox_positions_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
     "rod_mailbox_positions": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP]),
+    "rod_mailbox_exchange": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_longlong, _VP, ctypes.c_longlong, _VP]),
     "rod_mailbox_lockstep": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
     "rod_mailbox_status": (ctypes.c_int, [_VP, _VP]),
     "rod_steps_done": (ctypes.c_int64, [_VP]),
@@ -292,6 +293,17 @@ def rod_mailbox_positions(h, rod, out):
     array); returns the global step it was taken after (-1: none yet)."""
     step = ctypes.c_longlong(0)
     _check(load().rod_mailbox_positions(h, int(rod), _ptr(out), ctypes.addressof(step)), "rod_mailbox_positions")
+    return int(step.value)
+
+
+def rod_mailbox_exchange(h, drive, rod, target_step, out, timeout_us=1_000_000):
+    """One haptic tick: writes drive (None: no write), waits until rod `rod`'s snapshot of a
+    step >= target_step is published, copies it into out ([N, 4] float32 host array) and
+    returns its step."""
+    d = None if drive is None else np.ascontiguousarray(drive, dtype=np.float32)
+    step = ctypes.c_longlong(0)
+    _check(load().rod_mailbox_exchange(h, None if d is None else d.ctypes.data, int(rod), int(target_step), _ptr(out),
+                                       int(timeout_us), ctypes.addressof(step)), "rod_mailbox_exchange")
     return int(step.value)
 
 

@@ -1,6 +1,7 @@
 // C ABI of the CoRdE stepper: creation (derived constants and packing on the device),
 // kernel-variant plans, the persistent step launches, state I/O and diagnostics.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -1518,6 +1519,46 @@ int rod_mailbox_positions(rod_handle h, int rod, float* out, long long* step) {
     }
   }
   return fail(CORDE_ERR_BUSY, "rod_mailbox_positions: no consistent snapshot after 10000 attempts");
+}
+
+constexpr long long kExchangePollNs = 300;  // host poll interval of rod_mailbox_exchange
+
+int rod_mailbox_exchange(rod_handle h, const float* drive, int rod, long long target_step, float* out,
+                         long long timeout_us, long long* step) {
+  if (!h || !out || !step) return fail(CORDE_ERR_ARG, "rod_mailbox_exchange: NULL argument");
+  if (!h->mb_pos_host) return fail(CORDE_ERR_ARG, "rod_mailbox_exchange: position snapshots not enabled");
+  if (rod < 0 || rod >= h->n_rods) return fail(CORDE_ERR_ARG, "rod_mailbox_exchange: bad rod");
+  if (timeout_us < 0) return fail(CORDE_ERR_ARG, "rod_mailbox_exchange: timeout_us must be >= 0");
+  if (drive)
+    if (int rc = rod_mailbox_write(h, drive)) return rc;
+  // spin on the rod's publication count and the newest slot's step only; copy once
+  const unsigned* hdr = static_cast<const unsigned*>(h->mb_pos_host) + 32 * (size_t)rod;
+  const unsigned* status = static_cast<const unsigned*>(h->mb_out_host) + (size_t)h->n_rods * 16;
+  const auto t0 = std::chrono::steady_clock::now();
+  for (unsigned long long k = 0;; ++k) {
+    const unsigned pubs = __atomic_load_n(&hdr[0], __ATOMIC_ACQUIRE);
+    if (pubs > 0u) {
+      const unsigned p = pubs - 1u;
+      const unsigned* sh = hdr + 4 + 4 * (p % kPosSlots);
+      const unsigned s1 = __atomic_load_n(&sh[0], __ATOMIC_ACQUIRE);
+      if (s1 == 2u * p + 2u) {
+        const unsigned lo = __atomic_load_n(&sh[1], __ATOMIC_RELAXED), hi = __atomic_load_n(&sh[2], __ATOMIC_RELAXED);
+        if ((long long)(((unsigned long long)hi << 32) | lo) >= target_step)
+          return rod_mailbox_positions(h, rod, out, step);
+      }
+    }
+    if ((k & 63u) == 63u) {
+      if (__atomic_load_n(status, __ATOMIC_ACQUIRE) != 0u)
+        return fail(CORDE_ERR_BUSY, "rod_mailbox_exchange: a lock-step wait of the kernel ran out");
+      const long long us =
+          std::chrono::duration_cast<std::chrono::microseconds>(std::chrono::steady_clock::now() - t0).count();
+      if (us > timeout_us) return fail(CORDE_ERR_BUSY, "rod_mailbox_exchange: no snapshot of the target step in time");
+    }
+    // back off between polls without touching the shared lines
+    const auto tp = std::chrono::steady_clock::now();
+    while (std::chrono::steady_clock::now() - tp < std::chrono::nanoseconds(kExchangePollNs)) {
+    }
+  }
 }
 
 int rod_mailbox_disable(rod_handle h) {

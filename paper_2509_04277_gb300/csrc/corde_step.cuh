@@ -656,17 +656,11 @@ struct RodMailbox {
     return false;
   }
 
-  // After step `step`: feedback records and the position snapshot.
+  // After step `step`: the position snapshot, then the feedback records.
   template <class Halo>
   __device__ __forceinline__ void after_step(const Halo& H, int step, const float3 (&r)[EPT], const float3 (&v)[EPT],
                                              const float (&w)[EPT]) {
     if (mb.period <= 0 || (step + 1) % mb.period != 0) return;
-    if (owns_base) mailbox_write(rec_base, seq_base, mb.step0 + step + 1, r[0], v[0]);
-    if (owns_tip) {
-#pragma unroll
-      for (int e = 0; e < EPT; ++e)
-        if (e0 + e == R.n - 1) mailbox_write(rec_tip, seq_tip, mb.step0 + step + 1, r[e], v[e]);
-    }
     if (mb.pos != nullptr) {
       // snapshot p of every position into ring slot p % kPosSlots, under the slot's
       // seqlock (2p + 1 while the rod's threads write, barrier-ordered after the first
@@ -700,6 +694,13 @@ struct RodMailbox {
         st_release_sys(hdr, seq_pos + 1u);
       }
       ++seq_pos;
+    }
+    // base and tip records after the snapshot: their fences do not delay it
+    if (owns_base) mailbox_write(rec_base, seq_base, mb.step0 + step + 1, r[0], v[0]);
+    if (owns_tip) {
+#pragma unroll
+      for (int e = 0; e < EPT; ++e)
+        if (e0 + e == R.n - 1) mailbox_write(rec_tip, seq_tip, mb.step0 + step + 1, r[e], v[e]);
     }
   }
 };

@@ -254,3 +254,39 @@ def test_lockstep_pair_with_moving_binding_offset(corde):
     corde.rod_mailbox_disable(a.handle)
     a.close()
     b.close()
+
+
+def test_exchange_ticks_replay_exactly_and_report_a_lost_wait(corde):
+    """rod_mailbox_exchange (one call per tick: write the drive, wait for the snapshot of
+    the tick's last step, copy it) drives a lock-step launch; every snapshot equals the
+    positions of ordinary 10-step launches with the same drives.  Then the host stops
+    sending: the kernel's 20 ms wait runs out, and the next exchange reports it."""
+    import torch
+
+    rod = W.guidewire(512, seed=660)
+    a, b = corde.RodBatch([rod]), corde.RodBatch([rod])
+    corde.rod_mailbox_enable(a.handle, 10, 64)
+    corde.rod_mailbox_positions_enable(a.handle)
+    corde.rod_mailbox_lockstep(a.handle, True, 20_000)
+    drives = W.sinusoid_drive(661, 15, 10 * rod.dt).astype(np.float32)
+    base = corde.rod_steps_done(a.handle)
+    out = np.zeros((512, 4), np.float32)
+    snaps = []
+    a.step(400)  # 40 ticks' worth; the host stops after 15
+    for k in range(15):
+        got = corde.rod_mailbox_exchange(a.handle, drives[k].reshape(1, 8), 0, base + 10 * (k + 1), out, 5_000_000)
+        assert got == base + 10 * (k + 1)
+        snaps.append(out.copy())
+    with pytest.raises(corde.CordeError):
+        corde.rod_mailbox_exchange(a.handle, None, 0, base + 10 * 16, out, 5_000_000)
+    torch.cuda.synchronize()
+    assert corde.rod_mailbox_status(a.handle) & 1
+    for k in range(15):
+        b.set_input(drives[k].reshape(1, 8))
+        b.step(10)
+        np.testing.assert_array_equal(snaps[k], b.state_numpy()["pos4"])
+    with pytest.raises(corde.CordeError):
+        corde.rod_mailbox_exchange(a.handle, None, 0, 0, out, -1)
+    corde.rod_mailbox_disable(a.handle)
+    a.close()
+    b.close()
