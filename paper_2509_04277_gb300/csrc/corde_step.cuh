@@ -69,6 +69,10 @@ struct BlockHalo {
     return f3(f[0], f[NT], f[2 * NT]);
   }
   __device__ __forceinline__ void sync() const { block_sync<SYNC_NT>(); }
+  // a barrier in two halves (arrive after the exchange stores, wait before the neighbour
+  // loads); one block has no split barrier, so the wait is the whole barrier
+  __device__ __forceinline__ void arrive() const {}
+  __device__ __forceinline__ void wait() const { block_sync<SYNC_NT>(); }
   // block-wide OR of x (a barrier)
   __device__ __forceinline__ int any(int x) const {
     if constexpr (SYNC_NT == 32) {
@@ -107,6 +111,9 @@ struct ClusterHalo {
   __device__ __forceinline__ float3 next3(const float4* hb, int slot) const { return f3(next(hb, slot)); }
   __device__ __forceinline__ float3 prev3(const float4* hb, int slot) const { return f3(prev(hb, slot)); }
   __device__ __forceinline__ void sync() const { cooperative_groups::this_cluster().sync(); }
+  // the cluster barrier in two halves: thread-local work between them overlaps its latency
+  __device__ __forceinline__ void arrive() const { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
+  __device__ __forceinline__ void wait() const { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
 };
 
 // Bend/twist torques of the joint between frames a and b (Eq. 3): with
@@ -283,6 +290,7 @@ __device__ __forceinline__ void step_body(const RodDev& R, const Halo& H, float3
   hb[t] = make_float4(r[0].x, r[0].y, r[0].z, w[0]);
   hb[NT + t] = q[0];
   hb[2 * NT + t] = make_float4(r[EPT - 1].x, r[EPT - 1].y, r[EPT - 1].z, w[EPT - 1]);
+  H.arrive();
 
   // ---- elastic forces and torques.  Joint j couples frames j and j + 1, segment j nodes
   // j and j + 1 (with frame j); all but the thread's last joint and segment are local, and
@@ -321,7 +329,7 @@ __device__ __forceinline__ void step_body(const RodDev& R, const Halo& H, float3
 #pragma unroll
   for (int e = 0; e + 1 < EPT; ++e) joint_and_segment(e, q[e + 1], r[e + 1]);
 
-  H.sync();
+  H.wait();
   float3 r_next = zero3(), r_prev = zero3();
   float w_next = 0.f, w_prev = 0.f;
   float4 q_next = make_float4(0.f, 0.f, 0.f, 1.f);
@@ -351,15 +359,11 @@ __device__ __forceinline__ void step_body(const RodDev& R, const Halo& H, float3
   ++xc;
   H.put3(hb, 0, F_carry);
   H.put3(hb, 1, tau_carry);
-  H.sync();
-  if (has_prev) {
-    F[0] += H.prev3(hb, 0);
-    tau[0] += H.prev3(hb, 1);
-  }
+  H.arrive();
 
-  // ---- integrate forces and torques into velocities
-#pragma unroll
-  for (int e = 0; e < EPT; ++e) {
+  // ---- integrate forces and torques into velocities; on a cluster, elements 1 .. EPT - 1
+  // (they take no carry) run while the exchange barrier completes
+  auto integrate = [&](int e) {
     const int i = e0 + e;
     if (w[e] > 0.f) {
       const float3 a = f3(w[e] * F[e].x + R.gx, w[e] * F[e].y + R.gy, w[e] * F[e].z + R.gz);
@@ -373,6 +377,21 @@ __device__ __forceinline__ void step_body(const RodDev& R, const Halo& H, float3
       const float3 on = f3(o.x + dt * R.Jinv1 * rhs.x, o.y + dt * R.Jinv1 * rhs.y, o.z + dt * R.Jinv3 * rhs.z);
       om[e] = R.damp * on;
     }
+  };
+  if constexpr (Halo::kCluster) {
+#pragma unroll
+    for (int e = 1; e < EPT; ++e) integrate(e);
+  }
+  H.wait();
+  if (has_prev) {
+    F[0] += H.prev3(hb, 0);
+    tau[0] += H.prev3(hb, 1);
+  }
+  if constexpr (Halo::kCluster) {
+    integrate(0);
+  } else {
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) integrate(e);
   }
   if (clamp && e0 == 0) {
     v[0] = v_drive;
@@ -450,6 +469,7 @@ __device__ __forceinline__ void step_body(const RodDev& R, const Halo& H, float3
       ++xc;
       H.put3(hb, 0, v[0]);
       H.put3(hb, 1, v[EPT - 1]);
+      H.arrive();
       // odd segments inside the thread: they move elements 1 .. EPT - 2 only, which the
       // exchange and the boundary segments do not read, so they run while the barrier waits
 #pragma unroll
@@ -459,7 +479,7 @@ __device__ __forceinline__ void step_body(const RodDev& R, const Halo& H, float3
         v[a] -= w[a] * g;
         v[b] += w[b] * g;
       }
-      H.sync();
+      H.wait();
       // odd segments across the two thread boundaries, in one packed evaluation
       {
         const float3 vn = has_next ? H.next3(hb, 0) : zero3();
