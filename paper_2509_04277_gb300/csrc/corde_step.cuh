@@ -695,15 +695,10 @@ struct RodMailbox {
       H.sync();
       // system-scope stores (volatile), ordered before the first thread's release by the
       // barrier (release/acquire among the rod's threads) and its system-scope fence
-      volatile float4* dst = mb.pos + slot * mb.n_elem + R.off;
+      float4* dst = mb.pos + slot * mb.n_elem + R.off;
 #pragma unroll
       for (int e = 0; e < EPT; ++e)
-        if (e0 + e < R.n) {
-          dst[e0 + e].x = r[e].x;
-          dst[e0 + e].y = r[e].y;
-          dst[e0 + e].z = r[e].z;
-          dst[e0 + e].w = w[e];
-        }
+        if (e0 + e < R.n) st_volatile_f4(dst + e0 + e, make_float4(r[e].x, r[e].y, r[e].z, w[e]));
       H.sync();
       if (owns_base) {
         fence_acq_rel_sys();
