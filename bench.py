@@ -734,14 +734,9 @@ def main_ours(args):
             "vs_baseline": round(value / 32.0, 5),
             "dtype": "f32",
             "data": "synthetic (seeded guidewire, 1 kHz sinusoidal insertion/twist drive)",
-            "config": {
-                "workload": "guidewire: 1 inextensible rod, 512 elements, L=1.5 m, r=0.45 mm, E=60 GPa, "
-                            "10 constraint iterations, dt=1e-4 s, 10 time steps per persistent launch",
-                "n_rods": 1, "n_elements": 512, "steps_per_launch": STEPS_PER_LAUNCH,
-                "time_steps_per_bench_step": STEPS_PER_LAUNCH * LAUNCHES_PER_BENCH_STEP,
-                "l2": "flushed (256 MiB write) between bench steps, outside the timed intervals",
-                "parallelism": f"replicas x{world}" if world > 1 else "single GPU, one thread block per rod",
-            },
+            "config": dict(workload_config(),
+                           l2="flushed (256 MiB write) between bench steps, outside the timed intervals",
+                           parallelism=f"replicas x{world}" if world > 1 else "single GPU, one thread block per rod"),
             "gpu_launches": single["launches"],
             "e2e": {"value": round(e2e, 4), "unit": UNIT,
                     "h2d_bytes_per_step": 32 * LAUNCHES_PER_BENCH_STEP,
@@ -838,6 +833,16 @@ def main_ours(args):
 # --------------------------------------------------------------------------- reference arm
 
 
+def workload_config():
+    """The bench workload, the same for both arms."""
+    return {
+        "workload": "guidewire: 1 inextensible rod, 512 elements, L=1.5 m, r=0.45 mm, E=60 GPa, "
+                    "10 constraint iterations, dt=1e-4 s, 10 time steps per persistent launch",
+        "n_rods": 1, "n_elements": 512, "steps_per_launch": STEPS_PER_LAUNCH,
+        "time_steps_per_bench_step": STEPS_PER_LAUNCH * LAUNCHES_PER_BENCH_STEP,
+    }
+
+
 def main_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -867,8 +872,7 @@ def main_reference(args):
         "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(el * 1e3 / args.steps, 4),
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "guidewire: 1 inextensible rod, 512 elements, 10 constraint iterations, dt=1e-4 s, "
-                               "10 time steps per call", "time_steps_per_bench_step": steps_per_bench},
+        "config": dict(workload_config(), parallelism="oracle on 1 host core, 10 time steps per call"),
         "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"{args.steps} x {steps_per_bench} time steps of the 512-element guidewire"},
         "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
