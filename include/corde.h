@@ -278,11 +278,11 @@ int rod_mailbox_positions_enable(rod_handle h, int enable);
 /* Lock-step haptic loop (enable != 0): at every poll point (every `period` steps) the
  * thread owning a rod's base waits for a new input instead of skipping when there is
  * none, so each input drives exactly the next `period` steps; the rod's other threads
- * wait at a block barrier.  The wait is bounded by timeout_us of GPU time (checked with
- * the GPU's global timer, backing off between reads); when it runs out the launch stops
- * stepping at that point, stores its state and sets bit 0 of the mailbox status.  The
- * host still counts the launch's n_steps in rod_steps_done.  Single-block rods only
- * (CORDE_ERR_UNSUPPORTED for a rod planned on a cluster).  Synchronous. */
+ * wait at a block barrier (a cluster barrier for a rod on a cluster).  The wait is
+ * bounded by timeout_us of GPU time (checked with the GPU's global timer, backing off
+ * between reads); when it runs out the launch stops stepping at that point, stores its
+ * state and sets bit 0 of the mailbox status.  The host still counts the launch's n_steps
+ * in rod_steps_done.  Synchronous. */
 int rod_mailbox_lockstep(rod_handle h, int enable, int timeout_us);
 /* Mailbox status word, cleared by the read: bit 0 = a lock-step wait ran out. */
 int rod_mailbox_status(rod_handle h, unsigned* status);

@@ -1449,11 +1449,6 @@ int rod_mailbox_lockstep(rod_handle h, int enable, int timeout_us) {
   if (int rc = check_handle(h)) return rc;
   if (h->mb_period <= 0) return fail(CORDE_ERR_ARG, "rod_mailbox_lockstep: mailbox not enabled");
   if (enable && timeout_us < 1) return fail(CORDE_ERR_ARG, "rod_mailbox_lockstep: timeout_us >= 1");
-  if (enable)
-    for (int r = 0; r < h->n_rods; ++r)
-      if (h->plan_cluster[r] > 0)
-        return fail(CORDE_ERR_UNSUPPORTED, "rod_mailbox_lockstep: single-block rods only (rod " + std::to_string(r) +
-                                               " runs on a cluster)");
   CK(cudaDeviceSynchronize());
   h->mb_dev.lockstep = enable ? 1 : 0;
   h->mb_dev.wait_ns = enable ? (unsigned long long)timeout_us * 1000ull : 0ull;

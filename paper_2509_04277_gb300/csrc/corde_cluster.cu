@@ -30,9 +30,7 @@ cluster_step_kernel(const RodDev* __restrict__ rods, const int* __restrict__ wor
   const int rid = work[blockIdx.x / C];
   const RodDev R = rods[rid];
   const ClusterHalo<NT> H{(int)threadIdx.x, c, C};
-  MailboxDev m = mb;
-  m.lockstep = 0;  // lock-step is for single-block rods (the host refuses it for clusters)
-  run_rod<EPT, NT>(R, H, rid, x4, x4, v4, q4, o4, u4, k4, drive, n_steps, traj, n_elem, m, smem, pos_out);
+  run_rod<EPT, NT>(R, H, rid, x4, x4, v4, q4, o4, u4, k4, drive, n_steps, traj, n_elem, mb, smem, pos_out);
   // no block leaves while a neighbour may still read its exchange buffer
   cluster.sync();
 }

@@ -111,6 +111,20 @@ struct ClusterHalo {
   __device__ __forceinline__ float3 next3(const float4* hb, int slot) const { return f3(next(hb, slot)); }
   __device__ __forceinline__ float3 prev3(const float4* hb, int slot) const { return f3(prev(hb, slot)); }
   __device__ __forceinline__ void sync() const { cooperative_groups::this_cluster().sync(); }
+  // OR of x over the rod's threads on all C blocks (a block-wide OR, each block's result
+  // in its shared memory, read by every thread through distributed shared memory between
+  // two cluster barriers)
+  __device__ __forceinline__ int any(int x) const {
+    __shared__ int block_or;
+    const int b = __syncthreads_or(x);
+    if (t == 0) block_or = b;
+    cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
+    cl.sync();
+    int r = 0;
+    for (int k = 0; k < C; ++k) r |= *cl.map_shared_rank(&block_or, k);
+    cl.sync();
+    return r;
+  }
   // the cluster barrier in two halves: thread-local work between them overlaps its latency
   __device__ __forceinline__ void arrive() const { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
   __device__ __forceinline__ void wait() const { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
@@ -663,14 +677,12 @@ struct RodMailbox {
   __device__ __forceinline__ bool before_step(const Halo& H, int step, float3& vd, float3& wd,
                                               float* slot3 = nullptr) {
     if (mb.period <= 0 || step % mb.period != 0) return false;
-    if constexpr (!Halo::kCluster) {
-      if (mb.lockstep) {
-        // lock-step: the base's thread waits (bounded) for the next input; the block waits
-        // at the OR and leaves together if the wait ran out
-        int lost = 0;
-        if (owns_base) lost = !mailbox_wait(mb, rid, last, vd, wd, mb.step0 + step, slot3);
-        return H.any(lost) != 0;
-      }
+    if (mb.lockstep) {
+      // lock-step: the base's thread waits (bounded) for the next input; the rod's other
+      // threads wait at the OR (block or cluster) and all leave together if it ran out
+      int lost = 0;
+      if (owns_base) lost = !mailbox_wait(mb, rid, last, vd, wd, mb.step0 + step, slot3);
+      return H.any(lost) != 0;
     }
     if (owns_base && mailbox_poll(mb, rid, last, vd, wd, slot3)) mailbox_log(mb, mb.step0 + step, last);
     return false;

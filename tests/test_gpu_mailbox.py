@@ -207,13 +207,44 @@ def test_lockstep_wait_runs_out_cleanly(corde):
     corde.rod_mailbox_disable(a.handle)
     a.step(10)  # the context is fine
     torch.cuda.synchronize()
-    long_rod = corde.RodBatch([W.guidewire(3000, seed=641)])
-    corde.rod_mailbox_enable(long_rod.handle, 10, 64)
-    with pytest.raises(corde.CordeError):
-        corde.rod_mailbox_lockstep(long_rod.handle, True, 1000)
-    corde.rod_mailbox_disable(long_rod.handle)
-    long_rod.close()
     a.close()
+
+
+def test_lockstep_on_a_cluster_replays_exactly_and_runs_out_cleanly(corde):
+    """A 3000-node rod on a thread-block cluster in lock-step: the base's thread waits, the
+    other blocks wait at the cluster-wide OR.  Ten ticks equal ordinary 10-step launches
+    bit for bit; then no input comes, the wait runs out after 20 ms, every block leaves,
+    and the status reports it."""
+    import torch
+
+    rod = W.guidewire(3000, seed=641)
+    a, b = corde.RodBatch([rod]), corde.RodBatch([rod])
+    assert a.plan()[0][2] > 1  # on a cluster
+    corde.rod_mailbox_enable(a.handle, 10, 64)
+    corde.rod_mailbox_positions_enable(a.handle)
+    corde.rod_mailbox_lockstep(a.handle, True, 20_000)
+    drives = W.sinusoid_drive(642, 10, 10 * rod.dt).astype(np.float32)
+    base = corde.rod_steps_done(a.handle)
+    out = np.zeros((3000, 4), np.float32)
+    snaps = []
+    t0 = time.time()
+    a.step(300)  # 30 ticks' worth; the host stops after 10
+    for k in range(10):
+        got = corde.rod_mailbox_exchange(a.handle, drives[k].reshape(1, 8), 0, base + 10 * (k + 1), out, 5_000_000)
+        assert got == base + 10 * (k + 1)
+        snaps.append(out.copy())
+    torch.cuda.synchronize()
+    assert time.time() - t0 < 10.0
+    assert corde.rod_mailbox_status(a.handle) & 1
+    for k in range(10):
+        b.set_input(drives[k].reshape(1, 8))
+        b.step(10)
+        np.testing.assert_array_equal(snaps[k], b.state_numpy()["pos4"])
+    corde.rod_mailbox_disable(a.handle)
+    a.step(10)  # the context is fine
+    torch.cuda.synchronize()
+    a.close()
+    b.close()
 
 
 def test_lockstep_pair_with_moving_binding_offset(corde):
