@@ -7,11 +7,16 @@ instrument; metric "us/step 512-elem rod (10 steps/launch)").  One bench step is
 launches = 1000 time steps = 0.1 s of simulated time.  L2 is flushed (a 256 MiB write)
 between bench steps, outside the timed intervals.
 
-Also reported: ``e2e`` (the haptic loop through the C ABI with host buffers: per launch
-the drive goes host->device, 10 steps run, the node positions come back and the stream
-is synchronised), ``roofline`` of the step kernel, ``cpu_baseline`` (the FP64 oracle on
-the host cores, one core, as the paper's serial CPU version), and ``batched`` (4096
-rods of log-uniform length in [16, 2048], element-steps/s and its rooflines).
+Also reported: ``e2e`` (the haptic loop through the C ABI with host buffers, host wall
+clock: one persistent launch in lock-step; per tick the host writes the drive into
+mapped pinned memory, the kernel runs 10 steps and publishes all node positions to
+pinned host memory, the host copies them; beside it a launch per tick through
+rod_step_io, with explicit copies, and the asynchronous mailbox loop), ``latency``
+(against the measured empty-barrier floors, with and without launch overlap),
+``roofline`` of the step kernel, ``cpu_baseline`` (the FP64 oracle on the host cores,
+one core, as the paper's serial CPU version), ``batched`` (4096 rods of log-uniform
+length in [16, 2048], element-steps/s and its rooflines), ``adjoint`` (adjoint/forward
+time), ``pair``, ``long_rods``, ``vessel_contact`` and ``self_collision``.
 
 ``--impl reference`` times the FP64 CPU oracle on the same workload and metric.
 For N > 1 (torchrun) every rank runs its own replica of the single-rod workload and the
