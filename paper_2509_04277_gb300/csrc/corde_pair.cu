@@ -196,7 +196,7 @@ pair_kernel(const RodDev* __restrict__ rods, const int4* __restrict__ pairs, flo
   if constexpr (MB) {
     // beta is written by the inner rod's first thread only (here, and by its mailbox polls)
     if (group == 1 && t == 0) beta_sh = beta;
-    RodMailbox<EPT> box(mb, R, rid, t * EPT);
+    RodMailbox<EPT> box(mb, R, rid, t * EPT, NT, group);
     for (int step = 0; step < n_steps; ++step) {
       if (box.before_step(H, step, v_drive, w_drive, group == 1 ? &beta_sh : nullptr)) break;
       step_body<EPT, NT, false>(R, H, r, v, q, om, w, par_u, par_k, halo, xc, v_drive, w_drive, nullptr, nullptr,

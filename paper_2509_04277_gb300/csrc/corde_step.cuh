@@ -48,6 +48,7 @@ struct BlockHalo {
   static constexpr bool kCluster = false;
   int t;
   __device__ __forceinline__ int tg() const { return t; }
+  __device__ __forceinline__ int rod_threads() const { return NT; }
   __device__ __forceinline__ bool has_next() const { return t + 1 < NT; }
   __device__ __forceinline__ bool has_prev() const { return t > 0; }
   __device__ __forceinline__ float4 next(const float4* hb, int slot) const { return hb[slot * NT + t + 1]; }
@@ -92,6 +93,7 @@ struct ClusterHalo {
   static constexpr bool kCluster = true;
   int t, c, C;
   __device__ __forceinline__ int tg() const { return c * NT + t; }
+  __device__ __forceinline__ int rod_threads() const { return C * NT; }
   __device__ __forceinline__ bool has_next() const { return t + 1 < NT || c + 1 < C; }
   __device__ __forceinline__ bool has_prev() const { return t > 0 || c > 0; }
   __device__ __forceinline__ float4 next(const float4* hb, int slot) const {
@@ -650,20 +652,28 @@ template <int EPT>
 struct RodMailbox {
   const MailboxDev& mb;  // the launch's parameter
   const RodDev& R;
-  int rid, e0;
+  int rid, e0, group;
   bool owns_base, owns_tip;
+  // With position snapshots the base record is written by the rod's thread 32 (another
+  // warp, the same block), from values the base's thread stages in shared memory, so the
+  // base's thread goes straight on to the next input wait.
+  bool writes_base;
   unsigned last = 0u, seq_base = 0u, seq_tip = 0u, seq_pos = 0u;
   unsigned* rec_base = nullptr;
   unsigned* rec_tip = nullptr;
 
-  __device__ __forceinline__ RodMailbox(const MailboxDev& m, const RodDev& R_, int rid_, int e0_)
-      : mb(m), R(R_), rid(rid_), e0(e0_) {
+  // rod_threads: threads holding the rod; group: the rod's index in its block (0, or the
+  // pair kernel's group)
+  __device__ __forceinline__ RodMailbox(const MailboxDev& m, const RodDev& R_, int rid_, int e0_, int rod_threads,
+                                        int group_ = 0)
+      : mb(m), R(R_), rid(rid_), e0(e0_), group(group_) {
     owns_base = e0 == 0;
     owns_tip = e0 <= R.n - 1 && R.n - 1 < e0 + EPT;
+    writes_base = (mb.pos != nullptr && rod_threads > 32) ? e0 == 32 * EPT : owns_base;
     if (mb.period > 0) {
       rec_base = mb.out + 16 * (int64_t)rid;
       rec_tip = rec_base + 8;
-      if (owns_base) seq_base = ld_relaxed_sys(rec_base) & ~1u;
+      if (writes_base) seq_base = ld_relaxed_sys(rec_base) & ~1u;
       if (owns_tip) seq_tip = ld_relaxed_sys(rec_tip) & ~1u;
       // every thread keeps the publication count (it selects the ring slot); read before
       // the first barrier, so before any publication of this launch
@@ -693,6 +703,7 @@ struct RodMailbox {
   __device__ __forceinline__ void after_step(const Halo& H, int step, const float3 (&r)[EPT], const float3 (&v)[EPT],
                                              const float (&w)[EPT]) {
     if (mb.period <= 0 || (step + 1) % mb.period != 0) return;
+    __shared__ float4 base_stage[2][2];  // [group]: base position, velocity
     if (mb.pos != nullptr) {
       // snapshot p of every position into ring slot p % kPosSlots, under the slot's
       // seqlock (2p + 1 while the rod's threads write, barrier-ordered after the first
@@ -701,6 +712,8 @@ struct RodMailbox {
       const int slot = (int)(seq_pos % kPosSlots);
       unsigned* sh = hdr + 4 + 4 * slot;
       if (owns_base) {
+        base_stage[group][0] = make_float4(r[0].x, r[0].y, r[0].z, 0.f);
+        base_stage[group][1] = make_float4(v[0].x, v[0].y, v[0].z, 0.f);
         st_relaxed_sys(sh, 2u * seq_pos + 1u);
         fence_acq_rel_sys();
       }
@@ -723,7 +736,14 @@ struct RodMailbox {
       ++seq_pos;
     }
     // base and tip records after the snapshot: their fences do not delay it
-    if (owns_base) mailbox_write(rec_base, seq_base, mb.step0 + step + 1, r[0], v[0]);
+    if (writes_base) {
+      float3 rb = r[0], vb = v[0];
+      if (!owns_base) {  // staged before the snapshot's second barrier
+        rb = f3(base_stage[group][0]);
+        vb = f3(base_stage[group][1]);
+      }
+      mailbox_write(rec_base, seq_base, mb.step0 + step + 1, rb, vb);
+    }
     if (owns_tip) {
 #pragma unroll
       for (int e = 0; e < EPT; ++e)
@@ -755,7 +775,7 @@ __device__ __forceinline__ void run_rod(const RodDev& R, const Halo& H, const in
     v_drive = f3(drive[2 * rid]);
     w_drive = f3(drive[2 * rid + 1]);
   }
-  RodMailbox<EPT> box(mb, R, rid, e0);
+  RodMailbox<EPT> box(mb, R, rid, e0, H.rod_threads());
 
   int xc = 0;  // exchange counter selects the ping-pong buffer
   for (int step = 0; step < n_steps; ++step) {
