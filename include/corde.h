@@ -258,15 +258,17 @@ int rod_set_graph_mode(rod_handle h, int mode);
  *  rod_mailbox_disable  frees the mailbox (synchronous).
  *  rod_mailbox_positions_enable  (enable != 0) every rod additionally publishes all its
  *                       positions every `period` steps into mapped pinned host memory,
- *                       into a ring of 4 snapshot slots, each under its own seqlock (the
- *                       graphics/haptic thread pulls the whole rod while the kernel runs;
- *                       a slot is rewritten only every 4th publication, so the host has
- *                       3 periods to copy one); allocates 4 x n_elements x 16 B of
- *                       mapped memory (synchronous); needs rod_mailbox_enable first.
+ *                       into a ring of 4 snapshot slots followed by a publication count
+ *                       (the graphics/haptic thread pulls the whole rod while the kernel
+ *                       runs; a slot is rewritten only after the count that retires it
+ *                       is visible, so the host has 3 periods to copy one); allocates
+ *                       4 x n_elements x 16 B of mapped memory (synchronous); needs
+ *                       rod_mailbox_enable first.
  *  rod_mailbox_positions  consistent copy of rod `rod`'s latest snapshot: out [N][4]
  *                       floats (x, y, z, inverse mass), *step the global step it was
  *                       taken after (-1: none yet).  Host-only and non-blocking for the
- *                       device; a torn read is retried, CORDE_ERR_BUSY after 10000 tries.
+ *                       device; a copy during which the count advanced by 3 or more is
+ *                       retried, CORDE_ERR_BUSY after 10000 tries.
  * With the mailbox enabled rod_step launches directly (no graph).  rod_steps_done: steps
  * taken by rod_step on this handle (the log's step index). */
 int rod_mailbox_enable(rod_handle h, int period, int log_capacity);

@@ -1492,8 +1492,9 @@ int rod_mailbox_positions(rod_handle h, int rod, float* out, long long* step) {
   const size_t hbytes = (size_t)h->n_rods * 32 * sizeof(unsigned);
   const size_t nf = 4 * (size_t)h->n_nodes[rod];
   for (int attempt = 0; attempt < 10000; ++attempt) {
-    // newest complete publication p lives in slot p % kPosSlots under seq 2p + 2; the
-    // kernel rewrites that slot only kPosSlots publications later
+    // the newest publication p (count p + 1) lives in slot p % kPosSlots; the kernel
+    // rewrites that slot only after count p + kPosSlots is visible, so the copy is whole
+    // if the count, read again after it, has not reached p + kPosSlots
     const unsigned pubs = __atomic_load_n(&hdr[0], __ATOMIC_ACQUIRE);
     if (pubs == 0u) {
       *step = -1;
@@ -1501,14 +1502,12 @@ int rod_mailbox_positions(rod_handle h, int rod, float* out, long long* step) {
     }
     const unsigned p = pubs - 1u;
     const unsigned* sh = hdr + 4 + 4 * (p % kPosSlots);
-    const unsigned s1 = __atomic_load_n(&sh[0], __ATOMIC_ACQUIRE);
-    if (s1 != 2u * p + 2u) continue;
     const unsigned lo = __atomic_load_n(&sh[1], __ATOMIC_RELAXED), hi = __atomic_load_n(&sh[2], __ATOMIC_RELAXED);
     const float* src = reinterpret_cast<const float*>(static_cast<const char*>(h->mb_pos_host) + hbytes) +
                        4 * ((size_t)(p % kPosSlots) * h->n_elem + h->off[rod]);
     std::memcpy(out, src, nf * sizeof(float));
     __atomic_thread_fence(__ATOMIC_SEQ_CST);
-    if (__atomic_load_n(&sh[0], __ATOMIC_RELAXED) == s1) {
+    if (__atomic_load_n(&hdr[0], __ATOMIC_RELAXED) - pubs <= (unsigned)(kPosSlots - 2)) {
       *step = (long long)(((unsigned long long)hi << 32) | lo);
       return CORDE_OK;
     }
@@ -1535,12 +1534,9 @@ int rod_mailbox_exchange(rod_handle h, const float* drive, int rod, long long ta
     if (pubs > 0u) {
       const unsigned p = pubs - 1u;
       const unsigned* sh = hdr + 4 + 4 * (p % kPosSlots);
-      const unsigned s1 = __atomic_load_n(&sh[0], __ATOMIC_ACQUIRE);
-      if (s1 == 2u * p + 2u) {
-        const unsigned lo = __atomic_load_n(&sh[1], __ATOMIC_RELAXED), hi = __atomic_load_n(&sh[2], __ATOMIC_RELAXED);
-        if ((long long)(((unsigned long long)hi << 32) | lo) >= target_step)
-          return rod_mailbox_positions(h, rod, out, step);
-      }
+      const unsigned lo = __atomic_load_n(&sh[1], __ATOMIC_RELAXED), hi = __atomic_load_n(&sh[2], __ATOMIC_RELAXED);
+      if ((long long)(((unsigned long long)hi << 32) | lo) >= target_step)
+        return rod_mailbox_positions(h, rod, out, step);
     }
     if ((k & 63u) == 63u) {
       if (__atomic_load_n(status, __ATOMIC_ACQUIRE) != 0u)

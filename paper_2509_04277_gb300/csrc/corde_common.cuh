@@ -34,7 +34,8 @@ static_assert(sizeof(RodDev) == 112, "RodDev layout");
 //  log: (global step, input seq) of every input a rod picked up, *log_count entries;
 //  pos_seq / pos (optional): position snapshots published every period steps into a ring of
 //       kPosSlots slots per rod: pos_seq[rid][32] words = (publications, _, _, _) then per
-//       slot (seq, step low, step high, _); pos[slot][n_elem] = (x, y, z, inverse mass).
+//       slot (_, step low, step high, _); pos[slot][n_elem] = (x, y, z, inverse mass).  A
+//       slot is rewritten only after the count that retires it is visible.
 struct MailboxDev {
   const unsigned* in_seq;
   const float* in_drive;

@@ -705,19 +705,20 @@ struct RodMailbox {
     if (mb.period <= 0 || (step + 1) % mb.period != 0) return;
     __shared__ float4 base_stage[2][2];  // [group]: base position, velocity
     if (mb.pos != nullptr) {
-      // snapshot p of every position into ring slot p % kPosSlots, under the slot's
-      // seqlock (2p + 1 while the rod's threads write, barrier-ordered after the first
-      // thread's system-scope fence; 2p + 2 after), then the publication count p + 1
+      // Snapshot p of every position into ring slot p % kPosSlots, its step into the
+      // slot's header, then the publication count p + 1 (release).  The first thread's
+      // fence after that release orders the count before the next snapshot's stores, so
+      // a slot is rewritten (at publication p + 4) only after count p + 4 is visible: a
+      // host that copied slot p % kPosSlots and then still reads a count <= p + 3 copied
+      // publication p whole.  The fence comes after the release, so the host sees the
+      // count without waiting for it.
       unsigned* hdr = mb.pos_seq + 32 * (int64_t)rid;
       const int slot = (int)(seq_pos % kPosSlots);
       unsigned* sh = hdr + 4 + 4 * slot;
       if (owns_base) {
         base_stage[group][0] = make_float4(r[0].x, r[0].y, r[0].z, 0.f);
         base_stage[group][1] = make_float4(v[0].x, v[0].y, v[0].z, 0.f);
-        st_relaxed_sys(sh, 2u * seq_pos + 1u);
-        fence_acq_rel_sys();
       }
-      H.sync();
       // system-scope stores (volatile), ordered before the first thread's release by the
       // barrier (release/acquire among the rod's threads) and its system-scope fence
       float4* dst = mb.pos + slot * mb.n_elem + R.off;
@@ -730,15 +731,15 @@ struct RodMailbox {
         const long long st = mb.step0 + step + 1;
         st_relaxed_sys(sh + 1, (unsigned)(st & 0xffffffffll));
         st_relaxed_sys(sh + 2, (unsigned)(st >> 32));
-        st_release_sys(sh, 2u * seq_pos + 2u);
         st_release_sys(hdr, seq_pos + 1u);
+        fence_acq_rel_sys();
       }
       ++seq_pos;
     }
     // base and tip records after the snapshot: their fences do not delay it
     if (writes_base) {
       float3 rb = r[0], vb = v[0];
-      if (!owns_base) {  // staged before the snapshot's second barrier
+      if (!owns_base) {  // staged before the snapshot's barrier
         rb = f3(base_stage[group][0]);
         vb = f3(base_stage[group][1]);
       }
