@@ -102,8 +102,9 @@ struct PairHook {
       if (group == 1) {
 #pragma unroll
         for (int e = 0; e < EPT; ++e) {
-          if (inv[e] == 0.f) continue;
-          const int k = t * EPT + e + k0;
+          // branch-free: an unbound node (inv = 0) reads an in-range point and adds an
+          // exact zero
+          const int k = min(max(t * EPT + e + k0, 0), n_out - 2);
           float3 vk = f3(out_v[k]), vk1 = f3(out_v[k + 1]);
           v[e] += w[e] * binding(e, v[e], vk, vk1);
         }
