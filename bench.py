@@ -433,7 +433,13 @@ def run_adjoint(args, torch, corde, W, n_rods=1):
     # checkpoint); the per-segment recomputed states stay L2-resident
     adj_bytes = el_steps * 16.0 + sum(r.n_nodes for r in rods) * 64.0 * (n_steps // ckpt)
     hbm = _peaks()[0].get("hbm_gbs", 6800.0)
+    # the library's choice (rod_set_adjoint_record_budget, default 64 MiB): record each
+    # segment's sweeps when they fit, else recompute every step before its reverse
+    nt = 128
+    rec_bytes = ckpt * n_rods * (2 * rods[0].n_iters * 2 * nt + 3 * nt) * 16
+    mode = "record" if rec_bytes <= (64 << 20) else "recompute"
     return {"n_rods": n_rods, "n_nodes": 256, "n_steps": n_steps, "ckpt_every": ckpt,
+            "reverse_pass": f"{mode} mode ({rec_bytes / 2**20:.1f} MiB of sweep records per segment)",
             "roofline_hbm": {"bytes": adj_bytes, "achieved_gbs": round(adj_bytes / (adj_ms * 1e-3) / 1e9, 2),
                              "peak_gbs": hbm, "frac": round(adj_bytes / (adj_ms * 1e-3) / 1e9 / hbm, 5),
                              "note": "latency-bound like the forward: one block per rod"},
