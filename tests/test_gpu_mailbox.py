@@ -318,6 +318,12 @@ def test_exchange_ticks_replay_exactly_and_report_a_lost_wait(corde):
         np.testing.assert_array_equal(snaps[k], b.state_numpy()["pos4"])
     with pytest.raises(corde.CordeError):
         corde.rod_mailbox_exchange(a.handle, None, 0, 0, out, -1)
+    # no launch running: the host-side wait gives up after its timeout
+    corde.rod_mailbox_status(a.handle)  # clear the bit from the lost wait above
+    t0 = time.time()
+    with pytest.raises(corde.CordeError):
+        corde.rod_mailbox_exchange(a.handle, drives[0].reshape(1, 8), 0, base + 10**9, out, 20_000)
+    assert 0.015 < time.time() - t0 < 2.0
     corde.rod_mailbox_disable(a.handle)
     a.close()
     b.close()
