@@ -745,9 +745,7 @@ def main_ours(args):
             "vs_baseline": round(value / 32.0, 5),
             "dtype": "f32",
             "data": "synthetic (seeded guidewire, 1 kHz sinusoidal insertion/twist drive)",
-            "config": dict(workload_config(),
-                           l2="flushed (256 MiB write) between bench steps, outside the timed intervals",
-                           parallelism=f"replicas x{world}" if world > 1 else "single GPU, one thread block per rod"),
+            "config": workload_config(world),
             "gpu_launches": single["launches"],
             "e2e": {"value": round(e2e, 4), "unit": UNIT,
                     "h2d_bytes_per_step": 32 * LAUNCHES_PER_BENCH_STEP,
@@ -844,13 +842,15 @@ def main_ours(args):
 # --------------------------------------------------------------------------- reference arm
 
 
-def workload_config():
-    """The bench workload, the same for both arms."""
+def workload_config(world=1):
+    """The bench workload and its timing conditions, the same for both arms."""
     return {
         "workload": "guidewire: 1 inextensible rod, 512 elements, L=1.5 m, r=0.45 mm, E=60 GPa, "
                     "10 constraint iterations, dt=1e-4 s, 10 time steps per persistent launch",
         "n_rods": 1, "n_elements": 512, "steps_per_launch": STEPS_PER_LAUNCH,
         "time_steps_per_bench_step": STEPS_PER_LAUNCH * LAUNCHES_PER_BENCH_STEP,
+        "l2": "flushed (256 MiB write) between bench steps, outside the timed intervals",
+        "parallelism": f"replicas x{world}" if world > 1 else "single GPU, one thread block per rod",
     }
 
 
@@ -883,7 +883,7 @@ def main_reference(args):
         "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(el * 1e3 / args.steps, 4),
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": dict(workload_config(), parallelism="oracle on 1 host core, 10 time steps per call"),
+        "config": workload_config(args.gpus),
         "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"{args.steps} x {steps_per_bench} time steps of the 512-element guidewire"},
         "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
