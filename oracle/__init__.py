@@ -67,7 +67,7 @@ def lib():
             L.oracle_step.argtypes = [_P, _D, _D, _D, _D, _D, _D, _D, _D, _D, ctypes.c_int]
             L.oracle_rollout.argtypes = [_P, _D, _D, _D, _D, _D, _D, _D, _D, _D, ctypes.c_int, _D, ctypes.c_int]
             L.oracle_rollout_jvp.argtypes = [_P, _D, _D, _D, _D, _D, _D, _D, _D, _D, ctypes.c_int, _D, _D, _D, _D,
-                                             _D, _D]
+                                             _D, _D, _D, _D]
             L.oracle_count_flops.argtypes = [_P, _D, _D, _D, ctypes.c_int]
             L.oracle_count_flops.restype = ctypes.c_int64
             L.oracle_step_batch.argtypes = [ctypes.c_int, _P, _D, _D, _D, _D, _D, ctypes.c_int]
@@ -192,8 +192,10 @@ def rollout(rod, state, n_steps, drive_table=None, K=None, uhat=None):
 
 
 def rollout_jvp(rod, state, n_steps, drive_table=None, K=None, uhat=None, d_pos=None, d_vel=None, d_K=None,
-                d_uhat=None):
-    """Trajectory and its exact directional derivative (forward mode, dual numbers)."""
+                d_uhat=None, d_quat=None, d_omega=None):
+    """Trajectory and its exact directional derivative (forward mode, dual numbers) along
+    tangents of the initial positions, velocities, frames ((N-1) x 4, xyzw components) and
+    body angular velocities, and of the per-joint stiffness and intrinsic Darboux vectors."""
     s = {k: _arr(v) for k, v in state.items()}
     traj = np.zeros((n_steps, rod.n_nodes, 3))
     dtraj = np.zeros_like(traj)
@@ -201,7 +203,8 @@ def rollout_jvp(rod, state, n_steps, drive_table=None, K=None, uhat=None, d_pos=
                                     _ptr(_arr(K)), _ptr(_arr(uhat)), _ptr(s["pos"]), _ptr(s["quat"]),
                                     _ptr(s["vel"]), _ptr(s["omega"]), _ptr(_arr(drive_table)), int(n_steps),
                                     _ptr(_arr(d_pos)), _ptr(_arr(d_vel)), _ptr(_arr(d_K)), _ptr(_arr(d_uhat)),
-                                    _ptr(traj), _ptr(dtraj)), "oracle_rollout_jvp")
+                                    _ptr(_arr(d_quat)), _ptr(_arr(d_omega)), _ptr(traj), _ptr(dtraj)),
+           "oracle_rollout_jvp")
     return traj, dtraj
 
 

@@ -788,12 +788,16 @@ int oracle_rollout(const OracleParams* p, const double* rest_quat, const double*
 
 // Forward-mode derivative of a rollout (dual numbers): perturbs the initial positions
 // (d_pos, N x 3), initial velocities (d_vel, N x 3), per-joint stiffness (d_K, absolute,
-// (M-1) x 3) and intrinsic Darboux vectors (d_uhat, (M-1) x 3); any may be NULL.
+// (M-1) x 3), intrinsic Darboux vectors (d_uhat, (M-1) x 3), initial frames (d_quat,
+// M x 4, tangents of the four quaternion components x, y, z, w) and initial body angular
+// velocities (d_omega, M x 3); any may be NULL.  The state the method evolves is the
+// centreline, the frames and their velocities (Section 2.1), so each is an input here.
 // Writes the position trajectory (traj, n_steps x N x 3) and its tangent (dtraj).
 int oracle_rollout_jvp(const OracleParams* p, const double* rest_quat, const double* stiff_mul, const double* K_abs,
                        const double* uhat_abs, const double* pos, const double* quat, const double* vel,
                        const double* omega, const double* drive_table, int n_steps, const double* d_pos,
-                       const double* d_vel, const double* d_K, const double* d_uhat, double* traj, double* dtraj) {
+                       const double* d_vel, const double* d_K, const double* d_uhat, const double* d_quat,
+                       const double* d_omega, double* traj, double* dtraj) {
   if (!valid(p) || !pos || !quat || n_steps < 0) return -1;
   Derived d = derive(*p);
   Material<double> base;
@@ -813,6 +817,13 @@ int oracle_rollout_jvp(const OracleParams* p, const double* rest_quat, const dou
   for (int i = 0; i < d.N; ++i) {
     if (d_pos) { s.r[i].x.d = d_pos[3 * i]; s.r[i].y.d = d_pos[3 * i + 1]; s.r[i].z.d = d_pos[3 * i + 2]; }
     if (d_vel) { s.v[i].x.d = d_vel[3 * i]; s.v[i].y.d = d_vel[3 * i + 1]; s.v[i].z.d = d_vel[3 * i + 2]; }
+  }
+  for (int j = 0; j < d.M; ++j) {
+    if (d_quat) {
+      s.q[j].x.d = d_quat[4 * j]; s.q[j].y.d = d_quat[4 * j + 1];
+      s.q[j].z.d = d_quat[4 * j + 2]; s.q[j].w.d = d_quat[4 * j + 3];
+    }
+    if (d_omega) { s.om[j].x.d = d_omega[3 * j]; s.om[j].y.d = d_omega[3 * j + 1]; s.om[j].z.d = d_omega[3 * j + 2]; }
   }
   for (int k = 0; k < n_steps; ++k) {
     step(*p, d, mat, s, drive_table ? drive_table + 8 * k : nullptr, nullptr, nullptr);

@@ -229,6 +229,100 @@ def test_rayleigh_damping_decay():
     np.testing.assert_allclose(s["vel"], np.broadcast_to(expect, s["vel"].shape), rtol=1e-9)
 
 
+# ------------------------------------------------------------------ frames as rigid bodies
+#
+# Force integration treats each frame as a rigid body (end of Section 2.1, Fig. 5): the
+# body-frame angular velocity follows Euler's equations J dw/dt = tau - w x (J w), the
+# orientation follows dq/dt = 1/2 q (x) (0, w).  A single free frame (2 nodes, no joint,
+# a negligible penalty constant, a soft axial spring, no gravity) is torque-free, so its motion is the
+# textbook symmetric top: with J = diag(J1, J1, J3), w3 is constant and (w1, w2) turns
+# at Omega = (J3 - J1) / J1 * w3 in the positive sense about the body z axis, and the
+# world-frame angular momentum R(q) J w is constant.
+
+
+def _free_frame(dt, alpha=0.0):
+    return W.straight_rod(2, 0.01, radius=1e-3, E_bend=1e9, E_stretch=1.0, G=0.4e9, density=6500.0, dt=dt,
+                          n_iters=0, inextensible=False, clamp=0, damping_alpha=alpha, Kp=1e-300,
+                          mass_scale=1.0, inertia_scale=1.0)
+
+
+def _spin(rod, w0, n):
+    st = oracle.state_of(rod)
+    st["omega"][0] = w0
+    return st, oracle.step(rod, st, n)
+
+
+def test_free_frame_precesses_as_a_symmetric_top():
+    """Torque-free symmetric top, t = 0.5 s: w3 is constant, the transverse part turns
+    by +Omega t about body z (a sign error or a dropped w x Jw turns it by -Omega t or
+    not at all), its length and the world angular momentum are kept to first order in dt
+    (the error halves with dt), and the nodes do not move."""
+    d = oracle.derive(_free_frame(1e-4))
+    J = np.array([d["J1"], d["J2"], d["J3"]])
+    assert J[0] == J[1] and J[2] == pytest.approx(2 * J[0], rel=1e-14)  # rho l0 diag(I, I, 2I)
+    w0 = np.array([3.0, 0.0, 10.0])
+    Om = (J[2] - J[0]) / J[0] * w0[2]
+    T = 0.5
+    errs = []
+    for dt in (1e-4, 5e-5):
+        rod = _free_frame(dt)
+        n = int(round(T / dt))
+        st, s = _spin(rod, w0, n)
+        w = s["omega"][0]
+        assert w[2] == pytest.approx(w0[2], rel=1e-13)
+        phase = math.atan2(w[1], w[0])
+        dphase = (phase - Om * T + math.pi) % (2 * math.pi) - math.pi
+        assert abs(dphase) < 1e-5, (dt, phase, Om * T)
+        mag_err = abs(math.hypot(w[0], w[1]) / 3.0 - 1.0)
+        L0 = R.from_quat(st["quat"][0]).apply(J * w0)
+        L1 = R.from_quat(s["quat"][0]).apply(J * w)
+        L_err = np.linalg.norm(L1 - L0) / np.linalg.norm(L0)
+        assert mag_err < 0.5 * Om**2 * dt * T * 1.01  # explicit Euler: (1 + Om^2 dt^2)^(n/2)
+        assert L_err < 1e-3
+        np.testing.assert_allclose(s["pos"], st["pos"], rtol=0, atol=1e-200)  # penalty constant 1e-300
+        errs.append((mag_err, L_err))
+    for k in range(2):
+        assert 1.8 < errs[0][k] / errs[1][k] < 2.2, errs
+
+
+def test_free_frame_spin_about_body_axis():
+    """Spin about the body z axis (a principal axis, no gyroscopic term): w stays put
+    and the frame turns about its own third director (body frame, q (x) w, not w (x) q)
+    by w t, to second order in dt per step."""
+    rod = _free_frame(1e-4)
+    w0 = np.array([0.0, 0.0, 7.0])
+    n = 300
+    st, s = _spin(rod, w0, n)
+    np.testing.assert_allclose(s["omega"][0], w0, rtol=1e-15, atol=1e-200)
+    rel = R.from_quat(st["quat"][0]).inv() * R.from_quat(s["quat"][0])
+    rv = rel.as_rotvec()
+    np.testing.assert_allclose(rv[:2], 0.0, atol=1e-12)
+    assert abs(rv[2] - n * rod.dt * w0[2]) < 1e-6
+    # the third director turned about the world image of body z, i.e. it stays put,
+    # while the first director turned by w t in the plane normal to it
+    d3_0 = R.from_quat(st["quat"][0]).apply([0, 0, 1])
+    d3_1 = R.from_quat(s["quat"][0]).apply([0, 0, 1])
+    np.testing.assert_allclose(d3_1, d3_0, atol=1e-12)
+
+
+def test_free_frame_angular_damping():
+    """Implicit Rayleigh damping of the angular velocity: w3 decays exactly as
+    (1 + alpha dt)^-n, and the transverse part, turned as in the undamped top, decays at
+    the same rate up to the first-order growth of explicit Euler."""
+    alpha, dt, n = 40.0, 1e-4, 2000
+    rod = _free_frame(dt, alpha=alpha)
+    w0 = np.array([2.0, -1.0, 10.0])
+    st, s = _spin(rod, w0, n)
+    w = s["omega"][0]
+    decay = (1 + alpha * dt) ** -n
+    assert w[2] == pytest.approx(w0[2] * decay, rel=1e-12)
+    ratio = math.hypot(w[0], w[1]) / math.hypot(w0[0], w0[1]) / decay
+    assert abs(ratio - 1.0) < 0.5 * 100.0 * dt * n * dt * 1.01  # Omega <= 10: (Omega dt)^2 n / 2
+    # no damping of a pure spin's direction: w stays along body z
+    st2, s2 = _spin(rod, np.array([0.0, 0.0, 5.0]), n)
+    np.testing.assert_allclose(s2["omega"][0], [0.0, 0.0, 5.0 * decay], rtol=1e-12, atol=1e-200)
+
+
 def test_two_node_constraint_projection_exact():
     """One distance constraint (N = 2): after the step |r_1 - r_0| = l0 exactly, the
     impulse is along the constraint direction and momentum is conserved."""
@@ -363,18 +457,30 @@ def test_jvp_matches_central_differences():
     d_vel = g.standard_normal(st["vel"].shape) * 1e-2
     d_K = g.standard_normal(K.shape) * K * 0.1
     d_uhat = g.standard_normal(uhat.shape) * 0.5
-    _, dtraj = oracle.rollout_jvp(rod, st, steps, K=K, uhat=uhat, d_pos=d_pos, d_vel=d_vel, d_K=d_K, d_uhat=d_uhat)
+    d_quat = g.standard_normal(st["quat"].shape) * 1e-2  # raw components (also off the unit sphere)
+    d_omega = g.standard_normal(st["omega"].shape) * 1.0
+    st["omega"] = g.standard_normal(st["omega"].shape) * 2.0  # spinning frames: the gyroscopic term is active
     h = 1e-6
 
-    def run(sg):
+    def run(sg, which):
         s2 = {k: v.copy() for k, v in st.items()}
-        s2["pos"] = st["pos"] + sg * h * d_pos
-        s2["vel"] = st["vel"] + sg * h * d_vel
-        traj, _ = oracle.rollout(rod, s2, steps, K=K + sg * h * d_K, uhat=uhat + sg * h * d_uhat)
+        on = lambda k: sg * h if k in which else 0.0  # noqa: E731
+        s2["pos"] = st["pos"] + on("pos") * d_pos
+        s2["vel"] = st["vel"] + on("vel") * d_vel
+        s2["quat"] = st["quat"] + on("quat") * d_quat
+        s2["omega"] = st["omega"] + on("omega") * d_omega
+        traj, _ = oracle.rollout(rod, s2, steps, K=K + on("K") * d_K, uhat=uhat + on("uhat") * d_uhat)
         return traj
 
-    fd = (run(1) - run(-1)) / (2 * h)
-    np.testing.assert_allclose(dtraj, fd, rtol=1e-4, atol=1e-6 * np.abs(fd).max())
+    zero = {k: None for k in ("d_pos", "d_vel", "d_K", "d_uhat", "d_quat", "d_omega")}
+    full = dict(d_pos=d_pos, d_vel=d_vel, d_K=d_K, d_uhat=d_uhat, d_quat=d_quat, d_omega=d_omega)
+    for which in (("pos", "vel", "K", "uhat"), ("quat",), ("omega",), ("pos", "vel", "K", "uhat", "quat", "omega")):
+        kw = dict(zero)
+        kw.update({"d_" + k: full["d_" + k] for k in which})
+        _, dtraj = oracle.rollout_jvp(rod, st, steps, K=K, uhat=uhat, **kw)
+        fd = (run(1, which) - run(-1, which)) / (2 * h)
+        assert np.abs(fd).max() > 0, which
+        np.testing.assert_allclose(dtraj, fd, rtol=1e-4, atol=5e-6 * np.abs(fd).max(), err_msg=str(which))
 
 
 def test_flop_count_linear_in_elements():
