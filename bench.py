@@ -52,8 +52,6 @@ FLOPS_PER_EL_ITER = 41.0
 # Algorithmic HBM bytes per element per launch: state read + written (r, w, v, q, omega:
 # 4 float4 = 64 B each way) plus the per-joint parameters read (u-hat, K: 32 B).
 BYTES_PER_EL_LAUNCH = 64 + 64 + 32
-FP32_LANES_PER_SM = 128
-NUM_SMS = 152
 
 
 def _peaks():
@@ -62,7 +60,7 @@ def _peaks():
         with open(p) as f:
             d = json.load(f)
         return d, "measured"
-    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
 class ClockSampler:
@@ -137,6 +135,26 @@ def _traffic(kernel_key):
     if not e or e.get("source_hash") != _kernel_source_hash():
         return None, None
     return e.get("dram_bytes_per_launch"), e.get("units_per_launch")
+
+
+def measure_fp32_peak(corde):
+    """The device's FP32 FMA throughput, measured by the library's micro-benchmark
+    (rod_fp32_peak): every SM full of independent FMA chains, plain and through the
+    paired-lane FMA.  Burst: best of three short launches (~10 ms), the peak for a kernel
+    timed alone; sustained: one launch of about two seconds, the peak for a kernel timed
+    inside a long step."""
+    info = corde.rod_device_info()
+    burst = {}
+    for packed in (False, True):
+        burst["packed" if packed else "scalar"] = max(corde.rod_fp32_peak(packed, 4, 512, 20000) for _ in range(3))
+    best = max(burst, key=burst.get)
+    t0 = time.perf_counter()
+    sustained = corde.rod_fp32_peak(best == "packed", 4, 512, 8_000_000)
+    return {"burst_tflops": round(burst[best], 3), "sustained_tflops": round(sustained, 3),
+            "by_form_tflops": {k: round(v, 3) for k, v in burst.items()}, "n_sms": info["n_sms"],
+            "sustained_seconds": round(time.perf_counter() - t0, 2),
+            "how": "rod_fp32_peak: 4 blocks of 512 threads per SM, 8 independent FMA chains per thread "
+                   "(scalar FMA, and float2 through the paired-lane FMA); CUDA events; best form"}
 
 
 def flops_per_el_step(n_iters: int, inextensible: bool = True) -> float:
@@ -450,7 +468,7 @@ def run_adjoint(args, torch, corde, W, n_rods=1):
             "adjoint_element_steps_per_s": el_steps / (adj_ms * 1e-3), "gradients_finite": finite}
 
 
-def run_pair(args, torch, corde, W):
+def run_pair(args, torch, corde, W, fp32):
     """Catheter/guidewire pair, 2 x 512 elements, binding modes v0/v1/v2, 1, 10 and 50 time
     steps per launch (about 1000 steps each), drives updated every launch."""
     stream = torch.cuda.current_stream()
@@ -490,15 +508,61 @@ def run_pair(args, torch, corde, W):
             n += 10
         cpu[f"v{mode}"] = round((time.perf_counter() - t0) * 1e6 / n, 2)
     flops_step = 2 * 512 * flops_per_el_step(10)  # the two rods' steps (binding not counted)
-    peak = NUM_SMS * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
+    peak = fp32["burst_tflops"]
     frac = {k: round(flops_step / (v * 1e-6) / 1e12 / peak, 7) for k, v in out.items()}
+    sms = fp32["n_sms"]
     return {"unit": "us/step", "workload": "2 x 512 inextensible rods (catheter r=1 mm E=2 GPa, guidewire "
                                            "r=0.45 mm E=60 GPa), one thread block per pair", "us_per_step": out,
             "roofline_alu": {"flops_per_step": flops_step, "peak_tflops": round(peak, 2),
-                             "frac_of_gpu": frac, "note": "one pair = one thread block on one SM: at most 1/152 "
-                                                          "of the GPU; x152 gives the fraction of that SM"},
+                             "peak_source": "measured (rod_fp32_peak, burst)",
+                             "frac_of_gpu": frac, "note": f"one pair = one thread block on one SM: at most 1/{sms} "
+                                                          f"of the GPU; x{sms} gives the fraction of that SM"},
             "cpu_oracle_us_per_step": cpu,
             "speedup_vs_oracle_1core_10ts": {f"v{m}": round(cpu[f"v{m}"] / out[f"v{m}_10ts"], 1) for m in (0, 1, 2)}}
+
+
+def run_extensible(args, torch, corde, W):
+    """The plain extensible rod (no constraint iterations): the 64-element clamped
+    pendulum as configured (L = 1 m, r = 1 mm, E = 50 GPa, G = 20 GPa, gravity, Rayleigh
+    damping 0.1, dt = 1e-5 s) and the same rod with 1000 elements, the length of the
+    paper's extensible comparison (Table 1); 1000 steps at 10 steps per launch, timed
+    after 100 steps, beside the oracle on one host core."""
+    import oracle
+
+    stream = torch.cuda.current_stream()
+    out = {}
+    for n in (64, 1000):
+        rod = W.extensible_pendulum(n, seed=1)
+        b = corde.RodBatch([rod])
+        b.autotune(STEPS_PER_LAUNCH)
+        for _ in range(10):
+            b.step(STEPS_PER_LAUNCH)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(100):
+            b.step(STEPS_PER_LAUNCH)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        us = e0.elapsed_time(e1) * 1e3 / (100 * STEPS_PER_LAUNCH)
+        plan = [int(x) for x in b.plan()[0]]
+        b.close()
+        # the oracle on one host core, a bounded sample (about one second)
+        s = oracle.state_of(rod)
+        k, t0 = 0, time.perf_counter()
+        while k == 0 or time.perf_counter() - t0 < 1.0:
+            s = oracle.step(rod, s, STEPS_PER_LAUNCH)
+            k += STEPS_PER_LAUNCH
+        cpu_us = (time.perf_counter() - t0) * 1e6 / k
+        out[str(n)] = {"us_per_step": round(us, 4), "plan": plan, "cpu_oracle_1core_us_per_step": round(cpu_us, 2),
+                       "speedup_vs_oracle_1core": round(cpu_us / us, 1)}
+    return {"unit": "us/step", "steps_per_launch": STEPS_PER_LAUNCH, "by_elements": out,
+            "workload": "extensible clamped pendulum (L=1 m, r=1 mm, E=50 GPa, G=20 GPa, rho=6500, gravity, "
+                        "Rayleigh damping 0.1, dt=1e-5 s), 1000 steps at 10 per launch",
+            "paper_context": {"extensible_gpu_us_per_step_10tskl": {"100": 26.0, "1000": 31.0},
+                              "extensible_speedup_vs_original_corde": 40.0,
+                              "hardware": "GeForce GTX 560 (Fermi), host-visible times (Table 1)"}}
 
 
 def run_long_rods(args, torch, corde, W):
@@ -698,20 +762,23 @@ def main_ours(args):
     if args.only is not None:
         part = {"single": lambda: run_single_rod(args, torch, corde, W, rank),
                 "batched": lambda: run_batched(args, torch, corde, W, rank, world),
-                "pair": lambda: run_pair(args, torch, corde, W),
+                "pair": lambda: run_pair(args, torch, corde, W, measure_fp32_peak(corde)),
                 "long": lambda: run_long_rods(args, torch, corde, W),
                 "tube": lambda: run_tube(args, torch, corde, W),
                 "knot": lambda: run_knot(args, torch, corde, W),
+                "extensible": lambda: run_extensible(args, torch, corde, W),
                 "adjoint": lambda: run_adjoint(args, torch, corde, W, 1)}[args.only]()
         if rank == 0:
             print(json.dumps({"only": args.only, "result": part}, default=str), flush=True)
         return
     single = run_single_rod(args, torch, corde, W, rank)
     batched = run_batched(args, torch, corde, W, rank, world) if not args.skip_batched else None
-    pair = run_pair(args, torch, corde, W) if not args.skip_pair else None
+    fp32 = measure_fp32_peak(corde)
+    pair = run_pair(args, torch, corde, W, fp32) if not args.skip_pair else None
     long_rods = run_long_rods(args, torch, corde, W) if not args.skip_long else None
     tube = run_tube(args, torch, corde, W) if not args.skip_tube else None
     knot = run_knot(args, torch, corde, W) if not args.skip_knot else None
+    extensible = run_extensible(args, torch, corde, W) if not args.skip_extensible else None
     adjoint = None
     if not args.skip_adjoint:
         adjoint = {"single": run_adjoint(args, torch, corde, W, 1), "batched": run_adjoint(args, torch, corde, W, 256)}
@@ -726,8 +793,8 @@ def main_ours(args):
     out = None
     if rank == 0:
         peaks, which = _peaks()
-        sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-        fp32_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s
+        fp32_peak = fp32["burst_tflops"]  # the single rod's kernel is timed alone
+        n_sms = fp32["n_sms"]
         flops_launch = flops_per_el_step(single["n_iters"]) * single["n_nodes"] * STEPS_PER_LAUNCH
         achieved = flops_launch / (single["kernel_ms_avg"] * 1e-3) / 1e12
         traffic, _ = _traffic("step_kernel_guidewire512")
@@ -771,11 +838,11 @@ def main_ours(args):
                                 "never waits for the host, so this is simulated steps over host wall time"}},
             "roofline": {"bound": "alu", "achieved": round(achieved, 6), "peak": round(fp32_peak, 2),
                          "unit": "TFLOP/s", "frac": round(achieved / fp32_peak, 8), "traffic": traffic,
-                         "peak_source": f"derived: {NUM_SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
-                                        f"{sm_mhz:.0f} MHz ({which} sm_max_mhz)",
-                         "note": "one rod = one thread block on one of 152 SMs; latency-bound by design",
+                         "peak_source": "measured (rod_fp32_peak, burst: the kernel is timed alone)",
+                         "fp32_peak": fp32,
+                         "note": f"one rod = one thread block on one of {n_sms} SMs; latency-bound by design",
                          "kernel": "step_kernel<ept=%d, nt=%d>" % tuple(single["plan"]),
-                         "frac_of_one_sm": round(achieved / (fp32_peak / NUM_SMS), 6),
+                         "frac_of_one_sm": round(achieved / (fp32_peak / n_sms), 6),
                          "kernel_us_per_launch": round(single["kernel_ms_avg"] * 1e3, 3),
                          "duration": "timed region / launches (includes launch gaps); one launch bracketed "
                                      "alone by events: %.3f us" % (single["kernel_ms_isolated"] * 1e3)},
@@ -813,9 +880,10 @@ def main_ours(args):
                 "launches": batched["launches"],
                 "gpu_launches": batched["gpu_launches"], "ms_per_launch": round(batched["ms_per_launch"], 4),
                 "plan": batched["plan"], "max_len_err": batched["max_len_err"],
-                "roofline_alu": {"achieved": batched["flops_per_launch"] / sec / 1e12, "peak": round(fp32_peak, 2),
-                                 "unit": "TFLOP/s",
-                                 "frac": batched["flops_per_launch"] / sec / 1e12 / fp32_peak},
+                "roofline_alu": {"achieved": batched["flops_per_launch"] / sec / 1e12,
+                                 "peak": fp32["sustained_tflops"], "unit": "TFLOP/s",
+                                 "peak_source": "measured (rod_fp32_peak, sustained: the batch runs for seconds)",
+                                 "frac": batched["flops_per_launch"] / sec / 1e12 / fp32["sustained_tflops"]},
                 "roofline_hbm": {"achieved": batched["bytes_per_launch"] / sec / 1e9, "peak": bw, "unit": "GB/s",
                                  "frac": batched["bytes_per_launch"] / sec / 1e9 / bw},
                 "cpu_baseline": cpu_baseline_batched(args.cpu_seconds) if not args.skip_cpu_batched else None,
@@ -831,6 +899,8 @@ def main_ours(args):
             out["vessel_contact"] = tube
         if knot is not None:
             out["self_collision"] = knot
+        if extensible is not None:
+            out["extensible"] = extensible
         print(json.dumps(out), flush=True)
     _barrier(torch)
     if world > 1:
@@ -908,7 +978,8 @@ def main():
     ap.add_argument("--skip-long", action="store_true")
     ap.add_argument("--skip-tube", action="store_true")
     ap.add_argument("--skip-knot", action="store_true")
-    ap.add_argument("--only", choices=["single", "batched", "pair", "adjoint", "long", "tube", "knot"], default=None,
+    ap.add_argument("--skip-extensible", action="store_true")
+    ap.add_argument("--only", choices=["single", "batched", "pair", "adjoint", "long", "tube", "knot", "extensible"], default=None,
                     help="run one part only and print its raw result (profiling aid, not a bench line)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="fixed kernel plan (single rod <2, 256>, batch default plan)")

@@ -357,8 +357,11 @@ int rod_set_adjoint_record_budget(rod_handle h, long long bytes);
  * Limits: N <= 512 and (ceil(n_steps / ckpt_every) + min(ckpt_every, n_steps)) * 64 * N
  * bytes plus about 100 * N bytes must fit in 16 MiB; larger requests return CORDE_ERR_ARG
  * with the size needed.  It calls no cudaMalloc, cudaFree or other allocating routine.
- * The first call on each device looks up the array's device address (cudaGetSymbolAddress)
- * with that device current: make that first call before any stream capture.  Every call
+ * The first call on each device, with that device current, looks up the array's device
+ * address (cudaGetSymbolAddress) and loads every kernel the entry point can launch (with
+ * lazy module loading, the CUDA default, a kernel's first launch would load its module,
+ * which takes device memory): make that first call before any stream capture and outside
+ * the real-time part of the program; later calls load nothing.  Every call
  * shares the one array and overwrites it; calls that overlap on the GPU (other streams,
  * other host threads) race and give wrong results.  Asynchronous on `stream`. */
 int rod_adjoint_noalloc(const RodParams* params, const float* pos, const float* quat, const float* rest_quat,
@@ -377,6 +380,20 @@ int rod_adjoint_noalloc(const RodParams* params, const float* pos, const float* 
  *           runtime rejects the launch if they cannot be co-resident; it never hangs)
  * Returns CORDE_ERR_ARG for bad sizes, CORDE_ERR_CUDA if the launch is rejected. */
 int rod_barrier_floor(int scope, int threads, int cluster, int n_iters, double* ns_per_barrier, void* stream);
+
+/* Device facts read from the runtime (current device): number of SMs and resident
+ * threads per SM; either pointer may be NULL.  CORDE_ERR_UNSUPPORTED without a GPU. */
+int rod_device_info(int* n_sms, int* max_threads_per_sm);
+
+/* FP32 arithmetic peak of the current device, measured (synchronous): the roofline that
+ * the step kernels' per-element arithmetic (the force and torque evaluation of Eq. 2, 3,
+ * 8 and the constraint impulses of Section 2.1) is compared against.  blocks_per_sm x
+ * (number of SMs) blocks of `threads` threads (a multiple of 32, <= 1024) each run 8
+ * independent fused multiply-add chains of n_iters steps; packed = 1 uses float2 chains
+ * through the paired-lane FMA (two FMAs per lane and instruction).  One untimed launch,
+ * then one timed with CUDA events on `stream`; *tflops receives 2 (packed: 4) x 8 x
+ * n_iters x threads x blocks flops over that time.  CORDE_ERR_ARG for bad sizes. */
+int rod_fp32_peak(int packed, int blocks_per_sm, int threads, int n_iters, double* tflops, void* stream);
 
 /* Free the device state (synchronises the device first).  NULL is ignored. */
 void rod_destroy(rod_handle h);

@@ -86,6 +86,9 @@ SIGNATURES = {
                                            ctypes.c_int, ctypes.c_int, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "rod_barrier_floor": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_double), _VP]),
+    "rod_device_info": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "rod_fp32_peak": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
     "rod_destroy": (None, [_VP]),
     "rod_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "rod_last_error": (ctypes.c_char_p, []),
@@ -345,6 +348,21 @@ def rod_barrier_floor(scope, threads=128, cluster=1, n_iters=100000, stream=None
     _check(load().rod_barrier_floor(int(scope), int(threads), int(cluster), int(n_iters), ctypes.byref(ns),
                                     _stream(stream)), "rod_barrier_floor")
     return ns.value
+
+
+def rod_device_info() -> dict:
+    """Number of SMs and resident threads per SM of the current device."""
+    n, t = ctypes.c_int(), ctypes.c_int()
+    _check(load().rod_device_info(ctypes.byref(n), ctypes.byref(t)), "rod_device_info")
+    return {"n_sms": n.value, "max_threads_per_sm": t.value}
+
+
+def rod_fp32_peak(packed=False, blocks_per_sm=4, threads=256, n_iters=20000, stream=None) -> float:
+    """Measured FP32 FMA throughput of the device in TFLOP/s (packed: float2 lanes)."""
+    tf = ctypes.c_double()
+    _check(load().rod_fp32_peak(int(bool(packed)), int(blocks_per_sm), int(threads), int(n_iters),
+                                ctypes.byref(tf), _stream(stream)), "rod_fp32_peak")
+    return tf.value
 
 
 def rod_adjoint_noalloc(params, pos, quat, rest_quat=None, vel=None, omega=None, stiff_mul=None, drive=None,

@@ -617,6 +617,17 @@ int adjoint_smem_bytes(int nt, int n_iters, bool record) {
   return (2 * ept * nt + 2 * kHaloSlots * nt + (record ? 2 : 1) * sweep) * (int)sizeof(float4);
 }
 
+cudaError_t preload_adjoint(int nt) {
+  cudaFuncAttributes at;
+  switch (nt) {
+    case 32: return cudaFuncGetAttributes(&at, adjoint_kernel<32, false>);
+    case 64: return cudaFuncGetAttributes(&at, adjoint_kernel<64, false>);
+    case 128: return cudaFuncGetAttributes(&at, adjoint_kernel<128, false>);
+    case 256: return cudaFuncGetAttributes(&at, adjoint_kernel<256, false>);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 cudaError_t launch_adjoint(int nt, const AdjointArgs& a, int n_blocks, int smem, cudaStream_t s) {
   switch (nt) {
     case 32: return launch_adjoint_nt<32>(a, n_blocks, smem, s);

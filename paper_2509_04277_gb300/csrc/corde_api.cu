@@ -1,9 +1,11 @@
 // C ABI of the CoRdE stepper: creation (derived constants and packing on the device),
 // kernel-variant plans, the persistent step launches, state I/O and diagnostics.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1658,7 +1660,9 @@ namespace {
 constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 constexpr int kMaxDevices = 64;
-void* g_noalloc_base[kMaxDevices] = {};
+// Device address of the array, per device; set once, by the first call on that device.
+std::atomic<void*> g_noalloc_base[kMaxDevices];
+std::mutex g_noalloc_init_mutex;
 
 __global__ void noalloc_setup_kernel(RodParams p, int n, RodParams* P, int* off, int* work, int* elem_rod,
                                      const float* drive_in, float4* drive) {
@@ -1738,14 +1742,35 @@ extern "C" int rod_adjoint_noalloc(const RodParams* params, const float* pos, co
   int dev = 0;
   CK(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDevices) return fail(CORDE_ERR_UNSUPPORTED, "rod_adjoint_noalloc: device index");
-  if (!g_noalloc_base[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p)
-      return fail(CORDE_ERR_CUDA, std::string("rod_adjoint_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-    g_noalloc_base[dev] = p;
+  void* base_addr = g_noalloc_base[dev].load(std::memory_order_acquire);
+  if (!base_addr) {
+    // First call on this device: look up the array's device address, and load every
+    // kernel this entry point can launch, so that no later call loads a module (with
+    // lazy module loading, the CUDA default, a kernel's first launch would otherwise
+    // load it, which takes device memory and can block).
+    std::lock_guard<std::mutex> lock(g_noalloc_init_mutex);
+    base_addr = g_noalloc_base[dev].load(std::memory_order_acquire);
+    if (!base_addr) {
+      void* p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess || !p)
+        return fail(CORDE_ERR_CUDA, std::string("rod_adjoint_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+      cudaFuncAttributes at;
+      e = cudaFuncGetAttributes(&at, noalloc_setup_kernel);
+      if (e == cudaSuccess) e = cudaFuncGetAttributes(&at, derive_kernel);
+      if (e == cudaSuccess) e = cudaFuncGetAttributes(&at, pack_kernel);
+      for (int nt = 32; e == cudaSuccess && nt <= 256; nt *= 2) {
+        const int v = find_variant(2, nt);
+        e = v < 0 ? cudaErrorInvalidValue : variants()[v].preload();
+        if (e == cudaSuccess) e = preload_adjoint(nt);
+      }
+      if (e != cudaSuccess)
+        return fail(CORDE_ERR_CUDA, std::string("rod_adjoint_noalloc: loading kernels: ") + cudaGetErrorString(e));
+      g_noalloc_base[dev].store(p, std::memory_order_release);
+      base_addr = p;
+    }
   }
-  unsigned char* base = static_cast<unsigned char*>(g_noalloc_base[dev]);
+  unsigned char* base = static_cast<unsigned char*>(base_addr);
   RodParams* d_P = reinterpret_cast<RodParams*>(base + o_P);
   int* d_off = reinterpret_cast<int*>(base + o_off);
   int* d_work = reinterpret_cast<int*>(base + o_work);
@@ -1771,7 +1796,9 @@ extern "C" int rod_adjoint_noalloc(const RodParams* params, const float* pos, co
   const int v = find_variant(2, nt);
   if (v < 0) return fail(CORDE_ERR_UNSUPPORTED, "rod_adjoint_noalloc: no step variant");
   StepArgs a = {};
-  a.pdl = 1;
+  // ordinary launches: a device-to-device copy of the checkpoint sits between
+  // consecutive step launches, so overlapped launch would change nothing here
+  a.pdl = 0;
   a.rods = d_rod;
   a.work = d_work;
   a.x4 = x4;

@@ -1,5 +1,6 @@
 // Empty-barrier floors: the cost of one synchronisation of each scope a rod kernel can
-// use, measured with nothing else in the loop.  The paper's multi-block kernel pays an
+// use, measured with nothing else in the loop; and the device's FP32 FMA throughput, the
+// peak the step kernels' arithmetic is measured against.  The paper's multi-block kernel pays an
 // inter-block barrier per exchange (Section 2.2, Fig. 5); these floors are what a
 // persistent step kernel's latency per step is compared against.
 #include <cooperative_groups.h>
@@ -51,9 +52,100 @@ __global__ void floor_grid(int n_iters, int* sink) {
   if (threadIdx.x == 0 && acc == -1) *sink = acc;
 }
 
+// FP32 issue peak: every thread runs 8 independent fused multiply-add chains (enough
+// independent work per warp to hide the FMA latency at a few resident warps per SMSP).
+// PACKED: the chains are float2 pairs through the paired-lane FMA (__ffma2_rn), which
+// does two FMAs per lane and instruction.  The values stay bounded (a < 1).
+template <bool PACKED>
+__global__ void fp32_peak_kernel(int n_iters, float a, float b, float* sink) {
+  if constexpr (PACKED) {
+    float2 x[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = make_float2(1e-3f * threadIdx.x + k, 2e-3f * threadIdx.x - k);
+    const float2 A = make_float2(a, a), B = make_float2(b, b);
+#pragma unroll 4
+    for (int i = 0; i < n_iters; ++i) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) x[k] = __ffma2_rn(x[k], A, B);
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += x[k].x + x[k].y;
+    if (s == -1.f) *sink = s;
+  } else {
+    float x[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = 1e-3f * threadIdx.x + k;
+#pragma unroll 4
+    for (int i = 0; i < n_iters; ++i) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) x[k] = fmaf(x[k], a, b);
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += x[k];
+    if (s == -1.f) *sink = s;
+  }
+}
+
 }  // namespace
 
 extern "C" {
+
+int rod_device_info(int* n_sms, int* max_threads_per_sm) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess && n_sms) e = cudaDeviceGetAttribute(n_sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess && max_threads_per_sm)
+    e = cudaDeviceGetAttribute(max_threads_per_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return corde::set_error(CORDE_ERR_UNSUPPORTED, std::string("rod_device_info: ") + cudaGetErrorString(e));
+  }
+  return CORDE_OK;
+}
+
+// FP32 FMA throughput (synchronous): blocks_per_sm x (number of SMs) blocks of `threads`
+// threads, each thread 8 independent FMA chains of n_iters steps (packed = 1: float2
+// chains through the paired-lane FMA); one untimed launch, then one timed.
+int rod_fp32_peak(int packed, int blocks_per_sm, int threads, int n_iters, double* tflops, void* stream) {
+  if (!tflops || n_iters < 1 || threads < 32 || threads > 1024 || (threads & 31) || blocks_per_sm < 1 ||
+      blocks_per_sm > 32 || (packed != 0 && packed != 1))
+    return corde::set_error(CORDE_ERR_ARG, "rod_fp32_peak: bad sizes");
+  int sms = 0;
+  if (int rc = rod_device_info(&sms, nullptr)) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  float* sink = nullptr;
+  if (cudaMalloc(&sink, sizeof(float)) != cudaSuccess) return corde::set_error(CORDE_ERR_OOM, "rod_fp32_peak");
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const dim3 grid(sms * blocks_per_sm), block(threads);
+  auto launch = [&]() {
+    if (packed)
+      fp32_peak_kernel<true><<<grid, block, 0, s>>>(n_iters, 0.9999f, 1e-4f, sink);
+    else
+      fp32_peak_kernel<false><<<grid, block, 0, s>>>(n_iters, 0.9999f, 1e-4f, sink);
+    return cudaGetLastError();
+  };
+  cudaError_t err = launch();
+  if (err == cudaSuccess) err = cudaEventRecord(e0, s);
+  if (err == cudaSuccess) err = launch();
+  if (err == cudaSuccess) err = cudaEventRecord(e1, s);
+  if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(sink);
+  if (err != cudaSuccess) {
+    cudaGetLastError();
+    return corde::set_error(CORDE_ERR_CUDA, std::string("rod_fp32_peak: ") + cudaGetErrorString(err));
+  }
+  const double flops = (double)grid.x * threads * (double)n_iters * 8.0 * (packed ? 4.0 : 2.0);
+  *tflops = flops / ((double)ms * 1e-3) / 1e12;
+  return CORDE_OK;
+}
 
 // Empty-barrier floor (synchronous): ns per barrier over n_iters back-to-back barriers
 // in one launch, minus nothing (the launch overhead is amortised by n_iters).

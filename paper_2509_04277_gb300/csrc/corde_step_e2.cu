@@ -15,7 +15,13 @@ static cudaError_t launch_step(const StepArgs& a, int n_blocks, cudaStream_t s) 
                        a.v4, a.q4, a.o4, a.u4, a.k4, a.drive, a.n_steps, a.traj, a.n_elem, a.mb, a.pos_out);
 }
 
-#define V(NT) {2, NT, step_smem_bytes<2, NT>(), &launch_step<2, NT>}
+template <int EPT, int NT>
+static cudaError_t preload_step() {
+  cudaFuncAttributes at;
+  return cudaFuncGetAttributes(&at, step_kernel<EPT, NT>);
+}
+
+#define V(NT) {2, NT, step_smem_bytes<2, NT>(), &launch_step<2, NT>, &preload_step<2, NT>}
 const StepVariant kStepVariantsE2[] = {V(32), V(64), V(128), V(256), V(512)};
 #undef V
 const int kNumStepVariantsE2 = 5;

@@ -57,12 +57,16 @@ cudaError_t launch_kernel(void (*kernel)(KArgs...), dim3 grid, dim3 block, int s
 }
 
 typedef cudaError_t (*StepLaunchFn)(const StepArgs& a, int n_blocks, cudaStream_t s);
+// Loads the variant's kernel into the current context now (cudaFuncGetAttributes), so
+// that its first launch does not load the module (lazy loading takes device memory).
+typedef cudaError_t (*StepPreloadFn)();
 
 struct StepVariant {
   int ept;
   int nt;
   int smem_bytes;
   StepLaunchFn launch;
+  StepPreloadFn preload;
   int capacity() const { return ept * nt; }
 };
 
@@ -91,6 +95,8 @@ struct AdjointArgs {
 // mode) or two (record mode: double-buffered copies) sweep-velocity buffers.
 int adjoint_smem_bytes(int nt, int n_iters, bool record = false);
 cudaError_t launch_adjoint(int nt, const AdjointArgs& a, int n_blocks, int smem, cudaStream_t s);
+// Loads the recompute-mode reverse kernel of `nt` threads into the current context.
+cudaError_t preload_adjoint(int nt);
 constexpr int kAdjointMaxNodes = 512;
 
 // Rods with self-collision (corde_self.cu): one rod per block, at most 1024 nodes.

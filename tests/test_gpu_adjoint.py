@@ -51,17 +51,37 @@ def _gpu_grad(corde, torch, rods, n_steps, ckpt, targets, drive=None):
     return out, loss, pj, b.offsets
 
 
-def _directions(rod, K, seed, n_dirs):
+def _frame_tangent(quat, dtheta):
+    """Tangents q (x) (0, dtheta / 2) of unit quaternions (xyzw rows): the first-order
+    change of each frame under a small body-frame rotation dtheta (on the unit sphere)."""
+    qv, qw = quat[:, :3], quat[:, 3:4]
+    v = 0.5 * dtheta
+    out = np.zeros_like(quat)
+    out[:, :3] = qw * v + np.cross(qv, v)
+    out[:, 3] = -(qv * v).sum(axis=1)
+    return out
+
+
+def _directions(rod, K, seed, n_dirs, frames=True):
+    """Seeded directions over the per-joint stiffness and intrinsic Darboux vectors and the
+    initial positions, velocities, frames (tangents of body-frame rotations) and body
+    angular velocities."""
     g = np.random.default_rng(seed)
     J, N = K.shape[0], rod.n_nodes
     dirs = []
     for _ in range(n_dirs):
-        dirs.append({
+        d = {
             "K": K * g.standard_normal(K.shape),
             "uhat": g.standard_normal((J, 3)) * 0.5,
             "vel": g.standard_normal((N, 3)) * 1e-2,
             "pos": g.standard_normal((N, 3)) * 1e-4,
-        })
+            "quat": np.zeros((N - 1, 4)),
+            "omega": np.zeros((N - 1, 3)),
+        }
+        if frames:
+            d["quat"] = _frame_tangent(np.asarray(rod.quat, np.float64), g.standard_normal((N - 1, 3)) * 1e-3)
+            d["omega"] = g.standard_normal((N - 1, 3)) * 0.1
+        dirs.append(d)
     return dirs
 
 
@@ -69,15 +89,18 @@ def _gpu_directional(grads, off, rod, d):
     n = rod.n_nodes
     J = n - 2
     sl = slice(off, off + n)
+    fr = slice(off, off + n - 1)
     return float((grads["K"][off:off + J, :3] * d["K"]).sum() + (grads["uhat"][off:off + J, :3] * d["uhat"]).sum()
-                 + (grads["vel0"][sl, :3] * d["vel"]).sum() + (grads["pos0"][sl, :3] * d["pos"]).sum())
+                 + (grads["vel0"][sl, :3] * d["vel"]).sum() + (grads["pos0"][sl, :3] * d["pos"]).sum()
+                 + (grads["quat0"][fr, :4] * d["quat"]).sum() + (grads["omega0"][fr, :3] * d["omega"]).sum())
 
 
 def _oracle_loss_and_jvp(rod, K, uhat, target, n_steps, d, drive_row=None):
     st = oracle.state_of(rod)
     table = None if drive_row is None else np.tile(np.asarray(drive_row, np.float64), (n_steps, 1))
     traj, dtraj = oracle.rollout_jvp(rod, st, n_steps, drive_table=table, K=K, uhat=uhat, d_pos=d["pos"],
-                                     d_vel=d["vel"], d_K=d["K"], d_uhat=d["uhat"])
+                                     d_vel=d["vel"], d_K=d["K"], d_uhat=d["uhat"], d_quat=d["quat"],
+                                     d_omega=d["omega"])
     diff = traj[:, -1, :] - target
     return float((diff ** 2).sum()), float((2 * diff * dtraj[:, -1, :]).sum())
 
@@ -89,6 +112,8 @@ def _oracle_fd(rod, K, uhat, target, n_steps, d, h=1e-6, drive_row=None):
         st = oracle.state_of(rod)
         st["pos"] = st["pos"] + sg * h * d["pos"]
         st["vel"] = st["vel"] + sg * h * d["vel"]
+        st["quat"] = st["quat"] + sg * h * d["quat"]
+        st["omega"] = st["omega"] + sg * h * d["omega"]
         traj, _ = oracle.rollout(rod, st, n_steps, drive_table=table, K=K + sg * h * d["K"],
                                  uhat=uhat + sg * h * d["uhat"])
         return float(((traj[:, -1, :] - target) ** 2).sum())
@@ -169,6 +194,40 @@ def test_adjoint_256_element_rod_200_steps(corde):
     _check(gv, fv, "GPU adjoint vs oracle central FD")
 
 
+def _frame_only(d):
+    out = {k: np.zeros_like(v) for k, v in d.items()}
+    out["quat"], out["omega"] = d["quat"], d["omega"]
+    return out
+
+
+@pytest.mark.parametrize("spin", [False, True])
+def test_adjoint_initial_frames_and_angular_velocities(corde, spin):
+    """dL/dq0 and dL/domega0 alone: directions over the initial frames (tangents of
+    body-frame rotations) and body angular velocities only, on a 64-node rod over 100
+    steps with checkpoints every 20, at rest and with spinning frames (the gyroscopic
+    term active), against the oracle's exact JVP and FP64 central differences."""
+    import torch
+
+    rod = W.adjoint_rod(64, seed=71)
+    if spin:
+        rod.omega = np.random.default_rng(72).standard_normal((63, 3)) * 0.5
+    n_steps = 100
+    target = W.tip_target(73, n_steps, rod.dt, rod.pos[-1] + np.array([0.0, 1e-3, 0.0]))
+    grads, _, pj, _ = _gpu_grad(corde, torch, [rod], n_steps, 20, [target])
+    assert np.abs(grads["omega0"][0, :3]).max() == 0.0  # frame 0 is kinematic: its omega comes from the drive
+    K, uhat = _material_from_gpu(pj, 0, rod.n_nodes)
+    gv, jv, fv = [], [], []
+    for d in _directions(rod, K, 74 + spin, 12):
+        d = _frame_only(d)
+        _, dL = _oracle_loss_and_jvp(rod, K, uhat, target, n_steps, d)
+        gv.append(_gpu_directional(grads, 0, rod, d))
+        jv.append(dL)
+        fv.append(_oracle_fd(rod, K, uhat, target, n_steps, d))
+    _check(jv, fv, "oracle JVP vs oracle central FD (frames)")
+    _check(gv, jv, "GPU adjoint vs oracle JVP (frames)")
+    _check(gv, fv, "GPU adjoint vs oracle central FD (frames)")
+
+
 def test_adjoint_batched_256_rods_sampled(corde):
     """The adjoint batched over 256 rods in one launch; 6 sampled rods checked."""
     import torch
@@ -203,7 +262,9 @@ def test_autograd_function_matches_adjoint(corde):
     uhat = pj[:, 4:8].clone().requires_grad_(True)
     vel0 = torch.as_tensor(st["vel4"], device="cuda").requires_grad_(True)
     pos0 = torch.as_tensor(st["pos4"], device="cuda").requires_grad_(True)
-    traj = RodRollout.apply(b, n_steps, 10, K, uhat, vel0, pos0)
+    quat0 = torch.as_tensor(st["quat4"], device="cuda").requires_grad_(True)
+    omega0 = torch.as_tensor(st["omega4"], device="cuda").requires_grad_(True)
+    traj = RodRollout.apply(b, n_steps, 10, K, uhat, vel0, pos0, quat0, omega0)
     target = torch.as_tensor(W.tip_target(59, n_steps, rod.dt, rod.pos[-1]), dtype=torch.float32, device="cuda")
     loss = ((traj[:, -1, :3] - target) ** 2).sum()
     loss.backward()
@@ -213,7 +274,9 @@ def test_autograd_function_matches_adjoint(corde):
     d = _directions(rod, Kn, 60, 1)[0]
     _, dL = _oracle_loss_and_jvp(rod, Kn, un, target.double().cpu().numpy(), n_steps, d)
     g = {"K": K.grad.double().cpu().numpy(), "uhat": uhat.grad.double().cpu().numpy(),
-         "vel0": vel0.grad.double().cpu().numpy(), "pos0": pos0.grad.double().cpu().numpy()}
+         "vel0": vel0.grad.double().cpu().numpy(), "pos0": pos0.grad.double().cpu().numpy(),
+         "quat0": quat0.grad.double().cpu().numpy(), "omega0": omega0.grad.double().cpu().numpy()}
+    assert np.abs(g["quat0"]).max() > 0
     _check([_gpu_directional(g, 0, rod, d)], [dL], "autograd.Function")
     b.close()
 
