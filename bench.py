@@ -354,12 +354,23 @@ def run_single_rod(args, torch, corde, W, rank):
     }
 
 
-def run_batched(args, torch, corde, W, rank, world):
+BATCH_ITERS = os.path.join(ROOT, "tests", "golden", "batch_iters_seed4.json")
+
+
+def batch_iteration_table():
+    """Per-rod constraint iterations of the 4096-rod batch for which the FP64 oracle holds
+    every segment within 1e-3 of its rest length over 1000 steps (written by
+    tests/golden/make_batch_iters.py from the oracle alone)."""
+    with open(BATCH_ITERS) as f:
+        return json.load(f)["n_iters"]
+
+
+def run_batched(args, torch, corde, W, rank, world, n_iters=None):
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream()
     from paper_2509_04277_gb300 import sharding
 
-    rods = W.batched_rods(4096, seed=4)
+    rods = W.batched_rods(4096, seed=4, n_iters=n_iters)
     mine = [rods[i] for i in sharding.shard([r.n_nodes for r in rods], rank, world)] if world > 1 else rods
     b = corde.RodBatch(mine)
     n_elem = b.n_elem
@@ -373,7 +384,9 @@ def run_batched(args, torch, corde, W, rank, world):
     n_launch = max(1, args.batched_steps // S)
     plan = b.plan()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    b.step(S)
+    st0 = b.state_numpy()
+    b.step(S)  # warm-up launch, then back to the initial state: the timed launches run steps 0 .. 999
+    corde.rod_set_state(b.handle, st0["pos4"], st0["quat4"], st0["vel4"], st0["omega4"])
     torch.cuda.synchronize()
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(n_launch)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(n_launch)]
@@ -406,7 +419,9 @@ def run_batched(args, torch, corde, W, rank, world):
         "plan": sorted({(int(a), int(c), int(k)) for a, c, k in plan}),
         "max_len_err": float(diag[:, 0].max()),
         "diag_rc": rc,
-        "flops_per_launch": flops_per_el_step(10) * n_elem * S,
+        "n_iters_histogram": {int(k): int(v) for k, v in zip(*np.unique([r.n_iters for r in mine],
+                                                                         return_counts=True))},
+        "flops_per_launch": sum(flops_per_el_step(r.n_iters) * r.n_nodes for r in mine) * S,
         "bytes_per_launch": BYTES_PER_EL_LAUNCH * n_elem,
     }
 
@@ -762,6 +777,8 @@ def main_ours(args):
     if args.only is not None:
         part = {"single": lambda: run_single_rod(args, torch, corde, W, rank),
                 "batched": lambda: run_batched(args, torch, corde, W, rank, world),
+                "batched_inextensible": lambda: run_batched(args, torch, corde, W, rank, world,
+                                                            n_iters=batch_iteration_table()),
                 "pair": lambda: run_pair(args, torch, corde, W, measure_fp32_peak(corde)),
                 "long": lambda: run_long_rods(args, torch, corde, W),
                 "tube": lambda: run_tube(args, torch, corde, W),
@@ -773,6 +790,9 @@ def main_ours(args):
         return
     single = run_single_rod(args, torch, corde, W, rank)
     batched = run_batched(args, torch, corde, W, rank, world) if not args.skip_batched else None
+    batched_inext = None
+    if not args.skip_batched and not args.skip_batched_inextensible:
+        batched_inext = run_batched(args, torch, corde, W, rank, world, n_iters=batch_iteration_table())
     fp32 = measure_fp32_peak(corde)
     pair = run_pair(args, torch, corde, W, fp32) if not args.skip_pair else None
     long_rods = run_long_rods(args, torch, corde, W) if not args.skip_long else None
@@ -783,10 +803,11 @@ def main_ours(args):
     if not args.skip_adjoint:
         adjoint = {"single": run_adjoint(args, torch, corde, W, 1), "batched": run_adjoint(args, torch, corde, W, 256)}
     value = _max_over_ranks(torch, single["us_per_step"])
-    if batched is not None:
-        el_steps = batched["n_elements"] * batched["steps_per_launch"] * batched["launches"]
-        batched_total_el_steps = _sum_over_ranks(torch, el_steps)
-        batched_max_seconds = _max_over_ranks(torch, batched["seconds"])
+    batched_totals = {}
+    for key, part in (("batched", batched), ("batched_inextensible", batched_inext)):
+        if part is not None:
+            el_steps = part["n_elements"] * part["steps_per_launch"] * part["launches"]
+            batched_totals[key] = (_sum_over_ranks(torch, el_steps), _max_over_ranks(torch, part["seconds"]))
     lock = single["e2e_lockstep"]
     e2e_path = "lockstep_persistent" if "us_per_step" in lock else "launch_per_tick"
     e2e = _max_over_ranks(torch, lock["us_per_step"] if "us_per_step" in lock else single["e2e_us"])
@@ -867,27 +888,39 @@ def main_ours(args):
                               "haptic_rate_khz": [0.5, 1.0],
                               "ours_vs_oracle_1core": round(cpu["value"] / value, 1) if cpu else None},
         }
-        if batched is not None:
-            bw = peaks.get("hbm_gbs", 6800.0)
-            sec = batched["seconds"] / batched["launches"]
+        bw = peaks.get("hbm_gbs", 6800.0)
+        for key, part in (("batched", batched), ("batched_inextensible", batched_inext)):
+            if part is None:
+                continue
+            sec = part["seconds"] / part["launches"]
             # whole job: element-steps of every rank over the slowest rank's time
-            batched["element_steps_per_s"] = batched_total_el_steps / batched_max_seconds
-            out["batched"] = {
-                "element_steps_per_s": batched["element_steps_per_s"],
-                "n_rods": batched["n_rods"], "n_elements": batched["n_elements"],
-                "steps_per_launch": batched["steps_per_launch"],
-                "steps_per_launch_autotuned": batched["steps_per_launch_autotuned"],
-                "launches": batched["launches"],
-                "gpu_launches": batched["gpu_launches"], "ms_per_launch": round(batched["ms_per_launch"], 4),
-                "plan": batched["plan"], "max_len_err": batched["max_len_err"],
-                "roofline_alu": {"achieved": batched["flops_per_launch"] / sec / 1e12,
+            tot_el_steps, max_seconds = batched_totals[key]
+            part["element_steps_per_s"] = tot_el_steps / max_seconds
+            out[key] = {
+                "element_steps_per_s": part["element_steps_per_s"],
+                "n_rods": part["n_rods"], "n_elements": part["n_elements"],
+                "n_iters": part["n_iters_histogram"],
+                "steps_per_launch": part["steps_per_launch"],
+                "steps_per_launch_autotuned": part["steps_per_launch_autotuned"],
+                "launches": part["launches"],
+                "gpu_launches": part["gpu_launches"], "ms_per_launch": round(part["ms_per_launch"], 4),
+                "plan": part["plan"], "max_len_err": part["max_len_err"],
+                "roofline_alu": {"achieved": part["flops_per_launch"] / sec / 1e12,
                                  "peak": fp32["sustained_tflops"], "unit": "TFLOP/s",
                                  "peak_source": "measured (rod_fp32_peak, sustained: the batch runs for seconds)",
-                                 "frac": batched["flops_per_launch"] / sec / 1e12 / fp32["sustained_tflops"]},
-                "roofline_hbm": {"achieved": batched["bytes_per_launch"] / sec / 1e9, "peak": bw, "unit": "GB/s",
-                                 "frac": batched["bytes_per_launch"] / sec / 1e9 / bw},
-                "cpu_baseline": cpu_baseline_batched(args.cpu_seconds) if not args.skip_cpu_batched else None,
+                                 "frac": part["flops_per_launch"] / sec / 1e12 / fp32["sustained_tflops"]},
+                "roofline_hbm": {"achieved": part["bytes_per_launch"] / sec / 1e9, "peak": bw, "unit": "GB/s",
+                                 "frac": part["bytes_per_launch"] / sec / 1e9 / bw},
             }
+        if "batched" in out:
+            out["batched"]["what"] = ("10 constraint iterations per rod (the paper's count); floppy long rods "
+                                      "stretch beyond 1e-3 (max_len_err)")
+            out["batched"]["cpu_baseline"] = (cpu_baseline_batched(args.cpu_seconds)
+                                              if not args.skip_cpu_batched else None)
+        if "batched_inextensible" in out:
+            out["batched_inextensible"]["what"] = (
+                "per-rod constraint iterations (10 to 640) for which the FP64 oracle holds every segment within "
+                "1e-3 of its rest length over the 1000 steps (tests/golden/batch_iters_seed4.json)")
         if adjoint is not None:
             out["adjoint"] = adjoint
         if pair is not None:
@@ -972,6 +1005,7 @@ def main():
                     help="steps per launch of the batch (default: autotuned among 10..200)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--skip-batched", action="store_true")
+    ap.add_argument("--skip-batched-inextensible", action="store_true")
     ap.add_argument("--skip-cpu-batched", action="store_true")
     ap.add_argument("--skip-adjoint", action="store_true")
     ap.add_argument("--skip-pair", action="store_true")
@@ -979,7 +1013,8 @@ def main():
     ap.add_argument("--skip-tube", action="store_true")
     ap.add_argument("--skip-knot", action="store_true")
     ap.add_argument("--skip-extensible", action="store_true")
-    ap.add_argument("--only", choices=["single", "batched", "pair", "adjoint", "long", "tube", "knot", "extensible"], default=None,
+    ap.add_argument("--only", choices=["single", "batched", "batched_inextensible", "pair", "adjoint", "long", "tube", "knot",
+                             "extensible"], default=None,
                     help="run one part only and print its raw result (profiling aid, not a bench line)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="fixed kernel plan (single rod <2, 256>, batch default plan)")

@@ -156,12 +156,17 @@ int rod_set_tube(rod_handle h, int rod, const double* tube);
  * self-colliding rods.  Synchronous. */
 int rod_set_self_collision(rod_handle h, int rod, const double* params);
 
-/* Self-collision statistics of rod `rod` from its last launch, into 4 host ints:
+/* Self-collision statistics of rod `rod` from its last launch, into 5 host ints:
  * candidate pairs at the last detection, the most candidates j > i of one mass point i,
- * pairs whose spheres overlapped at the last detection, and an overflow flag: bit 0 when
+ * pairs whose spheres overlapped at the last detection, an overflow flag (bit 0 when
  * some mass point had more than 16 candidates above it, bit 1 when the rod had more than
  * 3 N candidate pairs, bit 2 when a mass point touched more than 16 others in one
- * iteration (the excess is dropped; sticky until rod_set_self_collision).  Synchronous. */
+ * iteration: the excess is dropped; bit 3 when a skin list overflowed and the step fell
+ * back to the full detection; sticky until rod_set_self_collision), and the number of
+ * skin-list builds in the launch.  Rods held by blocks of up to 512 nodes keep, within a
+ * launch, a skin list: the detection runs with the reach grown by 2 s (s = r / 2) and
+ * later steps test only the listed partners at the plain reach, until a mass point has
+ * moved more than s; the candidate pairs are those of the full detection.  Synchronous. */
 int rod_self_collision_stats(rod_handle h, int rod, int* out);
 
 /* Copy the drive input [n_rods][8] (host or device) into the handle. */

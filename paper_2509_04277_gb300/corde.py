@@ -183,10 +183,10 @@ def rod_set_self_collision(h, rod, mu, enable=True):
 
 
 def rod_self_collision_stats(h, rod) -> dict:
-    out = np.zeros(4, dtype=np.int32)
+    out = np.zeros(5, dtype=np.int32)
     _check(load().rod_self_collision_stats(h, int(rod), out.ctypes.data), "rod_self_collision_stats")
     return {"candidate_pairs": int(out[0]), "max_partners_above": int(out[1]), "overlapping_pairs": int(out[2]),
-            "overflow": int(out[3])}
+            "overflow": int(out[3]), "skin_builds": int(out[4])}
 
 
 def rod_set_input(h, drive, stream=None):

@@ -404,6 +404,7 @@ adjoint_kernel(AdjointArgs a) {
   }
   const BlockHalo<NT, NT> H{t};
   int xc = 0;
+  StepCache<EPT> sc;  // launch constants of the step (filled on the first step)
   const int n_seg = (a.n_steps + a.ckpt_every - 1) / a.ckpt_every;
   bool params_loaded = false;
   for (int seg = n_seg - 1; seg >= 0; --seg) {
@@ -439,7 +440,7 @@ adjoint_kernel(AdjointArgs a) {
       for (int s = 0; s < cnt; ++s) {
         put_state(s);
         StepNeighbours nb;
-        step_body<EPT, NT, true>(R, H, r, v, q, om, w, par_u, par_k, halo, xc, v_drive, w_drive, rec_at(s), &nb);
+        step_body<EPT, NT, true>(R, H, r, v, q, om, w, par_u, par_k, halo, xc, sc, v_drive, w_drive, rec_at(s), &nb);
         float4* nr = nb_at(s);
         nr[0] = make_float4(nb.r_next.x, nb.r_next.y, nb.r_next.z, nb.w_next);
         nr[NT] = make_float4(nb.r_prev.x, nb.r_prev.y, nb.r_prev.z, nb.w_prev);
@@ -452,7 +453,7 @@ adjoint_kernel(AdjointArgs a) {
       for (int s = 0; s < cnt; ++s) {
         put_state(s);
         if (s + 1 < cnt)
-          step_body<EPT, NT, false>(R, H, r, v, q, om, w, par_u, par_k, halo, xc, v_drive, w_drive, nullptr, nullptr);
+          step_body<EPT, NT, false>(R, H, r, v, q, om, w, par_u, par_k, halo, xc, sc, v_drive, w_drive, nullptr, nullptr);
       }
     }
     // reverse the segment's steps
@@ -569,7 +570,7 @@ adjoint_kernel(AdjointArgs a) {
         }
         if (s > 0) prefetch(s - 1);
         StepNeighbours nb;
-        step_body<EPT, NT, true>(R, H, r, v, q, om, w, par_u, par_k, halo, xc, v_drive, w_drive, sweep_v, &nb);
+        step_body<EPT, NT, true>(R, H, r, v, q, om, w, par_u, par_k, halo, xc, sc, v_drive, w_drive, sweep_v, &nb);
         // loss gradient with respect to the positions after this step
         if (a.dLdpos != nullptr) {
 #pragma unroll

@@ -154,7 +154,7 @@ struct corde_rods {
   std::vector<char> paired;    // per rod
   std::vector<char> tube;      // per rod: vessel contact enabled
   std::vector<char> self;      // per rod: self-collision enabled
-  int4* d_self_stats = nullptr;  // [n_rods] self-collision statistics
+  int4* d_self_stats = nullptr;  // [n_rods][2] self-collision statistics
   struct PairBin {
     int ept, nt, count;
     int4* d_pairs;
@@ -390,7 +390,11 @@ int build_bins(rod_handle h) {
     for (int r = 0; r < h->n_rods; ++r)
       if (h->plan_cluster[r] == k.first && h->plan[r] == k.second && !(r < (int)h->paired.size() && h->paired[r]))
         rods.push_back(r);
-    std::stable_sort(rods.begin(), rods.end(), [&](int a, int b) { return h->n_nodes[a] > h->n_nodes[b]; });
+    // heaviest rods first: a rod's work per step grows with its nodes times (the force
+    // phase, about seven constraint iterations' worth, plus its constraint iterations)
+    std::stable_sort(rods.begin(), rods.end(), [&](int a, int b) {
+      return (int64_t)h->n_nodes[a] * (7 + h->n_iters[a]) > (int64_t)h->n_nodes[b] * (7 + h->n_iters[b]);
+    });
     Bin b{k.second, (int)rods.size(), nullptr, k.first};
     CK(cudaMalloc(&b.d_work, rods.size() * sizeof(int)));
     CK(cudaMemcpy(b.d_work, rods.data(), rods.size() * sizeof(int), cudaMemcpyHostToDevice));
@@ -1044,7 +1048,9 @@ int rod_autotune(rod_handle h, int n_steps, void* stream) {
         nmax = std::max(nmax, h->n_nodes[r]);
       }
     if (rods.empty()) continue;
-    std::stable_sort(rods.begin(), rods.end(), [&](int a, int bb) { return h->n_nodes[a] > h->n_nodes[bb]; });
+    std::stable_sort(rods.begin(), rods.end(), [&](int a, int bb) {
+      return (int64_t)h->n_nodes[a] * (7 + h->n_iters[a]) > (int64_t)h->n_nodes[bb] * (7 + h->n_iters[bb]);
+    });
     int* d_work = nullptr;
     if (cudaMalloc(&d_work, rods.size() * sizeof(int)) != cudaSuccess) { rc = fail(CORDE_ERR_OOM, "autotune work list"); break; }
     cudaMemcpy(d_work, rods.data(), rods.size() * sizeof(int), cudaMemcpyHostToDevice);
@@ -1149,8 +1155,8 @@ int rod_set_self_collision(rod_handle h, int rod, const double* p) {
                                              " nodes");
   }
   if (!h->d_self_stats) {
-    CK(cudaMalloc(&h->d_self_stats, h->n_rods * sizeof(int4)));
-    CK(cudaMemset(h->d_self_stats, 0, h->n_rods * sizeof(int4)));
+    CK(cudaMalloc(&h->d_self_stats, 2 * h->n_rods * sizeof(int4)));
+    CK(cudaMemset(h->d_self_stats, 0, 2 * h->n_rods * sizeof(int4)));
   }
   const double* dr = &h->derived[16 * (size_t)rod];
   const double radius = std::sqrt(dr[1] / kPi), l0 = dr[0];
@@ -1158,7 +1164,7 @@ int rod_set_self_collision(rod_handle h, int rod, const double* p) {
   set_self_kernel<<<1, 1>>>(h->d_rods, rod, (float)(2.0 * radius), (float)(3.0 * radius), (float)p[0], (float)sep,
                             enable);
   CK(cudaGetLastError());
-  CK(cudaMemset(h->d_self_stats + rod, 0, sizeof(int4)));
+  CK(cudaMemset(h->d_self_stats + 2 * rod, 0, 2 * sizeof(int4)));
   CK(cudaDeviceSynchronize());
   h->self[rod] = (char)enable;
   if (enable) {
@@ -1177,12 +1183,13 @@ int rod_set_self_collision(rod_handle h, int rod, const double* p) {
 int rod_self_collision_stats(rod_handle h, int rod, int* out) {
   if (int rc = check_handle(h)) return rc;
   if (rod < 0 || rod >= h->n_rods || !out) return fail(CORDE_ERR_ARG, "rod_self_collision_stats: bad rod or NULL out");
-  int4 st = make_int4(0, 0, 0, 0);
-  if (h->d_self_stats) CK(cudaMemcpy(&st, h->d_self_stats + rod, sizeof(int4), cudaMemcpyDeviceToHost));
-  out[0] = st.x;
-  out[1] = st.y;
-  out[2] = st.z;
-  out[3] = st.w;
+  int4 st[2] = {make_int4(0, 0, 0, 0), make_int4(0, 0, 0, 0)};
+  if (h->d_self_stats) CK(cudaMemcpy(st, h->d_self_stats + 2 * rod, 2 * sizeof(int4), cudaMemcpyDeviceToHost));
+  out[0] = st[0].x;
+  out[1] = st[0].y;
+  out[2] = st[0].z;
+  out[3] = st[0].w;
+  out[4] = st[1].x;
   return CORDE_OK;
 }
 

@@ -194,19 +194,20 @@ pair_kernel(const RodDev* __restrict__ rods, const int4* __restrict__ pairs, flo
 
   const BlockHalo<NT, 2 * NT> H{t};
   int xc = 0;
+  StepCache<EPT> sc;  // launch constants of the step (filled on the first step)
   if constexpr (MB) {
     // beta is written by the inner rod's first thread only (here, and by its mailbox polls)
     if (group == 1 && t == 0) beta_sh = beta;
     RodMailbox<EPT> box(mb, R, rid, t * EPT, NT, group);
     for (int step = 0; step < n_steps; ++step) {
       if (box.before_step(H, step, v_drive, w_drive, group == 1 ? &beta_sh : nullptr)) break;
-      step_body<EPT, NT, false>(R, H, r, v, q, om, w, par_u, par_k, halo, xc, v_drive, w_drive, nullptr, nullptr,
+      step_body<EPT, NT, false>(R, H, r, v, q, om, w, par_u, par_k, halo, xc, sc, v_drive, w_drive, nullptr, nullptr,
                                 hook);
       box.after_step(H, step, r, v, w);
     }
   } else {
     for (int step = 0; step < n_steps; ++step)
-      step_body<EPT, NT, false>(R, H, r, v, q, om, w, par_u, par_k, halo, xc, v_drive, w_drive, nullptr, nullptr,
+      step_body<EPT, NT, false>(R, H, r, v, q, om, w, par_u, par_k, halo, xc, sc, v_drive, w_drive, nullptr, nullptr,
                                 hook);
   }
   const int e0 = t * EPT;

@@ -14,6 +14,14 @@
 //                  list of at most 16 in shared memory;
 //   compaction   - the pairs get consecutive slots, ordered by (i, j) (a block prefix sum
 //                  over the points' counts).
+// Skin list (rods in blocks of up to 512 nodes): the broad and narrow phases run with the
+// reach grown by two skin widths s = r / 2 and keep every point's partners in a list, with
+// the positions they were found at; on later steps each point only tests its listed
+// partners at the plain reach.  A pair within the reach now was within reach + 2 s at the
+// build as long as no mass point has moved more than s since, so the block rebuilds the
+// list as soon as one has moved more than 0.999 s (and on the first step of a launch, and
+// detects from scratch whenever a build overflows the list): the candidate pairs of every
+// step are exactly those of the full detection.
 // In every constraint iteration, after the distance sweeps (and the vessel contact), the
 // velocities are staged in shared memory and (Jacobi: everything from the staged
 // velocities)
@@ -39,6 +47,8 @@ namespace {
 constexpr int kSelfGroup = 8;         // mass points per bounding sphere
 constexpr int kSelfMaxCand = 16;      // larger partners kept per mass point; touching pairs per point
 constexpr int kSelfPairsPerNode = 3;  // compacted pair capacity: 3 pairs per mass point
+constexpr int kSkinMax = 24;          // partners kept per mass point in the skin list
+constexpr int kSkinNodes = 512;       // rods held by blocks of up to this many nodes keep a skin list
 
 // Shared-memory layout of the self-collision area (bytes from its start).
 template <int EPT, int NT>
@@ -60,7 +70,12 @@ struct SelfLayout {
   static constexpr int off_scan = off_act + ((NP * 2 + 15) / 16) * 16;  // int [NT / 32 + 1]
   static constexpr int off_stat = off_scan + ((NT / 32 + 1) * 4 + 15) / 16 * 16;  // int [8]
   static constexpr int off_list = off_stat + 32;  // uint16 [kSelfMaxCand][NN]: partners, then slots
-  static constexpr int bytes = off_list + kSelfMaxCand * NN * 2;
+  // skin list (blocks of up to kSkinNodes nodes): partners j > i within the reach grown by
+  // two skin widths at the last build, ascending, and their counts
+  static constexpr bool kSkin = NN <= kSkinNodes;
+  static constexpr int off_skin = off_list + kSelfMaxCand * NN * 2;  // uint16 [kSkinMax][NN]
+  static constexpr int off_skincnt = off_skin + (kSkin ? kSkinMax * NN * 2 : 0);  // uint8 [NN]
+  static constexpr int bytes = off_skincnt + (kSkin ? (NN + 15) / 16 * 16 : 0);
 };
 
 template <int NT>
@@ -112,6 +127,10 @@ struct SelfHook {
   int t, n, min_sep;
   float dt, inv_dt, dist, reach, mu;
   mutable int n_pairs;  // compacted pairs this step (block-uniform)
+  // skin list: positions of the thread's mass points at the last build, and whether the
+  // block's list is complete (block-uniform)
+  mutable float3 rb[EPT];
+  mutable int skin_valid = 0;
 
   __device__ __forceinline__ float4* sr() const { return reinterpret_cast<float4*>(base + L::off_r); }
   __device__ __forceinline__ float4* sv() const { return reinterpret_cast<float4*>(base + L::off_v); }
@@ -131,21 +150,17 @@ struct SelfHook {
   __device__ __forceinline__ unsigned short* list() const {
     return reinterpret_cast<unsigned short*>(base + L::off_list);
   }
+  __device__ __forceinline__ unsigned short* skin() const {
+    return reinterpret_cast<unsigned short*>(base + L::off_skin);
+  }
+  __device__ __forceinline__ unsigned char* skin_cnt() const {
+    return reinterpret_cast<unsigned char*>(base + L::off_skincnt);
+  }
 
-  // Detection: broad phase over bounding spheres, narrow phase over mass points, then the
-  // pairs compacted into slots ordered by (i, j).
-  template <int E>
-  __device__ __forceinline__ void before_iterations(const float3 (&r)[E], const float (&w)[E]) const {
-    float4* R4 = sr();
-    const int e0 = t * EPT;
-#pragma unroll
-    for (int e = 0; e < EPT; ++e)
-      if (e0 + e < n) {
-        R4[e0 + e] = make_float4(r[e].x, r[e].y, r[e].z, w[e]);
-        nact()[e0 + e] = 0;
-      }
-    if (t < 3) stat()[t] = 0;
-    block_sync<NT>();
+  // Bounding spheres of kSelfGroup mass points and the bit matrix of sphere pairs (a <= b)
+  // closer than their radii plus `rch` (two barriers; R4 staged before).
+  __device__ __forceinline__ void build_groups(float rch) const {
+    const float4* R4 = sr();
     const int ng = (n + kSelfGroup - 1) / kSelfGroup;
     for (int g = t; g < ng; g += NT) {
       const int k0 = g * kSelfGroup;
@@ -170,24 +185,37 @@ struct SelfHook {
         const int b = min(wd * 16 + bb, ng - 1);
         const float4 cb = gs()[b];
         const float dx = cb.x - ca.x, dy = cb.y - ca.y, dz = cb.z - ca.z;
-        const float lim = (ca.w + cb.w + reach) * 1.001f + 1e-6f;  // conservative against rounding
+        const float lim = (ca.w + cb.w + rch) * 1.001f + 1e-6f;  // conservative against rounding
         // pairs (i < j) only: groups b >= a
         if (wd * 16 + bb >= a && wd * 16 + bb < ng && dx * dx + dy * dy + dz * dz <= lim * lim) word |= 1u << bb;
       }
       bits()[a * L::NGH + wd] = (unsigned short)word;
     }
     block_sync<NT>();
-    const float reach2 = reach * reach, dist2 = dist * dist;
-    int n_up[EPT];
-    int my_up = 0, st_max = 0, st_touch = 0, st_over = 0;
+  }
+
+  // Detection: broad phase over bounding spheres, narrow phase over mass points, then the
+  // pairs compacted into slots ordered by (i, j).
+  template <int E>
+  __device__ __forceinline__ void before_iterations(const float3 (&r)[E], const float (&w)[E]) const {
+    float4* R4 = sr();
+    const int e0 = t * EPT;
 #pragma unroll
-    for (int e = 0; e < EPT; ++e) {
-      const int i = e0 + e;
-      n_up[e] = 0;
-      if (i >= n) continue;
-      const float4 ri = R4[i];
+    for (int e = 0; e < EPT; ++e)
+      if (e0 + e < n) {
+        R4[e0 + e] = make_float4(r[e].x, r[e].y, r[e].z, w[e]);
+        nact()[e0 + e] = 0;
+      }
+    if (t < 3) stat()[t] = 0;
+    const int ng = (n + kSelfGroup - 1) / kSelfGroup;
+    const int nh = (ng + 15) / 16;
+    const float reach2 = reach * reach, dist2 = dist * dist;
+    // narrow phase of point i over the groups its bit row marks: the partners j > i
+    // (j - i >= min_sep) with |r_i - r_j|^2 < rch2, ascending, into out[c NN + i] for c < cap;
+    // returns their number; *touching counts those closer than the contact distance
+    auto narrow = [&](int i, float4 ri, float rch2, unsigned short* out, int cap, int* touching) {
       const int a = i / kSelfGroup;
-      int c = 0, touching = 0;
+      int c = 0;
       for (int wd = a / 16; wd < nh; ++wd) {
         unsigned word = bits()[a * L::NGH + wd];
         while (word) {
@@ -201,16 +229,79 @@ struct SelfHook {
             const float dx = rj.x - ri.x, dy = rj.y - ri.y, dz = rj.z - ri.z;
             const float d2 = dx * dx + dy * dy + dz * dz;
             const bool ok = j < n && j - i >= min_sep;
-            if (ok && d2 < reach2) hit |= 1u << jj;
-            if (ok && d2 < dist2) ++touching;
+            if (ok && d2 < rch2) hit |= 1u << jj;
+            if (ok && d2 < dist2) ++*touching;
           }
           while (hit) {
             const int j = jb + __ffs(hit) - 1;
             hit &= hit - 1u;
+            if (c < cap) out[c * L::NN + i] = (unsigned short)j;
+            ++c;
+          }
+        }
+      }
+      return c;
+    };
+    bool use_skin = false;
+    if constexpr (L::kSkin) {
+      // rebuild the skin list when a mass point has moved more than 0.999 s since the last
+      // build (s = reach / 6 = r / 2), or when there is none (first step of the launch)
+      const float s = reach * (1.f / 6.f);
+      const float move2 = (0.999f * s) * (0.999f * s);
+      int moved = !skin_valid;
+#pragma unroll
+      for (int e = 0; e < EPT; ++e)
+        if (e0 + e < n) {
+          const float3 d = r[e] - rb[e];
+          moved |= dot3(d, d) > move2;
+        }
+      if (block_or<NT>(moved)) {  // (a barrier: the staged positions are visible)
+        const float rch = reach + 2.f * s;
+        build_groups(rch);
+        int over = 0, dummy = 0;
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) {
+          const int i = e0 + e;
+          if (i >= n) continue;
+          const int c = narrow(i, R4[i], rch * rch, skin(), kSkinMax, &dummy);
+          skin_cnt()[i] = (unsigned char)min(c, kSkinMax);
+          over |= c > kSkinMax;
+          rb[e] = r[e];
+        }
+        skin_valid = !block_or<NT>(over);  // (a barrier: the lists are visible)
+        if (t == 0) ++stat()[5];           // builds in this launch
+      }
+      use_skin = skin_valid;
+      if (!use_skin && t == 0) atomicOr(&stat()[3], 8);  // a build overflowed: full detection
+    } else {
+      block_sync<NT>();
+      build_groups(reach);
+    }
+    int n_up[EPT];
+    int my_up = 0, st_max = 0, st_touch = 0, st_over = 0;
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) {
+      const int i = e0 + e;
+      n_up[e] = 0;
+      if (i >= n) continue;
+      const float4 ri = R4[i];
+      int c = 0, touching = 0;
+      if (use_skin) {
+        // the listed partners at the plain reach (ascending, as the full detection finds them)
+        const int k = skin_cnt()[i];
+        for (int m = 0; m < k; ++m) {
+          const int j = skin()[m * L::NN + i];
+          const float4 rj = R4[j];
+          const float dx = rj.x - ri.x, dy = rj.y - ri.y, dz = rj.z - ri.z;
+          const float d2 = dx * dx + dy * dy + dz * dz;
+          if (d2 < dist2) ++touching;
+          if (d2 < reach2) {
             if (c < kSelfMaxCand) list()[c * L::NN + i] = (unsigned short)j;
             ++c;
           }
         }
+      } else {
+        c = narrow(i, ri, reach2, list(), kSelfMaxCand, &touching);
       }
       st_over |= c > kSelfMaxCand;
       n_up[e] = min(c, kSelfMaxCand);
@@ -404,12 +495,16 @@ self_step_kernel(const RodDev* __restrict__ rods, const int* __restrict__ work, 
   hook.reach = R.self_reach;
   hook.mu = R.self_mu;
   hook.n_pairs = 0;
-  if (t == 0) hook.stat()[3] = 0;  // overflow flag of this launch (read after the last barrier)
+  if (t == 0) {
+    hook.stat()[3] = 0;  // overflow flags of this launch (read after the last barrier)
+    hook.stat()[5] = 0;  // skin-list builds of this launch
+  }
 
   const BlockHalo<NT, NT> H{t};
   int xc = 0;
+  StepCache<EPT> sc;  // launch constants of the step (filled on the first step)
   for (int step = 0; step < n_steps; ++step)
-    step_body<EPT, NT, false>(R, H, r, v, q, om, w, par_u, par_k, halo, xc, v_drive, w_drive, nullptr, nullptr,
+    step_body<EPT, NT, false>(R, H, r, v, q, om, w, par_u, par_k, halo, xc, sc, v_drive, w_drive, nullptr, nullptr,
                               hook);
   const int e0 = t * EPT;
 #pragma unroll
@@ -426,12 +521,13 @@ self_step_kernel(const RodDev* __restrict__ rods, const int* __restrict__ work, 
   block_sync<NT>();
   if (t == 0 && stats != nullptr) {
     const int* st = hook.stat();
-    int4 out = stats[rid];
+    int4 out = stats[2 * rid];
     out.x = st[0];   // candidate pairs at the last detection
     out.y = st[1];   // most larger partners of one mass point
     out.z = st[2];   // pairs whose spheres overlap at the last detection
-    out.w |= st[3];  // 1: partner list, 2: pair slots, 4: touching pairs of a point overflowed (sticky)
-    stats[rid] = out;
+    out.w |= st[3];  // 1: partner list, 2: pair slots, 4: touching pairs of a point, 8: skin list overflowed
+    stats[2 * rid] = out;
+    stats[2 * rid + 1] = make_int4(st[5], 0, 0, 0);  // skin-list builds in the launch
   }
 }
 

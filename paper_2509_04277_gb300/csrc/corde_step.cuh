@@ -188,6 +188,22 @@ __device__ __forceinline__ float3 constraint_impulse(float3 e, float3 va, float3
   return f3(__fmul_rn(s, d.x), __fmul_rn(s, d.y), __fmul_rn(s, d.z));
 }
 
+// Predictive impulse with the masses folded into per-launch scales: with
+// c_a = w_a / (dt (w_a + w_b)) and c_b = w_b / (dt (w_a + w_b)) (0 for a constraint that does
+// not exist), v_a -= (l0 c_a / |d| - c_a) d and v_b += (l0 c_b / |d| - c_b) d: the update of
+// constraint_impulse with two dependent operations after the reciprocal square root
+// instead of four (it holds four scales per constraint in registers instead of one).
+__device__ __forceinline__ void constraint_apply(float3 e, float3& va, float3& vb, float ca, float l0ca, float cb,
+                                                 float l0cb, float dt) {
+  const float3 d = f3(__fmaf_rn(dt, __fsub_rn(vb.x, va.x), e.x), __fmaf_rn(dt, __fsub_rn(vb.y, va.y), e.y),
+                      __fmaf_rn(dt, __fsub_rn(vb.z, va.z), e.z));
+  const float dd = __fmaf_rn(d.x, d.x, __fmaf_rn(d.y, d.y, __fmul_rn(d.z, d.z)));
+  const float il = rsqrtf(dd);
+  const float sa = __fmaf_rn(l0ca, il, -ca), sb = __fmaf_rn(l0cb, il, -cb);
+  va = f3(__fmaf_rn(-sa, d.x, va.x), __fmaf_rn(-sa, d.y, va.y), __fmaf_rn(-sa, d.z, va.z));
+  vb = f3(__fmaf_rn(sb, d.x, vb.x), __fmaf_rn(sb, d.y, vb.y), __fmaf_rn(sb, d.z, vb.z));
+}
+
 // Two independent constraints in the two lanes of packed FP32x2 operations (Blackwell
 // fma/mul/add.f32x2): lane x and lane y each compute exactly what constraint_impulse
 // computes for them (round-to-nearest per lane), with half the instructions.
@@ -271,6 +287,23 @@ struct StepNeighbours {
   float4 q_next;
 };
 
+// Per-thread constants of a launch that step_body derives on its first step: the
+// constraint scales 1 / (dt (w_a + w_b)) of the thread's even, odd and boundary segments
+// (inverse masses do not change during a launch) and, with two elements per thread, the
+// folded per-node scales of constraint_apply.
+template <int EPT>
+struct StepCache {
+  static constexpr int NE = EPT / 2, NO = EPT / 2 > 1 ? EPT / 2 - 1 : 1;
+  // fold the masses into the impulse scales (fewer dependent operations per impulse, more
+  // registers: with four elements per thread the 128-register budget of the batch layout
+  // would spill)
+  static constexpr bool kFold = EPT == 2;
+  bool ready = false;
+  float i_even[NE], i_odd[NO], i_right, i_left;
+  float ca_even[NE], cb_even[NE], la_even[NE], lb_even[NE];
+  float2 c_bnd, l_bnd;  // per lane the scale of the thread's own node (right: -c_a, left: +c_b)
+};
+
 // Dynamic shared memory of a <EPT, NT> block: per-element joint parameters (u-hat and
 // K), element-major so that thread t's accesses are conflict-free, then the two
 // ping-pong exchange buffers of three float4 slots per thread.
@@ -281,15 +314,16 @@ constexpr int step_smem_bytes() {
 }
 
 // One time step of the rod; H (BlockHalo or ClusterHalo) gives the thread's place in the
-// rod, its neighbours' exchange slots and the barrier.  With STORE, the velocities before
-// every constraint half-sweep are written to sweep_v ([2 n_iters][EPT][NT]) and the
-// neighbour data to *nb (for the adjoint).
+// rod, its neighbours' exchange slots and the barrier; sc holds the launch constants
+// (default-constructed before the first step).  With STORE, the velocities before every
+// constraint half-sweep are written to sweep_v ([2 n_iters][EPT][NT]) and the neighbour
+// data to *nb (for the adjoint).
 template <int EPT, int NT, bool STORE, class Halo, class Hook = NoHook>
 __device__ __forceinline__ void step_body(const RodDev& R, const Halo& H, float3 (&r)[EPT], float3 (&v)[EPT],
                                           float4 (&q)[EPT], float3 (&om)[EPT], const float (&w)[EPT],
                                           const float4* par_u, const float4* par_k, float4* halo, int& xc,
-                                          const float3 v_drive, const float3 w_drive, float4* sweep_v,
-                                          StepNeighbours* nb, const Hook& hook = Hook()) {
+                                          StepCache<EPT>& sc, const float3 v_drive, const float3 w_drive,
+                                          float4* sweep_v, StepNeighbours* nb, const Hook& hook = Hook()) {
   const int t = H.t;
   const int e0 = H.tg() * EPT;
   const int n = R.n;
@@ -377,8 +411,45 @@ __device__ __forceinline__ void step_body(const RodDev& R, const Halo& H, float3
   H.put3(hb, 1, tau_carry);
   H.arrive();
 
-  // ---- integrate forces and torques into velocities; on a cluster, elements 1 .. EPT - 1
-  // (they take no carry) run while the exchange barrier completes
+  // ---- while the exchange barrier completes: the constraint geometry of this step (the
+  // positions and masses do not change in the sweeps) and the force integration of
+  // elements 1 .. EPT - 1, which take no carry
+  constexpr int NE = StepCache<EPT>::NE, NO = StepCache<EPT>::NO;
+  float3 e_even[NE], e_odd[NO], e_r = zero3(), e_l = zero3();
+  if (inext) {
+    if (!sc.ready) {
+#pragma unroll
+      for (int k = 0; k < NE; ++k) sc.i_even[k] = inv_dt_wsum(e0 + 2 * k + 1 <= n - 1, w[2 * k], w[2 * k + 1], dt);
+#pragma unroll
+      for (int k = 0; k < NO; ++k) {
+        const bool ex = EPT / 2 > 1 && e0 + 2 * k + 2 <= n - 1;
+        sc.i_odd[k] = inv_dt_wsum(ex, w[(2 * k + 1) % EPT], w[(2 * k + 2) % EPT], dt);
+      }
+      // the two boundary constraints: right (my last, next first), left (previous last,
+      // my first)
+      sc.i_right = inv_dt_wsum(has_next && e0 + EPT <= n - 1, w[EPT - 1], w_next, dt);
+      sc.i_left = inv_dt_wsum(has_prev && e0 <= n - 1, w_prev, w[0], dt);
+      if constexpr (StepCache<EPT>::kFold) {
+#pragma unroll
+        for (int k = 0; k < NE; ++k) {
+          sc.ca_even[k] = w[2 * k] * sc.i_even[k];
+          sc.cb_even[k] = w[2 * k + 1] * sc.i_even[k];
+          sc.la_even[k] = R.l0 * sc.ca_even[k];
+          sc.lb_even[k] = R.l0 * sc.cb_even[k];
+        }
+        sc.c_bnd = make_float2(-w[EPT - 1] * sc.i_right, w[0] * sc.i_left);
+        sc.l_bnd = make_float2(R.l0 * sc.c_bnd.x, R.l0 * sc.c_bnd.y);
+      }
+      sc.ready = true;
+    }
+#pragma unroll
+    for (int k = 0; k < NE; ++k) e_even[k] = safe_segment(sc.i_even[k], segment_vector(r[2 * k], r[2 * k + 1]), R.l0);
+#pragma unroll
+    for (int k = 0; k < NO; ++k)
+      e_odd[k] = safe_segment(sc.i_odd[k], segment_vector(r[(2 * k + 1) % EPT], r[(2 * k + 2) % EPT]), R.l0);
+    e_r = safe_segment(sc.i_right, segment_vector(r[EPT - 1], r_next), R.l0);
+    e_l = safe_segment(sc.i_left, segment_vector(r_prev, r[0]), R.l0);
+  }
   auto integrate = [&](int e) {
     const int i = e0 + e;
     if (w[e] > 0.f) {
@@ -394,21 +465,14 @@ __device__ __forceinline__ void step_body(const RodDev& R, const Halo& H, float3
       om[e] = R.damp * on;
     }
   };
-  if constexpr (Halo::kCluster) {
 #pragma unroll
-    for (int e = 1; e < EPT; ++e) integrate(e);
-  }
+  for (int e = 1; e < EPT; ++e) integrate(e);
   H.wait();
   if (has_prev) {
     F[0] += H.prev3(hb, 0);
     tau[0] += H.prev3(hb, 1);
   }
-  if constexpr (Halo::kCluster) {
-    integrate(0);
-  } else {
-#pragma unroll
-    for (int e = 0; e < EPT; ++e) integrate(e);
-  }
+  integrate(0);
   if (clamp && e0 == 0) {
     v[0] = v_drive;
     om[0] = w_drive;
@@ -418,29 +482,9 @@ __device__ __forceinline__ void step_body(const RodDev& R, const Halo& H, float3
   if (inext) {
     hook.template before_iterations<EPT>(r, w);
     const float inv_dt = 1.f / dt;
-    // constraint geometry of this step (positions and masses do not change in the sweeps)
-    constexpr int NE = EPT / 2, NO = EPT / 2 > 1 ? EPT / 2 - 1 : 1;
-    float3 e_even[NE], e_odd[NO];
-    float i_even[NE], i_odd[NO];
-#pragma unroll
-    for (int k = 0; k < NE; ++k) {
-      i_even[k] = inv_dt_wsum(e0 + 2 * k + 1 <= n - 1, w[2 * k], w[2 * k + 1], dt);
-      e_even[k] = safe_segment(i_even[k], segment_vector(r[2 * k], r[2 * k + 1]), R.l0);
-    }
-#pragma unroll
-    for (int k = 0; k < NO; ++k) {
-      const bool ex = EPT / 2 > 1 && e0 + 2 * k + 2 <= n - 1;
-      i_odd[k] = inv_dt_wsum(ex, w[(2 * k + 1) % EPT], w[(2 * k + 2) % EPT], dt);
-      e_odd[k] = safe_segment(i_odd[k], segment_vector(r[(2 * k + 1) % EPT], r[(2 * k + 2) % EPT]), R.l0);
-    }
-    // the two boundary constraints, right (my last, next first) in lane x and left
-    // (previous last, my first) in lane y
-    const float i_right = inv_dt_wsum(has_next && e0 + EPT <= n - 1, w[EPT - 1], w_next, dt);
-    const float i_left = inv_dt_wsum(has_prev && e0 <= n - 1, w_prev, w[0], dt);
-    const float3 e_r = safe_segment(i_right, segment_vector(r[EPT - 1], r_next), R.l0);
-    const float3 e_l = safe_segment(i_left, segment_vector(r_prev, r[0]), R.l0);
+    // the two boundary constraints, right in lane x and left in lane y
     const Vec3x2 e_bnd{make_float2(e_r.x, e_l.x), make_float2(e_r.y, e_l.y), make_float2(e_r.z, e_l.z)};
-    const float2 i_bnd = make_float2(i_right, i_left);
+    const float2 i_bnd = make_float2(sc.i_right, sc.i_left);
     const float2 w_bnd = make_float2(-w[EPT - 1], w[0]);
 
     // one iteration; tube_on (a compile-time bool) adds the vessel contact
@@ -450,8 +494,13 @@ __device__ __forceinline__ void step_body(const RodDev& R, const Halo& H, float3
         for (int e = 0; e < EPT; ++e) sweep_v[((2 * it) * EPT + e) * NT + t] = make_float4(v[e].x, v[e].y, v[e].z, 0.f);
       }
       // even segments (e0 + 2k, e0 + 2k + 1): local to the thread, two per packed op
-      if constexpr (NE == 1) {
-        const float3 g = constraint_impulse(e_even[0], v[0], v[1], i_even[0], R.l0, dt);
+      if constexpr (StepCache<EPT>::kFold) {
+#pragma unroll
+        for (int k = 0; k < NE; ++k)
+          constraint_apply(e_even[k], v[2 * k], v[2 * k + 1], sc.ca_even[k], sc.la_even[k], sc.cb_even[k],
+                           sc.lb_even[k], dt);
+      } else if constexpr (NE == 1) {
+        const float3 g = constraint_impulse(e_even[0], v[0], v[1], sc.i_even[0], R.l0, dt);
         v[0] -= w[0] * g;
         v[1] += w[1] * g;
       } else {
@@ -462,7 +511,7 @@ __device__ __forceinline__ void step_body(const RodDev& R, const Halo& H, float3
                           make_float2(e_even[k].z, e_even[k + 1].z)};
           const Vec3x2 va{make_float2(v[a0].x, v[a1].x), make_float2(v[a0].y, v[a1].y), make_float2(v[a0].z, v[a1].z)};
           const Vec3x2 vb{make_float2(v[b0].x, v[b1].x), make_float2(v[b0].y, v[b1].y), make_float2(v[b0].z, v[b1].z)};
-          const Vec3x2 g = constraint_impulse2(ep, va, vb, make_float2(i_even[k], i_even[k + 1]), R.l0, dt);
+          const Vec3x2 g = constraint_impulse2(ep, va, vb, make_float2(sc.i_even[k], sc.i_even[k + 1]), R.l0, dt);
           v[a0] -= w[a0] * f3(g.x.x, g.y.x, g.z.x);
           v[a1] -= w[a1] * f3(g.x.y, g.y.y, g.z.y);
           v[b0] += w[b0] * f3(g.x.x, g.y.x, g.z.x);
@@ -470,7 +519,7 @@ __device__ __forceinline__ void step_body(const RodDev& R, const Halo& H, float3
         }
         if constexpr (NE % 2 == 1) {
           const int a = EPT - 2, b = EPT - 1;
-          const float3 g = constraint_impulse(e_even[NE - 1], v[a], v[b], i_even[NE - 1], R.l0, dt);
+          const float3 g = constraint_impulse(e_even[NE - 1], v[a], v[b], sc.i_even[NE - 1], R.l0, dt);
           v[a] -= w[a] * g;
           v[b] += w[b] * g;
         }
@@ -491,7 +540,7 @@ __device__ __forceinline__ void step_body(const RodDev& R, const Halo& H, float3
 #pragma unroll
       for (int k = 0; k + 1 < EPT / 2; ++k) {
         const int a = 2 * k + 1, b = 2 * k + 2;
-        const float3 g = constraint_impulse(e_odd[k], v[a], v[b], i_odd[k], R.l0, dt);
+        const float3 g = constraint_impulse(e_odd[k], v[a], v[b], sc.i_odd[k], R.l0, dt);
         v[a] -= w[a] * g;
         v[b] += w[b] * g;
       }
@@ -503,11 +552,26 @@ __device__ __forceinline__ void step_body(const RodDev& R, const Halo& H, float3
         const Vec3x2 va{make_float2(v[EPT - 1].x, vp.x), make_float2(v[EPT - 1].y, vp.y),
                         make_float2(v[EPT - 1].z, vp.z)};
         const Vec3x2 vb{make_float2(vn.x, v[0].x), make_float2(vn.y, v[0].y), make_float2(vn.z, v[0].z)};
-        const Vec3x2 g = constraint_impulse2(e_bnd, va, vb, i_bnd, R.l0, dt);
-        // right: v_last -= w_last g.x ; left: v_first += w_first g.y
-        const float2 nx = __ffma2_rn(w_bnd, g.x, make_float2(v[EPT - 1].x, v[0].x));
-        const float2 ny = __ffma2_rn(w_bnd, g.y, make_float2(v[EPT - 1].y, v[0].y));
-        const float2 nz = __ffma2_rn(w_bnd, g.z, make_float2(v[EPT - 1].z, v[0].z));
+        float2 nx, ny, nz;
+        if constexpr (StepCache<EPT>::kFold) {
+          const float2 dt2 = make_float2(dt, dt);
+          const float2 dx = __ffma2_rn(dt2, __fadd2_rn(vb.x, neg2(va.x)), e_bnd.x);
+          const float2 dy = __ffma2_rn(dt2, __fadd2_rn(vb.y, neg2(va.y)), e_bnd.y);
+          const float2 dz = __ffma2_rn(dt2, __fadd2_rn(vb.z, neg2(va.z)), e_bnd.z);
+          const float2 dd = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+          const float2 il = make_float2(rsqrtf(dd.x), rsqrtf(dd.y));
+          const float2 scl = __ffma2_rn(sc.l_bnd, il, neg2(sc.c_bnd));
+          // right: v_last -= c_a (l0 / |d| - 1) d ; left: v_first += c_b (l0 / |d| - 1) d
+          nx = __ffma2_rn(scl, dx, make_float2(v[EPT - 1].x, v[0].x));
+          ny = __ffma2_rn(scl, dy, make_float2(v[EPT - 1].y, v[0].y));
+          nz = __ffma2_rn(scl, dz, make_float2(v[EPT - 1].z, v[0].z));
+        } else {
+          const Vec3x2 g = constraint_impulse2(e_bnd, va, vb, i_bnd, R.l0, dt);
+          // right: v_last -= w_last g.x ; left: v_first += w_first g.y
+          nx = __ffma2_rn(w_bnd, g.x, make_float2(v[EPT - 1].x, v[0].x));
+          ny = __ffma2_rn(w_bnd, g.y, make_float2(v[EPT - 1].y, v[0].y));
+          nz = __ffma2_rn(w_bnd, g.z, make_float2(v[EPT - 1].z, v[0].z));
+        }
         v[EPT - 1] = f3(nx.x, ny.x, nz.x);
         v[0] = f3(nx.y, ny.y, nz.y);
       }
@@ -779,9 +843,10 @@ __device__ __forceinline__ void run_rod(const RodDev& R, const Halo& H, const in
   RodMailbox<EPT> box(mb, R, rid, e0, H.rod_threads());
 
   int xc = 0;  // exchange counter selects the ping-pong buffer
+  StepCache<EPT> sc;  // launch constants of the step (filled on the first step)
   for (int step = 0; step < n_steps; ++step) {
     if (box.before_step(H, step, v_drive, w_drive)) break;
-    step_body<EPT, NT, false>(R, H, r, v, q, om, w, par_u, par_k, halo, xc, v_drive, w_drive, nullptr, nullptr);
+    step_body<EPT, NT, false>(R, H, r, v, q, om, w, par_u, par_k, halo, xc, sc, v_drive, w_drive, nullptr, nullptr);
     if (traj != nullptr) {
 #pragma unroll
       for (int e = 0; e < EPT; ++e)

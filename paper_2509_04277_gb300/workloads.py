@@ -215,11 +215,12 @@ def catheter(n: int = 512, seed: int = 3) -> RodSpec:
 
 
 def batched_rods(n_rods: int = 4096, seed: int = 4, n_min: int = 16, n_max: int = 2048,
-                 dt: float = 1e-4) -> list[RodSpec]:
+                 dt: float = 1e-4, n_iters=None) -> list[RodSpec]:
     """Independent inextensible rods with log-uniform element counts in
     [n_min, n_max], E ~ U[1, 100] GPa, radius ~ U[0.2, 2] mm, L = 1 m, G = E / 2.6,
     rho = 6500, base orientation uniform on SO(3), gravity on (free-space pendulums
-    locked at one end, Section 3.1)."""
+    locked at one end, Section 3.1).  ``n_iters``: constraint iterations per rod (a
+    sequence of n_rods counts), else 10 for every rod."""
     g = rng(seed)
     ns = np.rint(np.exp(g.uniform(math.log(n_min), math.log(n_max), size=n_rods))).astype(int)
     ns = np.clip(ns, n_min, n_max)
@@ -233,7 +234,7 @@ def batched_rods(n_rods: int = 4096, seed: int = 4, n_min: int = 16, n_max: int 
             int(ns[k]), 1.0, orientation=orients[k], seg_sigma=1e-3, ang_sigma=1e-3,
             seed=int(seeds[k]), radius=float(rs[k]), E_bend=float(Es[k]),
             E_stretch=float(Es[k]), G=float(Es[k]) / 2.6, density=6500.0, dt=dt,
-            n_iters=10, inextensible=True, clamp=1, damping_alpha=0.0,
+            n_iters=10 if n_iters is None else int(n_iters[k]), inextensible=True, clamp=1, damping_alpha=0.0,
             gravity=(0.0, 0.0, -9.81),
         ))
     return rods

@@ -78,8 +78,10 @@ def test_self_one_step_parity(corde, n):
 
 
 def test_self_detection_matches_oracle(corde):
-    """The candidate pairs the GPU found at its last detection are the oracle's pairs of the
-    same positions (the broad phase drops none)."""
+    """The candidate pairs the GPU found at the last detection of a launch are the oracle's
+    pairs of the same positions (the broad phase drops none), on every step of launches
+    of 1 to 20 steps: within a launch later steps test only the skin list of the first
+    step's build (until a mass point has moved half a radius), and the set stays exact."""
     import torch
 
     rod = W.torus_knot(512, seed=710)
@@ -87,14 +89,26 @@ def test_self_detection_matches_oracle(corde):
     b.set_self_collision(0, MU)
     d = _drive(torch, PULL)
     b.step(30, drive=d)
-    st0 = b.rod_state(b.state_numpy(), 0)
-    b.step(1, drive=d)
-    stats = b.self_collision_stats(0)
-    cand, pairs = oracle.self_candidates(rod, st0["pos"])
-    assert stats["candidate_pairs"] == pairs
-    assert stats["max_partners_above"] == max(int(np.sum(c > i)) for i, c in enumerate(cand))
-    assert not stats["overflow"]
-    assert stats["overlapping_pairs"] >= 0
+    s0 = b.rod_state(b.state_numpy(), 0)
+    filtered = 0
+    for k in range(1, 21):
+        # the positions at the start of the last step of a k-step launch: the end of a
+        # (k - 1)-step launch from the same state (the same arithmetic, bit for bit)
+        b.set_rod_states([s0])
+        if k > 1:
+            b.step(k - 1, drive=d)
+        pos = b.rod_state(b.state_numpy(), 0)["pos"]
+        b.set_rod_states([s0])
+        b.step(k, drive=d)
+        stats = b.self_collision_stats(0)
+        cand, pairs = oracle.self_candidates(rod, pos)
+        assert stats["candidate_pairs"] == pairs, (k, stats, pairs)
+        assert stats["max_partners_above"] == max(int(np.sum(c > i)) for i, c in enumerate(cand)), k
+        assert not stats["overflow"], (k, stats)
+        assert stats["overlapping_pairs"] >= 0
+        assert 1 <= stats["skin_builds"] <= k
+        filtered += k - stats["skin_builds"]
+    assert filtered > 100  # most steps ran on the skin list
     b.close()
 
 
