@@ -459,6 +459,7 @@ def run_adjoint(args, torch, corde, W, n_rods=1):
         g[:, tip, :3] = 2.0 * (traj[:, tip, :3] - torch.as_tensor(targets[k], dtype=torch.float32, device="cuda"))
     adj_ms, grads = timed(lambda: b.adjoint(g))
     finite = bool(all(torch.isfinite(v).all().item() for v in grads.values()))
+    launch_info = corde.rod_adjoint_info(b.handle)
     b.close()
     el_steps = sum(r.n_nodes for r in rods) * n_steps
     # algorithmic DRAM bytes of the reverse pass: the loss gradient dL/dpos it reads
@@ -468,11 +469,12 @@ def run_adjoint(args, torch, corde, W, n_rods=1):
     hbm = _peaks()[0].get("hbm_gbs", 6800.0)
     # the library's choice (rod_set_adjoint_record_budget, default 64 MiB): record each
     # segment's sweeps when they fit, else recompute every step before its reverse
-    nt = 128
+    nt = launch_info["threads_per_block"]
     rec_bytes = ckpt * n_rods * (2 * rods[0].n_iters * 2 * nt + 3 * nt) * 16
-    mode = "record" if rec_bytes <= (64 << 20) else "recompute"
+    mode = launch_info["mode"]
     return {"n_rods": n_rods, "n_nodes": 256, "n_steps": n_steps, "ckpt_every": ckpt,
             "reverse_pass": f"{mode} mode ({rec_bytes / 2**20:.1f} MiB of sweep records per segment)",
+            "launch": launch_info,
             "roofline_hbm": {"bytes": adj_bytes, "achieved_gbs": round(adj_bytes / (adj_ms * 1e-3) / 1e9, 2),
                              "peak_gbs": hbm, "frac": round(adj_bytes / (adj_ms * 1e-3) / 1e9 / hbm, 5),
                              "note": "latency-bound like the forward: one block per rod"},

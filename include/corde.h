@@ -164,7 +164,7 @@ int rod_set_self_collision(rod_handle h, int rod, const double* params);
  * iteration: the excess is dropped; bit 3 when a skin list overflowed and the step fell
  * back to the full detection; sticky until rod_set_self_collision), and the number of
  * skin-list builds in the launch.  Rods held by blocks of up to 512 nodes keep, within a
- * launch, a skin list: the detection runs with the reach grown by 2 s (s = r / 2) and
+ * launch, a skin list: the detection runs with the reach grown by 2 s (s = r) and
  * later steps test only the listed partners at the plain reach, until a mass point has
  * moved more than s; the candidate pairs are those of the full detection.  Synchronous. */
 int rod_self_collision_stats(rod_handle h, int rod, int* out);
@@ -331,6 +331,13 @@ int rod_rollout(rod_handle h, int n_steps, int ckpt_every, float* pos_traj, void
  * rod_adjoint must not change.  CORDE_ERR_UNSUPPORTED when the limits are exceeded. */
 int rod_adjoint(rod_handle h, const float* dL_dpos_traj, float* dL_dK, float* dL_duhat, float* dL_dvel0,
                 float* dL_dpos0, float* dL_dquat0, float* dL_domega0, void* stream);
+
+/* How the last rod_adjoint ran its largest launch, into 5 host ints: 1 for record mode
+ * (0: recompute), threads per block, resident blocks per SM (occupancy API, with the
+ * launch's registers and shared memory), blocks of the launch (one per rod), and the
+ * device's SMs; blocks / (blocks per SM x SMs), rounded up, is the number of waves.
+ * Host-side only (zeros before the first rod_adjoint). */
+int rod_adjoint_info(rod_handle h, int* out);
 
 /* Scratch budget of rod_adjoint's record mode (default 64 MiB).  Within a checkpoint
  * segment the reverse pass needs every step's velocities before each constraint

@@ -63,6 +63,7 @@ SIGNATURES = {
     "rod_set_plan": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
     "rod_set_launch_overlap": (ctypes.c_int, [_VP, ctypes.c_int]),
     "rod_set_adjoint_record_budget": (ctypes.c_int, [_VP, ctypes.c_longlong]),
+    "rod_adjoint_info": (ctypes.c_int, [_VP, _VP]),
     "rod_set_plan_cluster": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "rod_autotune": (ctypes.c_int, [_VP, ctypes.c_int, _VP]),
     "rod_autotune_steps": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, _VP, _VP]),
@@ -340,6 +341,16 @@ def rod_adjoint(h, dL_dpos_traj=None, dL_dK=None, dL_duhat=None, dL_dvel0=None, 
                 dL_domega0=None, stream=None):
     _check(load().rod_adjoint(h, _ptr(dL_dpos_traj), _ptr(dL_dK), _ptr(dL_duhat), _ptr(dL_dvel0), _ptr(dL_dpos0),
                               _ptr(dL_dquat0), _ptr(dL_domega0), _stream(stream)), "rod_adjoint")
+
+
+def rod_adjoint_info(h) -> dict:
+    """How the last rod_adjoint ran its largest launch (mode, threads, blocks per SM, blocks, SMs)."""
+    out = np.zeros(5, dtype=np.int32)
+    _check(load().rod_adjoint_info(h, out.ctypes.data), "rod_adjoint_info")
+    per_sm, blocks, sms = int(out[2]), int(out[3]), int(out[4])
+    return {"mode": "record" if out[0] else "recompute", "threads_per_block": int(out[1]),
+            "blocks_per_sm": per_sm, "blocks": blocks, "sms": sms,
+            "waves": -(-blocks // (per_sm * sms)) if per_sm * sms > 0 else None}
 
 
 def rod_barrier_floor(scope, threads=128, cluster=1, n_iters=100000, stream=None) -> float:

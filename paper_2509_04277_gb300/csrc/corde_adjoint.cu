@@ -618,6 +618,23 @@ int adjoint_smem_bytes(int nt, int n_iters, bool record) {
   return (2 * ept * nt + 2 * kHaloSlots * nt + (record ? 2 : 1) * sweep) * (int)sizeof(float4);
 }
 
+template <int NT, bool RECORD>
+cudaError_t occupancy_mode(int smem, int* blocks) {
+  cudaError_t e = cudaFuncSetAttribute(adjoint_kernel<NT, RECORD>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, adjoint_kernel<NT, RECORD>, NT, (size_t)smem);
+}
+
+cudaError_t adjoint_occupancy(int nt, bool record, int smem, int* blocks) {
+  switch (nt) {
+    case 32: return record ? occupancy_mode<32, true>(smem, blocks) : occupancy_mode<32, false>(smem, blocks);
+    case 64: return record ? occupancy_mode<64, true>(smem, blocks) : occupancy_mode<64, false>(smem, blocks);
+    case 128: return record ? occupancy_mode<128, true>(smem, blocks) : occupancy_mode<128, false>(smem, blocks);
+    case 256: return record ? occupancy_mode<256, true>(smem, blocks) : occupancy_mode<256, false>(smem, blocks);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 cudaError_t preload_adjoint(int nt) {
   cudaFuncAttributes at;
   switch (nt) {

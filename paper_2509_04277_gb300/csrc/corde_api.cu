@@ -148,6 +148,7 @@ struct corde_rods {
   size_t nb_rec_cap = 0;
   long long adj_record_budget = 64ll << 20;
   int ro_steps = 0, ro_every = 0;
+  int adj_info[5] = {0, 0, 0, 0, 0};  // last rod_adjoint's largest launch: mode, nt, blocks/SM, blocks, SMs
   std::vector<Bin> adj_bins;  // variant = threads per block
   // catheter/guidewire pairs
   std::vector<int4> pairs;     // (outer, inner, mode, 0)
@@ -1391,6 +1392,7 @@ int rod_adjoint(rod_handle h, const float* dL_dpos_traj, float* dL_dK, float* dL
   a.dquat0 = dev_out[4];
   a.domega0 = dev_out[5];
   int launches = 0;
+  std::fill(h->adj_info, h->adj_info + 5, 0);
   for (size_t i = 0; i < h->adj_bins.size(); ++i) {
     const Bin& b = h->adj_bins[i];
     const int nt = variants()[b.variant].nt;
@@ -1403,11 +1405,24 @@ int rod_adjoint(rod_handle h, const float* dL_dpos_traj, float* dL_dK, float* dL
                                              std::to_string(smem_max) + " available (fewer constraint iterations " +
                                              "or shorter rods)");
     a.work = b.d_work;
+    if (b.count >= h->adj_info[3]) {
+      int per_sm = 0, sms = 0;
+      CK(adjoint_occupancy(nt, record[i] != 0, smem, &per_sm));
+      CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+      const int info[5] = {record[i] ? 1 : 0, nt, per_sm, b.count, sms};
+      std::copy(info, info + 5, h->adj_info);
+    }
     cudaError_t e = launch_adjoint(nt, a, b.count, smem, s);
     if (e != cudaSuccess) return fail(CORDE_ERR_CUDA, std::string("adjoint launch: ") + cudaGetErrorString(e));
     ++launches;
   }
   h->last_launches = launches;
+  return CORDE_OK;
+}
+
+int rod_adjoint_info(rod_handle h, int* out) {
+  if (!h || !out) return fail(CORDE_ERR_ARG, "rod_adjoint_info: NULL argument");
+  std::copy(h->adj_info, h->adj_info + 5, out);
   return CORDE_OK;
 }
 

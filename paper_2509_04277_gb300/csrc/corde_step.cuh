@@ -15,7 +15,9 @@
 //      variant, Section 2.1 "Constraints"): the even segments of a thread are local
 //      (EPT is even and every thread starts on an even element); the odd sweep needs one
 //      exchange (boundary velocities) for the segment crossing each thread boundary;
-//   5. integration of the velocities: r += dt v, q <- normalize(q + dt/2 q (x) (0, omega)).
+//   5. integration of the velocities: r += dt v, q <- normalize(q + dt/2 q (x) (0, omega))
+//      (the frames' update needs only omega, final after step 3, so it runs before the
+//      sweeps of step 4 and fills their latency).
 // A step costs 2 + n_iters block barriers (the paper's single-block kernel uses two
 // __syncthreads per constraint iteration, one thread per element).  Neighbour data moves
 // through a ping-pong pair of shared-memory buffers, so one barrier per exchange suffices.
@@ -477,6 +479,24 @@ __device__ __forceinline__ void step_body(const RodDev& R, const Halo& H, float3
     v[0] = v_drive;
     om[0] = w_drive;
   }
+  // ---- integrate the angular velocities into the frames (semi-implicit Euler): the
+  // constraint sweeps change only the node velocities, so the frames' update is final
+  // here and overlaps the sweeps' latency
+#pragma unroll
+  for (int e = 0; e < EPT; ++e) {
+    if (e0 + e <= n - 2) {
+      const float4 a = q[e];
+      const float3 o = om[e];
+      // q (x) (0, omega)
+      const float dx = a.w * o.x + a.y * o.z - a.z * o.y;
+      const float dy = a.w * o.y + a.z * o.x - a.x * o.z;
+      const float dz = a.w * o.z + a.x * o.y - a.y * o.x;
+      const float dwq = -(a.x * o.x + a.y * o.y + a.z * o.z);
+      const float4 b = make_float4(a.x + half_dt * dx, a.y + half_dt * dy, a.z + half_dt * dz, a.w + half_dt * dwq);
+      const float inv = rsqrtf(b.x * b.x + b.y * b.y + b.z * b.z + b.w * b.w);
+      q[e] = make_float4(b.x * inv, b.y * inv, b.z * inv, b.w * inv);
+    }
+  }
 
   // ---- distance-constraint iterations (inextensible rod), red-black
   if (inext) {
@@ -597,24 +617,9 @@ __device__ __forceinline__ void step_body(const RodDev& R, const Halo& H, float3
     }
   }
 
-  // ---- integrate linear and angular velocities (semi-implicit Euler)
+  // ---- integrate the node velocities into the positions (semi-implicit Euler)
 #pragma unroll
-  for (int e = 0; e < EPT; ++e) {
-    const int i = e0 + e;
-    r[e] += dt * v[e];
-    if (i <= n - 2) {
-      const float4 a = q[e];
-      const float3 o = om[e];
-      // q (x) (0, omega)
-      const float dx = a.w * o.x + a.y * o.z - a.z * o.y;
-      const float dy = a.w * o.y + a.z * o.x - a.x * o.z;
-      const float dz = a.w * o.z + a.x * o.y - a.y * o.x;
-      const float dwq = -(a.x * o.x + a.y * o.y + a.z * o.z);
-      const float4 b = make_float4(a.x + half_dt * dx, a.y + half_dt * dy, a.z + half_dt * dz, a.w + half_dt * dwq);
-      const float inv = rsqrtf(b.x * b.x + b.y * b.y + b.z * b.z + b.w * b.w);
-      q[e] = make_float4(b.x * inv, b.y * inv, b.z * inv, b.w * inv);
-    }
-  }
+  for (int e = 0; e < EPT; ++e) r[e] += dt * v[e];
 }
 
 // Loads the rod's elements owned by thread tg of the rod (registers) and their joint

@@ -97,6 +97,9 @@ int adjoint_smem_bytes(int nt, int n_iters, bool record = false);
 cudaError_t launch_adjoint(int nt, const AdjointArgs& a, int n_blocks, int smem, cudaStream_t s);
 // Loads the recompute-mode reverse kernel of `nt` threads into the current context.
 cudaError_t preload_adjoint(int nt);
+// Resident blocks per SM of the reverse kernel of `nt` threads with `smem` bytes of
+// dynamic shared memory (occupancy API).
+cudaError_t adjoint_occupancy(int nt, bool record, int smem, int* blocks);
 constexpr int kAdjointMaxNodes = 512;
 
 // Rods with self-collision (corde_self.cu): one rod per block, at most 1024 nodes.
