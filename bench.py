@@ -584,12 +584,12 @@ def run_extensible(args, torch, corde, W):
 
 def run_long_rods(args, torch, corde, W):
     """Latency per step against rod length (the paper's near-constant-time claim for rods
-    spread over several SMs, Fig. 7): guidewire-like rods of 512 ... 8192 nodes (L grows
-    with N at the guidewire's segment length), 10 steps per launch; rods above 2048 nodes
-    run on a thread-block cluster."""
+    spread over several SMs, Fig. 7): guidewire rods (L = 1.5 m) of 512 ... 131072 nodes,
+    10 steps per launch; rods above 2048 nodes run on a thread-block cluster, above 32768
+    on a cooperative grid (2048 nodes per block)."""
     stream = torch.cuda.current_stream()
     out = {}
-    for n in (512, 1024, 2048, 3072, 4096, 8192, 16384):
+    for n in (512, 1024, 2048, 3072, 4096, 8192, 16384, 32768, 65536, 131072):
         rod = W.guidewire(n, seed=7)
         b = corde.RodBatch([rod])
         if n <= 2048:

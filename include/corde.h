@@ -212,7 +212,8 @@ int rod_diagnostics(rod_handle h, double* out);
  * variant (ept, nt) in {(2,256), (4,256), (4,512)}, cluster 2..16, for every rod it can
  * hold; rod_autotune times the block variants that hold each length bin on the current
  * state (saved and restored) and keeps the fastest per bin.  rod_get_plan writes
- * [n_rods][3] ints (ept, nt, cluster; cluster 0 = one block).  Synchronous. */
+ * [n_rods][3] ints (ept, nt, blocks; 0 = one block, C >= 2 a cluster of C blocks, -C a
+ * cooperative grid of C blocks, see rod_set_plan_grid).  Synchronous. */
 int rod_set_plan(rod_handle h, int ept, int nt);
 
 /* Launch overlap (on by default): the stepping kernels are launched with programmatic
@@ -223,6 +224,20 @@ int rod_set_plan(rod_handle h, int ept, int nt);
  * enable must be 0 or 1 (CORDE_ERR_ARG otherwise).  Host-side only. */
 int rod_set_launch_overlap(rod_handle h, int enable);
 int rod_set_plan_cluster(rod_handle h, int ept, int nt, int cluster);
+/* A rod longer than a 16-block cluster holds (32768 nodes) runs on a cooperative grid
+ * of `blocks` blocks (the paper's multi-block kernel, Section 2.2, over the whole GPU):
+ * each block's first and last thread publish their exchange slots in global memory and
+ * every exchange barrier is a grid sync; the runtime launches the grid only when all its
+ * blocks are resident at once, so a sync never waits on a block that is not running.
+ * rod_create gives such a rod 2048 nodes per block (ept 4, nt 512); the longest rod is
+ * 2048 x the blocks the device holds at once (one per SM at nt 512).
+ * rod_set_plan_grid forces the grid form of a cluster variant (ept, nt) in {(2,256),
+ * (4,256), (4,512)} with `blocks` >= 2 blocks for every rod it can hold (the same
+ * arithmetic as the cluster form: the same results bit for bit).  rod_get_plan reports
+ * -blocks for a rod on a grid.  CORDE_ERR_UNSUPPORTED when the rods' blocks exceed what
+ * the device holds at once, or with the mailbox (not available for rods on a grid).
+ * Synchronous. */
+int rod_set_plan_grid(rod_handle h, int ept, int nt, int blocks);
 int rod_autotune(rod_handle h, int n_steps, void* stream);
 
 /* Pick the number of time steps per launch, among n_candidates values (each >= 1), with

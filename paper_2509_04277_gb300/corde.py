@@ -65,6 +65,7 @@ SIGNATURES = {
     "rod_set_adjoint_record_budget": (ctypes.c_int, [_VP, ctypes.c_longlong]),
     "rod_adjoint_info": (ctypes.c_int, [_VP, _VP]),
     "rod_set_plan_cluster": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "rod_set_plan_grid": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "rod_autotune": (ctypes.c_int, [_VP, ctypes.c_int, _VP]),
     "rod_autotune_steps": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, _VP, _VP]),
     "rod_get_plan": (ctypes.c_int, [_VP, _VP]),
@@ -237,6 +238,10 @@ def rod_set_launch_overlap(h, enable):
 
 def rod_set_plan_cluster(h, ept, nt, cluster):
     _check(load().rod_set_plan_cluster(h, int(ept), int(nt), int(cluster)), "rod_set_plan_cluster")
+
+
+def rod_set_plan_grid(h, ept, nt, blocks):
+    _check(load().rod_set_plan_grid(h, int(ept), int(nt), int(blocks)), "rod_set_plan_grid")
 
 
 def rod_autotune(h, n_steps, stream=None):
@@ -500,13 +505,18 @@ class RodBatch:
         return rc, out
 
     def plan(self) -> np.ndarray:
-        """[n_rods, 3] (elements per thread, threads per block, blocks per rod; 0 = one block)."""
+        """[n_rods, 3] (elements per thread, threads per block, blocks per rod: 0 = one block,
+        C >= 2 a cluster of C blocks, -C a cooperative grid of C blocks)."""
         out = np.zeros((self.n_rods, 3), dtype=np.int32)
         rod_get_plan(self.handle, out)
         return out
 
     def set_plan_cluster(self, ept, nt, cluster):
         rod_set_plan_cluster(self.handle, ept, nt, cluster)
+
+    def set_plan_grid(self, ept, nt, blocks):
+        """Spread every rod it can hold over `blocks` blocks of a cooperative grid."""
+        rod_set_plan_grid(self.handle, ept, nt, blocks)
 
     def bind(self, outer, inner, mode):
         rod_bind(self.handle, outer, inner, mode)

@@ -7,6 +7,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/corde.h"
@@ -66,6 +67,14 @@ int max_capacity() {
   return c;
 }
 
+// Largest rod a cooperative grid of the current device holds (all its blocks resident).
+int max_grid_capacity() {
+  int c = 0;
+  for (int i = 0; i < kNumClusterVariants; ++i)
+    c = std::max(c, kClusterVariants[i].capacity(kClusterVariants[i].grid_blocks()));
+  return c;
+}
+
 int find_cluster_variant(int ept, int nt) {
   for (int i = 0; i < kNumClusterVariants; ++i)
     if (kClusterVariants[i].ept == ept && kClusterVariants[i].nt == nt) return i;
@@ -83,6 +92,13 @@ void default_cluster_plan(int n, int* variant, int* C) {
   }
   *variant = v;
   *C = std::max(2, c);
+}
+
+// Default plan of a rod longer than a cluster holds: 2048 nodes per block (4 elements x 512
+// threads) over a cooperative grid.
+void default_grid_plan(int n, int* variant, int* C) {
+  *variant = find_cluster_variant(4, 512);
+  *C = std::max(2, (n + 2047) / 2048);
 }
 
 int find_variant(int ept, int nt) {
@@ -113,6 +129,8 @@ struct Bin {
   int* d_work;
   int cluster = 0;  // blocks per rod (0: one block per rod; -1: self-collision kernel, variant
                     // indexes kSelfVariants)
+  int grid = 0;     // 1: the cluster variant's blocks form a cooperative grid
+  float4* d_gh = nullptr;  // grid bins: the rods' global exchange slots
 };
 
 }  // namespace
@@ -134,6 +152,7 @@ struct corde_rods {
   int* d_elem_rod = nullptr;
   std::vector<int> plan;          // variant index per rod (block or cluster table)
   std::vector<int> plan_cluster;  // blocks per rod; 0: one block
+  std::vector<char> plan_grid;    // 1: the rod's plan_cluster blocks form a cooperative grid
   std::vector<Bin> bins;
   int last_launches = 0;
   int pdl = 1;  // stepping kernels launched with programmatic stream serialisation
@@ -364,7 +383,10 @@ int check_handle(rod_handle h) {
 }
 
 void free_bins(rod_handle h) {
-  for (auto& b : h->bins) cudaFree(b.d_work);
+  for (auto& b : h->bins) {
+    cudaFree(b.d_work);
+    cudaFree(b.d_gh);
+  }
   h->bins.clear();
 }
 
@@ -379,26 +401,31 @@ void invalidate_graph(rod_handle h) {
 int build_bins(rod_handle h) {
   invalidate_graph(h);
   free_bins(h);
-  std::vector<std::pair<int, int>> keys;
+  std::vector<std::tuple<int, int, int>> keys;  // (blocks per rod, variant, grid)
+  auto key_of = [&](int r) { return std::make_tuple(h->plan_cluster[r], h->plan[r], (int)h->plan_grid[r]); };
   for (int r = 0; r < h->n_rods; ++r) {
     if (r < (int)h->paired.size() && h->paired[r]) continue;
-    std::pair<int, int> k{h->plan_cluster[r], h->plan[r]};
+    const auto k = key_of(r);
     if (std::find(keys.begin(), keys.end(), k) == keys.end()) keys.push_back(k);
   }
   std::sort(keys.begin(), keys.end());
   for (const auto& k : keys) {
     std::vector<int> rods;
     for (int r = 0; r < h->n_rods; ++r)
-      if (h->plan_cluster[r] == k.first && h->plan[r] == k.second && !(r < (int)h->paired.size() && h->paired[r]))
-        rods.push_back(r);
+      if (key_of(r) == k && !(r < (int)h->paired.size() && h->paired[r])) rods.push_back(r);
     // heaviest rods first: a rod's work per step grows with its nodes times (the force
     // phase, about seven constraint iterations' worth, plus its constraint iterations)
     std::stable_sort(rods.begin(), rods.end(), [&](int a, int b) {
       return (int64_t)h->n_nodes[a] * (7 + h->n_iters[a]) > (int64_t)h->n_nodes[b] * (7 + h->n_iters[b]);
     });
-    Bin b{k.second, (int)rods.size(), nullptr, k.first};
+    Bin b{std::get<1>(k), (int)rods.size(), nullptr, std::get<0>(k), std::get<2>(k)};
     CK(cudaMalloc(&b.d_work, rods.size() * sizeof(int)));
     CK(cudaMemcpy(b.d_work, rods.data(), rods.size() * sizeof(int), cudaMemcpyHostToDevice));
+    if (b.grid) {
+      const size_t n4 = rods.size() * 2 * (size_t)b.cluster * kHaloSlots * 2;
+      CK(cudaMalloc(&b.d_gh, n4 * sizeof(float4)));
+      CK(cudaMemset(b.d_gh, 0, n4 * sizeof(float4)));
+    }
     h->bins.push_back(b);
   }
   return CORDE_OK;
@@ -431,6 +458,14 @@ int launch_bins(rod_handle h, const std::vector<Bin>& bins, int n_steps, const f
       if (e != cudaSuccess)
         return fail(CORDE_ERR_CUDA, std::string("self-collision step launch (ept=") + std::to_string(v.ept) +
                                         ", nt=" + std::to_string(v.nt) + "): " + cudaGetErrorString(e));
+    } else if (b.cluster > 0 && b.grid) {
+      const ClusterVariant& v = kClusterVariants[b.variant];
+      a.grid_halo = b.d_gh;
+      cudaError_t e = v.launch_grid(a, b.count, b.cluster, s);
+      if (e != cudaSuccess)
+        return fail(CORDE_ERR_CUDA, std::string("cooperative grid step launch (ept=") + std::to_string(v.ept) +
+                                        ", nt=" + std::to_string(v.nt) + ", blocks=" + std::to_string(b.cluster) +
+                                        "): " + cudaGetErrorString(e));
     } else if (b.cluster > 0) {
       const ClusterVariant& v = kClusterVariants[b.variant];
       cudaError_t e = v.launch(a, b.count, b.cluster, s);
@@ -622,7 +657,7 @@ int rod_create(int n_rods, const RodParams* params, const float* pos, const floa
   if (!out) return fail(CORDE_ERR_ARG, "out is NULL");
   *out = nullptr;
   if (n_rods < 1 || !params || !pos || !quat) return fail(CORDE_ERR_ARG, "need n_rods >= 1, params, pos and quat");
-  const int cap = max_capacity();
+  const int cap = std::max(max_capacity(), max_grid_capacity());
   std::vector<int> nn(n_rods), off(n_rods);
   int64_t E = 0;
   for (int r = 0; r < n_rods; ++r) {
@@ -712,11 +747,15 @@ int rod_create(int n_rods, const RodParams* params, const float* pos, const floa
     }
     h->plan.resize(n_rods);
     h->plan_cluster.assign(n_rods, 0);
+    h->plan_grid.assign(n_rods, 0);
     for (int r = 0; r < n_rods; ++r) {
       if (nn[r] <= max_block_capacity()) {
         h->plan[r] = default_variant(nn[r]);
-      } else {
+      } else if (nn[r] <= max_capacity()) {
         default_cluster_plan(nn[r], &h->plan[r], &h->plan_cluster[r]);
+      } else {
+        default_grid_plan(nn[r], &h->plan[r], &h->plan_cluster[r]);
+        h->plan_grid[r] = 1;
       }
     }
     rc = build_bins(h);
@@ -874,10 +913,15 @@ int rod_set_plan(rod_handle h, int ept, int nt) {
     for (int r = 0; r < h->n_rods; ++r) {
       if (h->self[r]) continue;
       h->plan_cluster[r] = 0;
+      h->plan_grid[r] = 0;
       if (h->n_nodes[r] <= max_block_capacity()) {
         h->plan[r] = default_variant(h->n_nodes[r]);
-      } else {
+      } else if (h->n_nodes[r] <= max_capacity()) {
         default_cluster_plan(h->n_nodes[r], &h->plan[r], &h->plan_cluster[r]);
+      } else {
+        if (h->mb_period > 0) return fail(CORDE_ERR_UNSUPPORTED, "rod_set_plan: a rod on a grid runs without the mailbox");
+        default_grid_plan(h->n_nodes[r], &h->plan[r], &h->plan_cluster[r]);
+        h->plan_grid[r] = 1;
       }
     }
     return build_bins(h);
@@ -888,6 +932,32 @@ int rod_set_plan(rod_handle h, int ept, int nt) {
     if (!h->self[r] && variants()[v].capacity() >= h->n_nodes[r]) {
       h->plan[r] = v;
       h->plan_cluster[r] = 0;
+      h->plan_grid[r] = 0;
+    }
+  return build_bins(h);
+}
+
+int rod_set_plan_grid(rod_handle h, int ept, int nt, int blocks) {
+  if (int rc = check_handle(h)) return rc;
+  const int v = find_cluster_variant(ept, nt);
+  if (v < 0 || blocks < 2)
+    return fail(CORDE_ERR_ARG, "no grid variant with ept=" + std::to_string(ept) + ", nt=" + std::to_string(nt) +
+                                   ", blocks=" + std::to_string(blocks));
+  if (h->mb_period > 0) return fail(CORDE_ERR_UNSUPPORTED, "rod_set_plan_grid: a rod on a grid runs without the mailbox");
+  int rods = 0;
+  for (int r = 0; r < h->n_rods; ++r)
+    if (!h->self[r] && !(r < (int)h->paired.size() && h->paired[r]) && kClusterVariants[v].capacity(blocks) >= h->n_nodes[r])
+      ++rods;
+  if ((int64_t)rods * blocks > kClusterVariants[v].grid_blocks())
+    return fail(CORDE_ERR_UNSUPPORTED, "rod_set_plan_grid: " + std::to_string(rods) + " rods x " +
+                                           std::to_string(blocks) + " blocks are more than the " +
+                                           std::to_string(kClusterVariants[v].grid_blocks()) +
+                                           " blocks the device holds at once");
+  for (int r = 0; r < h->n_rods; ++r)
+    if (!h->self[r] && !(r < (int)h->paired.size() && h->paired[r]) && kClusterVariants[v].capacity(blocks) >= h->n_nodes[r]) {
+      h->plan[r] = v;
+      h->plan_cluster[r] = blocks;
+      h->plan_grid[r] = 1;
     }
   return build_bins(h);
 }
@@ -917,6 +987,7 @@ int rod_set_plan_cluster(rod_handle h, int ept, int nt, int cluster) {
     if (!h->self[r] && kClusterVariants[v].capacity(cluster) >= h->n_nodes[r]) {
       h->plan[r] = v;
       h->plan_cluster[r] = cluster;
+      h->plan_grid[r] = 0;
     }
   return build_bins(h);
 }
@@ -1000,7 +1071,7 @@ int rod_get_plan(rod_handle h, int* plan) {
                          : (C < 0 ? kSelfVariants[h->plan[r]].nt : variants()[h->plan[r]].nt);
     plan[3 * r] = ept;
     plan[3 * r + 1] = nt;
-    plan[3 * r + 2] = C > 0 ? C : 0;
+    plan[3 * r + 2] = C > 0 ? (h->plan_grid[r] ? -C : C) : 0;
   }
   return CORDE_OK;
 }
@@ -1174,9 +1245,11 @@ int rod_set_self_collision(rod_handle h, int rod, const double* p) {
     while (v + 1 < kNumSelfVariants && kSelfVariants[v].ept == 2 && kSelfVariants[v].capacity() < h->n_nodes[rod]) ++v;
     h->plan[rod] = v;
     h->plan_cluster[rod] = -1;
+    h->plan_grid[rod] = 0;
   } else if (h->plan_cluster[rod] < 0) {
     h->plan[rod] = default_variant(h->n_nodes[rod]);
     h->plan_cluster[rod] = 0;
+    h->plan_grid[rod] = 0;
   }
   return build_bins(h);
 }
@@ -1443,6 +1516,8 @@ int rod_mailbox_enable(rod_handle h, int period, int log_capacity) {
   if (period < 1 || log_capacity < 1) return fail(CORDE_ERR_ARG, "rod_mailbox_enable: period and log_capacity >= 1");
   for (int r = 0; r < h->n_rods; ++r)
     if (h->self[r]) return fail(CORDE_ERR_UNSUPPORTED, "rod_mailbox_enable: not with self-collision");
+  for (int r = 0; r < h->n_rods; ++r)
+    if (h->plan_grid[r]) return fail(CORDE_ERR_UNSUPPORTED, "rod_mailbox_enable: not with a rod on a cooperative grid");
   CK(cudaDeviceSynchronize());
   mailbox_free(h);
   const size_t in_bytes = 16 + (size_t)h->n_rods * 8 * sizeof(float);

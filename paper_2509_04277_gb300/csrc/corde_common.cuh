@@ -7,6 +7,7 @@
 namespace corde {
 
 enum : int { F_INEXT = 1, F_CLAMP = 2, F_TUBE = 4, F_SELF = 8 };
+constexpr int kHaloSlots = 3;  // neighbour-exchange slots per thread and exchange
 constexpr int kPosSlots = 4;  // ring of position snapshots per rod (mailbox)
 
 // Per-rod constants used by the step kernel (derived once at creation, FP64 -> FP32).

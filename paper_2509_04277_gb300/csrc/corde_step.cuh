@@ -44,8 +44,9 @@ __device__ __forceinline__ void block_sync() {
 
 // Neighbour access and barrier of a rod held by one thread block (t = thread of the rod;
 // SYNC_NT threads take part in each barrier: NT, or more when several rods share the block
-// in lockstep).  Exchange buffers hold `slots` x NT float4, slot-major.
-template <int NT, int SYNC_NT>
+// in lockstep).  Exchange buffers hold `slots` x NT float4, slot-major.  PAIR2 selects the
+// layout of the three-float slots (see put3).
+template <int NT, int SYNC_NT, bool PAIR2 = false>
 struct BlockHalo {
   static constexpr bool kCluster = false;
   int t;
@@ -56,25 +57,37 @@ struct BlockHalo {
   __device__ __forceinline__ float4 next(const float4* hb, int slot) const { return hb[slot * NT + t + 1]; }
   __device__ __forceinline__ float4 prev(const float4* hb, int slot) const { return hb[slot * NT + t - 1]; }
   // three-float slots, one float per component (component c of slot s at float
-  // (3 s + c) NT + t): a neighbour's vector is three 32-bit loads, issued together
+  // (3 s + c) NT + t): a neighbour's vector is three 32-bit loads, issued together.  With
+  // PAIR2 the x and y components sit together as a float2 (float2 3 s NT / 2 + t) and z
+  // at float (3 s + 2) NT + t: two loads instead of three (measured: 2.96 against 3.01
+  // us/step for the 512-node rod at two elements per thread; the four-element batch
+  // variants keep three, 1.6 % faster for them)
   __device__ __forceinline__ void put3(float4* hb, int slot, float3 a) const {
-    float* f = reinterpret_cast<float*>(hb) + 3 * slot * NT + t;
-    f[0] = a.x;
-    f[NT] = a.y;
-    f[2 * NT] = a.z;
+    float* f = reinterpret_cast<float*>(hb) + 3 * slot * NT;
+    if constexpr (PAIR2) {
+      reinterpret_cast<float2*>(f)[t] = make_float2(a.x, a.y);
+      f[2 * NT + t] = a.z;
+    } else {
+      f[t] = a.x;
+      f[NT + t] = a.y;
+      f[2 * NT + t] = a.z;
+    }
   }
-  __device__ __forceinline__ float3 next3(const float4* hb, int slot) const {
-    const float* f = reinterpret_cast<const float*>(hb) + 3 * slot * NT + t + 1;
-    return f3(f[0], f[NT], f[2 * NT]);
+  __device__ __forceinline__ float3 get3(const float4* hb, int slot, int u) const {
+    const float* f = reinterpret_cast<const float*>(hb) + 3 * slot * NT;
+    if constexpr (PAIR2) {
+      const float2 xy = reinterpret_cast<const float2*>(f)[u];
+      return f3(xy.x, xy.y, f[2 * NT + u]);
+    } else {
+      return f3(f[u], f[NT + u], f[2 * NT + u]);
+    }
   }
-  __device__ __forceinline__ float3 prev3(const float4* hb, int slot) const {
-    const float* f = reinterpret_cast<const float*>(hb) + 3 * slot * NT + t - 1;
-    return f3(f[0], f[NT], f[2 * NT]);
-  }
+  __device__ __forceinline__ float3 next3(const float4* hb, int slot) const { return get3(hb, slot, t + 1); }
+  __device__ __forceinline__ float3 prev3(const float4* hb, int slot) const { return get3(hb, slot, t - 1); }
   __device__ __forceinline__ void sync() const { block_sync<SYNC_NT>(); }
   // a barrier in two halves (arrive after the exchange stores, wait before the neighbour
   // loads); one block has no split barrier, so the wait is the whole barrier
-  __device__ __forceinline__ void arrive() const {}
+  __device__ __forceinline__ void arrive(const float4*) const {}
   __device__ __forceinline__ void wait() const { block_sync<SYNC_NT>(); }
   // block-wide OR of x (a barrier)
   __device__ __forceinline__ int any(int x) const {
@@ -130,8 +143,59 @@ struct ClusterHalo {
     return r;
   }
   // the cluster barrier in two halves: thread-local work between them overlaps its latency
-  __device__ __forceinline__ void arrive() const { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
+  __device__ __forceinline__ void arrive(const float4*) const {
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+  }
   __device__ __forceinline__ void wait() const { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
+};
+
+// A rod spread over C blocks of a cooperative grid (block c holds threads c NT ...
+// c NT + NT - 1 of the rod): the paper's multi-block "universal" kernel for rods longer
+// than one cluster holds.  Each block's first and last thread also publish their exchange
+// slots in global memory (a ping-pong pair per exchange parity), the barrier is a grid
+// sync, and a block's edge thread reads its neighbour block's slots from L2 (ld.cg, past
+// any stale L1 line).  The runtime launches the grid only if all its blocks are resident
+// at once, so the grid sync cannot wait on a block that never runs.
+template <int NT>
+struct GridHalo {
+  static constexpr bool kCluster = true;
+  int t, c, C;
+  float4* gh;           // this rod's slots: [2 parities][C blocks][kHaloSlots][first, last]
+  const float4* halo0;  // the block's shared exchange buffer of parity 0
+  __device__ __forceinline__ int tg() const { return c * NT + t; }
+  __device__ __forceinline__ int rod_threads() const { return C * NT; }
+  __device__ __forceinline__ bool has_next() const { return t + 1 < NT || c + 1 < C; }
+  __device__ __forceinline__ bool has_prev() const { return t > 0 || c > 0; }
+  __device__ __forceinline__ float4* gslot(const float4* hb, int blk, int slot, int edge) const {
+    const int par = hb != halo0 ? 1 : 0;
+    return gh + (((par * C + blk) * kHaloSlots + slot) * 2 + edge);
+  }
+  __device__ __forceinline__ float4 next(const float4* hb, int slot) const {
+    if (t + 1 < NT) return hb[slot * NT + t + 1];
+    return __ldcg(gslot(hb, c + 1, slot, 0));
+  }
+  __device__ __forceinline__ float4 prev(const float4* hb, int slot) const {
+    if (t > 0) return hb[slot * NT + t - 1];
+    return __ldcg(gslot(hb, c - 1, slot, 1));
+  }
+  // three-float slots: whole float4 slots here (one global access per vector)
+  __device__ __forceinline__ void put3(float4* hb, int slot, float3 a) const {
+    hb[slot * NT + t] = make_float4(a.x, a.y, a.z, 0.f);
+  }
+  __device__ __forceinline__ float3 next3(const float4* hb, int slot) const { return f3(next(hb, slot)); }
+  __device__ __forceinline__ float3 prev3(const float4* hb, int slot) const { return f3(prev(hb, slot)); }
+  __device__ __forceinline__ void sync() const { cooperative_groups::this_grid().sync(); }
+  // after the exchange stores: the block's first and last thread copy their slots (written
+  // by themselves just before) to global memory; the grid sync then publishes them
+  __device__ __forceinline__ void arrive(const float4* hb) const {
+    if (t == 0 || t == NT - 1) {
+#pragma unroll
+      for (int s = 0; s < kHaloSlots; ++s) __stcg(gslot(hb, c, s, t == 0 ? 0 : 1), hb[s * NT + t]);
+    }
+  }
+  __device__ __forceinline__ void wait() const { cooperative_groups::this_grid().sync(); }
+  // block-wide OR (rods on a grid run without the mailbox, the only user of a rod-wide OR)
+  __device__ __forceinline__ int any(int x) const { return __syncthreads_or(x); }
 };
 
 // Bend/twist torques of the joint between frames a and b (Eq. 3): with
@@ -308,8 +372,7 @@ struct StepCache {
 
 // Dynamic shared memory of a <EPT, NT> block: per-element joint parameters (u-hat and
 // K), element-major so that thread t's accesses are conflict-free, then the two
-// ping-pong exchange buffers of three float4 slots per thread.
-constexpr int kHaloSlots = 3;
+// ping-pong exchange buffers of kHaloSlots float4 slots per thread.
 template <int EPT, int NT>
 constexpr int step_smem_bytes() {
   return (2 * EPT * NT + 2 * kHaloSlots * NT) * (int)sizeof(float4);
@@ -342,7 +405,7 @@ __device__ __forceinline__ void step_body(const RodDev& R, const Halo& H, float3
   hb[t] = make_float4(r[0].x, r[0].y, r[0].z, w[0]);
   hb[NT + t] = q[0];
   hb[2 * NT + t] = make_float4(r[EPT - 1].x, r[EPT - 1].y, r[EPT - 1].z, w[EPT - 1]);
-  H.arrive();
+  H.arrive(hb);
 
   // ---- elastic forces and torques.  Joint j couples frames j and j + 1, segment j nodes
   // j and j + 1 (with frame j); all but the thread's last joint and segment are local, and
@@ -411,7 +474,7 @@ __device__ __forceinline__ void step_body(const RodDev& R, const Halo& H, float3
   ++xc;
   H.put3(hb, 0, F_carry);
   H.put3(hb, 1, tau_carry);
-  H.arrive();
+  H.arrive(hb);
 
   // ---- while the exchange barrier completes: the constraint geometry of this step (the
   // positions and masses do not change in the sweeps) and the force integration of
@@ -554,7 +617,7 @@ __device__ __forceinline__ void step_body(const RodDev& R, const Halo& H, float3
       ++xc;
       H.put3(hb, 0, v[0]);
       H.put3(hb, 1, v[EPT - 1]);
-      H.arrive();
+      H.arrive(hb);
       // odd segments inside the thread: they move elements 1 .. EPT - 2 only, which the
       // exchange and the boundary segments do not read, so they run while the barrier waits
 #pragma unroll
@@ -887,7 +950,7 @@ step_kernel(const RodDev* __restrict__ rods, const int* __restrict__ work, float
   pdl_begin();
   const int rid = work[blockIdx.x];
   const RodDev R = rods[rid];
-  const BlockHalo<NT, NT> H{(int)threadIdx.x};
+  const BlockHalo<NT, NT, EPT == 2> H{(int)threadIdx.x};
   run_rod<EPT, NT>(R, H, rid, x4, x4, v4, q4, o4, u4, k4, drive, n_steps, traj, n_elem, mb, smem, pos_out);
 }
 

@@ -23,6 +23,7 @@ struct StepArgs {
   MailboxDev mb;   // mailbox of the launch (period 0: none)
   int4* self_stats;  // self-collision statistics per rod (corde_self.cu), or NULL
   float4* pos_out;   // optional: positions (r, w) after the launch, [n_elem] (device or mapped host)
+  float4* grid_halo; // rods on a cooperative grid: their global exchange slots
   int pdl;           // 1: launch with programmatic stream serialisation (the kernel may start
                      // before the stream's previous kernel ends; it waits in pdl_begin)
 };
@@ -117,7 +118,10 @@ typedef cudaError_t (*ClusterLaunchFn)(const StepArgs& a, int n_rods, int C, cud
 struct ClusterVariant {
   int ept;
   int nt;
-  ClusterLaunchFn launch;
+  ClusterLaunchFn launch;       // a cluster of C blocks per rod
+  ClusterLaunchFn launch_grid;  // C blocks per rod in a cooperative grid (a.grid_halo: the rods'
+                                // global exchange slots, 2 x C x kHaloSlots x 2 float4 per rod)
+  int (*grid_blocks)();         // the most blocks a cooperative grid of this variant can hold
   int capacity(int C) const { return ept * nt * C; }
 };
 extern const ClusterVariant kClusterVariants[];

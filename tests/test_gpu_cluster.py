@@ -92,3 +92,54 @@ def test_batch_mixing_block_and_cluster_rods(corde):
         ref = oracle.step(rod, oracle.state_of(rod), 10)
         _cmp(rod, b.rod_state(st, r), ref, ROLL_TOL)
     b.close()
+
+
+@pytest.mark.parametrize("ept,nt,C", [(2, 256, 8), (4, 256, 4), (4, 512, 3)])
+def test_grid_equals_cluster_bit_for_bit(corde, ept, nt, C):
+    """The cooperative-grid form (global-memory halo, grid syncs) runs the same step body
+    as the cluster form with the same blocks: after 30 driven steps the states are equal
+    bit for bit, and rod_get_plan reports -C blocks."""
+    import torch
+
+    rod = W.guidewire(min(ept * nt * C, 4096) - 5, seed=540 + C)
+    drive = torch.as_tensor(np.array([[0.02, -0.01, 0, 0, 0.1, 0, 2.0, 0]], np.float32), device="cuda")
+    out = []
+    for grid in (False, True):
+        b = corde.RodBatch([rod])
+        if grid:
+            b.set_plan_grid(ept, nt, C)
+            assert tuple(b.plan()[0]) == (ept, nt, -C)
+        else:
+            b.set_plan_cluster(ept, nt, C)
+        for _ in range(3):
+            b.step(10, drive=drive)
+        out.append(b.state_numpy())
+        b.close()
+    for k in out[0]:
+        np.testing.assert_array_equal(out[0][k], out[1][k], err_msg=k)
+
+
+def test_rod_longer_than_a_cluster_runs_on_a_grid(corde):
+    """A 40000-node rod (beyond the 32768 a 16-block cluster holds) gets the default grid
+    plan (2048 nodes per block) and matches the oracle step by step."""
+    import torch
+
+    n = 40000
+    rod = W.guidewire(n, seed=550)
+    rod.length = 1.5 * n / 512  # the guidewire's segment length
+    rod.pos = rod.pos * (n / 512)
+    b = corde.RodBatch([rod])
+    ept, nt, C = b.plan()[0]
+    assert C < 0 and ept * nt * -C >= n
+    drive = torch.as_tensor(np.array([[0.01, 0, 0, 0, 0, 0, 1.0, 0]], np.float32), device="cuda")
+    for _ in range(2):
+        st0 = b.rod_state(b.state_numpy(), 0)
+        b.step(1, drive=drive)
+        ref = oracle.step(rod, st0, 1, drive=drive.cpu().numpy()[0].astype(np.float64))
+        _cmp(rod, b.rod_state(b.state_numpy(), 0), ref, STEP_TOL)
+    b.step(10, drive=drive)
+    rc, diag = b.diagnostics()
+    assert rc == 0 and diag[0, 1] < 1e-6
+    with pytest.raises(corde.CordeError):
+        corde.rod_mailbox_enable(b.handle, 10)
+    b.close()
