@@ -347,20 +347,24 @@ int rod_rollout(rod_handle h, int n_steps, int ckpt_every, float* pos_traj, void
 int rod_adjoint(rod_handle h, const float* dL_dpos_traj, float* dL_dK, float* dL_duhat, float* dL_dvel0,
                 float* dL_dpos0, float* dL_dquat0, float* dL_domega0, void* stream);
 
-/* How the last rod_adjoint ran its largest launch, into 5 host ints: 1 for record mode
- * (0: recompute), threads per block, resident blocks per SM (occupancy API, with the
- * launch's registers and shared memory), blocks of the launch (one per rod), and the
- * device's SMs; blocks / (blocks per SM x SMs), rounded up, is the number of waves.
+/* How the last rod_adjoint ran its largest launch, into 5 host ints: the mode (0
+ * recompute; 1 record mode with one sweep buffer in shared memory; 2 record mode with
+ * two, the copy of a step's records overlapping the reverse of the step after it),
+ * threads per block, resident blocks per SM (occupancy API, with the launch's registers
+ * and shared memory), blocks of the launch (one per rod), and the device's SMs;
+ * blocks / (blocks per SM x SMs), rounded up, is the number of waves.
  * Host-side only (zeros before the first rod_adjoint). */
 int rod_adjoint_info(rod_handle h, int* out);
 
 /* Scratch budget of rod_adjoint's record mode (default 64 MiB).  Within a checkpoint
  * segment the reverse pass needs every step's velocities before each constraint
  * half-sweep.
- *  - Record mode (the scratch fits in `bytes` and the block's shared memory holds two
- *    copies of a step's sweeps): one forward pass over the segment keeps them in device
- *    memory, 2 n_iters x 64 B per node and step plus 48 B per node and step of neighbour
- *    data.  The reverse pass streams them back with asynchronous copies.
+ *  - Record mode (the scratch fits in `bytes`): one forward pass over the segment keeps
+ *    them in device memory, 2 n_iters x 64 B per node and step plus 48 B per node and
+ *    step of neighbour data.  The reverse pass streams them back with asynchronous
+ *    copies, into two shared-memory buffers (the copy of a step's records overlaps the
+ *    reverse of the step after it) or into one when two do not fit or when one buffer
+ *    lets more blocks share an SM and so runs the launch in fewer waves.
  *  - Recompute mode (otherwise, and always with bytes = 0): every step is run forward
  *    again before its reverse.
  * Both modes give the same gradients bit for bit.  bytes >= 0 (CORDE_ERR_ARG otherwise).

@@ -353,7 +353,8 @@ def rod_adjoint_info(h) -> dict:
     out = np.zeros(5, dtype=np.int32)
     _check(load().rod_adjoint_info(h, out.ctypes.data), "rod_adjoint_info")
     per_sm, blocks, sms = int(out[2]), int(out[3]), int(out[4])
-    return {"mode": "record" if out[0] else "recompute", "threads_per_block": int(out[1]),
+    return {"mode": "record" if out[0] else "recompute", "record_buffers": int(out[0]),
+            "threads_per_block": int(out[1]),
             "blocks_per_sm": per_sm, "blocks": blocks, "sms": sms,
             "waves": -(-blocks // (per_sm * sms)) if per_sm * sms > 0 else None}
 

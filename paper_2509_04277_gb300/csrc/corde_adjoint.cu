@@ -369,10 +369,15 @@ __device__ __forceinline__ void reverse_step(const RodDev& R, const int t, const
   for (int e = 0; e < EPT; ++e) qb[e] = qbi[e];
 }
 
-// Reverse pass over the whole rollout of one rod per block.
-template <int NT, bool RECORD>
+// Reverse pass over the whole rollout of one rod per block.  MODE 0: recompute every
+// step before its reverse; 1: record mode with one sweep buffer (a step's records are
+// copied in after the step before it is reversed); 2: record mode with two buffers (the
+// copy overlaps the reverse of the step before).
+template <int NT, int MODE>
 __global__ void __launch_bounds__(NT)
 adjoint_kernel(AdjointArgs a) {
+  constexpr bool RECORD = MODE > 0;
+  constexpr int NBUF = MODE == 2 ? 2 : 1;
   constexpr int EPT = 2;
   extern __shared__ float4 smem[];
   float4* par_u = smem;
@@ -447,7 +452,7 @@ adjoint_kernel(AdjointArgs a) {
         nr[2 * NT] = nb.q_next;
       }
       put_state(cnt);
-      fetch(cnt - 1, sweep_v + ((cnt - 1) & 1) * rec_stride);
+      fetch(cnt - 1, sweep_v + ((cnt - 1) % NBUF) * rec_stride);
     } else {
       // recompute the segment's states into scratch
       for (int s = 0; s < cnt; ++s) {
@@ -522,16 +527,23 @@ adjoint_kernel(AdjointArgs a) {
         nb.r_prev = f3(pn1);
         nb.w_prev = pn1.w;
         nb.q_next = pn2;
-        // step s's sweeps; the copy of step s - 1's starts once every thread is done with
-        // the buffer it reuses (step s + 1's)
+        // step s's sweeps (threads read their neighbours' entries too); with two buffers the
+        // copy of step s - 1's starts once every thread is done with the buffer it reuses
+        // (step s + 1's), with one buffer once every thread is done with step s's
         cp_async_wait_all();
         block_sync<NT>();
         if (s > 0) {
-          fetch(s - 1, sweep_v + ((s - 1) & 1) * rec_stride);
+          if constexpr (NBUF == 2) fetch(s - 1, sweep_v + ((s - 1) & 1) * rec_stride);
           prefetch(s - 1);
         }
         reverse_step<EPT, NT>(R, t, r_in, q_in, om_in, w, om, q, nb, par_u, par_k, halo, xc,
-                              sweep_v + (s & 1) * rec_stride, rb, vb, qb, ob, Kb, ub);
+                              sweep_v + (s % NBUF) * rec_stride, rb, vb, qb, ob, Kb, ub);
+        if constexpr (NBUF == 1) {
+          if (s > 0) {
+            block_sync<NT>();
+            fetch(s - 1, sweep_v);
+          }
+        }
       }
     } else {
       // each step's state and loss gradient loaded one step ahead, as in record mode
@@ -597,40 +609,53 @@ adjoint_kernel(AdjointArgs a) {
   }
 }
 
-template <int NT, bool RECORD>
+template <int NT, int MODE>
 cudaError_t launch_adjoint_mode(const AdjointArgs& a, int n_blocks, int smem, cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(adjoint_kernel<NT, RECORD>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = cudaFuncSetAttribute(adjoint_kernel<NT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  adjoint_kernel<NT, RECORD><<<n_blocks, NT, smem, s>>>(a);
+  adjoint_kernel<NT, MODE><<<n_blocks, NT, smem, s>>>(a);
   return cudaGetLastError();
 }
 template <int NT>
-cudaError_t launch_adjoint_nt(const AdjointArgs& a, int n_blocks, int smem, cudaStream_t s) {
-  return a.sweep_rec != nullptr ? launch_adjoint_mode<NT, true>(a, n_blocks, smem, s)
-                                : launch_adjoint_mode<NT, false>(a, n_blocks, smem, s);
+cudaError_t launch_adjoint_nt(const AdjointArgs& a, int mode, int n_blocks, int smem, cudaStream_t s) {
+  switch (mode) {
+    case 0: return launch_adjoint_mode<NT, 0>(a, n_blocks, smem, s);
+    case 1: return launch_adjoint_mode<NT, 1>(a, n_blocks, smem, s);
+    case 2: return launch_adjoint_mode<NT, 2>(a, n_blocks, smem, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace
 
-int adjoint_smem_bytes(int nt, int n_iters, bool record) {
+int adjoint_smem_bytes(int nt, int n_iters, int mode) {
   const int ept = 2;
   const int sweep = 2 * (n_iters > 0 ? n_iters : 1) * ept * nt;
-  return (2 * ept * nt + 2 * kHaloSlots * nt + (record ? 2 : 1) * sweep) * (int)sizeof(float4);
+  return (2 * ept * nt + 2 * kHaloSlots * nt + (mode == 2 ? 2 : 1) * sweep) * (int)sizeof(float4);
 }
 
-template <int NT, bool RECORD>
+template <int NT, int MODE>
 cudaError_t occupancy_mode(int smem, int* blocks) {
-  cudaError_t e = cudaFuncSetAttribute(adjoint_kernel<NT, RECORD>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = cudaFuncSetAttribute(adjoint_kernel<NT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, adjoint_kernel<NT, RECORD>, NT, (size_t)smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, adjoint_kernel<NT, MODE>, NT, (size_t)smem);
+}
+template <int NT>
+cudaError_t occupancy_nt(int mode, int smem, int* blocks) {
+  switch (mode) {
+    case 0: return occupancy_mode<NT, 0>(smem, blocks);
+    case 1: return occupancy_mode<NT, 1>(smem, blocks);
+    case 2: return occupancy_mode<NT, 2>(smem, blocks);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
-cudaError_t adjoint_occupancy(int nt, bool record, int smem, int* blocks) {
+cudaError_t adjoint_occupancy(int nt, int mode, int smem, int* blocks) {
   switch (nt) {
-    case 32: return record ? occupancy_mode<32, true>(smem, blocks) : occupancy_mode<32, false>(smem, blocks);
-    case 64: return record ? occupancy_mode<64, true>(smem, blocks) : occupancy_mode<64, false>(smem, blocks);
-    case 128: return record ? occupancy_mode<128, true>(smem, blocks) : occupancy_mode<128, false>(smem, blocks);
-    case 256: return record ? occupancy_mode<256, true>(smem, blocks) : occupancy_mode<256, false>(smem, blocks);
+    case 32: return occupancy_nt<32>(mode, smem, blocks);
+    case 64: return occupancy_nt<64>(mode, smem, blocks);
+    case 128: return occupancy_nt<128>(mode, smem, blocks);
+    case 256: return occupancy_nt<256>(mode, smem, blocks);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -638,20 +663,21 @@ cudaError_t adjoint_occupancy(int nt, bool record, int smem, int* blocks) {
 cudaError_t preload_adjoint(int nt) {
   cudaFuncAttributes at;
   switch (nt) {
-    case 32: return cudaFuncGetAttributes(&at, adjoint_kernel<32, false>);
-    case 64: return cudaFuncGetAttributes(&at, adjoint_kernel<64, false>);
-    case 128: return cudaFuncGetAttributes(&at, adjoint_kernel<128, false>);
-    case 256: return cudaFuncGetAttributes(&at, adjoint_kernel<256, false>);
+    case 32: return cudaFuncGetAttributes(&at, adjoint_kernel<32, 0>);
+    case 64: return cudaFuncGetAttributes(&at, adjoint_kernel<64, 0>);
+    case 128: return cudaFuncGetAttributes(&at, adjoint_kernel<128, 0>);
+    case 256: return cudaFuncGetAttributes(&at, adjoint_kernel<256, 0>);
     default: return cudaErrorInvalidValue;
   }
 }
 
-cudaError_t launch_adjoint(int nt, const AdjointArgs& a, int n_blocks, int smem, cudaStream_t s) {
+cudaError_t launch_adjoint(int nt, int mode, const AdjointArgs& a, int n_blocks, int smem, cudaStream_t s) {
+  if ((mode > 0) != (a.sweep_rec != nullptr)) return cudaErrorInvalidValue;
   switch (nt) {
-    case 32: return launch_adjoint_nt<32>(a, n_blocks, smem, s);
-    case 64: return launch_adjoint_nt<64>(a, n_blocks, smem, s);
-    case 128: return launch_adjoint_nt<128>(a, n_blocks, smem, s);
-    case 256: return launch_adjoint_nt<256>(a, n_blocks, smem, s);
+    case 32: return launch_adjoint_nt<32>(a, mode, n_blocks, smem, s);
+    case 64: return launch_adjoint_nt<64>(a, mode, n_blocks, smem, s);
+    case 128: return launch_adjoint_nt<128>(a, mode, n_blocks, smem, s);
+    case 256: return launch_adjoint_nt<256>(a, mode, n_blocks, smem, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -2,6 +2,7 @@
 // kernel-variant plans, the persistent step launches, state I/O and diagnostics.
 #include <algorithm>
 #include <atomic>
+#include <climits>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -1426,20 +1427,33 @@ int rod_adjoint(rod_handle h, const float* dL_dpos_traj, float* dL_dK, float* dL
   int iters = 0;
   for (int r = 0; r < h->n_rods; ++r) iters = std::max(iters, h->n_iters[r]);
   const int rec_iters = iters > 0 ? iters : 1;
-  // record mode per launch: two sweep buffers in shared memory and the scratch within budget
+  // record mode per launch when its scratch fits the budget: two sweep buffers in shared
+  // memory (the copy of a step's records overlaps the reverse of the step after it), or
+  // one when two do not fit or when one lets the launch run in fewer waves (more resident
+  // blocks per SM); recompute mode otherwise
   const size_t K = (size_t)h->ro_every;
-  std::vector<char> record(h->adj_bins.size(), 0);
+  int sms = 0;
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  std::vector<int> mode(h->adj_bins.size(), 0);
   size_t sweep_need = 0, nb_need = 0;
   for (size_t i = 0; i < h->adj_bins.size(); ++i) {
     const Bin& b = h->adj_bins[i];
     const int nt = variants()[b.variant].nt;
     const size_t sw = K * b.count * 2 * rec_iters * 2 * nt, nbn = K * b.count * 3 * nt;  // float4 entries
-    if (adjoint_smem_bytes(nt, iters, true) <= smem_max &&
-        (long long)((sw + nbn) * sizeof(float4)) <= h->adj_record_budget) {
-      record[i] = 1;
-      sweep_need = std::max(sweep_need, sw);
-      nb_need = std::max(nb_need, nbn);
+    if ((long long)((sw + nbn) * sizeof(float4)) > h->adj_record_budget) continue;
+    const int smem1 = adjoint_smem_bytes(nt, iters, 1), smem2 = adjoint_smem_bytes(nt, iters, 2);
+    if (smem1 > smem_max) continue;
+    int m = 1;
+    if (smem2 <= smem_max) {
+      int occ1 = 0, occ2 = 0;
+      CK(adjoint_occupancy(nt, 1, smem1, &occ1));
+      CK(adjoint_occupancy(nt, 2, smem2, &occ2));
+      auto waves = [&](int occ) { return occ > 0 ? (b.count + occ * sms - 1) / (occ * sms) : INT_MAX; };
+      m = waves(occ2) <= waves(occ1) ? 2 : 1;
     }
+    mode[i] = m;
+    sweep_need = std::max(sweep_need, sw);
+    nb_need = std::max(nb_need, nbn);
   }
   const bool any_record = sweep_need > 0;
   if (int rc = ensure_capacity(&h->d_seg, &h->seg_cap, (K + (any_record ? 1 : 0)) * 4 * E)) return rc;
@@ -1469,9 +1483,9 @@ int rod_adjoint(rod_handle h, const float* dL_dpos_traj, float* dL_dK, float* dL
   for (size_t i = 0; i < h->adj_bins.size(); ++i) {
     const Bin& b = h->adj_bins[i];
     const int nt = variants()[b.variant].nt;
-    const int smem = adjoint_smem_bytes(nt, iters, record[i] != 0);
-    a.sweep_rec = record[i] ? h->d_sweep_rec : nullptr;
-    a.nb_rec = record[i] ? h->d_nb_rec : nullptr;
+    const int smem = adjoint_smem_bytes(nt, iters, mode[i]);
+    a.sweep_rec = mode[i] ? h->d_sweep_rec : nullptr;
+    a.nb_rec = mode[i] ? h->d_nb_rec : nullptr;
     a.rec_iters = rec_iters;
     if (smem > smem_max)
       return fail(CORDE_ERR_UNSUPPORTED, "adjoint needs " + std::to_string(smem) + " B of shared memory per block; " +
@@ -1479,13 +1493,12 @@ int rod_adjoint(rod_handle h, const float* dL_dpos_traj, float* dL_dK, float* dL
                                              "or shorter rods)");
     a.work = b.d_work;
     if (b.count >= h->adj_info[3]) {
-      int per_sm = 0, sms = 0;
-      CK(adjoint_occupancy(nt, record[i] != 0, smem, &per_sm));
-      CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-      const int info[5] = {record[i] ? 1 : 0, nt, per_sm, b.count, sms};
+      int per_sm = 0;
+      CK(adjoint_occupancy(nt, mode[i], smem, &per_sm));
+      const int info[5] = {mode[i], nt, per_sm, b.count, sms};
       std::copy(info, info + 5, h->adj_info);
     }
-    cudaError_t e = launch_adjoint(nt, a, b.count, smem, s);
+    cudaError_t e = launch_adjoint(nt, mode[i], a, b.count, smem, s);
     if (e != cudaSuccess) return fail(CORDE_ERR_CUDA, std::string("adjoint launch: ") + cudaGetErrorString(e));
     ++launches;
   }
@@ -1944,7 +1957,7 @@ extern "C" int rod_adjoint_noalloc(const RodParams* params, const float* pos, co
   ad.dpos0 = dev_out[4];
   ad.dquat0 = nullptr;
   ad.domega0 = nullptr;
-  cudaError_t e = launch_adjoint(nt, ad, 1, smem, s);
+  cudaError_t e = launch_adjoint(nt, 0, ad, 1, smem, s);
   if (e != cudaSuccess) return fail(CORDE_ERR_CUDA, std::string("rod_adjoint_noalloc: adjoint: ") + cudaGetErrorString(e));
   return CORDE_OK;
 }

@@ -92,15 +92,19 @@ struct AdjointArgs {
   float4* nb_rec = nullptr;
   int rec_iters = 0;
 };
-// Shared memory of the reverse kernel: parameters, exchange buffers and one (recompute
-// mode) or two (record mode: double-buffered copies) sweep-velocity buffers.
-int adjoint_smem_bytes(int nt, int n_iters, bool record = false);
-cudaError_t launch_adjoint(int nt, const AdjointArgs& a, int n_blocks, int smem, cudaStream_t s);
+// Reverse-kernel modes: 0 recompute; 1 record, one sweep buffer (the copy of a step's
+// records waits for the reverse of the step after it); 2 record, two sweep buffers (the
+// copy overlaps that reverse).  All three give the same gradients bit for bit.
+// Shared memory of the reverse kernel: parameters, exchange buffers and one (modes 0, 1)
+// or two (mode 2) sweep-velocity buffers.
+int adjoint_smem_bytes(int nt, int n_iters, int mode = 0);
+// mode > 0 exactly when a.sweep_rec is set (cudaErrorInvalidValue otherwise).
+cudaError_t launch_adjoint(int nt, int mode, const AdjointArgs& a, int n_blocks, int smem, cudaStream_t s);
 // Loads the recompute-mode reverse kernel of `nt` threads into the current context.
 cudaError_t preload_adjoint(int nt);
 // Resident blocks per SM of the reverse kernel of `nt` threads with `smem` bytes of
 // dynamic shared memory (occupancy API).
-cudaError_t adjoint_occupancy(int nt, bool record, int smem, int* blocks);
+cudaError_t adjoint_occupancy(int nt, int mode, int smem, int* blocks);
 constexpr int kAdjointMaxNodes = 512;
 
 // Rods with self-collision (corde_self.cu): one rod per block, at most 1024 nodes.

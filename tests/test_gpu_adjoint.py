@@ -296,31 +296,42 @@ def test_adjoint_requires_rollout_and_rejects_long_rods(corde):
 def test_record_and_recompute_modes_give_identical_gradients(corde):
     """The reverse pass either keeps each segment's sweep velocities from one forward pass
     (record mode, the default when the scratch fits) or runs every step forward again
-    (recompute mode, budget 0).  Several rods of ragged lengths and different iteration
-    counts, a segment length that leaves a short last segment, and a 300-node rod whose
-    256-thread block has no room for two sweep buffers (recompute in both cases)."""
+    (recompute mode, budget 0).  Record mode streams a step's records into two shared
+    buffers, or into one when two do not fit the block (a 300-node rod on 256 threads) or
+    when one lets more blocks share an SM and so saves a wave (8 more rods of 150 nodes
+    than the GPU has SMs: one block per SM with two buffers, two with one).  Several rods of ragged lengths and
+    different iteration counts, and a segment length that leaves a short last segment."""
     import dataclasses
 
     import torch
 
     rods = [dataclasses.replace(W.adjoint_rod(n, seed=970 + n), n_iters=it)
             for n, it in ((7, 3), (33, 10), (100, 6), (256, 10))]
+    n_sms = corde.rod_device_info()["n_sms"]
+    many = [W.adjoint_rod(150, seed=1200 + k) for k in range(n_sms + 8)]
+    groups = (rods, [W.adjoint_rod(300, seed=975)], many)
     n_steps, ckpt = 47, 10
-    out = []
-    for budget in (64 << 20, 0):
-        for group in (rods, [W.adjoint_rod(300, seed=975)]):
+    out, modes = {}, {}
+    for budget in (1 << 30, 0):
+        for gi, group in enumerate(groups):
             b = corde.RodBatch(group)
             b.set_adjoint_record_budget(budget)
             traj = b.rollout(n_steps, ckpt)
             g = torch.zeros_like(traj)
             g[:, :, :3] = 1e-2 * torch.sin(traj[:, :, :3] * 37.0)
             grads = b.adjoint(g)
-            out.append({k: v.cpu().numpy() for k, v in grads.items()})
+            out[budget, gi] = {k: v.cpu().numpy() for k, v in grads.items()}
+            modes[budget, gi] = corde.rod_adjoint_info(b.handle)
             b.close()
-    for a, c in ((out[0], out[2]), (out[1], out[3])):
+    # record mode: two buffers where they fit and cost no wave, else one
+    assert [modes[1 << 30, gi]["record_buffers"] for gi in range(3)] == [2, 1, 1], modes
+    assert modes[1 << 30, 2]["blocks_per_sm"] == 2 and modes[1 << 30, 2]["waves"] == 1, modes
+    assert all(modes[0, gi]["mode"] == "recompute" for gi in range(3)), modes
+    for gi in range(3):
+        a, c = out[1 << 30, gi], out[0, gi]
         for key in a:
             assert np.isfinite(a[key]).all(), key
-            np.testing.assert_array_equal(a[key], c[key], err_msg=key)
+            np.testing.assert_array_equal(a[key], c[key], err_msg=f"group {gi}: {key}")
     h = corde.RodBatch(rods[:1])
     with pytest.raises(corde.CordeError):
         corde.rod_set_adjoint_record_budget(h.handle, -1)
