@@ -467,13 +467,18 @@ def run_adjoint(args, torch, corde, W, n_rods=1):
     # checkpoint); the per-segment recomputed states stay L2-resident
     adj_bytes = el_steps * 16.0 + sum(r.n_nodes for r in rods) * 64.0 * (n_steps // ckpt)
     hbm = _peaks()[0].get("hbm_gbs", 6800.0)
-    # the library's choice (rod_set_adjoint_record_budget, default 64 MiB): record each
-    # segment's sweeps when they fit, else recompute every step before its reverse
+    # the library's choice (rod_set_adjoint_record_budget, default 1 GiB): record each
+    # segment's sweeps when they fit (compact layout for more rods than SMs), else
+    # recompute every step before its reverse
     nt = launch_info["threads_per_block"]
-    rec_bytes = ckpt * n_rods * (2 * rods[0].n_iters * 2 * nt + 3 * nt) * 16
+    slots = rods[0].n_iters + 1 if launch_info["compact_records"] else 2 * rods[0].n_iters
+    rec_bytes = ckpt * n_rods * (slots * 2 * nt + 3 * nt) * 16
     mode = launch_info["mode"]
+    layout = ", compact" if launch_info["compact_records"] else ""
+    desc = (f"record mode ({rec_bytes / 2**20:.1f} MiB of sweep records per segment{layout})" if mode == "record"
+            else "recompute mode")
     return {"n_rods": n_rods, "n_nodes": 256, "n_steps": n_steps, "ckpt_every": ckpt,
-            "reverse_pass": f"{mode} mode ({rec_bytes / 2**20:.1f} MiB of sweep records per segment)",
+            "reverse_pass": desc,
             "launch": launch_info,
             "roofline_hbm": {"bytes": adj_bytes, "achieved_gbs": round(adj_bytes / (adj_ms * 1e-3) / 1e9, 2),
                              "peak_gbs": hbm, "frac": round(adj_bytes / (adj_ms * 1e-3) / 1e9 / hbm, 5),
@@ -786,7 +791,8 @@ def main_ours(args):
                 "tube": lambda: run_tube(args, torch, corde, W),
                 "knot": lambda: run_knot(args, torch, corde, W),
                 "extensible": lambda: run_extensible(args, torch, corde, W),
-                "adjoint": lambda: run_adjoint(args, torch, corde, W, 1)}[args.only]()
+                "adjoint": lambda: {"single": run_adjoint(args, torch, corde, W, 1),
+                                "batched": run_adjoint(args, torch, corde, W, 256)}}[args.only]()
         if rank == 0:
             print(json.dumps({"only": args.only, "result": part}, default=str), flush=True)
         return

@@ -341,33 +341,38 @@ int rod_rollout(rod_handle h, int n_steps, int ckpt_every, float* pos_traj, void
  *  dL_duhat   per-joint intrinsic Darboux vector (x, y, z, 0)
  *  dL_dvel0, dL_dpos0   initial node velocities / positions (xyz, 0)
  *  dL_dquat0  initial frames (x, y, z, w components), dL_domega0 initial body angular velocities
- * Rods of at most 512 nodes; shared memory bounds the constraint iterations (about 20
- * for 256-node rods).  The material, drive and state set between rod_rollout and
+ * Rods of at most 512 nodes; shared memory bounds the constraint iterations (50 for
+ * rods of up to 256 nodes, 22 for longer ones).  The material, drive and state set between rod_rollout and
  * rod_adjoint must not change.  CORDE_ERR_UNSUPPORTED when the limits are exceeded. */
 int rod_adjoint(rod_handle h, const float* dL_dpos_traj, float* dL_dK, float* dL_duhat, float* dL_dvel0,
                 float* dL_dpos0, float* dL_dquat0, float* dL_domega0, void* stream);
 
-/* How the last rod_adjoint ran its largest launch, into 5 host ints: the mode (0
+/* How the last rod_adjoint ran its largest launch, into 6 host ints: the mode (0
  * recompute; 1 record mode with one sweep buffer in shared memory; 2 record mode with
  * two, the copy of a step's records overlapping the reverse of the step after it),
  * threads per block, resident blocks per SM (occupancy API, with the launch's registers
- * and shared memory), blocks of the launch (one per rod), and the device's SMs;
+ * and shared memory), blocks of the launch (one per rod), the device's SMs, and 1 when
+ * the records use the compact layout (see rod_set_adjoint_record_budget);
  * blocks / (blocks per SM x SMs), rounded up, is the number of waves.
  * Host-side only (zeros before the first rod_adjoint). */
 int rod_adjoint_info(rod_handle h, int* out);
 
-/* Scratch budget of rod_adjoint's record mode (default 64 MiB).  Within a checkpoint
+/* Scratch budget of rod_adjoint's record mode (default 1 GiB).  Within a checkpoint
  * segment the reverse pass needs every step's velocities before each constraint
  * half-sweep.
  *  - Record mode (the scratch fits in `bytes`): one forward pass over the segment keeps
- *    them in device memory, 2 n_iters x 64 B per node and step plus 48 B per node and
- *    step of neighbour data.  The reverse pass streams them back with asynchronous
+ *    them in device memory, 2 n_iters x 16 B per node and step, plus 24 B per node and
+ *    step of neighbour data.  A launch with more rods than the GPU has SMs (or one whose
+ *    full records do not fit) keeps the compact layout instead: the velocities before
+ *    the first even and every odd half-sweep, (n_iters + 1) x 16 B per node and step;
+ *    its reverse pass repeats each odd half-sweep on its record to get the input of the
+ *    next even one.  The reverse pass streams the records back with asynchronous
  *    copies, into two shared-memory buffers (the copy of a step's records overlaps the
  *    reverse of the step after it) or into one when two do not fit or when one buffer
  *    lets more blocks share an SM and so runs the launch in fewer waves.
  *  - Recompute mode (otherwise, and always with bytes = 0): every step is run forward
  *    again before its reverse.
- * Both modes give the same gradients bit for bit.  bytes >= 0 (CORDE_ERR_ARG otherwise).
+ * All modes give the same gradients bit for bit.  bytes >= 0 (CORDE_ERR_ARG otherwise).
  * Host-side only. */
 int rod_set_adjoint_record_budget(rod_handle h, long long bytes);
 

@@ -349,12 +349,13 @@ def rod_adjoint(h, dL_dpos_traj=None, dL_dK=None, dL_duhat=None, dL_dvel0=None, 
 
 
 def rod_adjoint_info(h) -> dict:
-    """How the last rod_adjoint ran its largest launch (mode, threads, blocks per SM, blocks, SMs)."""
-    out = np.zeros(5, dtype=np.int32)
+    """How the last rod_adjoint ran its largest launch (mode, record buffers and layout,
+    threads, blocks per SM, blocks, SMs)."""
+    out = np.zeros(6, dtype=np.int32)
     _check(load().rod_adjoint_info(h, out.ctypes.data), "rod_adjoint_info")
     per_sm, blocks, sms = int(out[2]), int(out[3]), int(out[4])
     return {"mode": "record" if out[0] else "recompute", "record_buffers": int(out[0]),
-            "threads_per_block": int(out[1]),
+            "compact_records": bool(out[5]), "threads_per_block": int(out[1]),
             "blocks_per_sm": per_sm, "blocks": blocks, "sms": sms,
             "waves": -(-blocks // (per_sm * sms)) if per_sm * sms > 0 else None}
 

@@ -172,12 +172,15 @@ __device__ __forceinline__ float3 vjp_apply(const VjpGeo& G, float inv, float wa
   return inv * ((1.f - G.rho) * g_bar + (G.rho * dot3(G.n, g_bar)) * G.n);
 }
 
-template <int EPT, int NT>
+// One step of the reverse pass.  sweep_v holds the step's velocity records in the layout
+// step_body writes with STORE == 2 (COMPACT) or STORE == 1.
+template <int EPT, int NT, bool COMPACT>
 __device__ __forceinline__ void reverse_step(const RodDev& R, const int t, const float3 (&r)[EPT],
                                              const float4 (&q)[EPT], const float3 (&om)[EPT], const float (&w)[EPT],
                                              const float3 (&om1)[EPT], const float4 (&qo)[EPT],
                                              const StepNeighbours& nb, const float4* par_u, const float4* par_k,
-                                             float4* halo, int& xc, const float4* sweep_v, float3 (&rb)[EPT],
+                                             float4* halo, int& xc, const float4* sweep_v,
+                                             const StepCache<EPT>& sc, float3 (&rb)[EPT],
                                              float3 (&vb)[EPT], float4 (&qb)[EPT], float3 (&ob)[EPT],
                                              float3 (&Kb)[EPT], float3 (&ub)[EPT]) {
   const int e0 = t * EPT;
@@ -225,11 +228,30 @@ __device__ __forceinline__ void reverse_step(const RodDev& R, const int t, const
     const float inv_r = vjp_inv(t + 1 < NT && e0 + EPT <= n - 1, w[EPT - 1], nb.w_next, dt);
     const float inv_l = vjp_inv(t > 0 && e0 <= n - 1, nb.w_prev, w[0], dt);
     const int tn = min(t + 1, NT - 1), tp = max(t - 1, 0);  // in-range neighbour slots
+    // the forward's boundary segment vectors (positions are fixed during the sweeps)
+    static_assert(!COMPACT || EPT == 2, "the rebuilt even-sweep input assumes no odd segment inside a thread");
+    const float3 e_r = safe_segment(sc.i_right, segment_vector(r[EPT - 1], nb.r_next), R.l0);
+    const float3 e_l = safe_segment(sc.i_left, segment_vector(nb.r_prev, r[0]), R.l0);
+    const Vec3x2 e_bnd{make_float2(e_r.x, e_l.x), make_float2(e_r.y, e_l.y), make_float2(e_r.z, e_l.z)};
 #pragma unroll 2
     for (int it = R.n_iters - 1; it >= 0; --it) {
       // geometry of this iteration's constraints, from the recorded velocities
-      const float4* so = sweep_v + (2 * it + 1) * EPT * NT;  // before the odd half-sweep
-      const float4* se = sweep_v + (2 * it) * EPT * NT;      // before the even half-sweep
+      const float4* so = sweep_v + (COMPACT ? 1 + it : 2 * it + 1) * EPT * NT;  // before the odd half-sweep
+      // the velocities before the even half-sweep: recorded; in the compact layout only for
+      // the first iteration, and for a later one the odd half-sweep of the iteration before
+      // repeated on its recorded input (the forward's own arithmetic, so the same values)
+      float3 ve[EPT];
+      {
+        // slot 2 it; compact: slot 0, or the record before the previous odd half-sweep
+        const float4* sp = sweep_v + (COMPACT ? it : 2 * it) * EPT * NT;
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) ve[e] = f3(sp[e * NT + t]);
+        if (COMPACT && it > 0) {
+          const float3 vn = t + 1 < NT ? f3(sp[tn]) : zero3();
+          const float3 vp = t > 0 ? f3(sp[(EPT - 1) * NT + tp]) : zero3();
+          boundary_apply(e_bnd, sc.l_bnd, sc.c_bnd, dt, vn, vp, ve[EPT - 1], ve[0]);
+        }
+      }
       VjpGeo g_o[NO], g_e[NE];
 #pragma unroll
       for (int k = 0; k + 1 < EPT / 2; ++k) {
@@ -241,7 +263,7 @@ __device__ __forceinline__ void reverse_step(const RodDev& R, const int t, const
 #pragma unroll
       for (int k = 0; k < NE; ++k) {
         const int a = 2 * k, b = 2 * k + 1;
-        g_e[k] = vjp_geo(r[a], f3(se[a * NT + t]), r[b], f3(se[b * NT + t]), inv_e[k], R.l0, dt);
+        g_e[k] = vjp_geo(r[a], ve[a], r[b], ve[b], inv_e[k], R.l0, dt);
       }
       // exchange of the adjoint velocities of the first and last element
       float4* hb = halo + (xc & 1) * kHaloSlots * NT;
@@ -373,10 +395,11 @@ __device__ __forceinline__ void reverse_step(const RodDev& R, const int t, const
 // step before its reverse; 1: record mode with one sweep buffer (a step's records are
 // copied in after the step before it is reversed); 2: record mode with two buffers (the
 // copy overlaps the reverse of the step before).
-template <int NT, int MODE>
+template <int NT, int MODE, bool COMPACT>
 __global__ void __launch_bounds__(NT)
 adjoint_kernel(AdjointArgs a) {
   constexpr bool RECORD = MODE > 0;
+  constexpr int STORE = COMPACT ? 2 : 1;  // step_body's record layout
   constexpr int NBUF = MODE == 2 ? 2 : 1;
   constexpr int EPT = 2;
   extern __shared__ float4 smem[];
@@ -384,7 +407,8 @@ adjoint_kernel(AdjointArgs a) {
   float4* par_k = smem + EPT * NT;
   float4* halo = smem + 2 * EPT * NT;
   float4* sweep_v = halo + 2 * kHaloSlots * NT;
-  const int64_t rec_stride = (int64_t)2 * a.rec_iters * EPT * NT;  // float4 per (step, block) record
+  // float4 per (step, block) record: 1 + n_iters (compact) or 2 n_iters slots of EPT NT
+  const int64_t rec_stride = (int64_t)(COMPACT ? a.rec_iters + 1 : 2 * a.rec_iters) * EPT * NT;
 
   const int rid = a.work[blockIdx.x];
   const RodDev R = a.rods[rid];
@@ -436,7 +460,7 @@ adjoint_kernel(AdjointArgs a) {
     // copies this thread's entries of step s's record into a shared buffer
     auto fetch = [&](int s, float4* dst) {
       const float4* src = rec_at(s);
-      const int n_ent = 2 * R.n_iters * EPT;
+      const int n_ent = R.n_iters > 0 ? (COMPACT ? R.n_iters + 1 : 2 * R.n_iters) * EPT : 0;
       for (int k = 0; k < n_ent; ++k) cp_async16(dst + k * NT + t, src + k * NT + t);
       cp_async_commit();
     };
@@ -445,7 +469,7 @@ adjoint_kernel(AdjointArgs a) {
       for (int s = 0; s < cnt; ++s) {
         put_state(s);
         StepNeighbours nb;
-        step_body<EPT, NT, true>(R, H, r, v, q, om, w, par_u, par_k, halo, xc, sc, v_drive, w_drive, rec_at(s), &nb);
+        step_body<EPT, NT, STORE>(R, H, r, v, q, om, w, par_u, par_k, halo, xc, sc, v_drive, w_drive, rec_at(s), &nb);
         float4* nr = nb_at(s);
         nr[0] = make_float4(nb.r_next.x, nb.r_next.y, nb.r_next.z, nb.w_next);
         nr[NT] = make_float4(nb.r_prev.x, nb.r_prev.y, nb.r_prev.z, nb.w_prev);
@@ -458,7 +482,7 @@ adjoint_kernel(AdjointArgs a) {
       for (int s = 0; s < cnt; ++s) {
         put_state(s);
         if (s + 1 < cnt)
-          step_body<EPT, NT, false>(R, H, r, v, q, om, w, par_u, par_k, halo, xc, sc, v_drive, w_drive, nullptr, nullptr);
+          step_body<EPT, NT, 0>(R, H, r, v, q, om, w, par_u, par_k, halo, xc, sc, v_drive, w_drive, nullptr, nullptr);
       }
     }
     // reverse the segment's steps
@@ -536,8 +560,8 @@ adjoint_kernel(AdjointArgs a) {
           if constexpr (NBUF == 2) fetch(s - 1, sweep_v + ((s - 1) & 1) * rec_stride);
           prefetch(s - 1);
         }
-        reverse_step<EPT, NT>(R, t, r_in, q_in, om_in, w, om, q, nb, par_u, par_k, halo, xc,
-                              sweep_v + (s % NBUF) * rec_stride, rb, vb, qb, ob, Kb, ub);
+        reverse_step<EPT, NT, COMPACT>(R, t, r_in, q_in, om_in, w, om, q, nb, par_u, par_k, halo, xc,
+                                       sweep_v + (s % NBUF) * rec_stride, sc, rb, vb, qb, ob, Kb, ub);
         if constexpr (NBUF == 1) {
           if (s > 0) {
             block_sync<NT>();
@@ -582,15 +606,15 @@ adjoint_kernel(AdjointArgs a) {
         }
         if (s > 0) prefetch(s - 1);
         StepNeighbours nb;
-        step_body<EPT, NT, true>(R, H, r, v, q, om, w, par_u, par_k, halo, xc, sc, v_drive, w_drive, sweep_v, &nb);
+        step_body<EPT, NT, STORE>(R, H, r, v, q, om, w, par_u, par_k, halo, xc, sc, v_drive, w_drive, sweep_v, &nb);
         // loss gradient with respect to the positions after this step
         if (a.dLdpos != nullptr) {
 #pragma unroll
           for (int e = 0; e < EPT; ++e)
             if (e0 + e < R.n) rb[e] += g_s[e];
         }
-        reverse_step<EPT, NT>(R, t, r_in, q_in, om_in, w, om, q, nb, par_u, par_k, halo, xc, sweep_v, rb, vb, qb, ob,
-                              Kb, ub);
+        reverse_step<EPT, NT, COMPACT>(R, t, r_in, q_in, om_in, w, om, q, nb, par_u, par_k, halo, xc, sweep_v, sc,
+                                       rb, vb, qb, ob, Kb, ub);
       }
     }
   }
@@ -609,77 +633,65 @@ adjoint_kernel(AdjointArgs a) {
   }
 }
 
-template <int NT, int MODE>
-cudaError_t launch_adjoint_mode(const AdjointArgs& a, int n_blocks, int smem, cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(adjoint_kernel<NT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
-  adjoint_kernel<NT, MODE><<<n_blocks, NT, smem, s>>>(a);
-  return cudaGetLastError();
-}
+using AdjointFn = void (*)(AdjointArgs);
 template <int NT>
-cudaError_t launch_adjoint_nt(const AdjointArgs& a, int mode, int n_blocks, int smem, cudaStream_t s) {
+AdjointFn adjoint_fn_nt(int mode, bool compact) {
   switch (mode) {
-    case 0: return launch_adjoint_mode<NT, 0>(a, n_blocks, smem, s);
-    case 1: return launch_adjoint_mode<NT, 1>(a, n_blocks, smem, s);
-    case 2: return launch_adjoint_mode<NT, 2>(a, n_blocks, smem, s);
-    default: return cudaErrorInvalidValue;
+    case 0: return compact ? adjoint_kernel<NT, 0, true> : adjoint_kernel<NT, 0, false>;
+    case 1: return compact ? adjoint_kernel<NT, 1, true> : adjoint_kernel<NT, 1, false>;
+    case 2: return compact ? adjoint_kernel<NT, 2, true> : adjoint_kernel<NT, 2, false>;
+    default: return nullptr;
+  }
+}
+// The reverse kernel of `nt` threads in `mode`, with the compact record layout or not
+// (nullptr for a thread count that does not exist).
+AdjointFn adjoint_fn(int nt, int mode, bool compact) {
+  switch (nt) {
+    case 32: return adjoint_fn_nt<32>(mode, compact);
+    case 64: return adjoint_fn_nt<64>(mode, compact);
+    case 128: return adjoint_fn_nt<128>(mode, compact);
+    case 256: return adjoint_fn_nt<256>(mode, compact);
+    default: return nullptr;
   }
 }
 
 }  // namespace
 
-int adjoint_smem_bytes(int nt, int n_iters, int mode) {
+int adjoint_smem_bytes(int nt, int n_iters, int mode, bool compact) {
   const int ept = 2;
-  const int sweep = 2 * (n_iters > 0 ? n_iters : 1) * ept * nt;
+  const int it = n_iters > 0 ? n_iters : 1;
+  const int sweep = (compact ? it + 1 : 2 * it) * ept * nt;  // record slots of one step
   return (2 * ept * nt + 2 * kHaloSlots * nt + (mode == 2 ? 2 : 1) * sweep) * (int)sizeof(float4);
 }
 
-template <int NT, int MODE>
-cudaError_t occupancy_mode(int smem, int* blocks) {
-  cudaError_t e = cudaFuncSetAttribute(adjoint_kernel<NT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+cudaError_t adjoint_occupancy(int nt, int mode, bool compact, int smem, int* blocks) {
+  const AdjointFn fn = adjoint_fn(nt, mode, compact);
+  if (fn == nullptr) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, adjoint_kernel<NT, MODE>, NT, (size_t)smem);
-}
-template <int NT>
-cudaError_t occupancy_nt(int mode, int smem, int* blocks) {
-  switch (mode) {
-    case 0: return occupancy_mode<NT, 0>(smem, blocks);
-    case 1: return occupancy_mode<NT, 1>(smem, blocks);
-    case 2: return occupancy_mode<NT, 2>(smem, blocks);
-    default: return cudaErrorInvalidValue;
-  }
-}
-
-cudaError_t adjoint_occupancy(int nt, int mode, int smem, int* blocks) {
-  switch (nt) {
-    case 32: return occupancy_nt<32>(mode, smem, blocks);
-    case 64: return occupancy_nt<64>(mode, smem, blocks);
-    case 128: return occupancy_nt<128>(mode, smem, blocks);
-    case 256: return occupancy_nt<256>(mode, smem, blocks);
-    default: return cudaErrorInvalidValue;
-  }
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fn, nt, (size_t)smem);
 }
 
 cudaError_t preload_adjoint(int nt) {
-  cudaFuncAttributes at;
-  switch (nt) {
-    case 32: return cudaFuncGetAttributes(&at, adjoint_kernel<32, 0>);
-    case 64: return cudaFuncGetAttributes(&at, adjoint_kernel<64, 0>);
-    case 128: return cudaFuncGetAttributes(&at, adjoint_kernel<128, 0>);
-    case 256: return cudaFuncGetAttributes(&at, adjoint_kernel<256, 0>);
-    default: return cudaErrorInvalidValue;
+  for (int c = 0; c < 2; ++c) {
+    const AdjointFn fn = adjoint_fn(nt, 0, c != 0);
+    if (fn == nullptr) return cudaErrorInvalidValue;
+    cudaFuncAttributes at;
+    cudaError_t e = cudaFuncGetAttributes(&at, fn);
+    if (e != cudaSuccess) return e;
   }
+  return cudaSuccess;
 }
 
-cudaError_t launch_adjoint(int nt, int mode, const AdjointArgs& a, int n_blocks, int smem, cudaStream_t s) {
+cudaError_t launch_adjoint(int nt, int mode, bool compact, const AdjointArgs& a, int n_blocks, int smem,
+                           cudaStream_t s) {
   if ((mode > 0) != (a.sweep_rec != nullptr)) return cudaErrorInvalidValue;
-  switch (nt) {
-    case 32: return launch_adjoint_nt<32>(a, mode, n_blocks, smem, s);
-    case 64: return launch_adjoint_nt<64>(a, mode, n_blocks, smem, s);
-    case 128: return launch_adjoint_nt<128>(a, mode, n_blocks, smem, s);
-    case 256: return launch_adjoint_nt<256>(a, mode, n_blocks, smem, s);
-    default: return cudaErrorInvalidValue;
-  }
+  const AdjointFn fn = adjoint_fn(nt, mode, compact);
+  if (fn == nullptr) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  fn<<<n_blocks, nt, smem, s>>>(a);
+  return cudaGetLastError();
 }
 
 }  // namespace corde

@@ -166,9 +166,10 @@ struct corde_rods {
   size_t sweep_rec_cap = 0;
   float4* d_nb_rec = nullptr;
   size_t nb_rec_cap = 0;
-  long long adj_record_budget = 64ll << 20;
+  long long adj_record_budget = 1ll << 30;
   int ro_steps = 0, ro_every = 0;
-  int adj_info[5] = {0, 0, 0, 0, 0};  // last rod_adjoint's largest launch: mode, nt, blocks/SM, blocks, SMs
+  // last rod_adjoint's largest launch: mode, nt, blocks/SM, blocks, SMs, compact records
+  int adj_info[6] = {0, 0, 0, 0, 0, 0};
   std::vector<Bin> adj_bins;  // variant = threads per block
   // catheter/guidewire pairs
   std::vector<int4> pairs;     // (outer, inner, mode, 0)
@@ -1427,33 +1428,47 @@ int rod_adjoint(rod_handle h, const float* dL_dpos_traj, float* dL_dK, float* dL
   int iters = 0;
   for (int r = 0; r < h->n_rods; ++r) iters = std::max(iters, h->n_iters[r]);
   const int rec_iters = iters > 0 ? iters : 1;
-  // record mode per launch when its scratch fits the budget: two sweep buffers in shared
-  // memory (the copy of a step's records overlaps the reverse of the step after it), or
-  // one when two do not fit or when one lets the launch run in fewer waves (more resident
-  // blocks per SM); recompute mode otherwise
+  // record mode per launch when its scratch fits the budget, recompute mode otherwise.
+  // Record layout: compact where the launch has more rods than the GPU has SMs (blocks
+  // share SMs, throughput and so the records' memory traffic decide), full otherwise (each
+  // rod's latency decides, and rebuilding the even half-sweeps' inputs lengthens it), or
+  // compact when only that fits.  Two sweep buffers in shared memory (the copy of a step's
+  // records overlaps the reverse of the step after it), or one when two do not fit or when
+  // one lets the launch run in fewer waves (more resident blocks per SM).
   const size_t K = (size_t)h->ro_every;
   int sms = 0;
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   std::vector<int> mode(h->adj_bins.size(), 0);
+  std::vector<char> compact(h->adj_bins.size(), 0);
   size_t sweep_need = 0, nb_need = 0;
   for (size_t i = 0; i < h->adj_bins.size(); ++i) {
     const Bin& b = h->adj_bins[i];
     const int nt = variants()[b.variant].nt;
-    const size_t sw = K * b.count * 2 * rec_iters * 2 * nt, nbn = K * b.count * 3 * nt;  // float4 entries
-    if ((long long)((sw + nbn) * sizeof(float4)) > h->adj_record_budget) continue;
-    const int smem1 = adjoint_smem_bytes(nt, iters, 1), smem2 = adjoint_smem_bytes(nt, iters, 2);
-    if (smem1 > smem_max) continue;
-    int m = 1;
-    if (smem2 <= smem_max) {
-      int occ1 = 0, occ2 = 0;
-      CK(adjoint_occupancy(nt, 1, smem1, &occ1));
-      CK(adjoint_occupancy(nt, 2, smem2, &occ2));
-      auto waves = [&](int occ) { return occ > 0 ? (b.count + occ * sms - 1) / (occ * sms) : INT_MAX; };
-      m = waves(occ2) <= waves(occ1) ? 2 : 1;
+    const size_t nbn = K * b.count * 3 * nt;  // float4 entries
+    const bool prefer_compact = b.count > sms;
+    for (int pass = 0; pass < 2 && mode[i] == 0; ++pass) {
+      const bool cpt = pass == 0 ? prefer_compact : true;
+      if (pass == 1 && prefer_compact) break;
+      const size_t sw = K * b.count * (cpt ? rec_iters + 1 : 2 * rec_iters) * 2 * nt;
+      if ((long long)((sw + nbn) * sizeof(float4)) > h->adj_record_budget) continue;
+      const int smem1 = adjoint_smem_bytes(nt, iters, 1, cpt), smem2 = adjoint_smem_bytes(nt, iters, 2, cpt);
+      if (smem1 > smem_max) continue;
+      int m = 1;
+      if (smem2 <= smem_max) {
+        int occ1 = 0, occ2 = 0;
+        CK(adjoint_occupancy(nt, 1, cpt, smem1, &occ1));
+        CK(adjoint_occupancy(nt, 2, cpt, smem2, &occ2));
+        auto waves = [&](int occ) { return occ > 0 ? (b.count + occ * sms - 1) / (occ * sms) : INT_MAX; };
+        m = waves(occ2) <= waves(occ1) ? 2 : 1;
+      }
+      mode[i] = m;
+      compact[i] = cpt;
+      sweep_need = std::max(sweep_need, sw);
+      nb_need = std::max(nb_need, nbn);
     }
-    mode[i] = m;
-    sweep_need = std::max(sweep_need, sw);
-    nb_need = std::max(nb_need, nbn);
+    // recompute mode keeps the step's records in shared memory only: the full layout
+    // unless only the compact one fits the block
+    if (mode[i] == 0) compact[i] = adjoint_smem_bytes(nt, iters, 0, false) > smem_max;
   }
   const bool any_record = sweep_need > 0;
   if (int rc = ensure_capacity(&h->d_seg, &h->seg_cap, (K + (any_record ? 1 : 0)) * 4 * E)) return rc;
@@ -1479,11 +1494,11 @@ int rod_adjoint(rod_handle h, const float* dL_dpos_traj, float* dL_dK, float* dL
   a.dquat0 = dev_out[4];
   a.domega0 = dev_out[5];
   int launches = 0;
-  std::fill(h->adj_info, h->adj_info + 5, 0);
+  std::fill(h->adj_info, h->adj_info + 6, 0);
   for (size_t i = 0; i < h->adj_bins.size(); ++i) {
     const Bin& b = h->adj_bins[i];
     const int nt = variants()[b.variant].nt;
-    const int smem = adjoint_smem_bytes(nt, iters, mode[i]);
+    const int smem = adjoint_smem_bytes(nt, iters, mode[i], compact[i] != 0);
     a.sweep_rec = mode[i] ? h->d_sweep_rec : nullptr;
     a.nb_rec = mode[i] ? h->d_nb_rec : nullptr;
     a.rec_iters = rec_iters;
@@ -1494,11 +1509,11 @@ int rod_adjoint(rod_handle h, const float* dL_dpos_traj, float* dL_dK, float* dL
     a.work = b.d_work;
     if (b.count >= h->adj_info[3]) {
       int per_sm = 0;
-      CK(adjoint_occupancy(nt, mode[i], smem, &per_sm));
-      const int info[5] = {mode[i], nt, per_sm, b.count, sms};
-      std::copy(info, info + 5, h->adj_info);
+      CK(adjoint_occupancy(nt, mode[i], compact[i] != 0, smem, &per_sm));
+      const int info[6] = {mode[i], nt, per_sm, b.count, sms, compact[i] ? 1 : 0};
+      std::copy(info, info + 6, h->adj_info);
     }
-    cudaError_t e = launch_adjoint(nt, mode[i], a, b.count, smem, s);
+    cudaError_t e = launch_adjoint(nt, mode[i], compact[i] != 0, a, b.count, smem, s);
     if (e != cudaSuccess) return fail(CORDE_ERR_CUDA, std::string("adjoint launch: ") + cudaGetErrorString(e));
     ++launches;
   }
@@ -1508,7 +1523,7 @@ int rod_adjoint(rod_handle h, const float* dL_dpos_traj, float* dL_dK, float* dL
 
 int rod_adjoint_info(rod_handle h, int* out) {
   if (!h || !out) return fail(CORDE_ERR_ARG, "rod_adjoint_info: NULL argument");
-  std::copy(h->adj_info, h->adj_info + 5, out);
+  std::copy(h->adj_info, h->adj_info + 6, out);
   return CORDE_OK;
 }
 
@@ -1937,7 +1952,9 @@ extern "C" int rod_adjoint_noalloc(const RodParams* params, const float* pos, co
   const int iters = params->inextensible ? params->n_iters : 0;
   int smem_max = 0;
   CK(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  const int smem = adjoint_smem_bytes(nt, iters);
+  // the compact record layout where the full one does not fit the block
+  const bool cpt = adjoint_smem_bytes(nt, iters, 0, false) > smem_max;
+  const int smem = adjoint_smem_bytes(nt, iters, 0, cpt);
   if (smem > smem_max) return fail(CORDE_ERR_UNSUPPORTED, "rod_adjoint_noalloc: shared memory");
   AdjointArgs ad;
   ad.rods = d_rod;
@@ -1957,7 +1974,7 @@ extern "C" int rod_adjoint_noalloc(const RodParams* params, const float* pos, co
   ad.dpos0 = dev_out[4];
   ad.dquat0 = nullptr;
   ad.domega0 = nullptr;
-  cudaError_t e = launch_adjoint(nt, 0, ad, 1, smem, s);
+  cudaError_t e = launch_adjoint(nt, 0, cpt, ad, 1, smem, s);
   if (e != cudaSuccess) return fail(CORDE_ERR_CUDA, std::string("rod_adjoint_noalloc: adjoint: ") + cudaGetErrorString(e));
   return CORDE_OK;
 }

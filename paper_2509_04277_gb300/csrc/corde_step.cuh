@@ -289,6 +289,32 @@ __device__ __forceinline__ Vec3x2 constraint_impulse2(const Vec3x2& e, const Vec
   return Vec3x2{__fmul2_rn(sv, dx), __fmul2_rn(sv, dy), __fmul2_rn(sv, dz)};
 }
 
+// The two odd constraints across a thread's boundaries with folded scales, in the two
+// lanes of packed operations: right (the thread's last node, the next thread's first) in
+// lane x, left (the previous thread's last node, the thread's first) in lane y.  e_bnd
+// holds their segment vectors, l_bnd and c_bnd the folded scales of the thread's own node
+// in each (right: -c_a, left: +c_b), vn and vp the neighbours' velocities; updates the
+// thread's last and first velocities.  The adjoint repeats this update on recorded
+// velocities, so both use this one function.
+__device__ __forceinline__ void boundary_apply(const Vec3x2& e_bnd, float2 l_bnd, float2 c_bnd, float dt, float3 vn,
+                                               float3 vp, float3& v_last, float3& v_first) {
+  const Vec3x2 va{make_float2(v_last.x, vp.x), make_float2(v_last.y, vp.y), make_float2(v_last.z, vp.z)};
+  const Vec3x2 vb{make_float2(vn.x, v_first.x), make_float2(vn.y, v_first.y), make_float2(vn.z, v_first.z)};
+  const float2 dt2 = make_float2(dt, dt);
+  const float2 dx = __ffma2_rn(dt2, __fadd2_rn(vb.x, neg2(va.x)), e_bnd.x);
+  const float2 dy = __ffma2_rn(dt2, __fadd2_rn(vb.y, neg2(va.y)), e_bnd.y);
+  const float2 dz = __ffma2_rn(dt2, __fadd2_rn(vb.z, neg2(va.z)), e_bnd.z);
+  const float2 dd = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+  const float2 il = make_float2(rsqrtf(dd.x), rsqrtf(dd.y));
+  const float2 scl = __ffma2_rn(l_bnd, il, neg2(c_bnd));
+  // right: v_last -= c_a (l0 / |d| - 1) d ; left: v_first += c_b (l0 / |d| - 1) d
+  const float2 nx = __ffma2_rn(scl, dx, make_float2(v_last.x, v_first.x));
+  const float2 ny = __ffma2_rn(scl, dy, make_float2(v_last.y, v_first.y));
+  const float2 nz = __ffma2_rn(scl, dz, make_float2(v_last.z, v_first.z));
+  v_last = f3(nx.x, ny.x, nz.x);
+  v_first = f3(nx.y, ny.y, nz.y);
+}
+
 // Per-step data of one constraint: e = r_b - r_a and 1 / (dt (w_a + w_b)); a constraint
 // that does not exist (or joins two kinematic nodes) gets 0 and a safe e.
 __device__ __forceinline__ float3 segment_vector(float3 ra, float3 rb) {
@@ -380,10 +406,13 @@ constexpr int step_smem_bytes() {
 
 // One time step of the rod; H (BlockHalo or ClusterHalo) gives the thread's place in the
 // rod, its neighbours' exchange slots and the barrier; sc holds the launch constants
-// (default-constructed before the first step).  With STORE, the velocities before every
-// constraint half-sweep are written to sweep_v ([2 n_iters][EPT][NT]) and the neighbour
-// data to *nb (for the adjoint).
-template <int EPT, int NT, bool STORE, class Halo, class Hook = NoHook>
+// (default-constructed before the first step).  STORE (for the adjoint) writes the
+// neighbour data to *nb and velocities to sweep_v: with STORE == 1 those before every
+// constraint half-sweep ([2 n_iters][EPT][NT], slot 2 it before the even and 2 it + 1
+// before the odd half-sweep of iteration it); with STORE == 2 (compact) those before the
+// first even half-sweep (slot 0) and before every odd one (slot 1 + it), from which the
+// adjoint rebuilds the others.
+template <int EPT, int NT, int STORE, class Halo, class Hook = NoHook>
 __device__ __forceinline__ void step_body(const RodDev& R, const Halo& H, float3 (&r)[EPT], float3 (&v)[EPT],
                                           float4 (&q)[EPT], float3 (&om)[EPT], const float (&w)[EPT],
                                           const float4* par_u, const float4* par_k, float4* halo, int& xc,
@@ -574,7 +603,9 @@ __device__ __forceinline__ void step_body(const RodDev& R, const Halo& H, float3
     auto iteration = [&](int it, auto tube_on) {
       if constexpr (STORE) {
 #pragma unroll
-        for (int e = 0; e < EPT; ++e) sweep_v[((2 * it) * EPT + e) * NT + t] = make_float4(v[e].x, v[e].y, v[e].z, 0.f);
+        for (int e = 0; e < EPT; ++e)
+          if (STORE == 1 || it == 0)
+            sweep_v[((STORE == 1 ? 2 * it : 0) * EPT + e) * NT + t] = make_float4(v[e].x, v[e].y, v[e].z, 0.f);
       }
       // even segments (e0 + 2k, e0 + 2k + 1): local to the thread, two per packed op
       if constexpr (StepCache<EPT>::kFold) {
@@ -610,7 +641,7 @@ __device__ __forceinline__ void step_body(const RodDev& R, const Halo& H, float3
       if constexpr (STORE) {
 #pragma unroll
         for (int e = 0; e < EPT; ++e)
-          sweep_v[((2 * it + 1) * EPT + e) * NT + t] = make_float4(v[e].x, v[e].y, v[e].z, 0.f);
+          sweep_v[((STORE == 1 ? 2 * it + 1 : it + 1) * EPT + e) * NT + t] = make_float4(v[e].x, v[e].y, v[e].z, 0.f);
       }
       // exchange 3: velocities of the first and last element
       hb = halo + (xc & 1) * kHaloSlots * NT;
@@ -632,31 +663,20 @@ __device__ __forceinline__ void step_body(const RodDev& R, const Halo& H, float3
       {
         const float3 vn = has_next ? H.next3(hb, 0) : zero3();
         const float3 vp = has_prev ? H.prev3(hb, 1) : zero3();
-        const Vec3x2 va{make_float2(v[EPT - 1].x, vp.x), make_float2(v[EPT - 1].y, vp.y),
-                        make_float2(v[EPT - 1].z, vp.z)};
-        const Vec3x2 vb{make_float2(vn.x, v[0].x), make_float2(vn.y, v[0].y), make_float2(vn.z, v[0].z)};
-        float2 nx, ny, nz;
         if constexpr (StepCache<EPT>::kFold) {
-          const float2 dt2 = make_float2(dt, dt);
-          const float2 dx = __ffma2_rn(dt2, __fadd2_rn(vb.x, neg2(va.x)), e_bnd.x);
-          const float2 dy = __ffma2_rn(dt2, __fadd2_rn(vb.y, neg2(va.y)), e_bnd.y);
-          const float2 dz = __ffma2_rn(dt2, __fadd2_rn(vb.z, neg2(va.z)), e_bnd.z);
-          const float2 dd = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
-          const float2 il = make_float2(rsqrtf(dd.x), rsqrtf(dd.y));
-          const float2 scl = __ffma2_rn(sc.l_bnd, il, neg2(sc.c_bnd));
-          // right: v_last -= c_a (l0 / |d| - 1) d ; left: v_first += c_b (l0 / |d| - 1) d
-          nx = __ffma2_rn(scl, dx, make_float2(v[EPT - 1].x, v[0].x));
-          ny = __ffma2_rn(scl, dy, make_float2(v[EPT - 1].y, v[0].y));
-          nz = __ffma2_rn(scl, dz, make_float2(v[EPT - 1].z, v[0].z));
+          boundary_apply(e_bnd, sc.l_bnd, sc.c_bnd, dt, vn, vp, v[EPT - 1], v[0]);
         } else {
+          const Vec3x2 va{make_float2(v[EPT - 1].x, vp.x), make_float2(v[EPT - 1].y, vp.y),
+                          make_float2(v[EPT - 1].z, vp.z)};
+          const Vec3x2 vb{make_float2(vn.x, v[0].x), make_float2(vn.y, v[0].y), make_float2(vn.z, v[0].z)};
           const Vec3x2 g = constraint_impulse2(e_bnd, va, vb, i_bnd, R.l0, dt);
           // right: v_last -= w_last g.x ; left: v_first += w_first g.y
-          nx = __ffma2_rn(w_bnd, g.x, make_float2(v[EPT - 1].x, v[0].x));
-          ny = __ffma2_rn(w_bnd, g.y, make_float2(v[EPT - 1].y, v[0].y));
-          nz = __ffma2_rn(w_bnd, g.z, make_float2(v[EPT - 1].z, v[0].z));
+          const float2 nx = __ffma2_rn(w_bnd, g.x, make_float2(v[EPT - 1].x, v[0].x));
+          const float2 ny = __ffma2_rn(w_bnd, g.y, make_float2(v[EPT - 1].y, v[0].y));
+          const float2 nz = __ffma2_rn(w_bnd, g.z, make_float2(v[EPT - 1].z, v[0].z));
+          v[EPT - 1] = f3(nx.x, ny.x, nz.x);
+          v[0] = f3(nx.y, ny.y, nz.y);
         }
-        v[EPT - 1] = f3(nx.x, ny.x, nz.x);
-        v[0] = f3(nx.y, ny.y, nz.y);
       }
       // collision response (analytic vessel), per node
       if constexpr (decltype(tube_on)::value) {

@@ -84,27 +84,32 @@ struct AdjointArgs {
   int64_t n_elem;
   float4 *dpos0, *dvel0, *dquat0, *domega0, *dK, *duhat;
   // Record mode (sweep_rec != NULL): the first pass over a checkpoint segment keeps, per
-  // step and block, the velocities before every constraint half-sweep
-  // (sweep_rec[(s gridDim + b) 2 rec_iters EPT NT ...]) and the neighbour data (nb_rec,
-  // 3 float4 per thread), and seg_states holds K + 1 states; the reverse pass then reads
-  // them instead of recomputing each step.  NULL: recompute mode.
+  // step and block, the velocities before every constraint half-sweep (compact layout:
+  // before the first even and every odd one) (sweep_rec[(s gridDim + b) slots EPT NT ...],
+  // 2 rec_iters or rec_iters + 1 slots) and the neighbour data (nb_rec, 3 float4 per
+  // thread), and seg_states holds K + 1 states; the reverse pass then reads them instead
+  // of recomputing each step.  NULL: recompute mode.
   float4* sweep_rec = nullptr;
   float4* nb_rec = nullptr;
   int rec_iters = 0;
 };
 // Reverse-kernel modes: 0 recompute; 1 record, one sweep buffer (the copy of a step's
 // records waits for the reverse of the step after it); 2 record, two sweep buffers (the
-// copy overlaps that reverse).  All three give the same gradients bit for bit.
+// copy overlaps that reverse).  compact: 1 + n_iters record slots per step instead of
+// 2 n_iters (the adjoint rebuilds the inputs of the later even half-sweeps: less memory
+// traffic and shared memory, a longer reverse).  All give the same gradients.
 // Shared memory of the reverse kernel: parameters, exchange buffers and one (modes 0, 1)
 // or two (mode 2) sweep-velocity buffers.
-int adjoint_smem_bytes(int nt, int n_iters, int mode = 0);
+int adjoint_smem_bytes(int nt, int n_iters, int mode = 0, bool compact = false);
 // mode > 0 exactly when a.sweep_rec is set (cudaErrorInvalidValue otherwise).
-cudaError_t launch_adjoint(int nt, int mode, const AdjointArgs& a, int n_blocks, int smem, cudaStream_t s);
-// Loads the recompute-mode reverse kernel of `nt` threads into the current context.
+cudaError_t launch_adjoint(int nt, int mode, bool compact, const AdjointArgs& a, int n_blocks, int smem,
+                           cudaStream_t s);
+// Loads the recompute-mode reverse kernels of `nt` threads (both layouts) into the
+// current context.
 cudaError_t preload_adjoint(int nt);
 // Resident blocks per SM of the reverse kernel of `nt` threads with `smem` bytes of
 // dynamic shared memory (occupancy API).
-cudaError_t adjoint_occupancy(int nt, int mode, int smem, int* blocks);
+cudaError_t adjoint_occupancy(int nt, int mode, bool compact, int smem, int* blocks);
 constexpr int kAdjointMaxNodes = 512;
 
 // Rods with self-collision (corde_self.cu): one rod per block, at most 1024 nodes.

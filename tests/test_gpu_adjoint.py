@@ -296,11 +296,15 @@ def test_adjoint_requires_rollout_and_rejects_long_rods(corde):
 def test_record_and_recompute_modes_give_identical_gradients(corde):
     """The reverse pass either keeps each segment's sweep velocities from one forward pass
     (record mode, the default when the scratch fits) or runs every step forward again
-    (recompute mode, budget 0).  Record mode streams a step's records into two shared
-    buffers, or into one when two do not fit the block (a 300-node rod on 256 threads) or
-    when one lets more blocks share an SM and so saves a wave (8 more rods of 150 nodes
-    than the GPU has SMs: one block per SM with two buffers, two with one).  Several rods of ragged lengths and
-    different iteration counts, and a segment length that leaves a short last segment."""
+    (recompute mode, budget 0).  Record mode keeps every half-sweep's input (full layout)
+    or, for launches with more rods than SMs and where only that fits, the first even and
+    every odd one (compact layout: the reverse pass rebuilds the others, bit for bit).  It
+    streams a step's records into two shared buffers, or into one when two do not fit the
+    block (a 300-node rod on 256 threads with 12 iterations) or when one lets more blocks
+    share an SM and so saves a wave (8 more rods of 150 nodes with 20 iterations than the
+    GPU has SMs: one block per SM with two buffers, two with one; with 10 iterations two
+    blocks fit with two buffers).  Several rods of ragged lengths and different iteration
+    counts, and a segment length that leaves a short last segment."""
     import dataclasses
 
     import torch
@@ -308,8 +312,9 @@ def test_record_and_recompute_modes_give_identical_gradients(corde):
     rods = [dataclasses.replace(W.adjoint_rod(n, seed=970 + n), n_iters=it)
             for n, it in ((7, 3), (33, 10), (100, 6), (256, 10))]
     n_sms = corde.rod_device_info()["n_sms"]
-    many = [W.adjoint_rod(150, seed=1200 + k) for k in range(n_sms + 8)]
-    groups = (rods, [W.adjoint_rod(300, seed=975)], many)
+    many = [dataclasses.replace(W.adjoint_rod(150, seed=1200 + k), n_iters=20) for k in range(n_sms + 8)]
+    many10 = [W.adjoint_rod(150, seed=1400 + k) for k in range(n_sms + 8)]
+    groups = (rods, [dataclasses.replace(W.adjoint_rod(300, seed=975), n_iters=12)], many, many10)
     n_steps, ckpt = 47, 10
     out, modes = {}, {}
     for budget in (1 << 30, 0):
@@ -323,11 +328,14 @@ def test_record_and_recompute_modes_give_identical_gradients(corde):
             out[budget, gi] = {k: v.cpu().numpy() for k, v in grads.items()}
             modes[budget, gi] = corde.rod_adjoint_info(b.handle)
             b.close()
-    # record mode: two buffers where they fit and cost no wave, else one
-    assert [modes[1 << 30, gi]["record_buffers"] for gi in range(3)] == [2, 1, 1], modes
-    assert modes[1 << 30, 2]["blocks_per_sm"] == 2 and modes[1 << 30, 2]["waves"] == 1, modes
-    assert all(modes[0, gi]["mode"] == "recompute" for gi in range(3)), modes
-    for gi in range(3):
+    # record mode: two buffers where they fit and cost no wave, else one; compact records
+    # for more rods than SMs or where only they fit
+    rec = [modes[1 << 30, gi] for gi in range(len(groups))]
+    assert [m["record_buffers"] for m in rec] == [2, 1, 1, 2], modes
+    assert [m["compact_records"] for m in rec] == [False, True, True, True], modes
+    assert all(m["blocks_per_sm"] == 2 and m["waves"] == 1 for m in rec[2:]), modes
+    assert all(modes[0, gi]["mode"] == "recompute" for gi in range(len(groups))), modes
+    for gi in range(len(groups)):
         a, c = out[1 << 30, gi], out[0, gi]
         for key in a:
             assert np.isfinite(a[key]).all(), key
