@@ -341,8 +341,8 @@ int rod_rollout(rod_handle h, int n_steps, int ckpt_every, float* pos_traj, void
  *  dL_duhat   per-joint intrinsic Darboux vector (x, y, z, 0)
  *  dL_dvel0, dL_dpos0   initial node velocities / positions (xyz, 0)
  *  dL_dquat0  initial frames (x, y, z, w components), dL_domega0 initial body angular velocities
- * Rods of at most 512 nodes; shared memory bounds the constraint iterations (50 for
- * rods of up to 256 nodes, 22 for longer ones).  The material, drive and state set between rod_rollout and
+ * Rods of at most 512 nodes; shared memory bounds the constraint iterations (68 for
+ * rods of up to 256 nodes, 30 for longer ones).  The material, drive and state set between rod_rollout and
  * rod_adjoint must not change.  CORDE_ERR_UNSUPPORTED when the limits are exceeded. */
 int rod_adjoint(rod_handle h, const float* dL_dpos_traj, float* dL_dK, float* dL_duhat, float* dL_dvel0,
                 float* dL_dpos0, float* dL_dquat0, float* dL_domega0, void* stream);
@@ -361,10 +361,10 @@ int rod_adjoint_info(rod_handle h, int* out);
  * segment the reverse pass needs every step's velocities before each constraint
  * half-sweep.
  *  - Record mode (the scratch fits in `bytes`): one forward pass over the segment keeps
- *    them in device memory, 2 n_iters x 16 B per node and step, plus 24 B per node and
+ *    them in device memory, 2 n_iters x 12 B per node and step, plus 24 B per node and
  *    step of neighbour data.  A launch with more rods than the GPU has SMs (or one whose
  *    full records do not fit) keeps the compact layout instead: the velocities before
- *    the first even and every odd half-sweep, (n_iters + 1) x 16 B per node and step;
+ *    the first even and every odd half-sweep, (n_iters + 1) x 12 B per node and step;
  *    its reverse pass repeats each odd half-sweep on its record to get the input of the
  *    next even one.  The reverse pass streams the records back with asynchronous
  *    copies, into two shared-memory buffers (the copy of a step's records overlaps the

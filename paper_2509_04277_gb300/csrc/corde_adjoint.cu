@@ -236,19 +236,19 @@ __device__ __forceinline__ void reverse_step(const RodDev& R, const int t, const
 #pragma unroll 2
     for (int it = R.n_iters - 1; it >= 0; --it) {
       // geometry of this iteration's constraints, from the recorded velocities
-      const float4* so = sweep_v + (COMPACT ? 1 + it : 2 * it + 1) * EPT * NT;  // before the odd half-sweep
+      const int so = COMPACT ? 1 + it : 2 * it + 1;  // record slot before the odd half-sweep
       // the velocities before the even half-sweep: recorded; in the compact layout only for
       // the first iteration, and for a later one the odd half-sweep of the iteration before
       // repeated on its recorded input (the forward's own arithmetic, so the same values)
       float3 ve[EPT];
       {
         // slot 2 it; compact: slot 0, or the record before the previous odd half-sweep
-        const float4* sp = sweep_v + (COMPACT ? it : 2 * it) * EPT * NT;
+        const int sp = COMPACT ? it : 2 * it;
 #pragma unroll
-        for (int e = 0; e < EPT; ++e) ve[e] = f3(sp[e * NT + t]);
+        for (int e = 0; e < EPT; ++e) ve[e] = rec_get<EPT, NT>(sweep_v, sp, e, t);
         if (COMPACT && it > 0) {
-          const float3 vn = t + 1 < NT ? f3(sp[tn]) : zero3();
-          const float3 vp = t > 0 ? f3(sp[(EPT - 1) * NT + tp]) : zero3();
+          const float3 vn = t + 1 < NT ? rec_get<EPT, NT>(sweep_v, sp, 0, tn) : zero3();
+          const float3 vp = t > 0 ? rec_get<EPT, NT>(sweep_v, sp, EPT - 1, tp) : zero3();
           boundary_apply(e_bnd, sc.l_bnd, sc.c_bnd, dt, vn, vp, ve[EPT - 1], ve[0]);
         }
       }
@@ -256,10 +256,13 @@ __device__ __forceinline__ void reverse_step(const RodDev& R, const int t, const
 #pragma unroll
       for (int k = 0; k + 1 < EPT / 2; ++k) {
         const int a = 2 * k + 1, b = 2 * k + 2;
-        g_o[k] = vjp_geo(r[a], f3(so[a * NT + t]), r[b], f3(so[b * NT + t]), inv_o[k], R.l0, dt);
+        g_o[k] = vjp_geo(r[a], rec_get<EPT, NT>(sweep_v, so, a, t), r[b], rec_get<EPT, NT>(sweep_v, so, b, t),
+                         inv_o[k], R.l0, dt);
       }
-      const VjpGeo g_r = vjp_geo(r[EPT - 1], f3(so[(EPT - 1) * NT + t]), nb.r_next, f3(so[tn]), inv_r, R.l0, dt);
-      const VjpGeo g_l = vjp_geo(nb.r_prev, f3(so[(EPT - 1) * NT + tp]), r[0], f3(so[t]), inv_l, R.l0, dt);
+      const VjpGeo g_r = vjp_geo(r[EPT - 1], rec_get<EPT, NT>(sweep_v, so, EPT - 1, t), nb.r_next,
+                                 rec_get<EPT, NT>(sweep_v, so, 0, tn), inv_r, R.l0, dt);
+      const VjpGeo g_l = vjp_geo(nb.r_prev, rec_get<EPT, NT>(sweep_v, so, EPT - 1, tp), r[0],
+                                 rec_get<EPT, NT>(sweep_v, so, 0, t), inv_l, R.l0, dt);
 #pragma unroll
       for (int k = 0; k < NE; ++k) {
         const int a = 2 * k, b = 2 * k + 1;
@@ -402,13 +405,15 @@ adjoint_kernel(AdjointArgs a) {
   constexpr int STORE = COMPACT ? 2 : 1;  // step_body's record layout
   constexpr int NBUF = MODE == 2 ? 2 : 1;
   constexpr int EPT = 2;
+  static_assert((3 * EPT * NT) % 4 == 0, "a record slot is a whole number of 16-byte pieces");
   extern __shared__ float4 smem[];
   float4* par_u = smem;
   float4* par_k = smem + EPT * NT;
   float4* halo = smem + 2 * EPT * NT;
   float4* sweep_v = halo + 2 * kHaloSlots * NT;
-  // float4 per (step, block) record: 1 + n_iters (compact) or 2 n_iters slots of EPT NT
-  const int64_t rec_stride = (int64_t)(COMPACT ? a.rec_iters + 1 : 2 * a.rec_iters) * EPT * NT;
+  // float4 per (step, block) record: 1 + n_iters (compact) or 2 n_iters slots of 3 EPT NT
+  // floats (rec_put)
+  const int64_t rec_stride = (int64_t)(COMPACT ? a.rec_iters + 1 : 2 * a.rec_iters) * 3 * EPT * NT / 4;
 
   const int rid = a.work[blockIdx.x];
   const RodDev R = a.rods[rid];
@@ -457,11 +462,14 @@ adjoint_kernel(AdjointArgs a) {
     };
     auto rec_at = [&](int s) { return a.sweep_rec + ((int64_t)s * gridDim.x + blockIdx.x) * rec_stride; };
     auto nb_at = [&](int s) { return a.nb_rec + (((int64_t)s * gridDim.x + blockIdx.x) * 3) * NT + t; };
-    // copies this thread's entries of step s's record into a shared buffer
+    // copies step s's record into a shared buffer: 16-byte pieces spread over the block
+    // (a barrier orders them before any thread's reads, and the recording pass's stores
+    // before them)
     auto fetch = [&](int s, float4* dst) {
       const float4* src = rec_at(s);
-      const int n_ent = R.n_iters > 0 ? (COMPACT ? R.n_iters + 1 : 2 * R.n_iters) * EPT : 0;
-      for (int k = 0; k < n_ent; ++k) cp_async16(dst + k * NT + t, src + k * NT + t);
+      const int slots = R.n_iters > 0 ? (COMPACT ? R.n_iters + 1 : 2 * R.n_iters) : 0;
+      const int n16 = slots * 3 * EPT * NT / 4;
+      for (int k = t; k < n16; k += NT) cp_async16(dst + k, src + k);
       cp_async_commit();
     };
     if constexpr (RECORD) {
@@ -660,7 +668,7 @@ AdjointFn adjoint_fn(int nt, int mode, bool compact) {
 int adjoint_smem_bytes(int nt, int n_iters, int mode, bool compact) {
   const int ept = 2;
   const int it = n_iters > 0 ? n_iters : 1;
-  const int sweep = (compact ? it + 1 : 2 * it) * ept * nt;  // record slots of one step
+  const int sweep = (compact ? it + 1 : 2 * it) * 3 * ept * nt / 4;  // record slots of one step, in float4
   return (2 * ept * nt + 2 * kHaloSlots * nt + (mode == 2 ? 2 : 1) * sweep) * (int)sizeof(float4);
 }
 

@@ -1449,7 +1449,8 @@ int rod_adjoint(rod_handle h, const float* dL_dpos_traj, float* dL_dK, float* dL
     for (int pass = 0; pass < 2 && mode[i] == 0; ++pass) {
       const bool cpt = pass == 0 ? prefer_compact : true;
       if (pass == 1 && prefer_compact) break;
-      const size_t sw = K * b.count * (cpt ? rec_iters + 1 : 2 * rec_iters) * 2 * nt;
+      // float4 entries: 12 B per node and slot
+      const size_t sw = K * b.count * (cpt ? rec_iters + 1 : 2 * rec_iters) * 3 * 2 * nt / 4;
       if ((long long)((sw + nbn) * sizeof(float4)) > h->adj_record_budget) continue;
       const int smem1 = adjoint_smem_bytes(nt, iters, 1, cpt), smem2 = adjoint_smem_bytes(nt, iters, 2, cpt);
       if (smem1 > smem_max) continue;

@@ -404,11 +404,27 @@ constexpr int step_smem_bytes() {
   return (2 * EPT * NT + 2 * kHaloSlots * NT) * (int)sizeof(float4);
 }
 
+// Velocity records of one step for the adjoint, slot-major and then by component,
+// element and thread ([slots][3][EPT][NT] floats): a thread's vector is three coalesced
+// 32-bit accesses, and a step's record is one contiguous block (12 B per node and slot).
+template <int EPT, int NT>
+__device__ __forceinline__ void rec_put(float4* rec, int slot, int e, int u, float3 v) {
+  float* f = reinterpret_cast<float*>(rec) + (slot * 3 * EPT + e) * NT + u;
+  f[0] = v.x;
+  f[EPT * NT] = v.y;
+  f[2 * EPT * NT] = v.z;
+}
+template <int EPT, int NT>
+__device__ __forceinline__ float3 rec_get(const float4* rec, int slot, int e, int u) {
+  const float* f = reinterpret_cast<const float*>(rec) + (slot * 3 * EPT + e) * NT + u;
+  return f3(f[0], f[EPT * NT], f[2 * EPT * NT]);
+}
+
 // One time step of the rod; H (BlockHalo or ClusterHalo) gives the thread's place in the
 // rod, its neighbours' exchange slots and the barrier; sc holds the launch constants
 // (default-constructed before the first step).  STORE (for the adjoint) writes the
-// neighbour data to *nb and velocities to sweep_v: with STORE == 1 those before every
-// constraint half-sweep ([2 n_iters][EPT][NT], slot 2 it before the even and 2 it + 1
+// neighbour data to *nb and velocities to sweep_v (rec_put): with STORE == 1 those
+// before every constraint half-sweep (2 n_iters slots: 2 it before the even and 2 it + 1
 // before the odd half-sweep of iteration it); with STORE == 2 (compact) those before the
 // first even half-sweep (slot 0) and before every odd one (slot 1 + it), from which the
 // adjoint rebuilds the others.
@@ -605,7 +621,7 @@ __device__ __forceinline__ void step_body(const RodDev& R, const Halo& H, float3
 #pragma unroll
         for (int e = 0; e < EPT; ++e)
           if (STORE == 1 || it == 0)
-            sweep_v[((STORE == 1 ? 2 * it : 0) * EPT + e) * NT + t] = make_float4(v[e].x, v[e].y, v[e].z, 0.f);
+            rec_put<EPT, NT>(sweep_v, STORE == 1 ? 2 * it : 0, e, t, v[e]);
       }
       // even segments (e0 + 2k, e0 + 2k + 1): local to the thread, two per packed op
       if constexpr (StepCache<EPT>::kFold) {
@@ -641,7 +657,7 @@ __device__ __forceinline__ void step_body(const RodDev& R, const Halo& H, float3
       if constexpr (STORE) {
 #pragma unroll
         for (int e = 0; e < EPT; ++e)
-          sweep_v[((STORE == 1 ? 2 * it + 1 : it + 1) * EPT + e) * NT + t] = make_float4(v[e].x, v[e].y, v[e].z, 0.f);
+          rec_put<EPT, NT>(sweep_v, STORE == 1 ? 2 * it + 1 : it + 1, e, t, v[e]);
       }
       // exchange 3: velocities of the first and last element
       hb = halo + (xc & 1) * kHaloSlots * NT;

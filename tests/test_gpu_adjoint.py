@@ -300,7 +300,7 @@ def test_record_and_recompute_modes_give_identical_gradients(corde):
     or, for launches with more rods than SMs and where only that fits, the first even and
     every odd one (compact layout: the reverse pass rebuilds the others, bit for bit).  It
     streams a step's records into two shared buffers, or into one when two do not fit the
-    block (a 300-node rod on 256 threads with 12 iterations) or when one lets more blocks
+    block (a 300-node rod on 256 threads with 16 iterations) or when one lets more blocks
     share an SM and so saves a wave (8 more rods of 150 nodes with 20 iterations than the
     GPU has SMs: one block per SM with two buffers, two with one; with 10 iterations two
     blocks fit with two buffers).  Several rods of ragged lengths and different iteration
@@ -314,7 +314,7 @@ def test_record_and_recompute_modes_give_identical_gradients(corde):
     n_sms = corde.rod_device_info()["n_sms"]
     many = [dataclasses.replace(W.adjoint_rod(150, seed=1200 + k), n_iters=20) for k in range(n_sms + 8)]
     many10 = [W.adjoint_rod(150, seed=1400 + k) for k in range(n_sms + 8)]
-    groups = (rods, [dataclasses.replace(W.adjoint_rod(300, seed=975), n_iters=12)], many, many10)
+    groups = (rods, [dataclasses.replace(W.adjoint_rod(300, seed=975), n_iters=16)], many, many10)
     n_steps, ckpt = 47, 10
     out, modes = {}, {}
     for budget in (1 << 30, 0):
