@@ -472,7 +472,7 @@ def run_adjoint(args, torch, corde, W, n_rods=1):
     # recompute every step before its reverse
     nt = launch_info["threads_per_block"]
     slots = rods[0].n_iters + 1 if launch_info["compact_records"] else 2 * rods[0].n_iters
-    rec_bytes = ckpt * n_rods * (slots * 2 * nt * 12 + 3 * nt * 16)
+    rec_bytes = ckpt * n_rods * slots * 2 * nt * 12
     mode = launch_info["mode"]
     layout = ", compact" if launch_info["compact_records"] else ""
     desc = (f"record mode ({rec_bytes / 2**20:.1f} MiB of sweep records per segment{layout})" if mode == "record"

@@ -361,8 +361,8 @@ int rod_adjoint_info(rod_handle h, int* out);
  * segment the reverse pass needs every step's velocities before each constraint
  * half-sweep.
  *  - Record mode (the scratch fits in `bytes`): one forward pass over the segment keeps
- *    them in device memory, 2 n_iters x 12 B per node and step, plus 24 B per node and
- *    step of neighbour data.  A launch with more rods than the GPU has SMs (or one whose
+ *    them in device memory, 2 n_iters x 12 B per node and step (beside the segment's
+ *    states, 48 B per node and step).  A launch with more rods than the GPU has SMs (or one whose
  *    full records do not fit) keeps the compact layout instead: the velocities before
  *    the first even and every odd half-sweep, (n_iters + 1) x 12 B per node and step;
  *    its reverse pass repeats each odd half-sweep on its record to get the input of the

@@ -454,14 +454,13 @@ adjoint_kernel(AdjointArgs a) {
       for (int e = 0; e < EPT; ++e) {
         if (e0 + e < R.n) {
           st[e0 + e] = make_float4(r[e].x, r[e].y, r[e].z, w[e]);
-          st[E + e0 + e] = make_float4(v[e].x, v[e].y, v[e].z, 0.f);
+          if constexpr (!RECORD) st[E + e0 + e] = make_float4(v[e].x, v[e].y, v[e].z, 0.f);  // record mode reads none
           st[2 * E + e0 + e] = q[e];
           st[3 * E + e0 + e] = make_float4(om[e].x, om[e].y, om[e].z, 0.f);
         }
       }
     };
     auto rec_at = [&](int s) { return a.sweep_rec + ((int64_t)s * gridDim.x + blockIdx.x) * rec_stride; };
-    auto nb_at = [&](int s) { return a.nb_rec + (((int64_t)s * gridDim.x + blockIdx.x) * 3) * NT + t; };
     // copies step s's record into a shared buffer: 16-byte pieces spread over the block
     // (a barrier orders them before any thread's reads, and the recording pass's stores
     // before them)
@@ -478,10 +477,6 @@ adjoint_kernel(AdjointArgs a) {
         put_state(s);
         StepNeighbours nb;
         step_body<EPT, NT, STORE>(R, H, r, v, q, om, w, par_u, par_k, halo, xc, sc, v_drive, w_drive, rec_at(s), &nb);
-        float4* nr = nb_at(s);
-        nr[0] = make_float4(nb.r_next.x, nb.r_next.y, nb.r_next.z, nb.w_next);
-        nr[NT] = make_float4(nb.r_prev.x, nb.r_prev.y, nb.r_prev.z, nb.w_prev);
-        nr[2 * NT] = nb.q_next;
       }
       put_state(cnt);
       fetch(cnt - 1, sweep_v + ((cnt - 1) % NBUF) * rec_stride);
@@ -514,10 +509,12 @@ adjoint_kernel(AdjointArgs a) {
             if (a.dLdpos != nullptr) pg[e] = f3(a.dLdpos[(int64_t)(t0 + s) * E + R.off + e0 + e]);
           }
         }
-        const float4* nr = nb_at(s);
-        pn0 = nr[0];
-        pn1 = nr[NT];
-        pn2 = nr[2 * NT];
+        // the neighbour data of the step: the neighbouring threads' nodes in the same state
+        // (read where the constraint or joint exists; an in-range node elsewhere)
+        const int in = min(e0 + EPT, R.n - 1), ip = min(max(e0 - 1, 0), R.n - 1);
+        pn0 = st[in];
+        pn1 = st[ip];
+        pn2 = st[2 * E + in];
       };
       {
         const float4* sn = a.seg_states + (int64_t)cnt * 4 * E + R.off;

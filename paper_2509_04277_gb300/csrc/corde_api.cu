@@ -164,8 +164,6 @@ struct corde_rods {
   size_t seg_cap = 0;
   float4* d_sweep_rec = nullptr;  // record mode of the reverse pass: sweeps and neighbour data
   size_t sweep_rec_cap = 0;
-  float4* d_nb_rec = nullptr;
-  size_t nb_rec_cap = 0;
   long long adj_record_budget = 1ll << 30;
   int ro_steps = 0, ro_every = 0;
   // last rod_adjoint's largest launch: mode, nt, blocks/SM, blocks, SMs, compact records
@@ -1440,18 +1438,17 @@ int rod_adjoint(rod_handle h, const float* dL_dpos_traj, float* dL_dK, float* dL
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   std::vector<int> mode(h->adj_bins.size(), 0);
   std::vector<char> compact(h->adj_bins.size(), 0);
-  size_t sweep_need = 0, nb_need = 0;
+  size_t sweep_need = 0;
   for (size_t i = 0; i < h->adj_bins.size(); ++i) {
     const Bin& b = h->adj_bins[i];
     const int nt = variants()[b.variant].nt;
-    const size_t nbn = K * b.count * 3 * nt;  // float4 entries
     const bool prefer_compact = b.count > sms;
     for (int pass = 0; pass < 2 && mode[i] == 0; ++pass) {
       const bool cpt = pass == 0 ? prefer_compact : true;
       if (pass == 1 && prefer_compact) break;
       // float4 entries: 12 B per node and slot
       const size_t sw = K * b.count * (cpt ? rec_iters + 1 : 2 * rec_iters) * 3 * 2 * nt / 4;
-      if ((long long)((sw + nbn) * sizeof(float4)) > h->adj_record_budget) continue;
+      if ((long long)(sw * sizeof(float4)) > h->adj_record_budget) continue;
       const int smem1 = adjoint_smem_bytes(nt, iters, 1, cpt), smem2 = adjoint_smem_bytes(nt, iters, 2, cpt);
       if (smem1 > smem_max) continue;
       int m = 1;
@@ -1465,7 +1462,6 @@ int rod_adjoint(rod_handle h, const float* dL_dpos_traj, float* dL_dK, float* dL
       mode[i] = m;
       compact[i] = cpt;
       sweep_need = std::max(sweep_need, sw);
-      nb_need = std::max(nb_need, nbn);
     }
     // recompute mode keeps the step's records in shared memory only: the full layout
     // unless only the compact one fits the block
@@ -1475,7 +1471,6 @@ int rod_adjoint(rod_handle h, const float* dL_dpos_traj, float* dL_dK, float* dL
   if (int rc = ensure_capacity(&h->d_seg, &h->seg_cap, (K + (any_record ? 1 : 0)) * 4 * E)) return rc;
   if (any_record) {
     if (int rc = ensure_capacity(&h->d_sweep_rec, &h->sweep_rec_cap, sweep_need)) return rc;
-    if (int rc = ensure_capacity(&h->d_nb_rec, &h->nb_rec_cap, nb_need)) return rc;
   }
   AdjointArgs a;
   a.rods = h->d_rods;
@@ -1501,7 +1496,6 @@ int rod_adjoint(rod_handle h, const float* dL_dpos_traj, float* dL_dK, float* dL
     const int nt = variants()[b.variant].nt;
     const int smem = adjoint_smem_bytes(nt, iters, mode[i], compact[i] != 0);
     a.sweep_rec = mode[i] ? h->d_sweep_rec : nullptr;
-    a.nb_rec = mode[i] ? h->d_nb_rec : nullptr;
     a.rec_iters = rec_iters;
     if (smem > smem_max)
       return fail(CORDE_ERR_UNSUPPORTED, "adjoint needs " + std::to_string(smem) + " B of shared memory per block; " +
@@ -1755,7 +1749,7 @@ void rod_destroy(rod_handle h) {
   cudaFree(h->d_x); cudaFree(h->d_v); cudaFree(h->d_q); cudaFree(h->d_o); cudaFree(h->d_u); cudaFree(h->d_k);
   cudaFree(h->d_drive); cudaFree(h->d_elem_rod); cudaFree(h->d_drive_graph);
   cudaFree(h->d_ckpt); cudaFree(h->d_seg); cudaFree(h->d_self_stats);
-  cudaFree(h->d_sweep_rec); cudaFree(h->d_nb_rec);
+  cudaFree(h->d_sweep_rec);
   for (auto& b : h->adj_bins) cudaFree(b.d_work);
   for (auto& pb : h->pair_bins) cudaFree(pb.d_pairs);
   if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);

@@ -86,11 +86,11 @@ struct AdjointArgs {
   // Record mode (sweep_rec != NULL): the first pass over a checkpoint segment keeps, per
   // step and block, the velocities before every constraint half-sweep (compact layout:
   // before the first even and every odd one) (sweep_rec[(s gridDim + b) slots 3 EPT NT / 4
-  // ...] float4, 2 rec_iters or rec_iters + 1 slots) and the neighbour data (nb_rec, 3
-  // float4 per thread), and seg_states holds K + 1 states; the reverse pass then reads
-  // them instead of recomputing each step.  NULL: recompute mode.
+  // ...] float4, 2 rec_iters or rec_iters + 1 slots), and seg_states holds K + 1 states
+  // (positions, frames and angular velocities: the neighbour data of each step comes
+  // from them); the reverse pass then reads them instead of recomputing each step.  NULL:
+  // recompute mode.
   float4* sweep_rec = nullptr;
-  float4* nb_rec = nullptr;
   int rec_iters = 0;
 };
 // Reverse-kernel modes: 0 recompute; 1 record, one sweep buffer (the copy of a step's
