@@ -277,12 +277,15 @@ struct Vec3x2 {
   float2 x, y, z;
 };
 __device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+// b - a as one packed fused operation, a (-1) + b: exactly the difference, rounded once
+// (a separate negation would put one more operation on the impulse chain)
+__device__ __forceinline__ float2 sub2(float2 b, float2 a) { return __ffma2_rn(a, make_float2(-1.f, -1.f), b); }
 __device__ __forceinline__ Vec3x2 constraint_impulse2(const Vec3x2& e, const Vec3x2& va, const Vec3x2& vb,
                                                       float2 inv_dtW, float l0, float dt) {
   const float2 dt2 = make_float2(dt, dt);
-  const float2 dx = __ffma2_rn(dt2, __fadd2_rn(vb.x, neg2(va.x)), e.x);
-  const float2 dy = __ffma2_rn(dt2, __fadd2_rn(vb.y, neg2(va.y)), e.y);
-  const float2 dz = __ffma2_rn(dt2, __fadd2_rn(vb.z, neg2(va.z)), e.z);
+  const float2 dx = __ffma2_rn(dt2, sub2(vb.x, va.x), e.x);
+  const float2 dy = __ffma2_rn(dt2, sub2(vb.y, va.y), e.y);
+  const float2 dz = __ffma2_rn(dt2, sub2(vb.z, va.z), e.z);
   const float2 dd = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
   const float2 il = make_float2(rsqrtf(dd.x), rsqrtf(dd.y));
   const float2 sv = __fmul2_rn(__ffma2_rn(make_float2(l0, l0), il, make_float2(-1.f, -1.f)), inv_dtW);
@@ -301,9 +304,9 @@ __device__ __forceinline__ void boundary_apply(const Vec3x2& e_bnd, float2 l_bnd
   const Vec3x2 va{make_float2(v_last.x, vp.x), make_float2(v_last.y, vp.y), make_float2(v_last.z, vp.z)};
   const Vec3x2 vb{make_float2(vn.x, v_first.x), make_float2(vn.y, v_first.y), make_float2(vn.z, v_first.z)};
   const float2 dt2 = make_float2(dt, dt);
-  const float2 dx = __ffma2_rn(dt2, __fadd2_rn(vb.x, neg2(va.x)), e_bnd.x);
-  const float2 dy = __ffma2_rn(dt2, __fadd2_rn(vb.y, neg2(va.y)), e_bnd.y);
-  const float2 dz = __ffma2_rn(dt2, __fadd2_rn(vb.z, neg2(va.z)), e_bnd.z);
+  const float2 dx = __ffma2_rn(dt2, sub2(vb.x, va.x), e_bnd.x);
+  const float2 dy = __ffma2_rn(dt2, sub2(vb.y, va.y), e_bnd.y);
+  const float2 dz = __ffma2_rn(dt2, sub2(vb.z, va.z), e_bnd.z);
   const float2 dd = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
   const float2 il = make_float2(rsqrtf(dd.x), rsqrtf(dd.y));
   const float2 scl = __ffma2_rn(l_bnd, il, neg2(c_bnd));
