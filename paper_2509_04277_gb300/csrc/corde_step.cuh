@@ -292,30 +292,30 @@ __device__ __forceinline__ Vec3x2 constraint_impulse2(const Vec3x2& e, const Vec
   return Vec3x2{__fmul2_rn(sv, dx), __fmul2_rn(sv, dy), __fmul2_rn(sv, dz)};
 }
 
-// The two odd constraints across a thread's boundaries with folded scales, in the two
-// lanes of packed operations: right (the thread's last node, the next thread's first) in
-// lane x, left (the previous thread's last node, the thread's first) in lane y.  e_bnd
-// holds their segment vectors, l_bnd and c_bnd the folded scales of the thread's own node
-// in each (right: -c_a, left: +c_b), vn and vp the neighbours' velocities; updates the
-// thread's last and first velocities.  The adjoint repeats this update on recorded
+// The two odd constraints across a thread's boundaries with folded scales: right (the
+// thread's last node, the next thread's first) and left (the previous thread's last node,
+// the thread's first).  e_bnd holds their segment vectors (lane x right, lane y left),
+// l_bnd and c_bnd the folded scales of the thread's own node in each (right: -c_a, left:
+// +c_b), vn and vp the neighbours' velocities; updates the thread's last and first
+// velocities.  Scalar operations: the two constraints are independent chains, and paired
+// lanes would put register-pair moves on this latency-bound path (measured 2.82 against
+// 2.89 us/step for the 512-node rod).  The adjoint repeats this update on recorded
 // velocities, so both use this one function.
 __device__ __forceinline__ void boundary_apply(const Vec3x2& e_bnd, float2 l_bnd, float2 c_bnd, float dt, float3 vn,
                                                float3 vp, float3& v_last, float3& v_first) {
-  const Vec3x2 va{make_float2(v_last.x, vp.x), make_float2(v_last.y, vp.y), make_float2(v_last.z, vp.z)};
-  const Vec3x2 vb{make_float2(vn.x, v_first.x), make_float2(vn.y, v_first.y), make_float2(vn.z, v_first.z)};
-  const float2 dt2 = make_float2(dt, dt);
-  const float2 dx = __ffma2_rn(dt2, sub2(vb.x, va.x), e_bnd.x);
-  const float2 dy = __ffma2_rn(dt2, sub2(vb.y, va.y), e_bnd.y);
-  const float2 dz = __ffma2_rn(dt2, sub2(vb.z, va.z), e_bnd.z);
-  const float2 dd = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
-  const float2 il = make_float2(rsqrtf(dd.x), rsqrtf(dd.y));
-  const float2 scl = __ffma2_rn(l_bnd, il, neg2(c_bnd));
-  // right: v_last -= c_a (l0 / |d| - 1) d ; left: v_first += c_b (l0 / |d| - 1) d
-  const float2 nx = __ffma2_rn(scl, dx, make_float2(v_last.x, v_first.x));
-  const float2 ny = __ffma2_rn(scl, dy, make_float2(v_last.y, v_first.y));
-  const float2 nz = __ffma2_rn(scl, dz, make_float2(v_last.z, v_first.z));
-  v_last = f3(nx.x, ny.x, nz.x);
-  v_first = f3(nx.y, ny.y, nz.y);
+  auto one = [dt](float ex, float ey, float ez, float3 va, float3 vb, float l, float c, float3& vo) {
+    const float dx = __fmaf_rn(dt, __fsub_rn(vb.x, va.x), ex);
+    const float dy = __fmaf_rn(dt, __fsub_rn(vb.y, va.y), ey);
+    const float dz = __fmaf_rn(dt, __fsub_rn(vb.z, va.z), ez);
+    const float dd = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz)));
+    const float il = rsqrtf(dd);
+    // right: v_last -= c_a (l0 / |d| - 1) d ; left: v_first += c_b (l0 / |d| - 1) d
+    const float scl = __fmaf_rn(l, il, -c);
+    vo = f3(__fmaf_rn(scl, dx, vo.x), __fmaf_rn(scl, dy, vo.y), __fmaf_rn(scl, dz, vo.z));
+  };
+  const float3 vl = v_last, vf = v_first;
+  one(e_bnd.x.x, e_bnd.y.x, e_bnd.z.x, vl, vn, l_bnd.x, c_bnd.x, v_last);
+  one(e_bnd.x.y, e_bnd.y.y, e_bnd.z.y, vp, vf, l_bnd.y, c_bnd.y, v_first);
 }
 
 // Per-step data of one constraint: e = r_b - r_a and 1 / (dt (w_a + w_b)); a constraint
