@@ -65,7 +65,8 @@ struct BlockHalo {
   __device__ __forceinline__ void put3(float4* hb, int slot, float3 a) const {
     float* f = reinterpret_cast<float*>(hb) + 3 * slot * NT;
     if constexpr (PAIR2) {
-      reinterpret_cast<float2*>(f)[t] = make_float2(a.x, a.y);
+      f[2 * t] = a.x;  // two 32-bit stores: no register pair to form on the way to the barrier
+      f[2 * t + 1] = a.y;
       f[2 * NT + t] = a.z;
     } else {
       f[t] = a.x;
