@@ -3,10 +3,11 @@
 //
 // One thread block per rod, two elements per thread (the step kernel's <2, NT> layout).
 // The forward rollout (rod_rollout) stores a checkpoint every K steps.  The reverse
-// kernel walks the segments backwards: it recomputes the K states of a segment into
-// scratch memory, then for each step (last to first) recomputes that step once more with
-// the velocities before every constraint half-sweep kept in shared memory, and applies
-// the transposed Jacobian of the step:
+// kernel walks the segments backwards.  For each segment it runs the K steps forward
+// from the checkpoint, keeping the states and (record mode) the velocities the
+// constraint half-sweeps start from in scratch memory; in recompute mode each step is
+// run once more just before its reverse, its velocity records in shared memory.  Then,
+// for each step (last to first), it applies the transposed Jacobian of the step:
 //   r' = r + dt v2, q' = normalize(q + dt/2 q (x) (0, omega1))       (position update)
 //   v2 = P(r, v1): 2 n_iters half-sweeps of distance impulses          (constraints)
 //   v1 = damp (v + dt (w F + g)), omega1 = damp (omega + dt J^-1 (tau - omega x J omega))
