@@ -436,18 +436,41 @@ struct SelfHook {
       if (!(w[e] > 0.f)) continue;
       float3 acc = zero3();
       float wphi = 0.f;
-      int prev = -1;
-      for (int q = 0; q < k; ++q) {
-        int next = 0x7fffffff;
-        for (int m = 0; m < k; ++m) {
-          const int sl = list()[m * L::NN + i];
-          if (sl > prev && sl < next) next = sl;
+      if (k <= 2) {
+        // one or two pairs: their slots in ascending order without a search
+        const int s0 = list()[i];
+        const int s1 = k == 2 ? list()[L::NN + i] : s0;
+        const int lo = min(s0, s1), hi = max(s0, s1);
+        const float4 a4 = P4[lo];
+        const bool a_first = pa()[lo].x == i;
+        float4 b4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        bool b_first = false;
+        if (k == 2) {
+          b4 = P4[hi];
+          b_first = pa()[hi].x == i;
         }
-        prev = next;
-        const float4 s4 = P4[next];
-        if (pa()[next].x == i) acc -= f3(s4);
-        else acc += f3(s4);
-        wphi += s4.w;
+        if (a_first) acc -= f3(a4);
+        else acc += f3(a4);
+        wphi += a4.w;
+        if (k == 2) {
+          if (b_first) acc -= f3(b4);
+          else acc += f3(b4);
+          wphi += b4.w;
+        }
+      } else {
+        int prev = -1;
+        for (int q = 0; q < k; ++q) {
+          int next = 0x7fffffff;
+          for (int m = 0; m < k; ++m) {
+            const int sl = list()[m * L::NN + i];
+            if (sl > prev && sl < next) next = sl;
+          }
+          prev = next;
+          const float4 s4 = P4[next];
+          if (pa()[next].x == i) acc -= f3(s4);
+          else acc += f3(s4);
+          wphi += s4.w;
+        }
       }
       if (wphi > 0.f) v[e] += __fdividef(w[e], wphi) * acc;
     }
