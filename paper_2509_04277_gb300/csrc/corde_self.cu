@@ -289,15 +289,24 @@ struct SelfHook {
       if (use_skin) {
         // the listed partners at the plain reach (ascending, as the full detection finds them)
         const int k = skin_cnt()[i];
-        for (int m = 0; m < k; ++m) {
-          const int j = skin()[m * L::NN + i];
-          const float4 rj = R4[j];
-          const float dx = rj.x - ri.x, dy = rj.y - ri.y, dz = rj.z - ri.z;
-          const float d2 = dx * dx + dy * dy + dz * dz;
-          if (d2 < dist2) ++touching;
-          if (d2 < reach2) {
-            if (c < kSelfMaxCand) list()[c * L::NN + i] = (unsigned short)j;
-            ++c;
+        // four partners at a time: their loads issued together
+        for (int m0 = 0; m0 < k; m0 += 4) {
+          int jj[4];
+          float4 rj[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) jj[u] = skin()[min(m0 + u, k - 1) * L::NN + i];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) rj[u] = R4[jj[u]];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if (m0 + u >= k) break;
+            const float dx = rj[u].x - ri.x, dy = rj[u].y - ri.y, dz = rj[u].z - ri.z;
+            const float d2 = dx * dx + dy * dy + dz * dz;
+            if (d2 < dist2) ++touching;
+            if (d2 < reach2) {
+              if (c < kSelfMaxCand) list()[c * L::NN + i] = (unsigned short)jj[u];
+              ++c;
+            }
           }
         }
       } else {
@@ -419,8 +428,8 @@ struct SelfHook {
       const float3 J = (phi * __fdividef(1.f, ri.w + rj.w)) * (dun * nrm - cut * ut);  // approximate reciprocal: ~2 ulp
       P4[p] = make_float4(J.x, J.y, J.z, phi);
       const int ka = atomicAdd(&nact()[ij.x], 1);
-      if (ka < kSelfMaxCand) list()[ka * L::NN + ij.x] = (unsigned short)p;
       const int kb = atomicAdd(&nact()[ij.y], 1);
+      if (ka < kSelfMaxCand) list()[ka * L::NN + ij.x] = (unsigned short)p;
       if (kb < kSelfMaxCand) list()[kb * L::NN + ij.y] = (unsigned short)p;
       if (ka >= kSelfMaxCand || kb >= kSelfMaxCand) atomicOr(&stat()[3], 4);
     }
