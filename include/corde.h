@@ -286,9 +286,10 @@ int rod_set_graph_mode(rod_handle h, int mode);
  *                       rod_mailbox_enable first.
  *  rod_mailbox_positions  consistent copy of rod `rod`'s latest snapshot: out [N][4]
  *                       floats (x, y, z, inverse mass), *step the global step it was
- *                       taken after (-1: none yet).  Host-only and non-blocking for the
- *                       device; a copy during which the count advanced by 3 or more is
- *                       retried, CORDE_ERR_BUSY after 10000 tries.
+ *                       taken after (-1: none yet); out NULL: *step only, nothing copied
+ *                       (a cheap poll).  Host-only and non-blocking for the device; a
+ *                       copy during which the count advanced by 3 or more is retried,
+ *                       CORDE_ERR_BUSY after 10000 tries.
  * With the mailbox enabled rod_step launches directly (no graph).  rod_steps_done: steps
  * taken by rod_step on this handle (the log's step index). */
 int rod_mailbox_enable(rod_handle h, int period, int log_capacity);

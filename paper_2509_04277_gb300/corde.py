@@ -299,9 +299,11 @@ def rod_mailbox_positions_enable(h, enable=True):
 
 def rod_mailbox_positions(h, rod, out):
     """Latest consistent position snapshot of rod `rod` into out ([N, 4] float32 host
-    array); returns the global step it was taken after (-1: none yet)."""
+    array; None: nothing is copied); returns the global step it was taken after (-1:
+    none yet)."""
     step = ctypes.c_longlong(0)
-    _check(load().rod_mailbox_positions(h, int(rod), _ptr(out), ctypes.addressof(step)), "rod_mailbox_positions")
+    _check(load().rod_mailbox_positions(h, int(rod), None if out is None else _ptr(out), ctypes.addressof(step)),
+           "rod_mailbox_positions")
     return int(step.value)
 
 

@@ -1607,7 +1607,7 @@ int rod_mailbox_positions_enable(rod_handle h, int enable) {
 }
 
 int rod_mailbox_positions(rod_handle h, int rod, float* out, long long* step) {
-  if (!h || !out || !step) return fail(CORDE_ERR_ARG, "rod_mailbox_positions: NULL argument");
+  if (!h || !step) return fail(CORDE_ERR_ARG, "rod_mailbox_positions: NULL argument");
   if (!h->mb_pos_host) return fail(CORDE_ERR_ARG, "rod_mailbox_positions: position snapshots not enabled");
   if (rod < 0 || rod >= h->n_rods) return fail(CORDE_ERR_ARG, "rod_mailbox_positions: bad rod");
   const unsigned* hdr = static_cast<const unsigned*>(h->mb_pos_host) + 32 * (size_t)rod;
@@ -1627,7 +1627,7 @@ int rod_mailbox_positions(rod_handle h, int rod, float* out, long long* step) {
     const unsigned lo = __atomic_load_n(&sh[1], __ATOMIC_RELAXED), hi = __atomic_load_n(&sh[2], __ATOMIC_RELAXED);
     const float* src = reinterpret_cast<const float*>(static_cast<const char*>(h->mb_pos_host) + hbytes) +
                        4 * ((size_t)(p % kPosSlots) * h->n_elem + h->off[rod]);
-    std::memcpy(out, src, nf * sizeof(float));
+    if (out) std::memcpy(out, src, nf * sizeof(float));  // out NULL: the step only
     __atomic_thread_fence(__ATOMIC_SEQ_CST);
     if (__atomic_load_n(&hdr[0], __ATOMIC_RELAXED) - pubs <= (unsigned)(kPosSlots - 2)) {
       *step = (long long)(((unsigned long long)hi << 32) | lo);

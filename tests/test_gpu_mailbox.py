@@ -119,6 +119,7 @@ def test_mailbox_position_snapshots_are_whole_steps(corde, n):
     corde.rod_mailbox_positions_enable(a.handle)
     out = np.zeros((n, 4), np.float32)
     assert corde.rod_mailbox_positions(a.handle, 0, out) == -1
+    assert corde.rod_mailbox_positions(a.handle, 0, None) == -1  # the step only
     a.step(20000)  # asynchronous: the host pulls snapshots while it runs
     steps, seen = [], 0
     t0 = time.time()
@@ -138,6 +139,7 @@ def test_mailbox_position_snapshots_are_whole_steps(corde, n):
     assert seen >= 3
     s = corde.rod_mailbox_positions(a.handle, 0, out)
     assert s == 20000
+    assert corde.rod_mailbox_positions(a.handle, 0, None) == 20000
     np.testing.assert_array_equal(out, a.state_numpy()["pos4"])
     corde.rod_mailbox_disable(a.handle)
     a.close()
