@@ -616,7 +616,6 @@ __device__ __forceinline__ void step_body(const RodDev& R, const Halo& H, float3
     const float inv_dt = 1.f / dt;
     // the two boundary constraints, right in lane x and left in lane y
     const Vec3x2 e_bnd{make_float2(e_r.x, e_l.x), make_float2(e_r.y, e_l.y), make_float2(e_r.z, e_l.z)};
-    const float2 i_bnd = make_float2(sc.i_right, sc.i_left);
     const float2 w_bnd = make_float2(-w[EPT - 1], w[0]);
 
     // one iteration; tube_on (a compile-time bool) adds the vessel contact
@@ -679,23 +678,18 @@ __device__ __forceinline__ void step_body(const RodDev& R, const Halo& H, float3
         v[b] += w[b] * g;
       }
       H.wait();
-      // odd segments across the two thread boundaries, in one packed evaluation
+      // odd segments across the two thread boundaries (two independent scalar chains)
       {
         const float3 vn = has_next ? H.next3(hb, 0) : zero3();
         const float3 vp = has_prev ? H.prev3(hb, 1) : zero3();
         if constexpr (StepCache<EPT>::kFold) {
           boundary_apply(e_bnd, sc.l_bnd, sc.c_bnd, dt, vn, vp, v[EPT - 1], v[0]);
         } else {
-          const Vec3x2 va{make_float2(v[EPT - 1].x, vp.x), make_float2(v[EPT - 1].y, vp.y),
-                          make_float2(v[EPT - 1].z, vp.z)};
-          const Vec3x2 vb{make_float2(vn.x, v[0].x), make_float2(vn.y, v[0].y), make_float2(vn.z, v[0].z)};
-          const Vec3x2 g = constraint_impulse2(e_bnd, va, vb, i_bnd, R.l0, dt);
-          // right: v_last -= w_last g.x ; left: v_first += w_first g.y
-          const float2 nx = __ffma2_rn(w_bnd, g.x, make_float2(v[EPT - 1].x, v[0].x));
-          const float2 ny = __ffma2_rn(w_bnd, g.y, make_float2(v[EPT - 1].y, v[0].y));
-          const float2 nz = __ffma2_rn(w_bnd, g.z, make_float2(v[EPT - 1].z, v[0].z));
-          v[EPT - 1] = f3(nx.x, ny.x, nz.x);
-          v[0] = f3(nx.y, ny.y, nz.y);
+          const float3 gr = constraint_impulse(e_r, v[EPT - 1], vn, sc.i_right, R.l0, dt);
+          const float3 gl = constraint_impulse(e_l, vp, v[0], sc.i_left, R.l0, dt);
+          v[EPT - 1] = f3(__fmaf_rn(w_bnd.x, gr.x, v[EPT - 1].x), __fmaf_rn(w_bnd.x, gr.y, v[EPT - 1].y),
+                          __fmaf_rn(w_bnd.x, gr.z, v[EPT - 1].z));
+          v[0] = f3(__fmaf_rn(w_bnd.y, gl.x, v[0].x), __fmaf_rn(w_bnd.y, gl.y, v[0].y), __fmaf_rn(w_bnd.y, gl.z, v[0].z));
         }
       }
       // collision response (analytic vessel), per node
