@@ -348,14 +348,15 @@ int rod_rollout(rod_handle h, int n_steps, int ckpt_every, float* pos_traj, void
 int rod_adjoint(rod_handle h, const float* dL_dpos_traj, float* dL_dK, float* dL_duhat, float* dL_dvel0,
                 float* dL_dpos0, float* dL_dquat0, float* dL_domega0, void* stream);
 
-/* How the last rod_adjoint ran its largest launch, into 6 host ints: the mode (0
+/* How the last rod_adjoint ran its largest launch, into 7 host ints: the mode (0
  * recompute; 1 record mode with one sweep buffer in shared memory; 2 record mode with
  * two, the copy of a step's records overlapping the reverse of the step after it),
  * threads per block, resident blocks per SM (occupancy API, with the launch's registers
- * and shared memory), blocks of the launch (one per rod), the device's SMs, and 1 when
- * the records use the compact layout (see rod_set_adjoint_record_budget);
- * blocks / (blocks per SM x SMs), rounded up, is the number of waves.
- * Host-side only (zeros before the first rod_adjoint). */
+ * and shared memory; 1 when pipelined), blocks of the launch (one per rod, two when
+ * pipelined), the device's SMs, 1 when the records use the compact layout (see
+ * rod_set_adjoint_record_budget), and 1 when the reverse pass was pipelined (see
+ * rod_set_adjoint_pipeline); blocks / (blocks per SM x SMs), rounded up, is the number
+ * of waves.  Host-side only (zeros before the first rod_adjoint). */
 int rod_adjoint_info(rod_handle h, int* out);
 
 /* Scratch budget of rod_adjoint's record mode (default 1 GiB).  Within a checkpoint
@@ -376,6 +377,16 @@ int rod_adjoint_info(rod_handle h, int* out);
  * All modes give the same gradients bit for bit.  bytes >= 0 (CORDE_ERR_ARG otherwise).
  * Host-side only. */
 int rod_set_adjoint_record_budget(rod_handle h, long long bytes);
+
+/* Pipelined reverse pass (enable != 0, the default).  A record-mode launch with the full
+ * layout and two sweep buffers whose rods each find two free SMs (2 x rods <= SMs) runs
+ * every rod on a cluster of two blocks: the first block records the checkpoint segments
+ * (last first), the second reverses each one a segment later, so that recording and
+ * reversing overlap; one cluster barrier per segment hands a segment's scratch over.  It
+ * takes twice the record scratch (segment states and records in two sets, by segment
+ * parity), within the record budget.  The gradients are the same bit for bit.  Host-side
+ * only. */
+int rod_set_adjoint_pipeline(rod_handle h, int enable);
 
 /* Gradient of one rod's rollout without any device allocation.  The paper has no
  * counterpart: this entry point exists for callers that cannot call cudaMalloc where

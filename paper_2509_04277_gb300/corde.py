@@ -63,6 +63,7 @@ SIGNATURES = {
     "rod_set_plan": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
     "rod_set_launch_overlap": (ctypes.c_int, [_VP, ctypes.c_int]),
     "rod_set_adjoint_record_budget": (ctypes.c_int, [_VP, ctypes.c_longlong]),
+    "rod_set_adjoint_pipeline": (ctypes.c_int, [_VP, ctypes.c_int]),
     "rod_adjoint_info": (ctypes.c_int, [_VP, _VP]),
     "rod_set_plan_cluster": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "rod_set_plan_grid": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
@@ -232,6 +233,11 @@ def rod_set_adjoint_record_budget(h, n_bytes):
     _check(load().rod_set_adjoint_record_budget(h, int(n_bytes)), "rod_set_adjoint_record_budget")
 
 
+def rod_set_adjoint_pipeline(h, enable=True):
+    """Pipelined reverse pass (a cluster of two blocks per rod) where it applies."""
+    _check(load().rod_set_adjoint_pipeline(h, 1 if enable else 0), "rod_set_adjoint_pipeline")
+
+
 def rod_set_launch_overlap(h, enable):
     _check(load().rod_set_launch_overlap(h, int(enable)), "rod_set_launch_overlap")
 
@@ -353,11 +359,11 @@ def rod_adjoint(h, dL_dpos_traj=None, dL_dK=None, dL_duhat=None, dL_dvel0=None, 
 def rod_adjoint_info(h) -> dict:
     """How the last rod_adjoint ran its largest launch (mode, record buffers and layout,
     threads, blocks per SM, blocks, SMs)."""
-    out = np.zeros(6, dtype=np.int32)
+    out = np.zeros(7, dtype=np.int32)
     _check(load().rod_adjoint_info(h, out.ctypes.data), "rod_adjoint_info")
     per_sm, blocks, sms = int(out[2]), int(out[3]), int(out[4])
     return {"mode": "record" if out[0] else "recompute", "record_buffers": int(out[0]),
-            "compact_records": bool(out[5]), "threads_per_block": int(out[1]),
+            "compact_records": bool(out[5]), "pipelined": bool(out[6]), "threads_per_block": int(out[1]),
             "blocks_per_sm": per_sm, "blocks": blocks, "sms": sms,
             "waves": -(-blocks // (per_sm * sms)) if per_sm * sms > 0 else None}
 
@@ -537,6 +543,9 @@ class RodBatch:
 
     def set_adjoint_record_budget(self, n_bytes: int):
         rod_set_adjoint_record_budget(self.handle, n_bytes)
+
+    def set_adjoint_pipeline(self, enable: bool):
+        rod_set_adjoint_pipeline(self.handle, enable)
 
     def set_launch_overlap(self, enable: bool):
         rod_set_launch_overlap(self.handle, 1 if enable else 0)

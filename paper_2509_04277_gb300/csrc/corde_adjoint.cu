@@ -398,10 +398,15 @@ __device__ __forceinline__ void reverse_step(const RodDev& R, const int t, const
 // Reverse pass over the whole rollout of one rod per block.  MODE 0: recompute every
 // step before its reverse; 1: record mode with one sweep buffer (a step's records are
 // copied in after the step before it is reversed); 2: record mode with two buffers (the
-// copy overlaps the reverse of the step before).
-template <int NT, int MODE, bool COMPACT>
+// copy overlaps the reverse of the step before).  PIPE (record mode, two buffers, full
+// layout): each rod has a cluster of two blocks; the first records the segments, the
+// second reverses them one segment behind, so that the recording of segment k - 1 runs
+// while segment k is reversed (segment scratch in two sets, by segment parity; one
+// cluster barrier per segment).
+template <int NT, int MODE, bool COMPACT, bool PIPE = false>
 __global__ void __launch_bounds__(NT)
 adjoint_kernel(AdjointArgs a) {
+  static_assert(!PIPE || (MODE == 2 && !COMPACT), "the pipelined form records the full layout");
   constexpr bool RECORD = MODE > 0;
   constexpr int STORE = COMPACT ? 2 : 1;  // step_body's record layout
   constexpr int NBUF = MODE == 2 ? 2 : 1;
@@ -416,7 +421,10 @@ adjoint_kernel(AdjointArgs a) {
   // floats (rec_put)
   const int64_t rec_stride = (int64_t)(COMPACT ? a.rec_iters + 1 : 2 * a.rec_iters) * 3 * EPT * NT / 4;
 
-  const int rid = a.work[blockIdx.x];
+  const int rod_slot = PIPE ? (int)blockIdx.x / 2 : (int)blockIdx.x;  // the rod's place in the launch
+  const int n_slots = PIPE ? (int)gridDim.x / 2 : (int)gridDim.x;
+  const int role = PIPE ? (int)(blockIdx.x & 1) : 0;  // PIPE: 0 records, 1 reverses (the cluster rank)
+  const int rid = a.work[rod_slot];
   const RodDev R = a.rods[rid];
   const int t = threadIdx.x;
   const int e0 = t * EPT;
@@ -442,90 +450,127 @@ adjoint_kernel(AdjointArgs a) {
   StepCache<EPT> sc;  // launch constants of the step (filled on the first step)
   const int n_seg = (a.n_steps + a.ckpt_every - 1) / a.ckpt_every;
   bool params_loaded = false;
-  for (int seg = n_seg - 1; seg >= 0; --seg) {
-    const int t0 = seg * a.ckpt_every;
-    const int cnt = min(a.ckpt_every, a.n_steps - t0);
-    const float4* ck = a.ckpt + (int64_t)seg * 4 * E;
-    load_rod<EPT, NT>(R, t, t, ck, ck + E, ck + 2 * E, ck + 3 * E, a.u4, a.k4, r, v, q, om, w,
-                      params_loaded ? nullptr : par_u, par_k);
-    params_loaded = true;
-    auto put_state = [&](int s) {
-      float4* st = a.seg_states + (int64_t)s * 4 * E + R.off;
+  // segment scratch: states 0 .. K and the velocity records of segment seg (two sets by
+  // segment parity with PIPE)
+  auto seg_base = [&](int seg) {
+    return a.seg_states + (PIPE ? (int64_t)(seg & 1) * (a.ckpt_every + 1) * 4 * E : (int64_t)0);
+  };
+  auto rec_at = [&](int seg, int s) {
+    return a.sweep_rec + ((int64_t)(PIPE ? (seg & 1) * a.ckpt_every : 0) + s) * n_slots * rec_stride +
+           (int64_t)rod_slot * rec_stride;
+  };
+  // copies step s's record into a shared buffer: 16-byte pieces spread over the block
+  // (a barrier orders them before any thread's reads; a block or cluster barrier orders
+  // the recording pass's stores before them)
+  auto fetch = [&](int seg, int s, float4* dst) {
+    const float4* src = rec_at(seg, s);
+    const int slots = R.n_iters > 0 ? (COMPACT ? R.n_iters + 1 : 2 * R.n_iters) : 0;
+    const int n16 = slots * 3 * EPT * NT / 4;
+    for (int k = t; k < n16; k += NT) cp_async16(dst + k, src + k);
+    cp_async_commit();
+  };
+  // rounds: without PIPE round j records (or recomputes) segment n_seg - 1 - j and then
+  // reverses it; with PIPE round j records segment n_seg - 1 - j (first block) while the
+  // second block reverses segment n_seg - j
+  const int n_round = PIPE ? n_seg + 1 : n_seg;
+  for (int j = 0; j < n_round; ++j) {
+    const int rec_seg = n_seg - 1 - j;
+    const int rev_seg = PIPE ? n_seg - j : rec_seg;
+    const bool do_rec = rec_seg >= 0 && role == 0;
+    const bool do_rev = rev_seg >= 0 && rev_seg < n_seg && (!PIPE || role == 1);
+    if (do_rec || !params_loaded) {
+      // the recording (or recomputing) block loads the segment's checkpoint; a reversing
+      // block only the inverse masses and joint parameters, once
+      const int ls = do_rec ? rec_seg : n_seg - 1;
+      const float4* ck = a.ckpt + (int64_t)ls * 4 * E;
+      load_rod<EPT, NT>(R, t, t, ck, ck + E, ck + 2 * E, ck + 3 * E, a.u4, a.k4, r, v, q, om, w,
+                        params_loaded ? nullptr : par_u, par_k);
+      params_loaded = true;
+    }
+    if (do_rec) {
+      const int cnt = min(a.ckpt_every, a.n_steps - rec_seg * a.ckpt_every);
+      auto put_state = [&](int s) {
+        float4* st = seg_base(rec_seg) + (int64_t)s * 4 * E + R.off;
 #pragma unroll
-      for (int e = 0; e < EPT; ++e) {
-        if (e0 + e < R.n) {
-          st[e0 + e] = make_float4(r[e].x, r[e].y, r[e].z, w[e]);
-          if constexpr (!RECORD) st[E + e0 + e] = make_float4(v[e].x, v[e].y, v[e].z, 0.f);  // record mode reads none
-          st[2 * E + e0 + e] = q[e];
-          st[3 * E + e0 + e] = make_float4(om[e].x, om[e].y, om[e].z, 0.f);
+        for (int e = 0; e < EPT; ++e) {
+          if (e0 + e < R.n) {
+            st[e0 + e] = make_float4(r[e].x, r[e].y, r[e].z, w[e]);
+            if constexpr (!RECORD) st[E + e0 + e] = make_float4(v[e].x, v[e].y, v[e].z, 0.f);  // record mode reads none
+            st[2 * E + e0 + e] = q[e];
+            st[3 * E + e0 + e] = make_float4(om[e].x, om[e].y, om[e].z, 0.f);
+          }
+        }
+      };
+      if constexpr (RECORD) {
+        // forward over the segment, keeping states 0 .. cnt and the velocity records
+        for (int s = 0; s < cnt; ++s) {
+          put_state(s);
+          StepNeighbours nb;
+          step_body<EPT, NT, STORE>(R, H, r, v, q, om, w, par_u, par_k, halo, xc, sc, v_drive, w_drive,
+                                    rec_at(rec_seg, s), &nb);
+        }
+        put_state(cnt);
+      } else {
+        // recompute the segment's states into scratch
+        for (int s = 0; s < cnt; ++s) {
+          put_state(s);
+          if (s + 1 < cnt)
+            step_body<EPT, NT, 0>(R, H, r, v, q, om, w, par_u, par_k, halo, xc, sc, v_drive, w_drive, nullptr,
+                                  nullptr);
         }
       }
-    };
-    auto rec_at = [&](int s) { return a.sweep_rec + ((int64_t)s * gridDim.x + blockIdx.x) * rec_stride; };
-    // copies step s's record into a shared buffer: 16-byte pieces spread over the block
-    // (a barrier orders them before any thread's reads, and the recording pass's stores
-    // before them)
-    auto fetch = [&](int s, float4* dst) {
-      const float4* src = rec_at(s);
-      const int slots = R.n_iters > 0 ? (COMPACT ? R.n_iters + 1 : 2 * R.n_iters) : 0;
-      const int n16 = slots * 3 * EPT * NT / 4;
-      for (int k = t; k < n16; k += NT) cp_async16(dst + k, src + k);
-      cp_async_commit();
-    };
+    }
+    if (!do_rev) {
+      if constexpr (PIPE) cooperative_groups::this_cluster().sync();
+      continue;
+    }
+    const int seg = rev_seg;
+    const int t0 = seg * a.ckpt_every;
+    const int cnt = min(a.ckpt_every, a.n_steps - t0);
     if constexpr (RECORD) {
-      // forward over the segment, keeping states 0 .. cnt, sweeps and neighbour data
-      for (int s = 0; s < cnt; ++s) {
-        put_state(s);
-        StepNeighbours nb;
-        step_body<EPT, NT, STORE>(R, H, r, v, q, om, w, par_u, par_k, halo, xc, sc, v_drive, w_drive, rec_at(s), &nb);
-      }
-      put_state(cnt);
-      fetch(cnt - 1, sweep_v + ((cnt - 1) % NBUF) * rec_stride);
-    } else {
-      // recompute the segment's states into scratch
-      for (int s = 0; s < cnt; ++s) {
-        put_state(s);
-        if (s + 1 < cnt)
-          step_body<EPT, NT, 0>(R, H, r, v, q, om, w, par_u, par_k, halo, xc, sc, v_drive, w_drive, nullptr, nullptr);
-      }
+      // the recording pass's stores are visible here: a block barrier follows each step's
+      // records within step_body, or (PIPE) the cluster barrier ended the round that wrote
+      // them
+      fetch(seg, cnt - 1, sweep_v + ((cnt - 1) % NBUF) * rec_stride);
     }
     // reverse the segment's steps
     if constexpr (RECORD) {
       // Each step's inputs are loaded one step ahead, while the step before is reversed:
       // the state before it, its neighbour data and the loss gradient after it.  The frame
-      // and angular velocity after step s are the state before step s + 1.
+      // and angular velocity after step s are the state before step s + 1.  The segment
+      // states are read from L2 (ld.cg): with PIPE another SM wrote them.
       float3 pr[EPT], pom[EPT], pg[EPT];
       float4 pq[EPT], pn0, pn1, pn2;
       float4 nq[EPT];
       float3 nom[EPT];
       auto prefetch = [&](int s) {
-        const float4* st = a.seg_states + (int64_t)s * 4 * E + R.off;
+        const float4* st = seg_base(seg) + (int64_t)s * 4 * E + R.off;
 #pragma unroll
         for (int e = 0; e < EPT; ++e) {
           pg[e] = zero3();
           if (e0 + e < R.n) {
-            pr[e] = f3(st[e0 + e]);
-            pq[e] = st[2 * E + e0 + e];
-            pom[e] = f3(st[3 * E + e0 + e]);
+            pr[e] = f3(__ldcg(st + e0 + e));
+            pq[e] = __ldcg(st + 2 * E + e0 + e);
+            pom[e] = f3(__ldcg(st + 3 * E + e0 + e));
             if (a.dLdpos != nullptr) pg[e] = f3(a.dLdpos[(int64_t)(t0 + s) * E + R.off + e0 + e]);
           }
         }
         // the neighbour data of the step: the neighbouring threads' nodes in the same state
         // (read where the constraint or joint exists; an in-range node elsewhere)
         const int in = min(e0 + EPT, R.n - 1), ip = min(max(e0 - 1, 0), R.n - 1);
-        pn0 = st[in];
-        pn1 = st[ip];
-        pn2 = st[2 * E + in];
+        pn0 = __ldcg(st + in);
+        pn1 = __ldcg(st + ip);
+        pn2 = __ldcg(st + 2 * E + in);
       };
       {
-        const float4* sn = a.seg_states + (int64_t)cnt * 4 * E + R.off;
+        const float4* sn = seg_base(seg) + (int64_t)cnt * 4 * E + R.off;
 #pragma unroll
         for (int e = 0; e < EPT; ++e) {
           nq[e] = q[e];
           nom[e] = om[e];
           if (e0 + e < R.n) {
-            nq[e] = sn[2 * E + e0 + e];
-            nom[e] = f3(sn[3 * E + e0 + e]);
+            nq[e] = __ldcg(sn + 2 * E + e0 + e);
+            nom[e] = f3(__ldcg(sn + 3 * E + e0 + e));
           }
         }
       }
@@ -563,7 +608,7 @@ adjoint_kernel(AdjointArgs a) {
         cp_async_wait_all();
         block_sync<NT>();
         if (s > 0) {
-          if constexpr (NBUF == 2) fetch(s - 1, sweep_v + ((s - 1) & 1) * rec_stride);
+          if constexpr (NBUF == 2) fetch(seg, s - 1, sweep_v + ((s - 1) & 1) * rec_stride);
           prefetch(s - 1);
         }
         reverse_step<EPT, NT, COMPACT>(R, t, r_in, q_in, om_in, w, om, q, nb, par_u, par_k, halo, xc,
@@ -571,7 +616,7 @@ adjoint_kernel(AdjointArgs a) {
         if constexpr (NBUF == 1) {
           if (s > 0) {
             block_sync<NT>();
-            fetch(s - 1, sweep_v);
+            fetch(seg, s - 1, sweep_v);
           }
         }
       }
@@ -580,7 +625,7 @@ adjoint_kernel(AdjointArgs a) {
       float3 pr[EPT], pv[EPT], pom[EPT], pg[EPT];
       float4 pq[EPT];
       auto prefetch = [&](int s) {
-        const float4* st = a.seg_states + (int64_t)s * 4 * E + R.off;
+        const float4* st = seg_base(seg) + (int64_t)s * 4 * E + R.off;
 #pragma unroll
         for (int e = 0; e < EPT; ++e) {
           pg[e] = zero3();
@@ -623,7 +668,9 @@ adjoint_kernel(AdjointArgs a) {
                                        rb, vb, qb, ob, Kb, ub);
       }
     }
+    if constexpr (PIPE) cooperative_groups::this_cluster().sync();  // end of the round
   }
+  if (PIPE && role == 0) return;  // the recording block holds no gradients
 #pragma unroll
   for (int e = 0; e < EPT; ++e) {
     const int i = e0 + e;
@@ -657,6 +704,17 @@ AdjointFn adjoint_fn(int nt, int mode, bool compact) {
     case 64: return adjoint_fn_nt<64>(mode, compact);
     case 128: return adjoint_fn_nt<128>(mode, compact);
     case 256: return adjoint_fn_nt<256>(mode, compact);
+    default: return nullptr;
+  }
+}
+
+// The pipelined reverse kernel (record mode, two buffers, full layout) of `nt` threads.
+AdjointFn adjoint_pipe_fn(int nt) {
+  switch (nt) {
+    case 32: return adjoint_kernel<32, 2, false, true>;
+    case 64: return adjoint_kernel<64, 2, false, true>;
+    case 128: return adjoint_kernel<128, 2, false, true>;
+    case 256: return adjoint_kernel<256, 2, false, true>;
     default: return nullptr;
   }
 }
@@ -698,6 +756,27 @@ cudaError_t launch_adjoint(int nt, int mode, bool compact, const AdjointArgs& a,
   if (e != cudaSuccess) return e;
   fn<<<n_blocks, nt, smem, s>>>(a);
   return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_pipe(int nt, const AdjointArgs& a, int n_rods, int smem, cudaStream_t s) {
+  if (a.sweep_rec == nullptr) return cudaErrorInvalidValue;
+  const AdjointFn fn = adjoint_pipe_fn(nt);
+  if (fn == nullptr) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2 * n_rods);
+  cfg.blockDim = dim3(nt);
+  cfg.dynamicSmemBytes = (size_t)smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, fn, a);
 }
 
 }  // namespace corde

@@ -166,8 +166,10 @@ struct corde_rods {
   size_t sweep_rec_cap = 0;
   long long adj_record_budget = 1ll << 30;
   int ro_steps = 0, ro_every = 0;
-  // last rod_adjoint's largest launch: mode, nt, blocks/SM, blocks, SMs, compact records
-  int adj_info[6] = {0, 0, 0, 0, 0, 0};
+  // last rod_adjoint's largest launch: mode, nt, blocks/SM, blocks, SMs, compact records,
+  // pipelined
+  int adj_info[7] = {0, 0, 0, 0, 0, 0, 0};
+  int adj_pipe = 1;  // pipelined reverse where it applies (rod_set_adjoint_pipeline)
   std::vector<Bin> adj_bins;  // variant = threads per block
   // catheter/guidewire pairs
   std::vector<int4> pairs;     // (outer, inner, mode, 0)
@@ -962,6 +964,12 @@ int rod_set_plan_grid(rod_handle h, int ept, int nt, int blocks) {
   return build_bins(h);
 }
 
+int rod_set_adjoint_pipeline(rod_handle h, int enable) {
+  if (int rc = check_handle(h)) return rc;
+  h->adj_pipe = enable ? 1 : 0;
+  return CORDE_OK;
+}
+
 int rod_set_adjoint_record_budget(rod_handle h, long long bytes) {
   if (int rc = check_handle(h)) return rc;
   if (bytes < 0) return fail(CORDE_ERR_ARG, "rod_set_adjoint_record_budget: bytes must be >= 0");
@@ -1423,6 +1431,8 @@ int rod_adjoint(rod_handle h, const float* dL_dpos_traj, float* dL_dK, float* dL
   int dev = 0, smem_max = 0;
   CK(cudaGetDevice(&dev));
   CK(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  int smem_sm = 0;
+  CK(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
   int iters = 0;
   for (int r = 0; r < h->n_rods; ++r) iters = std::max(iters, h->n_iters[r]);
   const int rec_iters = iters > 0 ? iters : 1;
@@ -1438,6 +1448,7 @@ int rod_adjoint(rod_handle h, const float* dL_dpos_traj, float* dL_dK, float* dL
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   std::vector<int> mode(h->adj_bins.size(), 0);
   std::vector<char> compact(h->adj_bins.size(), 0);
+  std::vector<char> pipe(h->adj_bins.size(), 0);
   size_t sweep_need = 0;
   for (size_t i = 0; i < h->adj_bins.size(); ++i) {
     const Bin& b = h->adj_bins[i];
@@ -1466,9 +1477,21 @@ int rod_adjoint(rod_handle h, const float* dL_dpos_traj, float* dL_dK, float* dL
     // recompute mode keeps the step's records in shared memory only: the full layout
     // unless only the compact one fits the block
     if (mode[i] == 0) compact[i] = adjoint_smem_bytes(nt, iters, 0, false) > smem_max;
+    // a rod's reverse pipelined over two SMs (a cluster of two blocks: one records the
+    // segments, the other reverses them one segment behind) when every rod of the launch
+    // gets its own two SMs and the doubled scratch fits the budget
+    if (h->adj_pipe && mode[i] == 2 && !compact[i] && 2 * b.count <= sms) {
+      const size_t sw = K * b.count * (2 * rec_iters) * 3 * 2 * nt / 4;
+      if ((long long)(2 * sw * sizeof(float4)) <= h->adj_record_budget) {
+        pipe[i] = 1;
+        sweep_need = std::max(sweep_need, 2 * sw);
+      }
+    }
   }
   const bool any_record = sweep_need > 0;
-  if (int rc = ensure_capacity(&h->d_seg, &h->seg_cap, (K + (any_record ? 1 : 0)) * 4 * E)) return rc;
+  const bool any_pipe = std::find(pipe.begin(), pipe.end(), 1) != pipe.end();
+  if (int rc = ensure_capacity(&h->d_seg, &h->seg_cap, (K + (any_record ? 1 : 0)) * (any_pipe ? 2 : 1) * 4 * E))
+    return rc;
   if (any_record) {
     if (int rc = ensure_capacity(&h->d_sweep_rec, &h->sweep_rec_cap, sweep_need)) return rc;
   }
@@ -1490,11 +1513,14 @@ int rod_adjoint(rod_handle h, const float* dL_dpos_traj, float* dL_dK, float* dL
   a.dquat0 = dev_out[4];
   a.domega0 = dev_out[5];
   int launches = 0;
-  std::fill(h->adj_info, h->adj_info + 6, 0);
+  std::fill(h->adj_info, h->adj_info + 7, 0);
   for (size_t i = 0; i < h->adj_bins.size(); ++i) {
     const Bin& b = h->adj_bins[i];
     const int nt = variants()[b.variant].nt;
-    const int smem = adjoint_smem_bytes(nt, iters, mode[i], compact[i] != 0);
+    int smem = adjoint_smem_bytes(nt, iters, mode[i], compact[i] != 0);
+    // pipelined: shared memory of more than half an SM keeps the cluster's two blocks on
+    // two SMs
+    if (pipe[i]) smem = std::min(smem_max, std::max(smem, smem_sm / 2));
     a.sweep_rec = mode[i] ? h->d_sweep_rec : nullptr;
     a.rec_iters = rec_iters;
     if (smem > smem_max)
@@ -1502,13 +1528,15 @@ int rod_adjoint(rod_handle h, const float* dL_dpos_traj, float* dL_dK, float* dL
                                              std::to_string(smem_max) + " available (fewer constraint iterations " +
                                              "or shorter rods)");
     a.work = b.d_work;
-    if (b.count >= h->adj_info[3]) {
-      int per_sm = 0;
-      CK(adjoint_occupancy(nt, mode[i], compact[i] != 0, smem, &per_sm));
-      const int info[6] = {mode[i], nt, per_sm, b.count, sms, compact[i] ? 1 : 0};
-      std::copy(info, info + 6, h->adj_info);
+    const int n_blocks = pipe[i] ? 2 * b.count : b.count;
+    if (n_blocks >= h->adj_info[3]) {
+      int per_sm = 1;
+      if (!pipe[i]) CK(adjoint_occupancy(nt, mode[i], compact[i] != 0, smem, &per_sm));
+      const int info[7] = {mode[i], nt, per_sm, n_blocks, sms, compact[i] ? 1 : 0, pipe[i] ? 1 : 0};
+      std::copy(info, info + 7, h->adj_info);
     }
-    cudaError_t e = launch_adjoint(nt, mode[i], compact[i] != 0, a, b.count, smem, s);
+    cudaError_t e = pipe[i] ? launch_adjoint_pipe(nt, a, b.count, smem, s)
+                            : launch_adjoint(nt, mode[i], compact[i] != 0, a, b.count, smem, s);
     if (e != cudaSuccess) return fail(CORDE_ERR_CUDA, std::string("adjoint launch: ") + cudaGetErrorString(e));
     ++launches;
   }
@@ -1518,7 +1546,7 @@ int rod_adjoint(rod_handle h, const float* dL_dpos_traj, float* dL_dK, float* dL
 
 int rod_adjoint_info(rod_handle h, int* out) {
   if (!h || !out) return fail(CORDE_ERR_ARG, "rod_adjoint_info: NULL argument");
-  std::copy(h->adj_info, h->adj_info + 6, out);
+  std::copy(h->adj_info, h->adj_info + 7, out);
   return CORDE_OK;
 }
 

@@ -110,6 +110,11 @@ cudaError_t preload_adjoint(int nt);
 // Resident blocks per SM of the reverse kernel of `nt` threads with `smem` bytes of
 // dynamic shared memory (occupancy API).
 cudaError_t adjoint_occupancy(int nt, int mode, bool compact, int smem, int* blocks);
+// The pipelined reverse kernel (record mode, two sweep buffers, full layout): a cluster of
+// two blocks per rod (grid 2 n_rods), the first recording the checkpoint segments and the
+// second reversing them one segment behind.  Its scratch is twice record mode's: segment
+// states and records in two sets, by segment parity.  smem should keep one block per SM.
+cudaError_t launch_adjoint_pipe(int nt, const AdjointArgs& a, int n_rods, int smem, cudaStream_t s);
 constexpr int kAdjointMaxNodes = 512;
 
 // Rods with self-collision (corde_self.cu): one rod per block, at most 1024 nodes.
