@@ -177,6 +177,7 @@ struct corde_rods {
   std::vector<char> tube;      // per rod: vessel contact enabled
   std::vector<char> self;      // per rod: self-collision enabled
   int4* d_self_stats = nullptr;  // [n_rods][2] self-collision statistics
+  unsigned char* d_self_skin = nullptr;  // [n_rods][kSelfSkinBytes] skin lists kept between launches
   struct PairBin {
     int ept, nt, count;
     int4* d_pairs;
@@ -448,6 +449,7 @@ int launch_bins(rod_handle h, const std::vector<Bin>& bins, int n_steps, const f
   a.traj = traj;
   a.n_elem = h->n_elem;
   a.self_stats = h->d_self_stats;
+  a.self_skin = h->d_self_skin;
   a.pos_out = h->io_pos;
   a.pdl = h->pdl;
   if (mb) a.mb = *mb;
@@ -1238,6 +1240,12 @@ int rod_set_self_collision(rod_handle h, int rod, const double* p) {
     CK(cudaMalloc(&h->d_self_stats, 2 * h->n_rods * sizeof(int4)));
     CK(cudaMemset(h->d_self_stats, 0, 2 * h->n_rods * sizeof(int4)));
   }
+  if (!h->d_self_skin) {
+    CK(cudaMalloc(&h->d_self_skin, (size_t)h->n_rods * kSelfSkinBytes));
+    CK(cudaMemset(h->d_self_skin, 0, (size_t)h->n_rods * kSelfSkinBytes));
+  }
+  // a kept skin list was built with the old settings: discard it
+  CK(cudaMemset(h->d_self_skin + (size_t)rod * kSelfSkinBytes, 0, 16));
   const double* dr = &h->derived[16 * (size_t)rod];
   const double radius = std::sqrt(dr[1] / kPi), l0 = dr[0];
   const int sep = std::max(2, (int)std::floor(2.0 * radius / l0) + 1);
@@ -1776,7 +1784,7 @@ void rod_destroy(rod_handle h) {
   cudaFree(h->d_rods); cudaFree(h->d_derived);
   cudaFree(h->d_x); cudaFree(h->d_v); cudaFree(h->d_q); cudaFree(h->d_o); cudaFree(h->d_u); cudaFree(h->d_k);
   cudaFree(h->d_drive); cudaFree(h->d_elem_rod); cudaFree(h->d_drive_graph);
-  cudaFree(h->d_ckpt); cudaFree(h->d_seg); cudaFree(h->d_self_stats);
+  cudaFree(h->d_ckpt); cudaFree(h->d_seg); cudaFree(h->d_self_stats); cudaFree(h->d_self_skin);
   cudaFree(h->d_sweep_rec);
   for (auto& b : h->adj_bins) cudaFree(b.d_work);
   for (auto& pb : h->pair_bins) cudaFree(pb.d_pairs);

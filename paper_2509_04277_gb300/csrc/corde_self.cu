@@ -19,9 +19,11 @@
 // the positions they were found at; on later steps each point only tests its listed
 // partners at the plain reach.  A pair within the reach now was within reach + 2 s at the
 // build as long as no mass point has moved more than s since, so the block rebuilds the
-// list as soon as one has moved more than 0.999 s (and on the first step of a launch, and
-// detects from scratch whenever a build overflows the list): the candidate pairs of every
-// step are exactly those of the full detection.
+// list as soon as one has moved more than 0.999 s (and when it has none: the list and the
+// positions it was built at are kept in device memory from one launch to the next,
+// discarded when the rod's self-collision settings change; it detects from scratch
+// whenever a build overflows the list): the candidate pairs of every step are exactly
+// those of the full detection.
 // In every constraint iteration, after the distance sweeps (and the vessel contact), the
 // velocities are staged in shared memory and (Jacobi: everything from the staged
 // velocities)
@@ -49,6 +51,17 @@ constexpr int kSelfMaxCand = 16;      // larger partners kept per mass point; to
 constexpr int kSelfPairsPerNode = 3;  // compacted pair capacity: 3 pairs per mass point
 constexpr int kSkinMax = 24;          // partners kept per mass point in the skin list
 constexpr int kSkinNodes = 512;       // rods held by blocks of up to this many nodes keep a skin list
+
+// A rod's skin list kept in device memory between launches (the record of rod r at
+// r x kBytes): its valid flag, then every mass point's list count, listed partners
+// ([kSkinMax][kSkinNodes] uint16) and position at the last build.
+struct SelfSkinStore {
+  static constexpr int off_cnt = 16;
+  static constexpr int off_list = off_cnt + kSkinNodes;
+  static constexpr int off_rb = off_list + kSkinMax * kSkinNodes * 2;
+  static constexpr int kBytes = off_rb + kSkinNodes * 16;
+};
+static_assert(SelfSkinStore::off_rb % 16 == 0, "skin store layout");
 
 // Shared-memory layout of the self-collision area (bytes from its start).
 template <int EPT, int NT>
@@ -496,7 +509,7 @@ __global__ void __launch_bounds__(NT, 1)
 self_step_kernel(const RodDev* __restrict__ rods, const int* __restrict__ work, float4* __restrict__ x4,
                  float4* __restrict__ v4, float4* __restrict__ q4, float4* __restrict__ o4,
                  const float4* __restrict__ u4, const float4* __restrict__ k4, const float4* __restrict__ drive,
-                 int n_steps, int4* __restrict__ stats, float4* __restrict__ pos_out) {
+                 int n_steps, int4* __restrict__ stats, float4* __restrict__ pos_out, unsigned char* __restrict__ skin_g) {
   extern __shared__ float4 smem[];
   pdl_begin();
   const int rid = work[blockIdx.x];
@@ -531,6 +544,30 @@ self_step_kernel(const RodDev* __restrict__ rods, const int* __restrict__ work, 
     hook.stat()[3] = 0;  // overflow flags of this launch (read after the last barrier)
     hook.stat()[5] = 0;  // skin-list builds of this launch
   }
+  using L = SelfLayout<EPT, NT>;
+  unsigned char* store = nullptr;  // this rod's skin list of the previous launch
+  if constexpr (L::kSkin) {
+    if (skin_g != nullptr) store = skin_g + (int64_t)rid * SelfSkinStore::kBytes;
+  }
+  if (store != nullptr) {
+    // a list from an earlier launch stays valid as long as no mass point has moved more
+    // than the skin width from the position it was built at, which the first step checks
+    // (a change of the rod's self-collision settings clears the flag)
+    hook.skin_valid = *reinterpret_cast<const int*>(store);
+    if (hook.skin_valid) {
+      const float4* rbg = reinterpret_cast<const float4*>(store + SelfSkinStore::off_rb);
+      const unsigned short* lg = reinterpret_cast<const unsigned short*>(store + SelfSkinStore::off_list);
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) {
+        const int i = t * EPT + e;
+        if (i >= R.n) continue;
+        const int c = store[SelfSkinStore::off_cnt + i];
+        hook.skin_cnt()[i] = (unsigned char)c;
+        for (int m = 0; m < c; ++m) hook.skin()[m * L::NN + i] = lg[m * kSkinNodes + i];
+        hook.rb[e] = f3(rbg[i]);
+      }
+    }
+  }
 
   const BlockHalo<NT, NT> H{t};
   int xc = 0;
@@ -549,6 +586,24 @@ self_step_kernel(const RodDev* __restrict__ rods, const int* __restrict__ work, 
       o4[R.off + i] = make_float4(om[e].x, om[e].y, om[e].z, 0.f);
       if (pos_out != nullptr) pos_out[R.off + i] = make_float4(r[e].x, r[e].y, r[e].z, w[e]);
     }
+  }
+  if (store != nullptr) {
+    // the list and the positions it was built at, for the next launch (each thread its
+    // own mass points, as it reads them back)
+    if (hook.skin_valid) {
+      float4* rbg = reinterpret_cast<float4*>(store + SelfSkinStore::off_rb);
+      unsigned short* lg = reinterpret_cast<unsigned short*>(store + SelfSkinStore::off_list);
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) {
+        const int i = t * EPT + e;
+        if (i >= R.n) continue;
+        const int c = hook.skin_cnt()[i];
+        store[SelfSkinStore::off_cnt + i] = (unsigned char)c;
+        for (int m = 0; m < c; ++m) lg[m * kSkinNodes + i] = hook.skin()[m * L::NN + i];
+        rbg[i] = make_float4(hook.rb[e].x, hook.rb[e].y, hook.rb[e].z, 0.f);
+      }
+    }
+    if (t == 0) *reinterpret_cast<int*>(store) = hook.skin_valid;
   }
   block_sync<NT>();
   if (t == 0 && stats != nullptr) {
@@ -572,7 +627,7 @@ cudaError_t launch_self_t(const StepArgs& a, int n_blocks, cudaStream_t s) {
     if (e != cudaSuccess) return e;
   }
   return launch_kernel(self_step_kernel<EPT, NT>, dim3(n_blocks), dim3(NT), smem, s, a.pdl, 0, a.rods, a.work, a.x4,
-                       a.v4, a.q4, a.o4, a.u4, a.k4, a.drive, a.n_steps, a.self_stats, a.pos_out);
+                       a.v4, a.q4, a.o4, a.u4, a.k4, a.drive, a.n_steps, a.self_stats, a.pos_out, a.self_skin);
 }
 
 }  // namespace
@@ -587,5 +642,6 @@ const StepVariant kSelfVariants[] = {
     {4, 256, self_smem_bytes<4, 256>(), &launch_self_t<4, 256>},
 };
 const int kNumSelfVariants = 7;
+const int kSelfSkinBytes = SelfSkinStore::kBytes;
 
 }  // namespace corde

@@ -22,6 +22,7 @@ struct StepArgs {
   int64_t n_elem;
   MailboxDev mb;   // mailbox of the launch (period 0: none)
   int4* self_stats;  // self-collision statistics per rod (corde_self.cu), or NULL
+  unsigned char* self_skin;  // self-collision skin lists kept between launches (corde_self.cu), or NULL
   float4* pos_out;   // optional: positions (r, w) after the launch, [n_elem] (device or mapped host)
   float4* grid_halo; // rods on a cooperative grid: their global exchange slots
   int pdl;           // 1: launch with programmatic stream serialisation (the kernel may start
@@ -121,6 +122,9 @@ constexpr int kAdjointMaxNodes = 512;
 extern const StepVariant kSelfVariants[];
 extern const int kNumSelfVariants;
 constexpr int kSelfMaxNodes = 1024;
+// Bytes per rod of StepArgs::self_skin: a rod's skin list kept between launches (rods in
+// blocks of up to 512 nodes); its first int is the valid flag, cleared to discard it.
+extern const int kSelfSkinBytes;
 
 // Catheter/guidewire pairs (corde_pair.cu): pairs[i] = (outer rod, inner rod, mode, 0);
 // ept in {2, 4}, nt (threads per rod) in {32, ..., 256}.
