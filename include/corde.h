@@ -149,7 +149,7 @@ int rod_set_tube(rod_handle h, int rod, const double* tube);
  * impulse that separates the predicted spheres, with a tangential cut of at most mu times
  * the normal change, and each mass point takes the penetration-weighted mean of its
  * pairs' velocity changes (one Jacobi pass).  The rod then runs in its own kernel (one
- * block, two elements per thread).
+ * block, two elements per thread up to 512 nodes, four beyond).
  * Errors: CORDE_ERR_ARG for a bad index, NULL params or mu < 0; CORDE_ERR_UNSUPPORTED for
  * an extensible rod, a rod of more than 1024 nodes, a rod bound in a pair, or a handle
  * with a mailbox.  rod_rollout, rod_adjoint, rod_mailbox_enable and rod_bind refuse

@@ -1256,9 +1256,10 @@ int rod_set_self_collision(rod_handle h, int rod, const double* p) {
   CK(cudaDeviceSynchronize());
   h->self[rod] = (char)enable;
   if (enable) {
-    // smallest two-elements-per-thread block holding the rod
+    // the first block of the list that holds the rod (two elements per thread up to 512
+    // nodes, four beyond)
     int v = 0;
-    while (v + 1 < kNumSelfVariants && kSelfVariants[v].ept == 2 && kSelfVariants[v].capacity() < h->n_nodes[rod]) ++v;
+    while (v + 1 < kNumSelfVariants && kSelfVariants[v].capacity() < h->n_nodes[rod]) ++v;
     h->plan[rod] = v;
     h->plan_cluster[rod] = -1;
     h->plan_grid[rod] = 0;

@@ -28,9 +28,9 @@
 // velocities are staged in shared memory and (Jacobi: everything from the staged
 // velocities)
 //   1. every pair's predicted offset delta = (r_j - r_i) + dt (v_j - v_i) is tested and the
-//      pairs with |delta| < 2 r are listed;
-//   2. each listed pair gets phi = 2 r - |delta|, n = delta / |delta|, du_n = phi / dt, the
-//      relative tangential velocity u_t and
+//      pairs with |delta| < 2 r are listed, each warp its own in a scratch of its own;
+//   2. right away, spread over the warp's lanes, each listed pair gets phi = 2 r - |delta|,
+//      n = delta / |delta|, du_n = phi / dt, the relative tangential velocity u_t and
 //        J = (du_n n - min(1, mu du_n / |u_t|) u_t) / (w_i + w_j)   (+J on j, -J on i),
 //      and its slot is appended to both mass points' short lists;
 //   3. each mass point sums its pairs in ascending slot order (= ascending partner order,
@@ -74,12 +74,12 @@ struct SelfLayout {
   static constexpr int off_r = 0;                                    // float4 [NN]: r, w
   static constexpr int off_v = off_r + NN * 16;                      // float4 [NN]: v
   static constexpr int off_pj = off_v + NN * 16;                     // float4 [NP]: phi J, phi
-  // (its first NN entries hold the predicted positions r + dt v, w during the touch test)
-  static constexpr int off_g = off_pj + NP * 16;                     // float4 [NG]: centre, radius
+  static constexpr int off_q = off_pj + NP * 16;                     // float4 [NN]: r + dt v, w
+  static constexpr int off_g = off_q + NN * 16;                      // float4 [NG]: centre, radius
   static constexpr int off_bits = off_g + NG * 16;                   // uint16 [NG][NGH]
   static constexpr int off_nact = off_bits + ((NG * NGH * 2 + 15) / 16) * 16;  // int [NN]
   static constexpr int off_pa = off_nact + NN * 4;                   // ushort2 [NP]: (i, j), i < j
-  static constexpr int off_act = off_pa + NP * 4;                    // uint16 [NP]: touching pairs
+  static constexpr int off_act = off_pa + NP * 4;                    // uint16 [NP]: touching pairs, 4 x 32 per warp
   static constexpr int off_scan = off_act + ((NP * 2 + 15) / 16) * 16;  // int [NT / 32 + 1]
   static constexpr int off_stat = off_scan + ((NT / 32 + 1) * 4 + 15) / 16 * 16;  // int [8]
   static constexpr int off_list = off_stat + 32;  // uint16 [kSelfMaxCand][NN]: partners, then slots
@@ -148,6 +148,7 @@ struct SelfHook {
   __device__ __forceinline__ float4* sr() const { return reinterpret_cast<float4*>(base + L::off_r); }
   __device__ __forceinline__ float4* sv() const { return reinterpret_cast<float4*>(base + L::off_v); }
   __device__ __forceinline__ float4* pj() const { return reinterpret_cast<float4*>(base + L::off_pj); }
+  __device__ __forceinline__ float4* qp() const { return reinterpret_cast<float4*>(base + L::off_q); }
   __device__ __forceinline__ float4* gs() const { return reinterpret_cast<float4*>(base + L::off_g); }
   __device__ __forceinline__ unsigned short* bits() const {
     return reinterpret_cast<unsigned short*>(base + L::off_bits);
@@ -158,7 +159,7 @@ struct SelfHook {
     return reinterpret_cast<unsigned short*>(base + L::off_act);
   }
   __device__ __forceinline__ int* scan() const { return reinterpret_cast<int*>(base + L::off_scan); }
-  // stat: [0] pairs, [1] most larger partners, [2] overlapping pairs, [3] overflow, [4] touching
+  // stat: [0] pairs, [1] most larger partners, [2] overlapping pairs, [3] overflow, [5] builds
   __device__ __forceinline__ int* stat() const { return reinterpret_cast<int*>(base + L::off_stat); }
   __device__ __forceinline__ unsigned short* list() const {
     return reinterpret_cast<unsigned short*>(base + L::off_list);
@@ -272,15 +273,16 @@ struct SelfHook {
         const float rch = reach + 2.f * s;
         build_groups(rch);
         int over = 0, dummy = 0;
-#pragma unroll
+#pragma unroll 1
         for (int e = 0; e < EPT; ++e) {
           const int i = e0 + e;
           if (i >= n) continue;
           const int c = narrow(i, R4[i], rch * rch, skin(), kSkinMax, &dummy);
           skin_cnt()[i] = (unsigned char)min(c, kSkinMax);
           over |= c > kSkinMax;
-          rb[e] = r[e];
         }
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) rb[e] = r[e];
         skin_valid = !block_or<NT>(over);  // (a barrier: the lists are visible)
         if (t == 0) ++stat()[5];           // builds in this launch
       }
@@ -292,6 +294,14 @@ struct SelfHook {
     }
     int n_up[EPT];
     int my_up = 0, st_max = 0, st_touch = 0, st_over = 0;
+    if (!use_skin) {
+      // the full narrow phase (one copy of its code: its counts parked in nact)
+#pragma unroll 1
+      for (int e = 0; e < EPT; ++e) {
+        const int i = e0 + e;
+        if (i < n) nact()[i] = narrow(i, R4[i], reach2, list(), kSelfMaxCand, &st_touch);
+      }
+    }
 #pragma unroll
     for (int e = 0; e < EPT; ++e) {
       const int i = e0 + e;
@@ -323,7 +333,8 @@ struct SelfHook {
           }
         }
       } else {
-        c = narrow(i, ri, reach2, list(), kSelfMaxCand, &touching);
+        c = nact()[i];
+        nact()[i] = 0;
       }
       st_over |= c > kSelfMaxCand;
       n_up[e] = min(c, kSelfMaxCand);
@@ -371,14 +382,13 @@ struct SelfHook {
     if (n_pairs == 0) return;  // block-uniform
     const int e0 = t * EPT;
     float4* V4 = sv();
-    float4* Q4 = pj();  // predicted positions, read by the touch test only
+    float4* Q4 = qp();  // predicted positions, read by the touch test only
 #pragma unroll
     for (int e = 0; e < EPT; ++e)
       if (e0 + e < n) {
         V4[e0 + e] = make_float4(v[e].x, v[e].y, v[e].z, 0.f);
         Q4[e0 + e] = make_float4(fmaf(dt, v[e].x, r[e].x), fmaf(dt, v[e].y, r[e].y), fmaf(dt, v[e].z, r[e].z), w[e]);
       }
-    if (t == 0) stat()[4] = 0;
     block_sync<NT>();
     const float4* R4 = sr();
     float4* P4 = pj();
@@ -387,6 +397,8 @@ struct SelfHook {
     // 1. which pairs touch: predicted positions closer than 2 r (the exact offset of step 2
     //    decides the impulse; a pair misjudged here within rounding of 2 r has phi = 0)
     constexpr int PH = 4;
+    static_assert(L::NP >= PH * NT, "each warp lists its touching pairs of one pass in the pair area");
+    unsigned short* wl = act() + (t >> 5) * (PH * 32);  // this warp's touching pairs
     for (int p0 = 0; p0 < n_pairs; p0 += PH * NT) {
       bool hit[PH];
       float4 qi[PH], qj[PH];
@@ -401,7 +413,7 @@ struct SelfHook {
         const float3 delta = f3(qj[h]) - f3(qi[h]);
         hit[h] = p0 + h * NT + t < n_pairs && dot3(delta, delta) < dist2 * 1.0001f && qi[h].w + qj[h].w > 0.f;
       }
-      // one list append per warp for the whole pass
+      // the warp's hits listed in its own scratch and spread over its lanes
       unsigned m[PH];
       int tot = 0;
 #pragma unroll
@@ -409,42 +421,40 @@ struct SelfHook {
         m[h] = __ballot_sync(0xffffffffu, hit[h]);
         tot += __popc(m[h]);
       }
-      if (tot > 0) {
+      if (tot > 0) {  // warp-uniform
         int at = 0;
-        if (lane == 0) at = atomicAdd(&stat()[4], tot);
-        at = __shfl_sync(0xffffffffu, at, 0);
         const unsigned below = (1u << lane) - 1u;
 #pragma unroll
         for (int h = 0; h < PH; ++h) {
-          if (hit[h]) act()[at + __popc(m[h] & below)] = (unsigned short)(p0 + h * NT + t);
+          if (hit[h]) wl[at + __popc(m[h] & below)] = (unsigned short)(p0 + h * NT + t);
           at += __popc(m[h]);
         }
+        __syncwarp();
+        // 2. impulses of the touching pairs
+        for (int q = lane; q < tot; q += 32) {
+          const int p = wl[q];
+          const ushort2 ij = pa()[p];
+          const float4 ri = R4[ij.x], rj = R4[ij.y];
+          const float3 u = f3(V4[ij.y]) - f3(V4[ij.x]);
+          const float3 delta = (f3(rj) - f3(ri)) + dt * u;
+          const float d2 = dot3(delta, delta);
+          const float il = rsqrtf(d2);
+          const float phi = fmaxf(dist - d2 * il, 0.f);  // rounding at the contact distance
+          const float3 nrm = il * delta;
+          const float dun = phi * inv_dt;
+          const float3 ut = u - dot3(u, nrm) * nrm;
+          const float ut2 = dot3(ut, ut);
+          const float cut = ut2 > 0.f ? fminf(1.f, mu * dun * rsqrtf(ut2)) : 0.f;
+          const float3 J = (phi * __fdividef(1.f, ri.w + rj.w)) * (dun * nrm - cut * ut);  // approximate reciprocal: ~2 ulp
+          P4[p] = make_float4(J.x, J.y, J.z, phi);
+          const int ka = atomicAdd(&nact()[ij.x], 1);
+          const int kb = atomicAdd(&nact()[ij.y], 1);
+          if (ka < kSelfMaxCand) list()[ka * L::NN + ij.x] = (unsigned short)p;
+          if (kb < kSelfMaxCand) list()[kb * L::NN + ij.y] = (unsigned short)p;
+          if (ka >= kSelfMaxCand || kb >= kSelfMaxCand) atomicOr(&stat()[3], 4);
+        }
+        __syncwarp();  // (the scratch is reused by the next pass)
       }
-    }
-    block_sync<NT>();
-    // 2. impulses of the touching pairs
-    const int na = stat()[4];
-    for (int q = t; q < na; q += NT) {
-      const int p = act()[q];
-      const ushort2 ij = pa()[p];
-      const float4 ri = R4[ij.x], rj = R4[ij.y];
-      const float3 u = f3(V4[ij.y]) - f3(V4[ij.x]);
-      const float3 delta = (f3(rj) - f3(ri)) + dt * u;
-      const float d2 = dot3(delta, delta);
-      const float il = rsqrtf(d2);
-      const float phi = fmaxf(dist - d2 * il, 0.f);  // rounding at the contact distance
-      const float3 nrm = il * delta;
-      const float dun = phi * inv_dt;
-      const float3 ut = u - dot3(u, nrm) * nrm;
-      const float ut2 = dot3(ut, ut);
-      const float cut = ut2 > 0.f ? fminf(1.f, mu * dun * rsqrtf(ut2)) : 0.f;
-      const float3 J = (phi * __fdividef(1.f, ri.w + rj.w)) * (dun * nrm - cut * ut);  // approximate reciprocal: ~2 ulp
-      P4[p] = make_float4(J.x, J.y, J.z, phi);
-      const int ka = atomicAdd(&nact()[ij.x], 1);
-      const int kb = atomicAdd(&nact()[ij.y], 1);
-      if (ka < kSelfMaxCand) list()[ka * L::NN + ij.x] = (unsigned short)p;
-      if (kb < kSelfMaxCand) list()[kb * L::NN + ij.y] = (unsigned short)p;
-      if (ka >= kSelfMaxCand || kb >= kSelfMaxCand) atomicOr(&stat()[3], 4);
     }
     block_sync<NT>();
     // 3. each mass point: its pairs in ascending slot order
@@ -637,11 +647,10 @@ const StepVariant kSelfVariants[] = {
     {2, 64, self_smem_bytes<2, 64>(), &launch_self_t<2, 64>},
     {2, 128, self_smem_bytes<2, 128>(), &launch_self_t<2, 128>},
     {2, 256, self_smem_bytes<2, 256>(), &launch_self_t<2, 256>},
-    {2, 512, self_smem_bytes<2, 512>(), &launch_self_t<2, 512>},
     {4, 128, self_smem_bytes<4, 128>(), &launch_self_t<4, 128>},
     {4, 256, self_smem_bytes<4, 256>(), &launch_self_t<4, 256>},
 };
-const int kNumSelfVariants = 7;
+const int kNumSelfVariants = 6;
 const int kSelfSkinBytes = SelfSkinStore::kBytes;
 
 }  // namespace corde
