@@ -163,10 +163,11 @@ int rod_set_self_collision(rod_handle h, int rod, const double* params);
  * 3 N candidate pairs, bit 2 when a mass point touched more than 16 others in one
  * iteration: the excess is dropped; bit 3 when a skin list overflowed and the step fell
  * back to the full detection; sticky until rod_set_self_collision), and the number of
- * skin-list builds in the launch.  Rods held by blocks of up to 512 nodes keep, within a
- * launch, a skin list: the detection runs with the reach grown by 2 s (s = r) and
- * later steps test only the listed partners at the plain reach, until a mass point has
- * moved more than s; the candidate pairs are those of the full detection.  Synchronous. */
+ * skin-list builds in the launch.  Rods held by blocks of up to 512 nodes keep a skin
+ * list (in device memory from one launch to the next): the detection runs with the reach
+ * grown by 2 s (s = 1.5 r) and later steps test only the listed partners at the plain
+ * reach, until a mass point has moved more than s since the list was built; the
+ * candidate pairs are those of the full detection.  Synchronous. */
 int rod_self_collision_stats(rod_handle h, int rod, int* out);
 
 /* Copy the drive input [n_rods][8] (host or device) into the handle. */

@@ -15,7 +15,7 @@
 //   compaction   - the pairs get consecutive slots, ordered by (i, j) (a block prefix sum
 //                  over the points' counts).
 // Skin list (rods in blocks of up to 512 nodes): the broad and narrow phases run with the
-// reach grown by two skin widths s = r and keep every point's partners in a list, with
+// reach grown by two skin widths s = 1.5 r and keep every point's partners in a list, with
 // the positions they were found at; on later steps each point only tests its listed
 // partners at the plain reach.  A pair within the reach now was within reach + 2 s at the
 // build as long as no mass point has moved more than s since, so the block rebuilds the
@@ -259,8 +259,8 @@ struct SelfHook {
     bool use_skin = false;
     if constexpr (L::kSkin) {
       // rebuild the skin list when a mass point has moved more than 0.999 s since the last
-      // build (s = reach / 3 = r), or when there is none (first step of the launch)
-      const float s = reach * (1.f / 3.f);
+      // build (s = reach / 2 = 1.5 r), or when there is none
+      const float s = reach * 0.5f;
       const float move2 = (0.999f * s) * (0.999f * s);
       int moved = !skin_valid;
 #pragma unroll
