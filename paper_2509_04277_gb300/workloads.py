@@ -363,6 +363,24 @@ def _chord_march(curve: np.ndarray, l0: float, n: int) -> np.ndarray:
     return out
 
 
+def _transported_frames(pos: np.ndarray, l0: float) -> list:
+    """Segment frames along a polyline of spacing l0: the first takes its director d3 = z to
+    the first segment, each next one follows by the smallest rotation between consecutive
+    segments (parallel transport)."""
+    t = np.diff(pos, axis=0) / l0
+    rots = []
+    cur = Rotation.align_vectors(t[0][None, :], np.array([[0.0, 0.0, 1.0]]))[0]
+    rots.append(cur)
+    for j in range(1, len(t)):
+        ax = np.cross(t[j - 1], t[j])
+        s = np.linalg.norm(ax)
+        ang = math.atan2(s, float(t[j - 1] @ t[j]))
+        step = Rotation.from_rotvec(ax / s * ang) if s > 0 else Rotation.identity()
+        cur = step * cur
+        rots.append(cur)
+    return rots
+
+
 def torus_knot(n: int = 512, seed: int = 21, gap: float = 1.05, spacing: float = 1.35):
     """Knot-like self-collision configuration (stands in for the haptic knot tying of
     Section 3.5): a guidewire (r = 0.45 mm, E = 60 GPa, straight at rest, base driven) laid
@@ -389,20 +407,36 @@ def torus_knot(n: int = 512, seed: int = 21, gap: float = 1.05, spacing: float =
     curve = np.stack([rho * np.cos(phi), rho * np.sin(phi), a * np.sin(th)], axis=1)
     pos = _chord_march(curve, l0, n)
     m = n - 1
-    t = np.diff(pos, axis=0) / l0
-    rots = []
-    cur = Rotation.align_vectors(t[0][None, :], np.array([[0.0, 0.0, 1.0]]))[0]
-    rots.append(cur)
-    for j in range(1, m):
-        ax = np.cross(t[j - 1], t[j])
-        s = np.linalg.norm(ax)
-        ang = math.atan2(s, float(t[j - 1] @ t[j]))
-        step = Rotation.from_rotvec(ax / s * ang) if s > 0 else Rotation.identity()
-        cur = step * cur
-        rots.append(cur)
+    rots = _transported_frames(pos, l0)
     frames = Rotation.concatenate(rots) * Rotation.from_rotvec(g.standard_normal((m, 3)) * 2e-5)
     rod.length = l0 * m
     rod.pos = pos - pos[0]
     rod.quat = _hemisphere_continuous(frames.as_quat())
     rod.rest_quat = np.tile(rots[0].as_quat()[None, :], (m, 1))
+    return rod
+
+
+def coil(n: int = 130, seed: int = 720, radius: float = 3.0, pitch: float = 1.96, spacing: float = 1.35):
+    """A guidewire (r = 0.45 mm) wound into a tight helix, coil radius `radius` r and
+    pitch `pitch` r (neighbouring turns pressed slightly into each other), nodes exactly
+    l0 = spacing r apart; the helix is also the rest shape, so the coil holds its form.
+    Dense on purpose: within 6 r a mass point has up to ~26 partners above it, within the
+    plain 3 r reach of the self-collision detection at most ~4."""
+    rod = guidewire(n, seed=seed)
+    g = rng(seed + 31)
+    r = rod.radius
+    l0 = spacing * r
+    rh, p = radius * r, pitch * r
+    turns = (n - 1) * l0 / (2.0 * math.pi * rh) + 2.0
+    th = np.linspace(0.0, 2.0 * math.pi * turns, 400 * n)
+    curve = np.stack([rh * np.cos(th), rh * np.sin(th), p * th / (2.0 * math.pi)], axis=1)
+    pos = _chord_march(curve, l0, n)
+    m = n - 1
+    rots = _transported_frames(pos, l0)
+    rest = Rotation.concatenate(rots)
+    frames = rest * Rotation.from_rotvec(g.standard_normal((m, 3)) * 2e-5)
+    rod.length = l0 * m
+    rod.pos = pos - pos[0]
+    rod.quat = _hemisphere_continuous(frames.as_quat())
+    rod.rest_quat = _hemisphere_continuous(rest.as_quat())
     return rod

@@ -80,8 +80,8 @@ def test_self_one_step_parity(corde, n):
 def test_self_detection_matches_oracle(corde):
     """The candidate pairs the GPU found at the last detection of a launch are the oracle's
     pairs of the same positions (the broad phase drops none), on every step of launches
-    of 1 to 20 steps: within a launch later steps test only the skin list of the first
-    step's build (until a mass point has moved half a radius), and the set stays exact."""
+    of 1 to 20 steps: later steps test only the skin list of an earlier build (until a
+    mass point has moved 1.5 radii since), and the set stays exact."""
     import torch
 
     rod = W.torus_knot(512, seed=710)
@@ -134,6 +134,33 @@ def test_self_skin_list_kept_between_launches(corde):
     assert b.self_collision_stats(0)["skin_builds"] == 1
     pos = b.rod_state(b.state_numpy(), 0)["pos"]
     assert np.isfinite(pos).all()
+    b.close()
+
+
+def test_self_skin_overflow_falls_back_to_full_detection(corde):
+    """A tight coil: within the grown reach of the skin list (6 r) some mass points have
+    more than the list's 24 places of partners above them, within the plain 3 r at most
+    four.  Every build overflows, so every step detects from scratch (overflow bit 3 and
+    no other); the candidate pairs are still the oracle's, and each step matches the
+    oracle's."""
+    import torch
+
+    rod = W.coil(130, seed=720)
+    b = corde.RodBatch([rod])
+    b.set_self_collision(0, MU)
+    d = _drive(torch, PULL)
+    for _ in range(3):
+        st0 = b.rod_state(b.state_numpy(), 0)
+        b.step(1, drive=d)
+        stats = b.self_collision_stats(0)
+        assert stats["overflow"] == 8, stats
+        cand, pairs = oracle.self_candidates(rod, st0["pos"])
+        assert stats["candidate_pairs"] == pairs, (stats, pairs)
+        assert stats["max_partners_above"] == max(int(np.sum(c > i)) for i, c in enumerate(cand))
+        ref = oracle.step_contact(rod, st0, self_mu=MU, n_steps=1, drive=_drive64(PULL))
+        _cmp(rod, b.rod_state(b.state_numpy(), 0), ref, STEP_TOL)
+    touching, _ = _touching(rod, ref["pos"])
+    assert touching > 0
     b.close()
 
 
