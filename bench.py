@@ -294,8 +294,8 @@ def run_single_rod(args, torch, corde, W, rank):
                       "steps": last - first}
 
     # Lock-step persistent loop: the kernel waits (bounded) at every 10th step for the
-    # host's next drive; the host writes drive k, waits for the snapshot after those 10
-    # steps, reads all positions and writes drive k + 1.
+    # host's next drive; the host writes drive 0, then per tick k one native call waits
+    # for the snapshot after tick k's 10 steps, writes drive k + 1 and reads all positions.
     corde.rod_mailbox_enable(b.handle, STEPS_PER_LAUNCH, 64)
     corde.rod_mailbox_positions_enable(b.handle)
     corde.rod_mailbox_lockstep(b.handle, True, 2_000_000)
@@ -305,17 +305,13 @@ def run_single_rod(args, torch, corde, W, rank):
     corde.rod_mailbox_write(b.handle, host_drive[0].reshape(1, 8))
     for k in range(n_ticks + 20):
         target = base + (k + 1) * STEPS_PER_LAUNCH
-        t_limit = time.perf_counter() + 10.0
-        # poll the snapshot header (no copy) until the tick's snapshot is published
-        s = corde.rod_mailbox_positions(b.handle, 0, None)
-        while s < target and time.perf_counter() < t_limit:
-            s = corde.rod_mailbox_positions(b.handle, 0, None)
-        if s < target:
+        # the next tick's drive goes out as soon as this tick's snapshot is seen, so the
+        # kernel steps while the host copies
+        nxt = host_drive[(k + 1) % host_drive.shape[0]].reshape(1, 8) if k + 1 < n_ticks + 20 else None
+        try:
+            s = corde.rod_mailbox_tick(b.handle, 0, target, nxt, snap, 10_000_000)
+        except corde.CordeError:
             break
-        # the next tick's drive first, so that the kernel steps while the host copies
-        if k + 1 < n_ticks + 20:
-            corde.rod_mailbox_write(b.handle, host_drive[(k + 1) % host_drive.shape[0]].reshape(1, 8))
-        s = corde.rod_mailbox_positions(b.handle, 0, snap)
         if s != target:
             break
         done += 1
@@ -855,12 +851,12 @@ def main_ours(args):
                     "d2h_bytes_per_step": 512 * 16 * LAUNCHES_PER_BENCH_STEP,
                     "path": e2e_path,
                     "what": {"lockstep_persistent": "one persistent launch in lock-step (rod_step once; per tick "
-                                                    "rod_mailbox_positions without a copy until the tick's snapshot "
-                                                    "is published, rod_mailbox_write of the next tick's drive, then "
-                                                    "rod_mailbox_positions copying the snapshot): the kernel waits "
-                                                    "for each drive, runs 10 steps and publishes all 512 positions "
-                                                    "to pinned host memory; the host's copy of tick k overlaps the "
-                                                    "kernel's tick k + 1; host wall clock",
+                                                    "one rod_mailbox_tick call: the host spins until the tick's "
+                                                    "snapshot is published, writes the next tick's drive at once, "
+                                                    "then copies the snapshot): the kernel waits for each drive, "
+                                                    "runs 10 steps and publishes all 512 positions to pinned host "
+                                                    "memory; the host's copy of tick k overlaps the kernel's tick "
+                                                    "k + 1; host wall clock",
                              "launch_per_tick": "per tick one rod_step_io call (the kernel reads the drive from "
                                                 "pinned host memory and writes the 512 positions to pinned host "
                                                 "memory) + stream sync; host wall clock"}[e2e_path],

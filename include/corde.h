@@ -320,6 +320,18 @@ int rod_mailbox_positions(rod_handle h, int rod, float* out, long long* step);
  * that a lock-step wait of the kernel ran out (the status word is left set). */
 int rod_mailbox_exchange(rod_handle h, const float* drive, int rod, long long target_step, float* out,
                          long long timeout_us, long long* step);
+/* One tick of a closed haptic loop in lock-step (Section 2.2: input and feedback
+ * exchanged with the running kernel every haptic frame): spins on the host until rod
+ * `rod`'s newest position snapshot was taken after a global step >= target_step, then
+ * writes next_drive (as rod_mailbox_write; NULL: no write) at once, so that the kernel's
+ * lock-step wait for the next tick ends while the host still copies, then copies the
+ * snapshot as rod_mailbox_positions does (out [N][4] host floats, NULL: none; *step its
+ * step).  The drive of tick k + 1 thus follows the end of tick k, with no host code
+ * between the two.  Errors as rod_mailbox_exchange (NULL step, snapshots not enabled,
+ * bad rod, timeout_us < 0: CORDE_ERR_ARG; the timeout or a lost lock-step wait:
+ * CORDE_ERR_BUSY, and next_drive is not written). */
+int rod_mailbox_tick(rod_handle h, int rod, long long target_step, const float* next_drive, float* out,
+                     long long timeout_us, long long* step);
 int64_t rod_steps_done(rod_handle h);
 
 /* Number of kernel launches the last rod_step enqueued (kernel nodes of the graph when

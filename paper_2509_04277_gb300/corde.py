@@ -80,6 +80,7 @@ SIGNATURES = {
     "rod_mailbox_positions_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
     "rod_mailbox_positions": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP]),
     "rod_mailbox_exchange": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_longlong, _VP, ctypes.c_longlong, _VP]),
+    "rod_mailbox_tick": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_longlong, _VP, _VP, ctypes.c_longlong, _VP]),
     "rod_mailbox_lockstep": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
     "rod_mailbox_status": (ctypes.c_int, [_VP, _VP]),
     "rod_steps_done": (ctypes.c_int64, [_VP]),
@@ -321,6 +322,18 @@ def rod_mailbox_exchange(h, drive, rod, target_step, out, timeout_us=1_000_000):
     step = ctypes.c_longlong(0)
     _check(load().rod_mailbox_exchange(h, None if d is None else d.ctypes.data, int(rod), int(target_step), _ptr(out),
                                        int(timeout_us), ctypes.addressof(step)), "rod_mailbox_exchange")
+    return int(step.value)
+
+
+def rod_mailbox_tick(h, rod, target_step, next_drive, out, timeout_us=1_000_000):
+    """One closed lock-step tick: waits until rod `rod`'s snapshot of a step >= target_step
+    is published, writes next_drive at once (None: no write), then copies the snapshot
+    into out ([N, 4] float32 host array; None: no copy) and returns its step."""
+    d = None if next_drive is None else np.ascontiguousarray(next_drive, dtype=np.float32)
+    step = ctypes.c_longlong(0)
+    _check(load().rod_mailbox_tick(h, int(rod), int(target_step), None if d is None else d.ctypes.data,
+                                   None if out is None else _ptr(out), int(timeout_us), ctypes.addressof(step)),
+           "rod_mailbox_tick")
     return int(step.value)
 
 

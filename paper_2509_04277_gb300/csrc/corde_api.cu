@@ -1674,17 +1674,11 @@ int rod_mailbox_positions(rod_handle h, int rod, float* out, long long* step) {
   return fail(CORDE_ERR_BUSY, "rod_mailbox_positions: no consistent snapshot after 10000 attempts");
 }
 
-constexpr long long kExchangePollNs = 300;  // host poll interval of rod_mailbox_exchange
+constexpr long long kExchangePollNs = 300;  // host poll interval of the snapshot waits
 
-int rod_mailbox_exchange(rod_handle h, const float* drive, int rod, long long target_step, float* out,
-                         long long timeout_us, long long* step) {
-  if (!h || !out || !step) return fail(CORDE_ERR_ARG, "rod_mailbox_exchange: NULL argument");
-  if (!h->mb_pos_host) return fail(CORDE_ERR_ARG, "rod_mailbox_exchange: position snapshots not enabled");
-  if (rod < 0 || rod >= h->n_rods) return fail(CORDE_ERR_ARG, "rod_mailbox_exchange: bad rod");
-  if (timeout_us < 0) return fail(CORDE_ERR_ARG, "rod_mailbox_exchange: timeout_us must be >= 0");
-  if (drive)
-    if (int rc = rod_mailbox_write(h, drive)) return rc;
-  // spin on the rod's publication count and the newest slot's step only; copy once
+// Spins until rod `rod`'s newest position snapshot was taken after a global step >=
+// target_step, polling only the rod's publication count and that slot's step.
+static int await_snapshot(rod_handle h, int rod, long long target_step, long long timeout_us, const char* who) {
   const unsigned* hdr = static_cast<const unsigned*>(h->mb_pos_host) + 32 * (size_t)rod;
   const unsigned* status = static_cast<const unsigned*>(h->mb_out_host) + (size_t)h->n_rods * 16;
   const auto t0 = std::chrono::steady_clock::now();
@@ -1694,21 +1688,48 @@ int rod_mailbox_exchange(rod_handle h, const float* drive, int rod, long long ta
       const unsigned p = pubs - 1u;
       const unsigned* sh = hdr + 4 + 4 * (p % kPosSlots);
       const unsigned lo = __atomic_load_n(&sh[1], __ATOMIC_RELAXED), hi = __atomic_load_n(&sh[2], __ATOMIC_RELAXED);
-      if ((long long)(((unsigned long long)hi << 32) | lo) >= target_step)
-        return rod_mailbox_positions(h, rod, out, step);
+      if ((long long)(((unsigned long long)hi << 32) | lo) >= target_step) return CORDE_OK;
     }
     if ((k & 63u) == 63u) {
       if (__atomic_load_n(status, __ATOMIC_ACQUIRE) != 0u)
-        return fail(CORDE_ERR_BUSY, "rod_mailbox_exchange: a lock-step wait of the kernel ran out");
+        return fail(CORDE_ERR_BUSY, std::string(who) + ": a lock-step wait of the kernel ran out");
       const long long us =
           std::chrono::duration_cast<std::chrono::microseconds>(std::chrono::steady_clock::now() - t0).count();
-      if (us > timeout_us) return fail(CORDE_ERR_BUSY, "rod_mailbox_exchange: no snapshot of the target step in time");
+      if (us > timeout_us) return fail(CORDE_ERR_BUSY, std::string(who) + ": no snapshot of the target step in time");
     }
     // back off between polls without touching the shared lines
     const auto tp = std::chrono::steady_clock::now();
     while (std::chrono::steady_clock::now() - tp < std::chrono::nanoseconds(kExchangePollNs)) {
     }
   }
+}
+
+static int check_snapshot_call(rod_handle h, int rod, long long timeout_us, const void* step, const char* who) {
+  if (!h || !step) return fail(CORDE_ERR_ARG, std::string(who) + ": NULL argument");
+  if (!h->mb_pos_host) return fail(CORDE_ERR_ARG, std::string(who) + ": position snapshots not enabled");
+  if (rod < 0 || rod >= h->n_rods) return fail(CORDE_ERR_ARG, std::string(who) + ": bad rod");
+  if (timeout_us < 0) return fail(CORDE_ERR_ARG, std::string(who) + ": timeout_us must be >= 0");
+  return CORDE_OK;
+}
+
+int rod_mailbox_exchange(rod_handle h, const float* drive, int rod, long long target_step, float* out,
+                         long long timeout_us, long long* step) {
+  if (!out) return fail(CORDE_ERR_ARG, "rod_mailbox_exchange: NULL argument");
+  if (int rc = check_snapshot_call(h, rod, timeout_us, step, "rod_mailbox_exchange")) return rc;
+  if (drive)
+    if (int rc = rod_mailbox_write(h, drive)) return rc;
+  if (int rc = await_snapshot(h, rod, target_step, timeout_us, "rod_mailbox_exchange")) return rc;
+  return rod_mailbox_positions(h, rod, out, step);
+}
+
+int rod_mailbox_tick(rod_handle h, int rod, long long target_step, const float* next_drive, float* out,
+                     long long timeout_us, long long* step) {
+  if (int rc = check_snapshot_call(h, rod, timeout_us, step, "rod_mailbox_tick")) return rc;
+  if (int rc = await_snapshot(h, rod, target_step, timeout_us, "rod_mailbox_tick")) return rc;
+  // the next drive goes out before the copy, so the kernel steps while the host copies
+  if (next_drive)
+    if (int rc = rod_mailbox_write(h, next_drive)) return rc;
+  return rod_mailbox_positions(h, rod, out, step);
 }
 
 int rod_mailbox_disable(rod_handle h) {

@@ -77,6 +77,7 @@ def test_argument_errors_are_reported_on_the_host(lib):
     assert lib.rod_set_launch_overlap(None, 1) == corde.CORDE_ERR_ARG
     assert lib.rod_set_adjoint_record_budget(None, 0) == corde.CORDE_ERR_ARG
     assert lib.rod_mailbox_exchange(None, None, 0, 0, None, 0, None) == corde.CORDE_ERR_ARG
+    assert lib.rod_mailbox_tick(None, 0, 0, None, None, 0, None) == corde.CORDE_ERR_ARG
     assert lib.rod_strerror(corde.CORDE_ERR_NONFINITE) == b"non-finite state"
 
 

@@ -329,3 +329,40 @@ def test_exchange_ticks_replay_exactly_and_report_a_lost_wait(corde):
     corde.rod_mailbox_disable(a.handle)
     a.close()
     b.close()
+
+
+def test_tick_closed_loop_replays_exactly(corde):
+    """rod_mailbox_tick (wait for tick k's snapshot, write tick k + 1's drive at once, then
+    copy): every snapshot of a 15-tick closed loop equals the positions of ordinary
+    10-step launches with the same drives; after the last tick no drive follows, the
+    kernel's 20 ms wait runs out and the next tick call reports it without writing."""
+    import torch
+
+    rod = W.guidewire(512, seed=670)
+    a, b = corde.RodBatch([rod]), corde.RodBatch([rod])
+    corde.rod_mailbox_enable(a.handle, 10, 64)
+    corde.rod_mailbox_positions_enable(a.handle)
+    corde.rod_mailbox_lockstep(a.handle, True, 20_000)
+    drives = W.sinusoid_drive(671, 15, 10 * rod.dt).astype(np.float32)
+    base = corde.rod_steps_done(a.handle)
+    out = np.zeros((512, 4), np.float32)
+    snaps = []
+    a.step(400)  # 40 ticks' worth; the host stops after 15
+    corde.rod_mailbox_write(a.handle, drives[0].reshape(1, 8))
+    for k in range(15):
+        nxt = drives[k + 1].reshape(1, 8) if k + 1 < 15 else None
+        got = corde.rod_mailbox_tick(a.handle, 0, base + 10 * (k + 1), nxt, out, 5_000_000)
+        assert got == base + 10 * (k + 1)
+        snaps.append(out.copy())
+    with pytest.raises(corde.CordeError):
+        corde.rod_mailbox_tick(a.handle, 0, base + 10 * 16, drives[0].reshape(1, 8), None, 5_000_000)
+    torch.cuda.synchronize()
+    assert corde.rod_mailbox_status(a.handle) & 1
+    for k in range(15):
+        b.set_input(drives[k].reshape(1, 8))
+        b.step(10)
+        np.testing.assert_array_equal(snaps[k], b.state_numpy()["pos4"])
+    corde.rod_mailbox_disable(a.handle)
+    a.close()
+    b.close()
+
