@@ -161,8 +161,8 @@ int rod_set_self_collision(rod_handle h, int rod, const double* params);
  * pairs whose spheres overlapped at the last detection, an overflow flag (bit 0 when
  * some mass point had more than 16 candidates above it, bit 1 when the rod had more than
  * 3 N candidate pairs, bit 2 when a mass point touched more than 16 others in one
- * iteration: the excess is dropped; bit 3 when a skin list overflowed and the step fell
- * back to the full detection; sticky until rod_set_self_collision), and the number of
+ * iteration: the excess is dropped; bit 3 when a skin list overflowed, so that the next
+ * step built it again instead of filtering it (the candidates stay exact); sticky until rod_set_self_collision), and the number of
  * skin-list builds in the launch.  Rods held by blocks of up to 512 nodes keep a skin
  * list (in device memory from one launch to the next): the detection runs with the reach
  * grown by 2 s (s = 1.5 r) and later steps test only the listed partners at the plain

@@ -16,14 +16,15 @@
 //                  over the points' counts).
 // Skin list (rods in blocks of up to 512 nodes): the broad and narrow phases run with the
 // reach grown by two skin widths s = 1.5 r and keep every point's partners in a list, with
-// the positions they were found at; on later steps each point only tests its listed
+// the positions they were found at; the build's narrow phase lists its own step's
+// partners at the plain reach too, and on later steps each point only tests its listed
 // partners at the plain reach.  A pair within the reach now was within reach + 2 s at the
 // build as long as no mass point has moved more than s since, so the block rebuilds the
 // list as soon as one has moved more than 0.999 s (and when it has none: the list and the
 // positions it was built at are kept in device memory from one launch to the next,
-// discarded when the rod's self-collision settings change; it detects from scratch
-// whenever a build overflows the list): the candidate pairs of every step are exactly
-// those of the full detection.
+// discarded when the rod's self-collision settings change; a build that overflowed the
+// list is repeated on the next step): the candidate pairs of every step are exactly those
+// of the full detection.
 // In every constraint iteration, after the distance sweeps (and the vessel contact), the
 // velocities are staged in shared memory and (Jacobi: everything from the staged
 // velocities)
@@ -226,16 +227,19 @@ struct SelfHook {
     const float reach2 = reach * reach, dist2 = dist * dist;
     // narrow phase of point i over the groups its bit row marks: the partners j > i
     // (j - i >= min_sep) with |r_i - r_j|^2 < rch2, ascending, into out[c NN + i] for c < cap;
-    // returns their number; *touching counts those closer than the contact distance
-    auto narrow = [&](int i, float4 ri, float rch2, unsigned short* out, int cap, int* touching) {
+    // returns their number; *touching counts those closer than the contact distance.  With
+    // out_plain, those also within plain2 (<= rch2) go, ascending, into out_plain the same
+    // way, *c_plain their number.
+    auto narrow = [&](int i, float4 ri, float rch2, unsigned short* out, int cap, int* touching, float plain2,
+                      unsigned short* out_plain, int* c_plain) {
       const int a = i / kSelfGroup;
-      int c = 0;
+      int c = 0, cp = 0;
       for (int wd = a / 16; wd < nh; ++wd) {
         unsigned word = bits()[a * L::NGH + wd];
         while (word) {
           const int jb = (wd * 16 + __ffs(word) - 1) * kSelfGroup;
           word &= word - 1u;
-          unsigned hit = 0u;
+          unsigned hit = 0u, hitp = 0u;
 #pragma unroll
           for (int jj = 0; jj < kSelfGroup; ++jj) {
             const int j = jb + jj;
@@ -244,6 +248,7 @@ struct SelfHook {
             const float d2 = dx * dx + dy * dy + dz * dz;
             const bool ok = j < n && j - i >= min_sep;
             if (ok && d2 < rch2) hit |= 1u << jj;
+            if (ok && d2 < plain2) hitp |= 1u << jj;
             if (ok && d2 < dist2) ++*touching;
           }
           while (hit) {
@@ -252,11 +257,24 @@ struct SelfHook {
             if (c < cap) out[c * L::NN + i] = (unsigned short)j;
             ++c;
           }
+          if (out_plain != nullptr) {
+            while (hitp) {
+              const int j = jb + __ffs(hitp) - 1;
+              hitp &= hitp - 1u;
+              if (cp < kSelfMaxCand) out_plain[cp * L::NN + i] = (unsigned short)j;
+              ++cp;
+            }
+          }
         }
       }
+      if (c_plain != nullptr) *c_plain = cp;
       return c;
     };
-    bool use_skin = false;
+    int n_up[EPT];
+    int my_up = 0, st_max = 0, st_touch = 0, st_over = 0;
+    // the candidate counts of this step come from a narrow phase (parked in nact), or
+    // from the skin list's filter
+    bool from_narrow = false;
     if constexpr (L::kSkin) {
       // rebuild the skin list when a mass point has moved more than 0.999 s since the last
       // build (s = reach / 2 = 1.5 r), or when there is none
@@ -270,37 +288,38 @@ struct SelfHook {
           moved |= dot3(d, d) > move2;
         }
       if (block_or<NT>(moved)) {  // (a barrier: the staged positions are visible)
+        // the build also lists this step's candidates at the plain reach (its groups cover
+        // them), so the step needs no filter, and a list that overflowed needs no second pass
         const float rch = reach + 2.f * s;
         build_groups(rch);
-        int over = 0, dummy = 0;
+        int over = 0;
 #pragma unroll 1
         for (int e = 0; e < EPT; ++e) {
           const int i = e0 + e;
           if (i >= n) continue;
-          const int c = narrow(i, R4[i], rch * rch, skin(), kSkinMax, &dummy);
+          int cp = 0;
+          const int c = narrow(i, R4[i], rch * rch, skin(), kSkinMax, &st_touch, reach2, list(), &cp);
           skin_cnt()[i] = (unsigned char)min(c, kSkinMax);
+          nact()[i] = cp;
           over |= c > kSkinMax;
         }
 #pragma unroll
         for (int e = 0; e < EPT; ++e) rb[e] = r[e];
         skin_valid = !block_or<NT>(over);  // (a barrier: the lists are visible)
         if (t == 0) ++stat()[5];           // builds in this launch
+        if (!skin_valid && t == 0) atomicOr(&stat()[3], 8);  // the next step builds again
+        from_narrow = true;
       }
-      use_skin = skin_valid;
-      if (!use_skin && t == 0) atomicOr(&stat()[3], 8);  // a build overflowed: full detection
     } else {
       block_sync<NT>();
       build_groups(reach);
-    }
-    int n_up[EPT];
-    int my_up = 0, st_max = 0, st_touch = 0, st_over = 0;
-    if (!use_skin) {
       // the full narrow phase (one copy of its code: its counts parked in nact)
 #pragma unroll 1
       for (int e = 0; e < EPT; ++e) {
         const int i = e0 + e;
-        if (i < n) nact()[i] = narrow(i, R4[i], reach2, list(), kSelfMaxCand, &st_touch);
+        if (i < n) nact()[i] = narrow(i, R4[i], reach2, list(), kSelfMaxCand, &st_touch, -1.f, nullptr, nullptr);
       }
+      from_narrow = true;
     }
 #pragma unroll
     for (int e = 0; e < EPT; ++e) {
@@ -309,7 +328,7 @@ struct SelfHook {
       if (i >= n) continue;
       const float4 ri = R4[i];
       int c = 0, touching = 0;
-      if (use_skin) {
+      if (!from_narrow) {
         // the listed partners at the plain reach (ascending, as the full detection finds them)
         const int k = skin_cnt()[i];
         // four partners at a time: their loads issued together
