@@ -644,7 +644,7 @@ def test_self_candidates_match_kdtree():
     at least min_sep apart in index and closer than 3 r, listed ascending per node."""
     from scipy.spatial import cKDTree
 
-    for rod in (W.torus_knot(64), W.torus_knot(512)):
+    for rod in (W.torus_knot(64), W.torus_knot(512), W.coil(130)):
         pos = rod.pos
         cand, pairs = oracle.self_candidates(rod, pos)
         l0 = rod.length / (rod.n_nodes - 1)
@@ -653,6 +653,30 @@ def test_self_candidates_match_kdtree():
         got = {(i, int(j)) for i in range(len(cand)) for j in cand[i] if j > i}
         assert got == ref and pairs == len(ref) and len(ref) > 100
         assert all(np.all(np.diff(c) > 0) for c in cand)
+
+
+def test_coil_overflows_a_skin_list_but_not_the_candidate_list():
+    """The coil input of the GPU overflow test keeps its purpose: within the skin list's
+    grown reach (3 r + 2 x 1.5 r) some mass point has more than the list's 24 places of
+    partners above it, within the plain 3 r none has more than the 16 candidate places,
+    and some neighbouring turns overlap (so the contact response runs)."""
+    from scipy.spatial import cKDTree
+
+    rod = W.coil(130)
+    pos = rod.pos
+    l0 = rod.length / (rod.n_nodes - 1)
+    m = max(2, int(np.floor(2 * rod.radius / l0)) + 1)
+
+    def most_above(reach):
+        count = np.zeros(rod.n_nodes, int)
+        for i, j in cKDTree(pos).query_pairs(reach):
+            if abs(j - i) >= m:
+                count[min(i, j)] += 1
+        return count.max()
+
+    assert most_above(6 * rod.radius) > 24
+    assert most_above(3 * rod.radius) <= 16
+    assert any(abs(j - i) >= m for i, j in cKDTree(pos).query_pairs(2 * rod.radius))
 
 
 def test_self_contact_single_pair_lands_on_contact_distance():
