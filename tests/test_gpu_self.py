@@ -59,7 +59,7 @@ def _touching(rod, pos):
 @pytest.mark.parametrize("n", [64, 130, 512, 1000])
 def test_self_one_step_parity(corde, n):
     """The knot after 40 steps of settling (strands pressed together), then 3 single steps
-    each restarted from the GPU state; plans from <2, 32> (warp-synchronous) to <2, 512>."""
+    each restarted from the GPU state; plans from <2, 32> (warp-synchronous) to <4, 256> (1000 nodes)."""
     import torch
 
     rod = W.torus_knot(n, seed=700 + n)
